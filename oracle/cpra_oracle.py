@@ -1,0 +1,451 @@
+"""FP64 CPU oracle of the carousel phase retrieval algorithm (CPRA) hot path.
+
+TEST INFRASTRUCTURE ONLY: used by ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU baseline of ``bench.py``; never by the GPU library, with which it
+shares no code.  Everything is float64 / complex128 numpy, written for
+readability: transforms are dense DFT matrices (a matmul as the one library
+step), pixel rules are ``np.where`` over whole arrays, loops follow the
+paper's order.
+
+Paper passages followed (arXiv 2402.05283, "Real time 3D coherent X-ray
+diffraction imaging"):
+  * Eq. 1-3   I_n = |FT2(O'_n)|^2: each measured pattern is the modulus of the
+              2D FT of one projected object (PO); Fourier slice theorem.
+  * Step A    one PO pre-reconstructed, the rest random (``n_pre``).
+  * Step B    episodes W_m; each PO runs N_ei conventional 2D iterations
+              starting from the Eq. 4 combination of the previous episode.
+  * Eq. 4     carousel coupling O_n = sum_k alpha_k O_{n+k}, periodic in n.
+  * Step C    centre-of-mass move Delta r_n = -int O'_n r dv before merging.
+  * Step D    interpolation of the spectra E_n into the 3D E(q); inverse 3D FT.
+  * HIO (Fienup, the paper's ref. 22) and ER updates; shrink-wrap (ref. 36)
+    with the paper's 0.1 relative threshold.
+
+Readings where the paper is silent or garbled (the same list is kept with the
+design notes):
+  R1  Eq. 4 index: O_n^(m) = sum_{k=-r..r} alpha_k O^(m-1)_{(n+k) mod Np}
+      (alpha_0 pairs with n itself).  Jacobi: every n reads episode m-1.
+  R2  Wrap across the 180 degree seam: LITERAL (default) uses the unmirrored
+      image; MIRROR flips u (x -> -x about the frame centre) once per wrap.
+  R3  What is blended: the stored iterate g (STATE, default) or P_{S+} g
+      (OBJECT).
+  R4  Schedule: global iteration t = 0..T-1; coupling before t when
+      t % n_ei == 0 (including t = 0); HIO while t < hio_iters, then ER;
+      shrink-wrap after t when (t + 1) % shrinkwrap_every == 0.
+  R5  Initial guess g0(x) = u * [x in S], u = (splitmix64(key) >> 40) * 2^-24,
+      key = ((seed * Np + n) * N + y) * N + x  (mod 2^64).
+  R6  The PO is real: g' = Re IDFT2(A * G / |G|); phase 1 where G = 0.
+  R7  Valid set V = {x in S and g'(x) >= 0}.  HIO: g' on V, g - beta g'
+      elsewhere; ER: g' on V, 0 elsewhere.
+  R8  Fourier error E_F = sqrt(sum(|G| - A)^2 / sum A^2) of the iterate
+      entering each iteration, full plane.
+  R9  Shrink-wrap: rho = P_{S+} g, b = wrapped Gaussian (sigma px, periodic,
+      normalised on the N x N torus) circularly convolved with rho,
+      S <- {b >= tau * max b}; S unchanged when max b <= 0.
+  R10 Assembly spectrum E_n = DFT2(P_{S+} g_n) * exp(+2 pi i k.c_n / N),
+      signed k in [-N/2, N/2), c_n the centre of mass in pixels (or N/2 when
+      com_align is off); this moves the mass centre to the origin.
+  R11 Gridding: sample (ku, kz) of angle theta lands at
+      (kx, ky, kz) = (ku cos theta, ku sin theta, kz); bilinear scatter in
+      (kx, ky), exact kz; divide by the summed weight; cells with summed
+      weight < 1e-12 are 0.  Volume = fftshift(IDFT3(V)).
+  R12 FFT conventions: forward unnormalised with exp(-2 pi i jk/N), inverse
+      carries 1/N per axis; intensities arrive centred and are ifftshifted.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HIO, ER = 0, 1
+WRAP_LITERAL, WRAP_MIRROR = 0, 1
+BLEND_STATE, BLEND_OBJECT = 0, 1
+
+__all__ = [
+    "HIO", "ER", "WRAP_LITERAL", "WRAP_MIRROR", "BLEND_STATE", "BLEND_OBJECT",
+    "dft_matrix", "dft2", "idft2", "dft3", "idft3", "fftshift2", "ifftshift2",
+    "fftshift3", "amplitudes", "a_sym", "splitmix64", "initial_guess",
+    "modulus_projection", "fourier_error_terms", "support_update",
+    "iterate_2d", "couple", "wrapped_gaussian", "blur", "shrinkwrap",
+    "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d",
+    "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
+    "r_factor",
+]
+
+
+# --------------------------------------------------------------------------
+# Discrete Fourier transforms by definition (R12)
+# --------------------------------------------------------------------------
+_DFT = {}
+
+
+def dft_matrix(N: int, sign: int) -> np.ndarray:
+    """F[k, j] = exp(sign * 2 pi i * (j k mod N) / N)."""
+    key = (N, sign)
+    if key not in _DFT:
+        j = np.arange(N)
+        jk = np.outer(j, j) % N
+        _DFT[key] = np.exp(sign * 2j * np.pi * jk / N)
+    return _DFT[key]
+
+
+def dft2(x: np.ndarray) -> np.ndarray:
+    """Unnormalised forward 2D DFT over the last two axes."""
+    N = x.shape[-1]
+    F = dft_matrix(N, -1)
+    return F @ x @ F  # F is symmetric
+
+
+def idft2(X: np.ndarray) -> np.ndarray:
+    """Inverse 2D DFT over the last two axes (1/N^2)."""
+    N = X.shape[-1]
+    F = dft_matrix(N, +1)
+    return (F @ X @ F) / (N * N)
+
+
+def _along(F: np.ndarray, x: np.ndarray, axis: int) -> np.ndarray:
+    return np.moveaxis(np.tensordot(F, x, axes=([1], [axis])), 0, axis)
+
+
+def dft3(x: np.ndarray) -> np.ndarray:
+    N = x.shape[-1]
+    F = dft_matrix(N, -1)
+    for ax in range(3):
+        x = _along(F, x, ax)
+    return x
+
+
+def idft3(X: np.ndarray) -> np.ndarray:
+    N = X.shape[-1]
+    F = dft_matrix(N, +1)
+    for ax in range(3):
+        X = _along(F, X, ax)
+    return X / float(N) ** 3
+
+
+def fftshift2(x):
+    N = x.shape[-1]
+    return np.roll(x, (N // 2, N // 2), axis=(-2, -1))
+
+
+def ifftshift2(x):
+    N = x.shape[-1]
+    return np.roll(x, (-(N // 2), -(N // 2)), axis=(-2, -1))
+
+
+def fftshift3(x):
+    N = x.shape[-1]
+    return np.roll(x, (N // 2,) * 3, axis=(-3, -2, -1))
+
+
+# --------------------------------------------------------------------------
+# Inputs (Eq. 1-3): amplitudes and the initial guess
+# --------------------------------------------------------------------------
+def amplitudes(I_centred: np.ndarray) -> np.ndarray:
+    """A = sqrt(I) in FFT order.  Negative or non-finite intensities are rejected."""
+    I = np.asarray(I_centred, dtype=np.float64)
+    if not np.all(np.isfinite(I)) or np.any(I < 0):
+        raise ValueError("intensities must be finite and non-negative")
+    return np.sqrt(ifftshift2(I))
+
+
+def _neg_index(N):
+    return (-np.arange(N)) % N
+
+
+def a_sym(A: np.ndarray) -> np.ndarray:
+    """Hermitian-symmetrised amplitude (A(k) + A(-k)) / 2 (used by the R6 identity pins)."""
+    m = _neg_index(A.shape[-1])
+    return 0.5 * (A + A[..., m[:, None], m[None, :]])
+
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(key: np.ndarray) -> np.ndarray:
+    """First output of SplitMix64 (Steele, Lea, Flood 2014) seeded with ``key``."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(key, dtype=np.uint64) + _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def initial_guess(seed: int, Np: int, N: int, S: np.ndarray) -> np.ndarray:
+    """Seeded random start (R5), zero outside the support."""
+    n = np.arange(Np, dtype=np.uint64)[:, None, None]
+    y = np.arange(N, dtype=np.uint64)[None, :, None]
+    x = np.arange(N, dtype=np.uint64)[None, None, :]
+    with np.errstate(over="ignore"):
+        key = ((np.uint64(seed) * np.uint64(Np) + n) * np.uint64(N) + y) * np.uint64(N) + x
+    u = (splitmix64(key) >> np.uint64(40)).astype(np.float64) * 2.0 ** -24
+    return np.where(S.astype(bool), u, 0.0)
+
+
+# --------------------------------------------------------------------------
+# One conventional 2D iteration (Step B inner loop; R6-R8)
+# --------------------------------------------------------------------------
+def modulus_projection(G: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """Replace |G| by A and keep the phase; phase 1 where G = 0."""
+    mag = np.abs(G)
+    phase = np.where(mag > 0, G / np.where(mag > 0, mag, 1.0), 1.0)
+    return A * phase
+
+
+def fourier_error_terms(G: np.ndarray, A: np.ndarray):
+    """(sum (|G| - A)^2, sum A^2) per pattern over the full plane."""
+    d = np.abs(G) - A
+    return (d * d).sum(axis=(-2, -1)), (A * A).sum(axis=(-2, -1))
+
+
+def support_update(g, gp, S, beta, algo):
+    """HIO or ER real-space step on the valid set V = S and g' >= 0."""
+    valid = S.astype(bool) & (gp >= 0)
+    if algo == HIO:
+        return np.where(valid, gp, g - beta * gp)
+    return np.where(valid, gp, 0.0)
+
+
+def iterate_2d(g, A, S, beta, algo):
+    """One iteration for a stack of POs; returns (g_new, err_num, err_den)."""
+    G = dft2(g)
+    num, den = fourier_error_terms(G, A)
+    gp = idft2(modulus_projection(G, A)).real
+    return support_update(g, gp, S, beta, algo), num, den
+
+
+# --------------------------------------------------------------------------
+# Carousel coupling, Eq. 4 (R1-R3)
+# --------------------------------------------------------------------------
+def _mirror_u(img):
+    N = img.shape[-1]
+    return img[..., _neg_index(N)]
+
+
+def object_estimate(g, S):
+    """P_{S+} g: the iterate on the valid set, zero elsewhere."""
+    return np.where(S.astype(bool) & (g >= 0), g, 0.0)
+
+
+def couple(g, alpha, wrap=WRAP_LITERAL, blend=BLEND_STATE, S=None):
+    """O_n <- sum_{k=-r..r} alpha_k O_{(n+k) mod Np}, all n from the old stack."""
+    Np = g.shape[0]
+    alpha = np.asarray(alpha, dtype=np.float64)
+    r = len(alpha) // 2
+    src = g if blend == BLEND_STATE else object_estimate(g, S)
+    out = np.zeros_like(g, dtype=np.float64)
+    for n in range(Np):
+        for k in range(-r, r + 1):
+            j = n + k
+            img = src[j % Np]
+            if wrap == WRAP_MIRROR and (j // Np) % 2 != 0:
+                img = _mirror_u(img)
+            out[n] += alpha[k + r] * img
+    return out
+
+
+# --------------------------------------------------------------------------
+# Shrink-wrap (R9)
+# --------------------------------------------------------------------------
+def wrapped_gaussian(N: int, sigma: float) -> np.ndarray:
+    """w[d] proportional to sum_m exp(-(d + mN)^2 / (2 sigma^2)), sum_d w = 1."""
+    d = np.arange(N, dtype=np.float64)
+    M = int(math.ceil(12 * sigma / N)) + 1
+    w = np.zeros(N)
+    for m in range(-M, M + 1):
+        w += np.exp(-((d + m * N) ** 2) / (2 * sigma * sigma))
+    return w / w.sum()
+
+
+def blur(rho: np.ndarray, sigma: float) -> np.ndarray:
+    """Circular convolution with the separable wrapped Gaussian: W rho W^T."""
+    N = rho.shape[-1]
+    w = wrapped_gaussian(N, sigma)
+    idx = (np.arange(N)[:, None] - np.arange(N)[None, :]) % N
+    W = w[idx]
+    return W @ rho @ W.T
+
+
+def shrinkwrap(g, S, sigma, tau):
+    """New support {blur(P_{S+} g) >= tau * max}, per pattern."""
+    b = blur(object_estimate(g, S), sigma)
+    mx = b.max(axis=(-2, -1), keepdims=True)
+    new = b >= tau * mx
+    return np.where(mx > 0, new, S.astype(bool))
+
+
+# --------------------------------------------------------------------------
+# Assembly, Steps C (mass centre) and D (R10, R11)
+# --------------------------------------------------------------------------
+def centre_of_mass(rho: np.ndarray) -> np.ndarray:
+    """(c_z, c_u) per pattern in pixels; (N/2, N/2) for an empty pattern."""
+    N = rho.shape[-1]
+    i = np.arange(N, dtype=np.float64)
+    m0 = rho.sum(axis=(-2, -1))
+    mz = (rho * i[:, None]).sum(axis=(-2, -1))
+    mu = (rho * i[None, :]).sum(axis=(-2, -1))
+    safe = np.where(m0 > 0, m0, 1.0)
+    cz = np.where(m0 > 0, mz / safe, N / 2)
+    cu = np.where(m0 > 0, mu / safe, N / 2)
+    return np.stack([cz, cu], axis=-1)
+
+
+def signed_freq(N: int) -> np.ndarray:
+    k = np.arange(N)
+    return np.where(k >= N // 2, k - N, k).astype(np.float64)
+
+
+def spectra(g, S, com_align=True):
+    """E_n[kz][ku] = DFT2(P_{S+} g_n) * exp(+2 pi i (kz c_z + ku c_u) / N)."""
+    N = g.shape[-1]
+    rho = object_estimate(g, S)
+    if com_align:
+        c = centre_of_mass(rho)
+    else:
+        c = np.full(g.shape[:-2] + (2,), N / 2.0)
+    k = signed_freq(N)
+    cz = c[..., 0][..., None, None]
+    cu = c[..., 1][..., None, None]
+    ramp = np.exp(2j * np.pi * (k[:, None] * cz + k[None, :] * cu) / N)
+    return dft2(rho) * ramp
+
+
+def grid_3d(E: np.ndarray, thetas, wmin: float = 1e-12) -> np.ndarray:
+    """Literal 3D bilinear scatter of all slices, divided by the summed weight.
+
+    Returns V[kz][ky][kx] in FFT index order.
+    """
+    Np, N, _ = E.shape
+    k = signed_freq(N)
+    num = np.zeros((N, N, N), dtype=np.complex128)
+    wsum = np.zeros((N, N, N), dtype=np.float64)
+    for n in range(Np):
+        px = k * math.cos(thetas[n])
+        py = k * math.sin(thetas[n])
+        i0 = np.floor(px)
+        j0 = np.floor(py)
+        fx = px - i0
+        fy = py - j0
+        for di in (0, 1):
+            for dj in (0, 1):
+                w = (fx if di else 1 - fx) * (fy if dj else 1 - fy)
+                ii = (i0.astype(np.int64) + di) % N
+                jj = (j0.astype(np.int64) + dj) % N
+                np.add.at(num, (slice(None), jj, ii), w[None, :] * E[n])
+                np.add.at(wsum, (slice(None), jj, ii), np.broadcast_to(w[None, :], (N, N)))
+    return np.where(wsum >= wmin, num / np.where(wsum >= wmin, wsum, 1.0), 0.0)
+
+
+def volume(V: np.ndarray) -> np.ndarray:
+    """Centred complex volume fftshift(IDFT3(V))."""
+    return fftshift3(idft3(V))
+
+
+def assemble(g, S, thetas, com_align=True):
+    return volume(grid_3d(spectra(g, S, com_align), thetas))
+
+
+# --------------------------------------------------------------------------
+# The whole schedule (Steps A, B; R4)
+# --------------------------------------------------------------------------
+@dataclass
+class OracleConfig:
+    N: int
+    Np: int
+    n_ei: int = 10
+    alpha: tuple = (0.2, 0.6, 0.2)
+    beta: float = 0.9
+    wrap: int = WRAP_LITERAL
+    blend: int = BLEND_STATE
+    hio_iters: int = 200
+    er_iters: int = 20
+    shrinkwrap_every: int = 0
+    sw_sigma: float = 2.0
+    sw_tau: float = 0.1
+    n_pre: int = 0
+    com_align: bool = True
+    seed: int = 0
+
+
+@dataclass
+class OracleRun:
+    """State of one reconstruction: amplitudes, support, iterate, history."""
+    cfg: OracleConfig
+    A: np.ndarray
+    S: np.ndarray
+    g: np.ndarray = None
+    t: int = 0
+    errors: list = field(default_factory=list)
+
+    @classmethod
+    def start(cls, cfg: OracleConfig, I_centred, S0=None, g0=None):
+        A = amplitudes(I_centred)
+        if S0 is None:
+            S0 = np.zeros((cfg.N, cfg.N), dtype=bool)
+            o = cfg.N // 4
+            S0[o:o + cfg.N // 2, o:o + cfg.N // 2] = True
+        S = np.broadcast_to(np.asarray(S0).astype(bool), A.shape).copy()
+        g = initial_guess(cfg.seed, cfg.Np, cfg.N, S) if g0 is None else np.array(g0, dtype=np.float64)
+        run = cls(cfg=cfg, A=A, S=S, g=g)
+        for _ in range(cfg.n_pre):  # Step A: angle 0 alone, HIO
+            g1, _, _ = iterate_2d(run.g[0:1], A[0:1], S[0:1], cfg.beta, HIO)
+            run.g[0] = g1[0]
+        return run
+
+    def step(self):
+        """One global iteration t (coupling first at episode starts)."""
+        c = self.cfg
+        if self.t % c.n_ei == 0:
+            self.g = couple(self.g, c.alpha, c.wrap, c.blend, self.S)
+        algo = HIO if self.t < c.hio_iters else ER
+        self.g, num, den = iterate_2d(self.g, self.A, self.S, c.beta, algo)
+        self.errors.append(np.sqrt(num / den))
+        if c.shrinkwrap_every > 0 and (self.t + 1) % c.shrinkwrap_every == 0:
+            self.S = shrinkwrap(self.g, self.S, c.sw_sigma, c.sw_tau)
+        self.t += 1
+        return self
+
+    def run(self, n):
+        for _ in range(n):
+            self.step()
+        return self
+
+    def po(self):
+        return object_estimate(self.g, self.S)
+
+    def assemble(self, thetas):
+        return assemble(self.g, self.S, thetas, self.cfg.com_align)
+
+
+# --------------------------------------------------------------------------
+# Evaluation metrics
+# --------------------------------------------------------------------------
+def r_factor(g, A):
+    """R = sum ||G| - A| / sum A per pattern."""
+    G = dft2(g)
+    return np.abs(np.abs(G) - A).sum(axis=(-2, -1)) / A.sum(axis=(-2, -1))
+
+
+def real_space_error(rec: np.ndarray, true: np.ndarray) -> float:
+    """min over {x, -x} and integer shifts of ||c rec - true|| / ||true||, best scale c.
+
+    The shift maximising the circular cross-correlation is found with an FFT
+    (library step); -x is the central inversion about index 0.
+    """
+    rec = np.asarray(rec, dtype=np.float64)
+    true = np.asarray(true, dtype=np.float64)
+    axes = tuple(range(rec.ndim))
+    best = np.inf
+    Ft = np.fft.fftn(true)
+    for cand in (rec, np.flip(rec, axis=axes)):
+        xc = np.fft.ifftn(Ft * np.conj(np.fft.fftn(cand))).real
+        shift = np.unravel_index(np.argmax(xc), xc.shape)
+        moved = np.roll(cand, shift, axis=axes)
+        den = (moved * moved).sum()
+        c = (moved * true).sum() / den if den > 0 else 0.0
+        err = np.linalg.norm(c * moved - true) / np.linalg.norm(true)
+        best = min(best, err)
+    return float(best)

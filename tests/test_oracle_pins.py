@@ -1,0 +1,381 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test ties one oracle function to something other than itself: closed
+forms, a library routine (numpy.fft), brute force on tiny inputs, values the
+paper prints, or invariants that a dropped term / wrong sign / transposed
+operand would break.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(1234)
+
+
+def _rand(*shape):
+    return rng.standard_normal(shape)
+
+
+# ---------------------------------------------------------------- transforms
+def test_dft_closed_forms():
+    N = 8
+    d = np.zeros((N, N)); d[0, 0] = 1.0
+    assert np.allclose(O.dft2(d), np.ones((N, N)), atol=1e-14)
+    # one plane wave -> one delta at its frequency
+    y, x = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    w = np.exp(2j * np.pi * (3 * y + 5 * x) / N)
+    W = O.dft2(w)
+    expect = np.zeros((N, N), complex); expect[3, 5] = N * N
+    assert np.allclose(W, expect, atol=1e-11)
+    # hand values: N = 2 -> [[a+b],[a-b]]; N = 4 row DFT of (1, 2, 3, 4)
+    assert np.allclose(O.dft_matrix(2, -1), [[1, 1], [1, -1]], atol=1e-15)
+    F4 = O.dft_matrix(4, -1)
+    assert np.allclose(F4 @ np.array([1, 2, 3, 4.0]), [10, -2 + 2j, -2, -2 - 2j], atol=1e-14)
+    # N = 3: exp(-2 pi i / 3) = -1/2 - i sqrt(3)/2
+    assert np.allclose(O.dft_matrix(3, -1)[1, 1], -0.5 - 0.5j * math.sqrt(3), atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [16, 24, 48, 64])
+def test_dft_matches_numpy_fft(N):
+    x = _rand(3, N, N) + 1j * _rand(3, N, N)
+    assert np.allclose(O.dft2(x), np.fft.fft2(x), rtol=0, atol=1e-10 * N * N)
+    assert np.allclose(O.idft2(x), np.fft.ifft2(x), rtol=0, atol=1e-12)
+
+
+def test_dft3_matches_numpy_and_roundtrip():
+    N = 12
+    x = _rand(N, N, N) + 1j * _rand(N, N, N)
+    assert np.allclose(O.dft3(x), np.fft.fftn(x), atol=1e-9)
+    assert np.allclose(O.idft3(O.dft3(x)), x, atol=1e-12)
+
+
+def test_parseval_and_roundtrip():
+    N = 32
+    x = _rand(N, N)
+    X = O.dft2(x)
+    assert abs((x * x).sum() - (np.abs(X) ** 2).sum() / N ** 2) < 1e-9
+    assert np.allclose(O.idft2(X).real, x, atol=1e-13)
+    assert np.max(np.abs(O.idft2(X).imag)) < 1e-13
+
+
+def test_shifts():
+    N = 6
+    x = np.arange(N * N).reshape(N, N)
+    assert np.array_equal(O.fftshift2(x), np.fft.fftshift(x))
+    assert np.array_equal(O.ifftshift2(x), np.fft.ifftshift(x))
+    v = np.arange(N ** 3).reshape(N, N, N)
+    assert np.array_equal(O.fftshift3(v), np.fft.fftshift(v))
+
+
+# ---------------------------------------------------------------- inputs
+def test_splitmix64_published_outputs():
+    # SplitMix64 seeded with 0: the first two outputs of the published generator
+    assert int(O.splitmix64(np.uint64(0))) == 0xE220A8397B1DCDAF
+    gamma = np.uint64(0x9E3779B97F4A7C15)
+    assert int(O.splitmix64(gamma)) == 0x6E789E6AA1B965F4
+
+
+def test_initial_guess_properties():
+    N, Np = 16, 3
+    S = np.zeros((N, N), bool); S[4:12, 4:12] = True
+    g = O.initial_guess(5, Np, N, np.broadcast_to(S, (Np, N, N)))
+    assert g.shape == (Np, N, N)
+    assert np.all(g[:, ~S] == 0)
+    assert np.all((g[:, S] >= 0) & (g[:, S] < 1))
+    assert not np.allclose(g[0], g[1])
+    assert np.array_equal(g, O.initial_guess(5, Np, N, np.broadcast_to(S, (Np, N, N))))
+    assert abs(g[:, S].mean() - 0.5) < 0.05
+    # values are multiples of 2^-24 (24-bit uniform)
+    assert np.all(np.mod(g * 2 ** 24, 1) == 0)
+
+
+def test_amplitudes_reject_negative_and_shift():
+    N = 8
+    I = np.zeros((N, N)); I[N // 2, N // 2] = 4.0  # centred q = 0
+    A = O.amplitudes(I)
+    assert A[0, 0] == 2.0 and A.sum() == 2.0
+    with pytest.raises(ValueError):
+        O.amplitudes(-I)
+    with pytest.raises(ValueError):
+        O.amplitudes(I * np.nan)
+
+
+# ---------------------------------------------------------------- projections
+def test_modulus_projection_idempotent_and_modulus():
+    N = 16
+    G = _rand(N, N) + 1j * _rand(N, N)
+    G[2, 3] = 0
+    A = np.abs(_rand(N, N))
+    P = O.modulus_projection(G, A)
+    assert np.allclose(np.abs(P), A, atol=1e-14)
+    assert np.allclose(O.modulus_projection(P, A), P, atol=1e-14)
+    assert P[2, 3] == A[2, 3]  # phase 1 where G = 0
+    # phase preserved
+    m = np.abs(G) > 0
+    assert np.allclose(np.angle(P[m & (A > 0)]), np.angle(G[m & (A > 0)]), atol=1e-12)
+
+
+def test_object_projection_idempotent():
+    g = _rand(2, 8, 8)
+    S = rng.random((2, 8, 8)) > 0.3
+    p = O.object_estimate(g, S)
+    assert np.array_equal(O.object_estimate(p, S), p)
+    assert np.all(p >= 0) and np.all(p[~S] == 0)
+
+
+def test_support_update_cases():
+    g = _rand(8, 8); gp = _rand(8, 8)
+    S = rng.random((8, 8)) > 0.5
+    # with everything allowed and g' >= 0, HIO and ER both return g'
+    full = np.ones((8, 8), bool)
+    assert np.array_equal(O.support_update(g, np.abs(gp), full, 0.9, O.HIO), np.abs(gp))
+    assert np.array_equal(O.support_update(g, np.abs(gp), full, 0.9, O.ER), np.abs(gp))
+    # outside the support ER gives 0, HIO gives g - beta g'
+    h = O.support_update(g, gp, S, 0.9, O.HIO)
+    e = O.support_update(g, gp, S, 0.9, O.ER)
+    assert np.all(e[~S] == 0) and np.allclose(h[~S], g[~S] - 0.9 * gp[~S])
+    neg = S & (gp < 0)
+    assert np.all(e[neg] == 0) and np.allclose(h[neg], g[neg] - 0.9 * gp[neg])
+
+
+def _true_case(N=32, seed=3):
+    r = np.random.default_rng(seed)
+    P = np.zeros((2, N, N))
+    P[:, N // 4:3 * N // 4, N // 4:3 * N // 4] = r.random((2, N // 2, N // 2))
+    A = np.abs(np.fft.fft2(P))  # library transform, independent of the oracle
+    return P, A
+
+
+def test_true_object_is_fixed_point():
+    P, A = _true_case()
+    S = P > 0
+    for algo in (O.HIO, O.ER):
+        g, num, den = O.iterate_2d(P, A, S, 0.9, algo)
+        assert np.max(np.abs(g - P)) < 1e-12
+        assert np.all(num / den < 1e-26)
+
+
+def test_real_state_identity_half_plane():
+    """Re IDFT(A G/|G|) = IDFT(A_sym G/|G|) and the error splits exactly (R6)."""
+    N = 16
+    g = _rand(N, N)
+    A = np.abs(_rand(N, N)) + 0.1  # not Hermitian-symmetric
+    G = np.fft.fft2(g)
+    full = np.fft.ifft2(O.modulus_projection(G, A)).real
+    As = O.a_sym(A)
+    half = np.fft.ifft2(O.modulus_projection(G, As))
+    assert np.max(np.abs(half.imag)) < 1e-13
+    assert np.allclose(full, half.real, atol=1e-13)
+    m = (-np.arange(N)) % N
+    D = 0.5 * (A - A[m[:, None], m[None, :]])
+    lhs = ((np.abs(G) - A) ** 2).sum()
+    rhs = ((np.abs(G) - As) ** 2).sum() + (D * D).sum()
+    assert abs(lhs - rhs) < 1e-9 * lhs
+
+
+# ---------------------------------------------------------------- coupling
+def test_coupling_paper_example_np3():
+    gold = json.load(open(os.path.join(GOLD, "coupling_np3.json")))
+    x = np.array(gold["inputs"])[:, None, None] * np.ones((3, 4, 4))
+    out = O.couple(x, gold["alpha"])
+    assert np.allclose(out[:, 0, 0], gold["expected"], atol=1e-15)
+
+
+def test_coupling_identity_constant_and_linearity():
+    g = _rand(5, 6, 6)
+    assert np.array_equal(O.couple(g, [1.0]), g)
+    assert np.allclose(O.couple(g, [0.0, 1.0, 0.0]), g)
+    c = np.broadcast_to(_rand(1, 6, 6), (5, 6, 6))
+    assert np.allclose(O.couple(c, [0.2, 0.6, 0.2]), c, atol=1e-15)
+    h = _rand(5, 6, 6)
+    a = [0.1, 0.2, 0.4, 0.2, 0.1]
+    assert np.allclose(O.couple(2 * g + h, a), 2 * O.couple(g, a) + O.couple(h, a))
+    # shift equivariance in n (periodic carousel)
+    assert np.allclose(O.couple(np.roll(g, 2, axis=0), a), np.roll(O.couple(g, a), 2, axis=0))
+
+
+def test_coupling_mirror_seam():
+    Np, N = 4, 6
+    g = _rand(Np, N, N)
+    out = O.couple(g, [0.25, 0.5, 0.25], wrap=O.WRAP_MIRROR)
+    mirror = lambda im: im[:, (-np.arange(N)) % N]  # noqa: E731
+    assert np.allclose(out[0], 0.25 * mirror(g[3]) + 0.5 * g[0] + 0.25 * g[1])
+    assert np.allclose(out[3], 0.25 * g[2] + 0.5 * g[3] + 0.25 * mirror(g[0]))
+    assert np.allclose(out[1], 0.25 * g[0] + 0.5 * g[1] + 0.25 * g[2])
+
+
+def test_coupling_object_blend():
+    g = _rand(3, 4, 4)
+    S = rng.random((3, 4, 4)) > 0.4
+    out = O.couple(g, [0.2, 0.6, 0.2], blend=O.BLEND_OBJECT, S=S)
+    p = np.where(S & (g >= 0), g, 0)
+    assert np.allclose(out[1], 0.2 * p[0] + 0.6 * p[1] + 0.2 * p[2])
+
+
+# ---------------------------------------------------------------- shrink-wrap
+def test_wrapped_gaussian():
+    w = O.wrapped_gaussian(32, 2.0)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(w[1:], w[1:][::-1])  # symmetric on the torus
+    # far from the wrap it is the plain normalised Gaussian
+    d = np.arange(-16, 16)
+    plain = np.exp(-d * d / 8.0); plain /= plain.sum()
+    assert np.allclose(np.roll(w, 16), plain, atol=1e-12)
+
+
+def test_blur_brute_force_and_fft():
+    N = 8
+    rho = rng.random((N, N))
+    b = O.blur(rho, 1.5)
+    w = O.wrapped_gaussian(N, 1.5)
+    brute = np.zeros((N, N))
+    for y in range(N):
+        for x in range(N):
+            for yy in range(N):
+                for xx in range(N):
+                    brute[y, x] += w[(y - yy) % N] * w[(x - xx) % N] * rho[yy, xx]
+    assert np.allclose(b, brute, atol=1e-14)
+    h = np.outer(w, w)
+    fft_form = np.fft.ifft2(np.fft.fft2(h) * np.fft.fft2(rho)).real
+    assert np.allclose(b, fft_form, atol=1e-13)
+    assert np.allclose(O.blur(np.full((N, N), 3.0), 1.5), 3.0)
+
+
+def test_shrinkwrap_point_source_radius():
+    """One bright pixel: support = disc where exp(-r^2 / 2 s^2) >= tau."""
+    N, s, tau = 64, 2.0, 0.1
+    g = np.zeros((1, N, N)); g[0, 32, 32] = 1.0
+    S = np.ones((1, N, N), bool)
+    new = O.shrinkwrap(g, S, s, tau)[0]
+    y, x = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    r2 = (y - 32) ** 2 + (x - 32) ** 2
+    expect = r2 <= 2 * s * s * math.log(1 / tau)
+    assert np.array_equal(new, expect)
+    # an all-zero estimate keeps the old support
+    assert np.array_equal(O.shrinkwrap(np.zeros((1, N, N)), S, s, tau), S)
+
+
+# ---------------------------------------------------------------- assembly
+def test_centre_of_mass_and_ramp_delta():
+    N = 16
+    g = np.zeros((1, N, N)); g[0, 5, 11] = 2.0
+    S = np.ones((1, N, N), bool)
+    assert np.allclose(O.centre_of_mass(g), [[5, 11]])
+    E = O.spectra(g, S, com_align=True)
+    assert np.allclose(E, 2.0, atol=1e-12)  # mass centre moved to the origin
+    E0 = O.spectra(g, S, com_align=False)  # centred at N/2 instead
+    k = O.signed_freq(N)
+    expect = 2 * np.exp(-2j * np.pi * (k[:, None] * (5 - 8) + k[None, :] * (11 - 8)) / N)
+    assert np.allclose(E0[0], expect, atol=1e-12)
+
+
+def _axis_projection(vol, axis):
+    return vol.sum(axis=axis)
+
+
+def test_fourier_slice_axis_aligned():
+    """DFT2 of the projection at 0 / 90 degrees is the central slice of the 3D DFT."""
+    N = 12
+    vol = rng.random((N, N, N))
+    F3 = np.fft.fftn(vol)  # [kz][ky][kx]
+    p0 = _axis_projection(vol, 1)  # theta = 0: sum over y -> [z][x]
+    p90 = _axis_projection(vol, 2)  # theta = 90: sum over x -> [z][y]
+    assert np.allclose(O.dft2(p0), F3[:, 0, :], atol=1e-10)
+    assert np.allclose(O.dft2(p90), F3[:, :, 0], atol=1e-10)
+
+
+def test_grid_single_slice_reproduces_plane():
+    N = 8
+    E = _rand(2, N, N) + 1j * _rand(2, N, N)
+    V = O.grid_3d(E[:1], [0.0])
+    assert np.allclose(V[:, 0, :], E[0], atol=1e-14)
+    V[:, 0, :] = 0
+    assert np.all(V == 0)
+    V = O.grid_3d(E[1:], [math.pi / 2])
+    assert np.allclose(V[:, :, 0], E[1], atol=1e-12)
+    V[:, :, 0] = 0
+    assert np.all(V == 0)
+
+
+def test_grid_bilinear_weights_hand_case():
+    """theta = 45 deg on N = 4 (ku in -2..1), only E(kz=0, ku=1) = 1, worked by hand.
+
+    ku = 1 lands at (c, c), c = 1/sqrt(2): weights c*c on cell (1,1),
+    c(1-c) on (0,1) and (1,0), (1-c)^2 on (0,0).  ku = 0 sits on (0,0) with
+    weight 1; ku = -1 at (-c, -c) also reaches (0,0) with weight (1-c)^2;
+    ku = -2 at (-2c, -2c) touches only cells -2 and -1 (indices 2, 3).
+    """
+    N = 4
+    E = np.zeros((1, N, N), complex)
+    E[0, 0, 1] = 1.0
+    V = O.grid_3d(E, [math.pi / 4])
+    c = 1 / math.sqrt(2)
+    w00 = (1 - c) ** 2
+    assert abs(V[0, 1, 1] - 1.0) < 1e-12  # only ku = 1 reaches (1,1)
+    assert abs(V[0, 0, 1] - 1.0) < 1e-12  # ku = 0 reaches (0,1) with weight 0
+    assert abs(V[0, 0, 0] - w00 / (1.0 + 2 * w00)) < 1e-12
+    assert np.all(V[1:] == 0)  # other kz planes carry no data
+
+
+def test_volume_of_exact_spectrum_is_object():
+    N = 10
+    vol = rng.random((N, N, N))
+    V = np.fft.fftn(np.fft.ifftshift(vol))
+    assert np.allclose(O.volume(V), vol, atol=1e-12)
+
+
+def test_assembly_axis_aligned_roundtrip():
+    """A volume symmetric enough that 0/90 degree slices + gridding recover its central planes."""
+    N = 16
+    vol = np.zeros((N, N, N))
+    vol[6:10, 6:10, 6:10] = rng.random((4, 4, 4))
+    F3 = np.fft.fftn(np.fft.ifftshift(vol))
+    E = np.stack([F3[:, 0, :], F3[:, :, 0]])
+    V = O.grid_3d(E, [0.0, math.pi / 2])
+    assert np.allclose(V[:, 0, 1:], F3[:, 0, 1:], atol=1e-10)
+    assert np.allclose(V[:, 1:, 0], F3[:, 1:, 0], atol=1e-10)
+    assert np.allclose(V[:, 0, 0], F3[:, 0, 0], atol=1e-10)
+
+
+# ---------------------------------------------------------------- schedule
+def test_schedule_coupling_and_switch():
+    """The run applies Eq. 4 at episode starts and switches HIO -> ER at hio_iters."""
+    P, A_true = _true_case(16, 7)
+    I = np.fft.fftshift(A_true ** 2, axes=(-2, -1))
+    cfg = O.OracleConfig(N=16, Np=2, n_ei=3, alpha=(0.25, 0.5, 0.25), hio_iters=4, er_iters=2, seed=1)
+    run = O.OracleRun.start(cfg, I)
+    g = run.g.copy()
+    S = run.S
+    A = run.A
+    for t in range(6):
+        if t % 3 == 0:
+            g = O.couple(g, cfg.alpha)
+        g, _, _ = O.iterate_2d(g, A, S, 0.9, O.HIO if t < 4 else O.ER)
+        run.step()
+        assert np.array_equal(run.g, g)
+    assert run.t == 6 and len(run.errors) == 6
+
+
+def test_phantom_recovery_noiseless_true_support():
+    """Noiseless patterns, tight support: ER polish brings E_F and the PO error down."""
+    import synth
+    N, Np = 32, 4
+    obj = synth.ellipsoid_phantom(16, 3, 11)
+    vol = synth.pad_volume(obj, N)
+    th = synth.angles(Np)
+    P = synth.project(vol, th, r_max=8).numpy()
+    I = np.fft.fftshift(np.abs(np.fft.fft2(P)) ** 2, axes=(-2, -1))
+    S = P > 1e-12
+    cfg = O.OracleConfig(N=N, Np=Np, n_ei=1000, alpha=(1.0,), hio_iters=400, er_iters=100, seed=3)
+    run = O.OracleRun.start(cfg, I, S0=S)
+    run.run(500)
+    err = np.array(run.errors)[-1]
+    rs = [O.real_space_error(run.po()[n], P[n]) for n in range(Np)]
+    assert np.max(err) < 2e-2, err
+    assert np.max(rs) < 0.05, rs
