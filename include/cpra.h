@@ -1,0 +1,216 @@
+/*
+ * cpra.h - C ABI of the GB300 carousel phase retrieval (CPRA) library.
+ *
+ * The library reconstructs Np projected objects (POs) from Np measured N x N
+ * far-field intensity patterns (Eq. 1-3 of arXiv 2402.05283), couples each PO
+ * with its periodic neighbours between episodes (Eq. 4, Step B), and
+ * assembles the retrieved spectra into a 3D reciprocal grid followed by an
+ * inverse 3D FFT (Step D).  All compute runs in hand-written sm_103a kernels
+ * on the caller's CUDA stream; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ *   - Images are row-major [z][u]: rows run along the rotation axis z,
+ *     columns along u.  Stacks are [angle][row][col].
+ *   - Intensities arrive centred (q = 0 at pixel (N/2, N/2)).
+ *   - Forward FFTs are unnormalised with exp(-2 pi i jk/N); inverse FFTs carry
+ *     1/N per axis.
+ *   - Pointers may be host or device memory; the library tells them apart
+ *     with cudaPointerGetAttributes.  Host memory is read or written with
+ *     stream-ordered copies; a call that reads host memory returns after its
+ *     data was consumed, a call that writes host memory returns after the
+ *     data is there.  Device pointers are used in stream order on the plan's
+ *     stream; the caller keeps them alive until the stream has passed them.
+ *   - Every call returns a cpra_status and never aborts or throws.  A failing
+ *     call records a message readable with cpra_last_error(plan)
+ *     (cpra_last_error(NULL) for failures without a plan).
+ */
+#ifndef CPRA_H
+#define CPRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cpra_plan_s* cpra_plan_t;
+
+typedef enum {
+  CPRA_OK = 0,
+  CPRA_ERR_INVALID_ARG = 1,   /* bad size, pointer, weight or input value   */
+  CPRA_ERR_OUT_OF_MEMORY = 2, /* the allocator returned NULL               */
+  CPRA_ERR_CUDA = 3,          /* a CUDA runtime call failed                */
+  CPRA_ERR_NOT_READY = 4,     /* inputs missing (e.g. angles not loaded)   */
+  CPRA_ERR_TIMEOUT = 5,       /* a bounded device wait gave up             */
+  CPRA_ERR_UNSUPPORTED = 6    /* valid request the library cannot run     */
+} cpra_status;
+
+enum { CPRA_WRAP_LITERAL = 0, CPRA_WRAP_MIRROR = 1 };
+enum { CPRA_BLEND_STATE = 0, CPRA_BLEND_OBJECT = 1 };
+enum { CPRA_FP32 = 0, CPRA_BF16_TC = 1, CPRA_FP16_TC = 2 };
+enum { CPRA_ENGINE_AUTO = 0, CPRA_ENGINE_TWO_PASS = 1, CPRA_ENGINE_FUSED = 2 };
+enum {
+  CPRA_RESULT_PO = 0,      /* Np*N*N float: P_{S+} g (iterate on its valid set)  */
+  CPRA_RESULT_STATE = 1,   /* Np*N*N float: the iterate g itself                 */
+  CPRA_RESULT_SUPPORT = 2, /* Np*N*N uint8: support, 1 inside                    */
+  CPRA_RESULT_ERRORS = 3,  /* t*Np double: Fourier error of every iteration so far,
+                              [iteration][angle]                                 */
+  CPRA_RESULT_VOLUME = 4   /* N*N*N complex64 [z][y][x], centred (after assemble) */
+};
+
+#define CPRA_MAX_TAPS 15
+
+/*
+ * Reconstruction parameters.  cpra_default_config fills the paper's example
+ * values; fields map to the paper as follows.
+ *   N, Np          pattern size and number of angles (Eq. 1-3).  N = 2^a 3^b,
+ *                  a multiple of 16, 16 <= N <= 1024; Np >= 1.
+ *   n_ei           conventional 2D iterations per episode, N_ei (Step B).
+ *   n_taps, alpha  coupling weights alpha_k, k = -(n_taps/2)..n_taps/2 (Eq. 4);
+ *                  n_taps odd, <= CPRA_MAX_TAPS, sum 1 within 1e-12.
+ *   beta           HIO feedback (Fienup); the paper uses 0.9.
+ *   wrap_mode      180-degree seam: LITERAL couples angle Np-1 with angle 0 as
+ *                  is; MIRROR flips u once per wrap.
+ *   blend_target   STATE blends the iterate g, OBJECT blends P_{S+} g.
+ *   hio_iters, er_iters  global schedule: iteration t runs HIO while
+ *                  t < hio_iters, ER afterwards.
+ *   shrinkwrap_every, sw_sigma, sw_tau   support update after iteration t
+ *                  when (t+1) % every == 0 (0 = off): blur P_{S+} g with a
+ *                  periodic Gaussian of sw_sigma pixels and keep pixels at or
+ *                  above sw_tau times the maximum (the paper's 0.1 threshold).
+ *   n_pre          Step A: HIO iterations run on angle 0 alone before t = 0.
+ *   precision      CPRA_FP32 (default) or tensor-core FFT stages.
+ *   com_align      1: move each PO's mass centre to the origin before
+ *                  assembly (Step C); 0: use the frame centre.
+ *   engine         kernel family; AUTO picks the fused cluster-resident
+ *                  iteration where it fits on chip, TWO_PASS otherwise.
+ *   seed           seeds the random initial guess (SplitMix64 per pixel).
+ *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
+ */
+typedef struct {
+  int32_t N, Np;
+  int32_t n_ei;
+  int32_t n_taps;
+  double alpha[CPRA_MAX_TAPS];
+  float beta;
+  int32_t wrap_mode;
+  int32_t blend_target;
+  int32_t hio_iters, er_iters;
+  int32_t shrinkwrap_every;
+  float sw_sigma, sw_tau;
+  int32_t n_pre;
+  int32_t precision;
+  int32_t com_align;
+  int32_t engine;
+  uint64_t seed;
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} cpra_config;
+
+/* Fill *cfg with defaults for an N x N, Np-angle problem: n_ei 10, alpha
+ * (0.2, 0.6, 0.2) and beta 0.9 (the paper's Eq. 4 example and HIO value),
+ * 200 HIO + 20 ER, shrink-wrap off, sigma 2, tau 0.1, LITERAL, STATE, FP32,
+ * com_align 1, seed 0, cudaMalloc.  Returns INVALID_ARG for a NULL cfg. */
+cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* cfg);
+
+/* Device bytes a plan for *cfg holds while iterating (iter_bytes) and the
+ * extra bytes cpra_assemble_3d allocates (assemble_bytes); either may be NULL.
+ * Used for admission by free HBM.  Validates cfg like cpra_plan. */
+cpra_status cpra_plan_bytes(const cpra_config* cfg, size_t* iter_bytes, size_t* assemble_bytes);
+
+/* Create a plan: validate *cfg (copied), allocate the iteration state through
+ * cfg->alloc and build FFT twiddle tables (FP64 on the host, stored FP32).
+ * stream is a cudaStream_t (NULL = legacy default stream); the plan uses it
+ * for all work.  On failure *out is NULL and the status says why
+ * (INVALID_ARG, UNSUPPORTED for N outside the supported set,
+ * OUT_OF_MEMORY, CUDA). */
+cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out);
+
+/* Load `count` centred intensity patterns I[count][N][N] (float32) for angles
+ * first_angle .. first_angle+count-1 with their angles theta_rad[count]
+ * (radians, host memory, may be NULL to keep theta_n = n*pi/Np).  Prepares
+ * A = sqrt(I) in FFT order, its Hermitian-symmetrised half plane and the FP64
+ * error constants (Eq. 1-3).  Non-finite or negative intensities give
+ * INVALID_ARG and leave the angles unloaded. */
+cpra_status cpra_load_intensities(cpra_plan_t plan, const float* I, int32_t first_angle,
+                                  int32_t count, const double* theta_rad);
+
+/* Set the support from S (uint8, nonzero = inside).  per_angle = 1: S is
+ * [Np][N][N]; per_angle = 0: one [N][N] mask for every angle.  S = NULL sets
+ * the padded bounding box (central N/2 x N/2 square) for every angle. */
+cpra_status cpra_load_support(cpra_plan_t plan, const uint8_t* S, int32_t per_angle);
+
+/* Checkpoint restore: set the iterate g[Np][N][N] (float32) and the global
+ * iteration counter t (>= 0).  Without this call the first cpra_iterate
+ * starts from the seeded random guess on the current support (Step A). */
+cpra_status cpra_load_state(cpra_plan_t plan, const float* g, int64_t t);
+
+/* Run n_iters global iterations (Step B): coupling (Eq. 4) before every
+ * iteration t with t % n_ei == 0, then FFT -> modulus projection -> inverse
+ * FFT -> HIO/ER update for every angle, shrink-wrap on schedule.  If err_out
+ * is not NULL it receives the Fourier error of every angle and iteration,
+ * err_out[i*Np + n] (double, host or device).  Returns NOT_READY until every
+ * angle has intensities. */
+cpra_status cpra_iterate(cpra_plan_t plan, int32_t n_iters, double* err_out);
+
+/* Step D: spectra of P_{S+} g with the centre-of-mass phase ramp, Fourier
+ * slice gridding (bilinear in kx, ky; exact kz) into an N^3 grid, inverse 3D
+ * FFT.  The centred complex64 volume [z][y][x] stays in the plan (read it
+ * with CPRA_RESULT_VOLUME) and is also copied to out_volume when that is not
+ * NULL (N^3 * 8 bytes, host or device). */
+cpra_status cpra_assemble_3d(cpra_plan_t plan, void* out_volume);
+
+/* Copy one result (CPRA_RESULT_*) into dst, which holds `bytes` bytes (host
+ * or device).  INVALID_ARG if bytes is smaller than the result, NOT_READY for
+ * a volume before cpra_assemble_3d. */
+cpra_status cpra_result(cpra_plan_t plan, int32_t what, void* dst, size_t bytes);
+
+/* Restart the reconstruction: t = 0, the error history is cleared and the
+ * next cpra_iterate starts again from the seeded guess (Step A).
+ * Intensities, angles and the current support are kept. */
+cpra_status cpra_reset(cpra_plan_t plan);
+
+/* Kernel classes for cpra_kernel_stats. */
+enum {
+  CPRA_KERNEL_COLPASS = 0,   /* two-pass engine: column FFT + modulus projection */
+  CPRA_KERNEL_ROWPASS = 1,   /* two-pass engine: C2R + HIO/ER + R2C rows          */
+  CPRA_KERNEL_PRIME = 2,     /* coupling (Eq. 4) + R2C rows                        */
+  CPRA_KERNEL_SHRINKWRAP = 3,
+  CPRA_KERNEL_ASSEMBLE = 4,
+  CPRA_KERNEL_FUSED = 5,     /* fused engine: one whole iteration                  */
+  CPRA_KERNEL_PREPARE = 6,
+  CPRA_KERNEL_KINDS = 7
+};
+
+/* Device-time profiling: with on = 1 the plan records CUDA events around each
+ * of its kernel launches on its stream (a small overhead per launch).
+ * cpra_kernel_stats waits for the stream and returns, for one kernel class,
+ * the summed device milliseconds and the launch count since profiling was
+ * switched on (or since the last cpra_set_profiling call). */
+cpra_status cpra_set_profiling(cpra_plan_t plan, int32_t on);
+cpra_status cpra_kernel_stats(cpra_plan_t plan, int32_t kind, double* total_ms, int64_t* launches);
+
+/* Number of kernels this library has launched in this process. */
+int64_t cpra_launch_count(void);
+
+/* Global iteration counter t of the plan (-1 for a NULL plan). */
+int64_t cpra_iteration(cpra_plan_t plan);
+
+/* Wait for the plan's stream; reports device-side failures (CUDA). */
+cpra_status cpra_sync(cpra_plan_t plan);
+
+/* Free every device buffer through cfg->free and the plan itself. */
+cpra_status cpra_destroy(cpra_plan_t plan);
+
+/* Message of the last failure on this plan (NULL plan: last failure of a
+ * call that had no plan on this thread).  The string lives until the next
+ * call on the same plan. */
+const char* cpra_last_error(cpra_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPRA_H */

@@ -67,7 +67,7 @@ __all__ = [
     "dft_matrix", "dft2", "idft2", "dft3", "idft3", "fftshift2", "ifftshift2",
     "fftshift3", "amplitudes", "a_sym", "splitmix64", "initial_guess",
     "modulus_projection", "fourier_error_terms", "support_update",
-    "iterate_2d", "couple", "wrapped_gaussian", "blur", "shrinkwrap",
+    "iterate_2d", "positivity_margin", "couple", "wrapped_gaussian", "blur", "shrinkwrap",
     "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d",
     "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
     "r_factor",
@@ -209,12 +209,21 @@ def support_update(g, gp, S, beta, algo):
     return np.where(valid, gp, 0.0)
 
 
-def iterate_2d(g, A, S, beta, algo):
-    """One iteration for a stack of POs; returns (g_new, err_num, err_den)."""
+def iterate_2d(g, A, S, beta, algo, return_gp=False):
+    """One iteration for a stack of POs; returns (g_new, err_num, err_den[, g'])."""
     G = dft2(g)
     num, den = fourier_error_terms(G, A)
     gp = idft2(modulus_projection(G, A)).real
-    return support_update(g, gp, S, beta, algo), num, den
+    out = support_update(g, gp, S, beta, algo)
+    return (out, num, den, gp) if return_gp else (out, num, den)
+
+
+def positivity_margin(gp, S):
+    """min over the support of |g'| / max |g'| per pattern: how close the
+    sign test of the support update came to flipping (a diagnostic)."""
+    sup = S.astype(bool)
+    inside = np.where(sup, np.abs(gp), np.inf).reshape(gp.shape[0], -1).min(axis=1)
+    return inside / np.maximum(np.abs(gp).reshape(gp.shape[0], -1).max(axis=1), 1e-300)
 
 
 # --------------------------------------------------------------------------
@@ -379,6 +388,7 @@ class OracleRun:
     g: np.ndarray = None
     t: int = 0
     errors: list = field(default_factory=list)
+    margins: list = field(default_factory=list)
 
     @classmethod
     def start(cls, cfg: OracleConfig, I_centred, S0=None, g0=None):
@@ -401,8 +411,9 @@ class OracleRun:
         if self.t % c.n_ei == 0:
             self.g = couple(self.g, c.alpha, c.wrap, c.blend, self.S)
         algo = HIO if self.t < c.hio_iters else ER
-        self.g, num, den = iterate_2d(self.g, self.A, self.S, c.beta, algo)
+        self.g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True)
         self.errors.append(np.sqrt(num / den))
+        self.margins.append(positivity_margin(gp, self.S))
         if c.shrinkwrap_every > 0 and (self.t + 1) % c.shrinkwrap_every == 0:
             self.S = shrinkwrap(self.g, self.S, c.sw_sigma, c.sw_tau)
         self.t += 1

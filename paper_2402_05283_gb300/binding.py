@@ -1,0 +1,329 @@
+"""ctypes binding of the C ABI declared in include/cpra.h.
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of libcpra.so.  The functions keep the C names (``cpra_plan``,
+``cpra_iterate`` ...); :class:`Plan` wraps them for convenience.  Arrays may
+be numpy arrays (host memory) or torch tensors (host or CUDA memory); the
+library tells host and device pointers apart itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcpra.so")
+
+OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_READY, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+WRAP_LITERAL, WRAP_MIRROR = 0, 1
+BLEND_STATE, BLEND_OBJECT = 0, 1
+FP32, BF16_TC, FP16_TC = 0, 1, 2
+ENGINE_AUTO, ENGINE_TWO_PASS, ENGINE_FUSED = 0, 1, 2
+RESULT_PO, RESULT_STATE, RESULT_SUPPORT, RESULT_ERRORS, RESULT_VOLUME = range(5)
+(KERNEL_COLPASS, KERNEL_ROWPASS, KERNEL_PRIME, KERNEL_SHRINKWRAP, KERNEL_ASSEMBLE, KERNEL_FUSED,
+ KERNEL_PREPARE, KERNEL_KINDS) = range(8)
+MAX_TAPS = 15
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class cpra_config(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("Np", C.c_int32), ("n_ei", C.c_int32), ("n_taps", C.c_int32),
+        ("alpha", C.c_double * MAX_TAPS), ("beta", C.c_float), ("wrap_mode", C.c_int32),
+        ("blend_target", C.c_int32), ("hio_iters", C.c_int32), ("er_iters", C.c_int32),
+        ("shrinkwrap_every", C.c_int32), ("sw_sigma", C.c_float), ("sw_tau", C.c_float),
+        ("n_pre", C.c_int32), ("precision", C.c_int32), ("com_align", C.c_int32),
+        ("engine", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+        ("alloc_ctx", C.c_void_p),
+    ]
+
+
+class CpraError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cpra status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libcpra.so; raises if it was not built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                              "(the CUDA library is required; there is no CPU path)")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        sigs = {
+            "cpra_default_config": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(cpra_config)]),
+            "cpra_plan_bytes": (C.c_int, [C.POINTER(cpra_config), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+            "cpra_plan": (C.c_int, [C.POINTER(cpra_config), P, C.POINTER(P)]),
+            "cpra_load_intensities": (C.c_int, [P, P, C.c_int32, C.c_int32, P]),
+            "cpra_load_support": (C.c_int, [P, P, C.c_int32]),
+            "cpra_load_state": (C.c_int, [P, P, C.c_int64]),
+            "cpra_iterate": (C.c_int, [P, C.c_int32, P]),
+            "cpra_assemble_3d": (C.c_int, [P, P]),
+            "cpra_result": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
+            "cpra_iteration": (C.c_int64, [P]),
+            "cpra_reset": (C.c_int, [P]),
+            "cpra_set_profiling": (C.c_int, [P, C.c_int32]),
+            "cpra_kernel_stats": (C.c_int, [P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+            "cpra_launch_count": (C.c_int64, []),
+            "cpra_sync": (C.c_int, [P]),
+            "cpra_destroy": (C.c_int, [P]),
+            "cpra_last_error": (C.c_char_p, [P]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, plan=None):
+    if st != OK:
+        msg = lib().cpra_last_error(plan)
+        raise CpraError(st, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, keep-alive) for a numpy array or torch tensor (or None)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return a.data_ptr(), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+# ------------------------------------------------------------ C-named calls
+def cpra_default_config(N: int, Np: int) -> cpra_config:
+    cfg = cpra_config()
+    _check(lib().cpra_default_config(N, Np, C.byref(cfg)))
+    return cfg
+
+
+def cpra_plan_bytes(cfg: cpra_config):
+    a, b = C.c_size_t(), C.c_size_t()
+    _check(lib().cpra_plan_bytes(C.byref(cfg), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def cpra_plan(cfg: cpra_config, stream: int | None = None):
+    h = C.c_void_p()
+    _check(lib().cpra_plan(C.byref(cfg), stream, C.byref(h)))
+    return h
+
+
+def cpra_load_intensities(plan, I, first: int, count: int, thetas=None):
+    p, keep = _ptr(I)
+    th = None
+    if thetas is not None:
+        th = np.ascontiguousarray(thetas, dtype=np.float64)
+    _check(lib().cpra_load_intensities(plan, p, first, count,
+                                       None if th is None else th.ctypes.data), plan)
+    return keep
+
+
+def cpra_load_support(plan, S, per_angle: int):
+    p, keep = _ptr(S)
+    _check(lib().cpra_load_support(plan, p, per_angle), plan)
+    return keep
+
+
+def cpra_load_state(plan, g, t: int):
+    p, keep = _ptr(g)
+    _check(lib().cpra_load_state(plan, p, t), plan)
+    return keep
+
+
+def cpra_iterate(plan, n_iters: int, err_out=None):
+    p, keep = _ptr(err_out)
+    _check(lib().cpra_iterate(plan, n_iters, p), plan)
+    return keep
+
+
+def cpra_assemble_3d(plan, out=None):
+    p, keep = _ptr(out)
+    _check(lib().cpra_assemble_3d(plan, p), plan)
+    return keep
+
+
+def cpra_result(plan, what: int, dst, nbytes: int):
+    p, keep = _ptr(dst)
+    _check(lib().cpra_result(plan, what, p, nbytes), plan)
+    return keep
+
+
+def cpra_iteration(plan) -> int:
+    return int(lib().cpra_iteration(plan))
+
+
+def cpra_reset(plan):
+    _check(lib().cpra_reset(plan), plan)
+
+
+def cpra_set_profiling(plan, on: bool):
+    _check(lib().cpra_set_profiling(plan, int(bool(on))), plan)
+
+
+def cpra_kernel_stats(plan, kind: int):
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().cpra_kernel_stats(plan, kind, C.byref(ms), C.byref(n)), plan)
+    return ms.value, n.value
+
+
+def cpra_launch_count() -> int:
+    return int(lib().cpra_launch_count())
+
+
+def cpra_sync(plan):
+    _check(lib().cpra_sync(plan), plan)
+
+
+def cpra_destroy(plan):
+    _check(lib().cpra_destroy(plan))
+
+
+def cpra_last_error(plan=None) -> str:
+    m = lib().cpra_last_error(plan)
+    return m.decode() if m else ""
+
+
+# ------------------------------------------------------------ convenience
+class TorchAllocator:
+    """Device memory from torch's caching allocator, handed to the library."""
+
+    def __init__(self, device=None):
+        import torch
+        self.torch = torch
+        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.blocks = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+
+    def _do_alloc(self, nbytes, ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:  # OOM is reported to the library as NULL
+            return None
+        self.blocks[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _do_free(self, ptr, ctx):
+        self.blocks.pop(ptr, None)
+
+
+def make_config(N: int, Np: int, **kw) -> cpra_config:
+    cfg = cpra_default_config(N, Np)
+    alpha = kw.pop("alpha", None)
+    if alpha is not None:
+        cfg.n_taps = len(alpha)
+        for i, a in enumerate(alpha):
+            cfg.alpha[i] = float(a)
+        for i in range(len(alpha), MAX_TAPS):
+            cfg.alpha[i] = 0.0
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(f"cpra_config has no field {k}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Plan:
+    """One reconstruction on one CUDA stream (see include/cpra.h)."""
+
+    def __init__(self, cfg: cpra_config, stream=None, allocator: str = "torch"):
+        self.cfg = cfg
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = TorchAllocator()
+            cfg.alloc = self._alloc._alloc
+            cfg.free = self._alloc._free
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = None
+        self.stream = stream
+        self.h = cpra_plan(cfg, stream)
+        self.N, self.Np = cfg.N, cfg.Np
+
+    def load_intensities(self, I, first: int = 0, thetas=None):
+        count = I.shape[0] if I.ndim == 3 else 1
+        cpra_load_intensities(self.h, I, first, count, thetas)
+
+    def load_support(self, S=None):
+        per = 1 if (S is not None and S.ndim == 3) else 0
+        if isinstance(S, np.ndarray):
+            S = S.astype(np.uint8)
+        cpra_load_support(self.h, S, per)
+
+    def load_state(self, g, t: int):
+        if isinstance(g, np.ndarray):
+            g = g.astype(np.float32)
+        cpra_load_state(self.h, g, t)
+
+    def iterate(self, n: int, errors: bool = False):
+        out = np.empty((n, self.Np), dtype=np.float64) if errors and n > 0 else None
+        cpra_iterate(self.h, n, out)
+        return out
+
+    def assemble_3d(self, out=None):
+        cpra_assemble_3d(self.h, out)
+        return out
+
+    def result(self, what: int):
+        N, Np = self.N, self.Np
+        if what in (RESULT_PO, RESULT_STATE):
+            a = np.empty((Np, N, N), np.float32)
+        elif what == RESULT_SUPPORT:
+            a = np.empty((Np, N, N), np.uint8)
+        elif what == RESULT_ERRORS:
+            a = np.empty((self.iteration, Np), np.float64)
+        elif what == RESULT_VOLUME:
+            a = np.empty((N, N, N), np.complex64)
+        else:
+            raise ValueError(what)
+        if a.nbytes:
+            cpra_result(self.h, what, a, a.nbytes)
+        return a
+
+    def reset(self):
+        cpra_reset(self.h)
+
+    def set_profiling(self, on: bool = True):
+        cpra_set_profiling(self.h, on)
+
+    def kernel_stats(self, kind: int):
+        return cpra_kernel_stats(self.h, kind)
+
+    @property
+    def iteration(self) -> int:
+        return cpra_iteration(self.h)
+
+    def sync(self):
+        cpra_sync(self.h)
+
+    def close(self):
+        if self.h:
+            cpra_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,660 @@
+// api.cu - the C ABI (include/cpra.h): plans, loading, the iteration
+// schedule of Steps A and B, assembly (Step D) and results.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cpra_internal.h"
+#include "tiling.cuh"
+
+using namespace cpra;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cpra_status fail(cpra_plan_s* p, cpra_status st, const std::string& msg) {
+  if (p) p->err = msg;
+  else g_last_error = msg;
+  return st;
+}
+
+cpra_status cuda_fail(cpra_plan_s* p, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(p, CPRA_ERR_CUDA, m);
+}
+
+#define CK(expr, where)                               \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return cuda_fail(p, _e, where); \
+  } while (0)
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void* dev_alloc(cpra_plan_s* p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  if (p->cfg.alloc) {
+    ptr = p->cfg.alloc(bytes, p->cfg.alloc_ctx);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (ptr) p->owned.push_back(ptr);
+  return ptr;
+}
+
+void dev_free(cpra_plan_s* p, void* ptr) {
+  if (!ptr) return;
+  for (size_t i = 0; i < p->owned.size(); ++i)
+    if (p->owned[i] == ptr) {
+      p->owned.erase(p->owned.begin() + i);
+      break;
+    }
+  if (p->cfg.free) p->cfg.free(ptr, p->cfg.alloc_ctx);
+  else if (!p->cfg.alloc) cudaFree(ptr);
+}
+
+struct Sizes {
+  size_t iter = 0, assemble = 0;
+};
+
+Sizes plan_sizes(const cpra_config& c) {
+  const size_t N = c.N, Np = c.Np, NN = N * N, W = (N + 31) / 32;
+  Sizes s;
+  s.iter = 2 * Np * NN * 4      // g, g_alt
+           + Np * NN * 4        // Hp (N x N/2 complex)
+           + Np * N * (N / 2) * 4 + Np * N * 4  // A_main, A_nyq
+           + 3 * Np * 8         // Cn, sumA2, err_acc
+           + Np * N * W * 4     // S
+           + N * 8              // twiddles
+           + Np * NN * 4        // staging
+           + 256 * Np * 8;      // initial error history
+  if (c.shrinkwrap_every > 0) s.iter += Np * NN * 4 + Np * 4 + N * 4;
+  s.assemble = Np * NN * 8 + N * NN * 8 + (NN + 1) * 4 + 4 * Np * N * 12 + 3 * Np * 8;
+  return s;
+}
+
+cpra_status validate(const cpra_config* c, std::string& why) {
+  if (!c) { why = "config is NULL"; return CPRA_ERR_INVALID_ARG; }
+  if (c->N < 16 || c->N > 1024 || c->N % 16 != 0) {
+    why = "N must be a multiple of 16 in [16, 1024]";
+    return c->N > 0 ? CPRA_ERR_UNSUPPORTED : CPRA_ERR_INVALID_ARG;
+  }
+  if (!n_supported(c->N)) { why = "N must be 2^a 3^b"; return CPRA_ERR_UNSUPPORTED; }
+  if (c->Np < 1 || c->Np > 65535) { why = "Np must be in [1, 65535]"; return CPRA_ERR_INVALID_ARG; }
+  if (c->n_ei < 1) { why = "n_ei must be >= 1"; return CPRA_ERR_INVALID_ARG; }
+  if (c->n_taps < 1 || c->n_taps > CPRA_MAX_TAPS || c->n_taps % 2 == 0) {
+    why = "n_taps must be odd and <= 15";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  double s = 0.0;
+  for (int i = 0; i < c->n_taps; ++i) {
+    if (!std::isfinite(c->alpha[i])) { why = "alpha not finite"; return CPRA_ERR_INVALID_ARG; }
+    s += c->alpha[i];
+  }
+  if (std::fabs(s - 1.0) > 1e-12) { why = "alpha must sum to 1 (within 1e-12)"; return CPRA_ERR_INVALID_ARG; }
+  if (!std::isfinite(c->beta)) { why = "beta not finite"; return CPRA_ERR_INVALID_ARG; }
+  if (c->wrap_mode != CPRA_WRAP_LITERAL && c->wrap_mode != CPRA_WRAP_MIRROR) {
+    why = "bad wrap_mode";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  if (c->blend_target != CPRA_BLEND_STATE && c->blend_target != CPRA_BLEND_OBJECT) {
+    why = "bad blend_target";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  if (c->hio_iters < 0 || c->er_iters < 0 || c->n_pre < 0 || c->shrinkwrap_every < 0) {
+    why = "negative iteration count";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  if (c->shrinkwrap_every > 0 && (!(c->sw_sigma > 0.0f) || !(c->sw_tau >= 0.0f) || !(c->sw_tau <= 1.0f))) {
+    why = "shrink-wrap needs sigma > 0 and 0 <= tau <= 1";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  if (c->precision != CPRA_FP32 && c->precision != CPRA_BF16_TC && c->precision != CPRA_FP16_TC) {
+    why = "bad precision";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  if (c->precision != CPRA_FP32) { why = "tensor-core precision not built into this engine"; return CPRA_ERR_UNSUPPORTED; }
+  if (c->engine != CPRA_ENGINE_AUTO && c->engine != CPRA_ENGINE_TWO_PASS && c->engine != CPRA_ENGINE_FUSED) {
+    why = "bad engine";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  if (c->engine == CPRA_ENGINE_FUSED) { why = "fused engine not available for this N"; return CPRA_ERR_UNSUPPORTED; }
+  if ((c->alloc == nullptr) != (c->free == nullptr)) {
+    why = "alloc and free must be given together";
+    return CPRA_ERR_INVALID_ARG;
+  }
+  return CPRA_OK;
+}
+
+// periodic Gaussian taps (FP64): w[d] ~ sum_m exp(-(d + mN)^2 / 2 sigma^2), sum 1
+std::vector<float> gaussian_taps(int N, double sigma, int& ntaps) {
+  std::vector<double> w(N, 0.0);
+  const int M = (int)std::ceil(12.0 * sigma / N) + 1;
+  for (int d = 0; d < N; ++d)
+    for (int m = -M; m <= M; ++m) {
+      const double t = d + (double)m * N;
+      w[d] += std::exp(-t * t / (2.0 * sigma * sigma));
+    }
+  double s = 0.0;
+  for (double v : w) s += v;
+  for (double& v : w) v /= s;
+  int R = 0;
+  while (R < N / 2 && w[R + 1] >= 1e-11 * w[0]) ++R;
+  std::vector<float> taps;
+  int lo;
+  if (2 * R + 1 >= N) {
+    ntaps = N;
+    lo = -(N / 2) + 1;
+  } else {
+    ntaps = 2 * R + 1;
+    lo = -R;
+  }
+  for (int t = 0; t < ntaps; ++t) taps.push_back((float)w[((lo + t) % N + N) % N]);
+  return taps;
+}
+
+cpra_status ensure_err_cap(cpra_plan_s* p, int64_t need) {
+  if (need <= p->err_cap) return CPRA_OK;
+  int64_t cap = p->err_cap > 0 ? p->err_cap : 256;
+  while (cap < need) cap *= 2;
+  double* nh = (double*)dev_alloc(p, sizeof(double) * cap * p->Np);
+  if (!nh) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "error history allocation failed");
+  if (p->err_hist && p->t > 0)
+    CK(cudaMemcpyAsync(nh, p->err_hist, sizeof(double) * p->t * p->Np, cudaMemcpyDeviceToDevice,
+                       p->stream), "err_hist copy");
+  CK(cudaStreamSynchronize(p->stream), "err_hist sync");
+  dev_free(p, p->err_hist);
+  p->err_hist = nh;
+  p->err_cap = cap;
+  return CPRA_OK;
+}
+
+cpra_status copy_out(cpra_plan_s* p, void* dst, const void* src, size_t bytes) {
+  const bool dd = is_device_ptr(dst);
+  CK(cudaMemcpyAsync(dst, src, bytes, dd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     p->stream), "result copy");
+  if (!dd) CK(cudaStreamSynchronize(p->stream), "result sync");
+  return CPRA_OK;
+}
+
+// Records CUDA events around a launch when the plan profiles its kernels.
+template <class F>
+cudaError_t timed(cpra_plan_s* p, int kind, F&& launch) {
+  if (!p->profiling) return launch();
+  cpra_plan_s::Timed ev;
+  if (!p->spare.empty()) {
+    ev = p->spare.back();
+    p->spare.pop_back();
+  } else {
+    cudaError_t e = cudaEventCreate(&ev.a);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
+    if (e != cudaSuccess) return e;
+  }
+  ev.kind = kind;
+  cudaError_t e = cudaEventRecord(ev.a, p->stream);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(ev.b, p->stream);
+  p->pending.push_back(ev);
+  return e;
+}
+
+cudaError_t drain_timings(cpra_plan_s* p) {
+  for (auto& ev : p->pending) {
+    cudaError_t e = cudaEventSynchronize(ev.b);
+    if (e != cudaSuccess) return e;
+    float ms = 0.0f;
+    e = cudaEventElapsedTime(&ms, ev.a, ev.b);
+    if (e != cudaSuccess) return e;
+    p->kms[ev.kind] += ms;
+    p->kcount[ev.kind] += 1;
+    p->spare.push_back(ev);
+  }
+  p->pending.clear();
+  return cudaSuccess;
+}
+
+// Steps A/B scheduling helpers
+cpra_status prime_plain(cpra_plan_s* p, int first, int count) {
+  CoupleArgs ca{};
+  ca.n_taps = 1;
+  ca.alpha[0] = 1.0f;
+  CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(p, first, count, p->g, p->g, p->Hp, ca); }),
+     "prime");
+  return CPRA_OK;
+}
+
+cpra_status build_gridding(cpra_plan_s* p) {
+  const int N = p->N, Np = p->Np, NN = N * N;
+  std::vector<double> wsum(NN, 0.0);
+  std::vector<int32_t> cnt(NN, 0);
+  struct Ent { int32_t cell, idx; double w; };
+  std::vector<Ent> ents;
+  ents.reserve((size_t)4 * Np * N);
+  for (int n = 0; n < Np; ++n) {
+    const double c = std::cos(p->theta[n]), s = std::sin(p->theta[n]);
+    for (int k = 0; k < N; ++k) {
+      const double ku = k < N / 2 ? k : k - N;
+      const double px = ku * c, py = ku * s;
+      const double i0 = std::floor(px), j0 = std::floor(py);
+      const double fx = px - i0, fy = py - j0;
+      for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj) {
+          const double w = (di ? fx : 1.0 - fx) * (dj ? fy : 1.0 - fy);
+          if (w == 0.0) continue;
+          const int ii = (int)(((long long)i0 + di) % N + N) % N;
+          const int jj = (int)(((long long)j0 + dj) % N + N) % N;
+          const int cell = jj * N + ii;
+          ents.push_back({cell, n * N + k, w});
+          wsum[cell] += w;
+        }
+    }
+  }
+  std::vector<int32_t> ptr(NN + 1, 0);
+  for (const Ent& e : ents)
+    if (wsum[e.cell] >= 1e-12) ptr[e.cell + 1]++;
+  for (int i = 0; i < NN; ++i) ptr[i + 1] += ptr[i];
+  const int64_t n_ent = ptr[NN];
+  std::vector<int32_t> idx(n_ent > 0 ? n_ent : 1);
+  std::vector<double> wv(n_ent > 0 ? n_ent : 1);
+  std::vector<int32_t> fillp(ptr.begin(), ptr.end() - 1);
+  for (const Ent& e : ents) {
+    if (wsum[e.cell] < 1e-12) continue;
+    const int32_t o = fillp[e.cell]++;
+    idx[o] = e.idx;
+    wv[o] = e.w / wsum[e.cell];
+  }
+  Assembly& a = p->asmb;
+  if (a.ent_idx && a.n_ent < n_ent) {
+    dev_free(p, a.ent_idx);
+    dev_free(p, a.ent_w);
+    a.ent_idx = nullptr;
+    a.ent_w = nullptr;
+  }
+  if (!a.ent_idx) {
+    const int64_t cap = n_ent > 0 ? n_ent : 1;
+    a.ent_idx = (int32_t*)dev_alloc(p, sizeof(int32_t) * cap);
+    a.ent_w = (double*)dev_alloc(p, sizeof(double) * cap);
+    if (!a.ent_idx || !a.ent_w) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "gridding allocation failed");
+  }
+  a.n_ent = n_ent;
+  CK(cudaMemcpyAsync(a.cell_ptr, ptr.data(), sizeof(int32_t) * (NN + 1), cudaMemcpyHostToDevice,
+                     p->stream), "grid ptr upload");
+  if (n_ent > 0) {
+    CK(cudaMemcpyAsync(a.ent_idx, idx.data(), sizeof(int32_t) * n_ent, cudaMemcpyHostToDevice,
+                       p->stream), "grid idx upload");
+    CK(cudaMemcpyAsync(a.ent_w, wv.data(), sizeof(double) * n_ent, cudaMemcpyHostToDevice,
+                       p->stream), "grid w upload");
+  }
+  CK(cudaStreamSynchronize(p->stream), "grid upload sync");
+  a.ready = true;
+  return CPRA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* c) {
+  if (!c) return fail(nullptr, CPRA_ERR_INVALID_ARG, "config is NULL");
+  std::memset(c, 0, sizeof(*c));
+  c->N = N;
+  c->Np = Np;
+  c->n_ei = 10;
+  c->n_taps = 3;
+  c->alpha[0] = 0.2;
+  c->alpha[1] = 0.6;
+  c->alpha[2] = 0.2;
+  c->beta = 0.9f;
+  c->wrap_mode = CPRA_WRAP_LITERAL;
+  c->blend_target = CPRA_BLEND_STATE;
+  c->hio_iters = 200;
+  c->er_iters = 20;
+  c->shrinkwrap_every = 0;
+  c->sw_sigma = 2.0f;
+  c->sw_tau = 0.1f;
+  c->n_pre = 0;
+  c->precision = CPRA_FP32;
+  c->com_align = 1;
+  c->engine = CPRA_ENGINE_AUTO;
+  c->seed = 0;
+  return CPRA_OK;
+}
+
+cpra_status cpra_plan_bytes(const cpra_config* cfg, size_t* iter_bytes, size_t* assemble_bytes) {
+  std::string why;
+  cpra_status st = validate(cfg, why);
+  if (st != CPRA_OK) return fail(nullptr, st, why);
+  Sizes s = plan_sizes(*cfg);
+  if (iter_bytes) *iter_bytes = s.iter;
+  if (assemble_bytes) *assemble_bytes = s.assemble;
+  return CPRA_OK;
+}
+
+cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
+  if (!out) return fail(nullptr, CPRA_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  cpra_status st = validate(cfg, why);
+  if (st != CPRA_OK) return fail(nullptr, st, why);
+  cpra_plan_s* p = new (std::nothrow) cpra_plan_s();
+  if (!p) return fail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "host allocation failed");
+  p->cfg = *cfg;
+  p->stream = (cudaStream_t)stream;
+  p->N = cfg->N;
+  p->Np = cfg->Np;
+  p->W = (cfg->N + 31) / 32;
+  p->engine = CPRA_ENGINE_TWO_PASS;
+  p->loaded.assign(p->Np, 0);
+  p->theta.resize(p->Np);
+  for (int n = 0; n < p->Np; ++n) p->theta[n] = n * M_PI / p->Np;
+  const size_t N = p->N, Np = p->Np, NN = N * N;
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* q = dev_alloc(p, bytes);
+    if (!q) ok = false;
+    return q;
+  };
+  p->g = (float*)A(Np * NN * 4);
+  p->g_alt = (float*)A(Np * NN * 4);
+  p->Hp = (float2*)A(Np * N * (N / 2) * 8);
+  p->A_main = (float*)A(Np * N * (N / 2) * 4);
+  p->A_nyq = (float*)A(Np * N * 4);
+  p->Cn = (double*)A(Np * 8);
+  p->sumA2 = (double*)A(Np * 8);
+  p->err_acc = (double*)A(Np * 8);
+  p->S = (uint32_t*)A(Np * N * p->W * 4);
+  p->tw = (float2*)A(N * 8);
+  p->stage = (float*)A(Np * NN * 4);
+  p->flag = (int*)A(sizeof(int) * 4);
+  if (ok && cfg->shrinkwrap_every > 0) {
+    std::vector<float> taps = gaussian_taps(p->N, cfg->sw_sigma, p->sw_ntaps);
+    p->sw_tmp = (float*)A(Np * NN * 4);
+    p->sw_max = (unsigned*)A(Np * 4);
+    p->sw_taps = (float*)A(taps.size() * 4);
+    if (ok) {
+      cudaError_t e = cudaMemcpy(p->sw_taps, taps.data(), taps.size() * 4, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) { cuda_fail(nullptr, e, "taps upload"); cpra_destroy(p); return CPRA_ERR_CUDA; }
+    }
+  }
+  if (!ok) {
+    cpra_destroy(p);
+    return fail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "device allocation failed");
+  }
+  std::vector<float2> tw(N);
+  for (size_t k = 0; k < N; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)N;
+    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  cudaError_t e = cudaMemcpyAsync(p->tw, tw.data(), N * 8, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->err_acc, 0, Np * 8, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->g, 0, Np * NN * 4, p->stream);
+  if (e == cudaSuccess) e = launch_support_box(p);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    cuda_fail(nullptr, e, "plan init");
+    cpra_destroy(p);
+    return CPRA_ERR_CUDA;
+  }
+  *out = p;
+  return CPRA_OK;
+}
+
+cpra_status cpra_load_intensities(cpra_plan_t p, const float* I, int32_t first, int32_t count,
+                                  const double* theta) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!I || count < 1 || first < 0 || first + count > p->Np)
+    return fail(p, CPRA_ERR_INVALID_ARG, "bad intensity range or pointer");
+  const size_t NN = (size_t)p->N * p->N;
+  const float* src = I;
+  if (!is_device_ptr(I)) {
+    CK(cudaMemcpyAsync(p->stage, I, sizeof(float) * NN * count, cudaMemcpyHostToDevice, p->stream),
+       "intensity upload");
+    src = p->stage;
+  }
+  CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream), "flag reset");
+  CK(timed(p, CPRA_KERNEL_PREPARE, [&] { return launch_prepare(p, src, first, count); }), "prepare");
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream), "flag read");
+  CK(cudaStreamSynchronize(p->stream), "prepare sync");
+  if (flag) return fail(p, CPRA_ERR_INVALID_ARG, "intensities must be finite and non-negative");
+  if (theta) {
+    for (int i = 0; i < count; ++i) {
+      if (!std::isfinite(theta[i])) return fail(p, CPRA_ERR_INVALID_ARG, "theta not finite");
+      p->theta[first + i] = theta[i];
+    }
+    p->asmb.ready = false;
+  }
+  for (int i = 0; i < count; ++i)
+    if (!p->loaded[first + i]) {
+      p->loaded[first + i] = 1;
+      p->n_loaded++;
+    }
+  return CPRA_OK;
+}
+
+cpra_status cpra_load_support(cpra_plan_t p, const uint8_t* S, int32_t per_angle) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!S) {
+    CK(launch_support_box(p), "support box");
+  } else {
+    const size_t bytes = (size_t)(per_angle ? p->Np : 1) * p->N * p->N;
+    const uint8_t* src = S;
+    if (!is_device_ptr(S)) {
+      CK(cudaMemcpyAsync(p->stage, S, bytes, cudaMemcpyHostToDevice, p->stream), "support upload");
+      src = (const uint8_t*)p->stage;
+    }
+    CK(launch_support_u8(p, src, per_angle ? 1 : 0), "support");
+  }
+  CK(cudaStreamSynchronize(p->stream), "support sync");
+  return CPRA_OK;
+}
+
+cpra_status cpra_load_state(cpra_plan_t p, const float* g, int64_t t) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!g || t < 0) return fail(p, CPRA_ERR_INVALID_ARG, "bad state pointer or counter");
+  const size_t bytes = sizeof(float) * p->Np * p->N * p->N;
+  CK(cudaMemcpyAsync(p->g, g, bytes, is_device_ptr(g) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     p->stream), "state upload");
+  CK(cudaStreamSynchronize(p->stream), "state sync");
+  cpra_status st = ensure_err_cap(p, t);
+  if (st != CPRA_OK) return st;
+  if (t > p->t) CK(cudaMemsetAsync(p->err_hist + p->t * p->Np, 0, sizeof(double) * (t - p->t) * p->Np, p->stream), "hist");
+  p->t = t;
+  p->state_ready = true;
+  p->hp_valid = false;
+  return CPRA_OK;
+}
+
+cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (n_iters < 0) return fail(p, CPRA_ERR_INVALID_ARG, "n_iters < 0");
+  if (p->n_loaded < p->Np) return fail(p, CPRA_ERR_NOT_READY, "not every angle has intensities");
+  const cpra_config& c = p->cfg;
+  if (!p->state_ready) {
+    CK(launch_init_guess(p), "initial guess");
+    for (int i = 0; i < c.n_pre; ++i) {  // Step A on angle 0
+      cpra_status st = prime_plain(p, 0, 1);
+      if (st != CPRA_OK) return st;
+      CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(p, 0, 1); }), "colpass");
+      CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(p, 0, 1, kHIO, -1, 0); }),
+         "rowpass");
+    }
+    p->state_ready = true;
+    p->hp_valid = false;
+  }
+  cpra_status st = ensure_err_cap(p, p->t + n_iters);
+  if (st != CPRA_OK) return st;
+  const int64_t t0 = p->t;
+  const int r = c.n_taps / 2;
+  for (int i = 0; i < n_iters; ++i) {
+    const int64_t t = p->t;
+    if (t % c.n_ei == 0) {
+      CoupleArgs ca{};
+      ca.n_taps = c.n_taps;
+      for (int k = 0; k < c.n_taps; ++k) ca.alpha[k] = (float)c.alpha[k];
+      ca.mirror = c.wrap_mode == CPRA_WRAP_MIRROR;
+      ca.object = c.blend_target == CPRA_BLEND_OBJECT;
+      ca.store_g = 1;
+      (void)r;
+      CK(timed(p, CPRA_KERNEL_PRIME,
+               [&] { return launch_prime(p, 0, p->Np, p->g, p->g_alt, p->Hp, ca); }),
+         "couple");
+      std::swap(p->g, p->g_alt);
+      p->hp_valid = true;
+    } else if (!p->hp_valid) {
+      st = prime_plain(p, 0, p->Np);
+      if (st != CPRA_OK) return st;
+      p->hp_valid = true;
+    }
+    CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(p, 0, p->Np); }), "colpass");
+    const int algo = t < c.hio_iters ? kHIO : kER;
+    const int forward = ((t + 1) % c.n_ei) != 0;
+    CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(p, 0, p->Np, algo, t, forward); }),
+       "rowpass");
+    p->hp_valid = forward != 0;
+    if (c.shrinkwrap_every > 0 && (t + 1) % c.shrinkwrap_every == 0)
+      CK(timed(p, CPRA_KERNEL_SHRINKWRAP, [&] { return launch_shrinkwrap(p); }), "shrinkwrap");
+    p->t++;
+  }
+  if (err_out && n_iters > 0) {
+    st = copy_out(p, err_out, p->err_hist + t0 * p->Np, sizeof(double) * n_iters * p->Np);
+    if (st != CPRA_OK) return st;
+  }
+  CK(cudaGetLastError(), "iterate");
+  return CPRA_OK;
+}
+
+cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->state_ready) return fail(p, CPRA_ERR_NOT_READY, "no iterate to assemble");
+  const size_t N = p->N, Np = p->Np, NN = N * N;
+  Assembly& a = p->asmb;
+  if (!a.F) {
+    a.F = (float2*)dev_alloc(p, Np * NN * 8);
+    a.vol = (float2*)dev_alloc(p, N * NN * 8);
+    a.cell_ptr = (int32_t*)dev_alloc(p, (NN + 1) * 4);
+    a.moments = (double*)dev_alloc(p, 3 * Np * 8);
+    if (!a.F || !a.vol || !a.cell_ptr || !a.moments)
+      return fail(p, CPRA_ERR_OUT_OF_MEMORY, "assembly allocation failed");
+  }
+  if (!a.ready) {
+    cpra_status st = build_gridding(p);
+    if (st != CPRA_OK) return st;
+  }
+  CK(timed(p, CPRA_KERNEL_ASSEMBLE, [&] { return launch_assemble(p); }), "assemble");
+  p->asmb.ready = true;
+  p->hp_valid = false;
+  if (out) return copy_out(p, out, a.vol, N * NN * 8);
+  return CPRA_OK;
+}
+
+cpra_status cpra_result(cpra_plan_t p, int32_t what, void* dst, size_t bytes) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!dst) return fail(p, CPRA_ERR_INVALID_ARG, "dst is NULL");
+  const size_t N = p->N, Np = p->Np, NN = N * N;
+  const bool dd = is_device_ptr(dst);
+  switch (what) {
+    case CPRA_RESULT_PO:
+    case CPRA_RESULT_SUPPORT: {
+      const size_t need = what == CPRA_RESULT_PO ? Np * NN * 4 : Np * NN;
+      if (bytes < need) return fail(p, CPRA_ERR_INVALID_ARG, "dst too small");
+      void* tgt = dst;
+      if (!dd) {
+        if (!p->po_tmp) p->po_tmp = (float*)dev_alloc(p, Np * NN * 4);
+        if (!p->po_tmp) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "result buffer");
+        tgt = p->po_tmp;
+      }
+      if (what == CPRA_RESULT_PO) CK(launch_export_po(p, (float*)tgt), "export po");
+      else CK(launch_export_support(p, (uint8_t*)tgt), "export support");
+      if (!dd) return copy_out(p, dst, tgt, need);
+      return CPRA_OK;
+    }
+    case CPRA_RESULT_STATE:
+      if (bytes < Np * NN * 4) return fail(p, CPRA_ERR_INVALID_ARG, "dst too small");
+      return copy_out(p, dst, p->g, Np * NN * 4);
+    case CPRA_RESULT_ERRORS: {
+      const size_t need = sizeof(double) * p->t * Np;
+      if (bytes < need) return fail(p, CPRA_ERR_INVALID_ARG, "dst too small");
+      if (need == 0) return CPRA_OK;
+      return copy_out(p, dst, p->err_hist, need);
+    }
+    case CPRA_RESULT_VOLUME:
+      if (!p->asmb.vol || !p->asmb.ready) return fail(p, CPRA_ERR_NOT_READY, "no volume yet");
+      if (bytes < N * NN * 8) return fail(p, CPRA_ERR_INVALID_ARG, "dst too small");
+      return copy_out(p, dst, p->asmb.vol, N * NN * 8);
+    default:
+      return fail(p, CPRA_ERR_INVALID_ARG, "unknown result");
+  }
+}
+
+int64_t cpra_iteration(cpra_plan_t p) { return p ? p->t : -1; }
+
+cpra_status cpra_reset(cpra_plan_t p) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  p->t = 0;
+  p->state_ready = false;
+  p->hp_valid = false;
+  return CPRA_OK;
+}
+
+cpra_status cpra_set_profiling(cpra_plan_t p, int32_t on) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  CK(drain_timings(p), "profiling drain");
+  for (int k = 0; k < CPRA_KERNEL_KINDS; ++k) {
+    p->kms[k] = 0.0;
+    p->kcount[k] = 0;
+  }
+  p->profiling = on != 0;
+  return CPRA_OK;
+}
+
+cpra_status cpra_kernel_stats(cpra_plan_t p, int32_t kind, double* total_ms, int64_t* launches) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (kind < 0 || kind >= CPRA_KERNEL_KINDS) return fail(p, CPRA_ERR_INVALID_ARG, "bad kernel kind");
+  CK(drain_timings(p), "profiling drain");
+  if (total_ms) *total_ms = p->kms[kind];
+  if (launches) *launches = p->kcount[kind];
+  return CPRA_OK;
+}
+
+int64_t cpra_launch_count(void) { return (int64_t)g_launches.load(); }
+
+cpra_status cpra_sync(cpra_plan_t p) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  CK(cudaStreamSynchronize(p->stream), "sync");
+  return CPRA_OK;
+}
+
+cpra_status cpra_destroy(cpra_plan_t p) {
+  if (!p) return CPRA_OK;
+  cudaStreamSynchronize(p->stream);
+  cudaGetLastError();
+  for (auto& ev : p->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+  for (auto& ev : p->spare) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+  std::vector<void*> own = p->owned;
+  for (void* q : own) {
+    if (p->cfg.free) p->cfg.free(q, p->cfg.alloc_ctx);
+    else if (!p->cfg.alloc) cudaFree(q);
+  }
+  delete p;
+  return CPRA_OK;
+}
+
+const char* cpra_last_error(cpra_plan_t p) {
+  return p ? p->err.c_str() : g_last_error.c_str();
+}
+
+}  // extern "C"

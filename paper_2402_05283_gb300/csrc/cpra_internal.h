@@ -1,0 +1,119 @@
+// cpra_internal.h - plan layout and kernel launchers shared by the .cu files.
+//
+// Device data of one plan (all stacks contiguous per angle):
+//   g, g_alt   [Np][N][N]    float   iterate (Jacobi double buffer for Eq. 4)
+//   Hp         [Np][N][N/2]  float2  row spectra of g, packed: column 0 holds
+//                                    (Re H(y,0), Re H(y,N/2)); the two-pass
+//                                    engine keeps it between its passes
+//   A_main     [Np][N][N/2]  float   Hermitian-symmetrised amplitude, kx < N/2
+//   A_nyq      [Np][N]       float   the same at kx = N/2
+//   Cn, sumA2  [Np]          double  antisymmetric-part energy, sum A^2
+//   S          [Np][N][W]    uint32  support bits, W = ceil(N/32) words a row
+//   err_acc    [Np]          double  per-iteration error accumulator
+//   err_hist   [cap][Np]     double  Fourier error history
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cpra.h"
+
+namespace cpra {
+
+struct Assembly {
+  float2* F = nullptr;        // [Np][N][N] z-transformed spectra, [n][ku][z]
+  float2* vol = nullptr;      // [N][N][N] grid, then the centred volume
+  int32_t* cell_ptr = nullptr;  // [N*N + 1] CSR rows (cells ky*N + kx)
+  int32_t* ent_idx = nullptr;   // sample index n*N + ku
+  double* ent_w = nullptr;      // normalised bilinear weight
+  double* moments = nullptr;    // [Np][3] sum rho, sum rho*z, sum rho*u
+  int64_t n_ent = 0;
+  bool ready = false;
+};
+
+}  // namespace cpra
+
+struct cpra_plan_s {
+  cpra_config cfg;
+  cudaStream_t stream = nullptr;
+  int N = 0, Np = 0, W = 0;
+  int64_t t = 0;
+  bool state_ready = false;
+  bool hp_valid = false;
+  int n_loaded = 0;
+  std::vector<uint8_t> loaded;
+  std::vector<double> theta;
+  int engine = CPRA_ENGINE_TWO_PASS;
+
+  float* g = nullptr;
+  float* g_alt = nullptr;
+  float2* Hp = nullptr;
+  float* A_main = nullptr;
+  float* A_nyq = nullptr;
+  double* Cn = nullptr;
+  double* sumA2 = nullptr;
+  double* err_acc = nullptr;
+  uint32_t* S = nullptr;
+  double* err_hist = nullptr;
+  int64_t err_cap = 0;
+  float2* tw = nullptr;        // forward twiddles exp(-2 pi i k/N)
+  float* stage = nullptr;      // staging for host inputs, Np*N*N floats
+  int* flag = nullptr;         // device status word
+  float* sw_tmp = nullptr;     // shrink-wrap scratch, Np*N*N floats
+  unsigned* sw_max = nullptr;  // per-angle max (float bits)
+  float* sw_taps = nullptr;    // periodic Gaussian taps
+  int sw_ntaps = 0;
+  float* po_tmp = nullptr;
+  cpra::Assembly asmb;
+
+  // device-time profiling of launches (cpra_set_profiling)
+  struct Timed { int kind; cudaEvent_t a, b; };
+  bool profiling = false;
+  std::vector<Timed> pending;
+  std::vector<Timed> spare;
+  double kms[CPRA_KERNEL_KINDS] = {0};
+  long long kcount[CPRA_KERNEL_KINDS] = {0};
+
+  std::string err;
+  std::vector<void*> owned;
+};
+
+namespace cpra {
+
+// kernels launched by this library in this process (cpra_launch_count)
+extern std::atomic<long long> g_launches;
+
+enum Algo { kHIO = 0, kER = 1 };
+
+// prepare / state kernels (k_prepare.cu)
+cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count);
+cudaError_t launch_support_box(cpra_plan_s* p);
+cudaError_t launch_support_u8(cpra_plan_s* p, const uint8_t* S, int per_angle);
+cudaError_t launch_init_guess(cpra_plan_s* p);
+cudaError_t launch_export_po(cpra_plan_s* p, float* out);
+cudaError_t launch_export_support(cpra_plan_s* p, uint8_t* out);
+
+// two-pass iteration (k_twopass.cu)
+struct CoupleArgs {
+  int n_taps;        // 1 = no coupling
+  float alpha[CPRA_MAX_TAPS];
+  int mirror;
+  int object;        // blend P_{S+} g instead of g
+  int store_g;       // write the coupled rows to g_dst
+};
+cudaError_t launch_prime(cpra_plan_s* p, int first, int count, const float* g_src, float* g_dst,
+                         float2* Hp, const CoupleArgs& ca);
+cudaError_t launch_colpass(cpra_plan_s* p, int first, int count);
+cudaError_t launch_rowpass(cpra_plan_s* p, int first, int count, int algo, int64_t err_slot,
+                           int forward);
+cudaError_t launch_shrinkwrap(cpra_plan_s* p);
+
+// assembly (k_assemble.cu)
+cudaError_t launch_assemble(cpra_plan_s* p);
+
+bool n_supported(int N);
+
+}  // namespace cpra

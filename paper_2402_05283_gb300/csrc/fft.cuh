@@ -1,0 +1,173 @@
+// fft.cuh - batched complex FFT building blocks in shared memory (sm_103a).
+//
+// Transforms are mixed-radix Stockham (self-sorting) passes over B
+// independent length-N lines that live in shared memory as
+// buf[i * PI + b] (element i of line b).  Each pass reads R elements per
+// butterfly into registers, applies twiddles, runs an R-point DFT and writes
+// back in place after a block barrier; the output order after the last pass
+// is natural, so no bit reversal is needed.  Threads take butterflies with
+// the line index b fastest, so a warp touches consecutive words.
+//
+// Twiddles come from a table tw[k] = exp(-2 pi i k / N), k = 0..N-1, computed
+// in FP64 on the host and rounded once to FP32.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace cpra {
+
+struct __align__(8) cf { float x, y; };
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (DIR = -1) or +i (DIR = +1)
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// R-point DFT in registers, y_k = sum_r x_r exp(DIR * 2 pi i r k / R).
+template <int R, int DIR> struct Dft;
+
+template <int DIR> struct Dft<2, DIR> {
+  static __device__ __forceinline__ void run(float2* v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <int DIR> struct Dft<4, DIR> {
+  static __device__ __forceinline__ void run(float2* v) {
+    float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    float2 s13 = cadd(v[1], v[3]), d13 = mul_i<DIR>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  }
+};
+
+template <int DIR> struct Dft<8, DIR> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float h = 0.70710678118654752440f;  // cos(pi/4)
+    // two 4-point DFTs on even and odd samples
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, DIR>::run(e);
+    Dft<4, DIR>::run(o);
+    // twiddles exp(DIR 2 pi i k / 8), k = 1, 2, 3
+    float2 o1 = make_float2(h * (o[1].x - DIR * o[1].y), h * (o[1].y + DIR * o[1].x));
+    float2 o2 = mul_i<DIR>(o[2]);
+    float2 o3 = make_float2(-h * (o[3].x + DIR * o[3].y), h * (DIR * o[3].x - o[3].y));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+};
+
+template <int DIR> struct Dft<3, DIR> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float c = -0.5f;                        // cos(2 pi / 3)
+    const float s = DIR * 0.86602540378443864676f;  // DIR * sin(2 pi / 3)
+    float2 a = v[0], b = v[1], d = v[2];
+    float2 t = cadd(b, d);
+    float2 u = csub(b, d);
+    float2 m = make_float2(a.x + c * t.x, a.y + c * t.y);
+    // i * s * u
+    float2 r = make_float2(-s * u.y, s * u.x);
+    v[0] = cadd(a, t);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+  }
+};
+
+__host__ __device__ constexpr int pick_radix(int rem) {
+  return (rem % 8 == 0) ? 8 : (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : 3;
+}
+
+__host__ __device__ constexpr bool fft_size_ok(int n) {
+  while (n % 2 == 0 && n > 1) n /= 2;
+  while (n % 3 == 0 && n > 1) n /= 3;
+  return n == 1;
+}
+
+// twiddle exp(DIR * 2 pi i k / N) from the forward table
+template <int DIR>
+__device__ __forceinline__ float2 twiddle(const float2* tw, int k) {
+  float2 w = tw[k];
+  return DIR < 0 ? w : make_float2(w.x, -w.y);
+}
+
+// One Stockham pass and the rest, recursively, for lines of length N.
+// NS = product of the radices already applied.  Caller's threads: NT.
+template <int N, int NS, int DIR, int B, int PI, int NT>
+__device__ __forceinline__ void stockham(float2* buf, const float2* tw) {
+  if constexpr (NS < N) {
+    constexpr int R = pick_radix(N / NS);
+    constexpr int NB = N / R;
+    constexpr int TASKS = B * NB;
+    constexpr int PER = (TASKS + NT - 1) / NT;
+    float2 v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int t = threadIdx.x + p * NT;
+      if (TASKS % NT == 0 || t < TASKS) {
+        const int b = t % B, j = t / B;
+        const int k = j % NS;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float2 x = buf[(j + r * NB) * PI + b];
+          if (NS > 1 && r > 0) x = cmul(x, twiddle<DIR>(tw, k * r * (N / (NS * R))));
+          v[p][r] = x;
+        }
+        Dft<R, DIR>::run(v[p]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int t = threadIdx.x + p * NT;
+      if (TASKS % NT == 0 || t < TASKS) {
+        const int b = t % B, j = t / B;
+        const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(base + r * NS) * PI + b] = v[p][r];
+      }
+    }
+    __syncthreads();
+    stockham<N, NS * R, DIR, B, PI, NT>(buf, tw);
+  }
+}
+
+// B lines of length N in buf[i * PI + b]; all NT threads of the block call it.
+// Entry and exit are block-synchronised.
+template <int N, int DIR, int B, int PI, int NT>
+__device__ __forceinline__ void fft_lines(float2* buf, const float2* tw) {
+  stockham<N, 1, DIR, B, PI, NT>(buf, tw);
+}
+
+// support bit x of the row whose first word is at S[row_off]
+__device__ __forceinline__ bool sbit(const uint32_t* S, size_t row_off, int x) {
+  return (S[row_off + (x >> 5)] >> (x & 31)) & 1u;
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t key) {
+  // first output of SplitMix64 (Steele, Lea, Flood 2014) seeded with key
+  uint64_t z = key + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace cpra

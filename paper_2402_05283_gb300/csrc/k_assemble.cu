@@ -1,0 +1,280 @@
+// k_assemble.cu - Step C mass-centre move and Step D assembly.
+//
+//   moments  FP64 sums of rho = P_{S+} g, rho*z, rho*u per angle
+//   spectra  E_n(kz, ku) = DFT2(rho_n) * exp(+2 pi i (kz c_z + ku c_u) / N)
+//            (signed k), then the inverse DFT along kz of every ku column:
+//            F[n][ku][z] (z stored fftshifted).  The R2C rows come from the
+//            row-pass kernel; this kernel does the columns.
+//   gather   V[z][ky][kx] = (-1)^(kx+ky) * sum_e w_e F[idx_e][z]; the cell
+//            lists (bilinear adjoint weights of every sample, normalised by
+//            their sum, FP64) are built on the host.  The sign makes the
+//            inverse transform land centred in x and y.
+//   c2c      inverse FFT along kx (rows) then ky (columns) of every z plane.
+// The inverse 3D DFT is applied as IDFT_z on each slice before gridding
+// (gridding acts on kx, ky only and its weights do not depend on kz), then
+// IDFT_xy on each z plane after gridding.
+#include "cpra_internal.h"
+#include "fft.cuh"
+#include "tiling.cuh"
+
+namespace cpra {
+
+__global__ void k_moments(const float* __restrict__ g, const uint32_t* __restrict__ S,
+                          double* moments, int N, int W) {
+  __shared__ double red[3][32];
+  const int y = blockIdx.x, n = blockIdx.y;
+  const size_t base = ((size_t)n * N + y) * N;
+  const size_t srow = ((size_t)n * N + y) * W;
+  double m0 = 0.0, mu = 0.0;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const float v = g[base + x];
+    const double r = (sbit(S, srow, x) && v >= 0.0f) ? (double)v : 0.0;
+    m0 += r;
+    mu += r * x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 += __shfl_down_sync(0xffffffffu, m0, o);
+    mu += __shfl_down_sync(0xffffffffu, mu, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { red[0][wid] = m0; red[1][wid] = mu; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += red[0][i]; c += red[1][i]; }
+    atomicAdd(moments + 3 * n + 0, a);
+    atomicAdd(moments + 3 * n + 1, a * y);
+    atomicAdd(moments + 3 * n + 2, c);
+  }
+}
+
+__device__ __forceinline__ float2 unit_phase(double turns) {
+  // exp(2 pi i * turns), argument reduced to [-1/2, 1/2) turns in FP64
+  const double r = turns - rint(turns);
+  double s, c;
+  sincospi(2.0 * r, &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+template <int N>
+struct SpecTile {
+  static constexpr int B = cmin(N >= 1024 ? 8 : 16, pow2_div(N / 2));
+  static constexpr int PI = B + 1;
+  static constexpr int NT = clampi(B * N / 32, 64, 1024);
+};
+
+template <int N>
+__global__ void __launch_bounds__(SpecTile<N>::NT)
+k_spectra(const float2* __restrict__ Hp, const double* __restrict__ moments, float2* F,
+          const float2* __restrict__ tw, int com_align) {
+  using T = SpecTile<N>;
+  constexpr int B = T::B, PI = T::PI, NT = T::NT, H = N / 2;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* G = tw_s + N;        // [ky][b], pitch B
+  float2* E = G + N * B;       // [kz][b], pitch PI
+  float2* rz = E + N * PI;     // exp(2 pi i kz c_z / N)
+  float2* ru = rz + N;         // [2B]: +ku then -ku ramps
+  const int n = blockIdx.y;
+  const int c0 = blockIdx.x * B;
+  for (int i = threadIdx.x; i < N; i += NT) tw_s[i] = tw[i];
+  const double m0 = moments[3 * n];
+  double cz = 0.5 * N, cu = 0.5 * N;
+  if (com_align && m0 > 0.0) {
+    cz = moments[3 * n + 1] / m0;
+    cu = moments[3 * n + 2] / m0;
+  }
+  for (int k = threadIdx.x; k < N; k += NT) {
+    const int ks = k < H ? k : k - N;
+    rz[k] = unit_phase((double)ks * cz / N);
+  }
+  for (int b = threadIdx.x; b < B; b += NT) {
+    const int c = c0 + b;
+    ru[b] = unit_phase((double)c * cu / N);
+    // the -ku partner of column 0 is the Nyquist column ku = -N/2
+    const int cm = (c == 0) ? -H : -c;
+    ru[B + b] = unit_phase((double)cm * cu / N);
+  }
+  const float2* Hn = Hp + (size_t)n * N * H;
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int y = idx / B, b = idx - y * B;
+    G[idx] = Hn[(size_t)y * H + c0 + b];
+  }
+  __syncthreads();
+  fft_lines<N, -1, B, B, NT>(G, tw_s);
+  const float inv = 1.0f / N;
+  float2* Fn = F + (size_t)n * N * N;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+      const int kz = idx / B, b = idx - kz * B;
+      const int c = c0 + b;
+      const int km = (N - kz) % N;
+      float2 v;
+      if (c == 0) {
+        const float2 z = G[kz * B], zm = G[km * B];
+        v = pass == 0 ? make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y))   // G(kz, 0)
+                      : make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));  // G(kz, N/2)
+      } else {
+        v = pass == 0 ? G[kz * B + b] : cconj(G[km * B + b]);  // G(kz, c) or G(kz, -c)
+      }
+      v = cmul(cmul(v, rz[kz]), ru[pass * B + b]);
+      E[kz * PI + b] = v;
+    }
+    __syncthreads();
+    fft_lines<N, +1, B, PI, NT>(E, tw_s);
+    for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+      const int b = idx / N, z = idx - b * N;
+      const int c = c0 + b;
+      const int ku = pass == 0 ? c : (c == 0 ? H : N - c);
+      Fn[(size_t)ku * N + ((z + H) % N)] = cscale(E[z * PI + b], inv);
+    }
+    __syncthreads();
+  }
+}
+
+// V[z][cell] for a chunk of 8 planes; one thread per cell.
+__global__ void k_gather(const float2* __restrict__ F, const int32_t* __restrict__ cell_ptr,
+                         const int32_t* __restrict__ ent_idx, const double* __restrict__ ent_w,
+                         float2* V, int N) {
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const int NN = N * N;
+  if (cell >= NN) return;
+  const int z0 = blockIdx.y * 8;
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
+  const int e0 = cell_ptr[cell], e1 = cell_ptr[cell + 1];
+  for (int e = e0; e < e1; ++e) {
+    const float w = (float)ent_w[e];
+    const float4* src = reinterpret_cast<const float4*>(F + (size_t)ent_idx[e] * N + z0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 f = __ldg(src + q);
+      acc[4 * q + 0] = fmaf(w, f.x, acc[4 * q + 0]);
+      acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
+      acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
+      acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
+    }
+  }
+  const int ky = cell / N, kx = cell - ky * N;
+  const float sg = ((kx + ky) & 1) ? -1.0f : 1.0f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    V[(size_t)(z0 + i) * NN + cell] = make_float2(sg * acc[2 * i], sg * acc[2 * i + 1]);
+}
+
+// inverse FFT along x of P lines (rows of the N^2 x N array), in place
+template <int N>
+__global__ void __launch_bounds__(RowTile<N>::NT) k_c2c_rows(float2* V, const float2* __restrict__ tw) {
+  using T = RowTile<N>;
+  constexpr int P = T::P, PI = T::PI, NT = T::NT;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* buf = smem + N;
+  for (int i = threadIdx.x; i < N; i += NT) tw_s[i] = tw[i];
+  float2* rows = V + (size_t)blockIdx.x * P * N;
+  for (int idx = threadIdx.x; idx < P * N; idx += NT) {
+    const int p = idx / N, x = idx - p * N;
+    buf[x * PI + p] = rows[idx];
+  }
+  __syncthreads();
+  fft_lines<N, +1, P, PI, NT>(buf, tw_s);
+  const float inv = 1.0f / N;
+  for (int idx = threadIdx.x; idx < P * N; idx += NT) {
+    const int p = idx / N, x = idx - p * N;
+    rows[idx] = cscale(buf[x * PI + p], inv);
+  }
+}
+
+// inverse FFT along y of B adjacent columns of one z plane, in place
+template <int N>
+__global__ void __launch_bounds__(ColTile<N>::NT) k_c2c_cols(float2* V, const float2* __restrict__ tw) {
+  using T = ColTile<N>;
+  constexpr int B = T::B, NT = T::NT;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* buf = smem + N;
+  for (int i = threadIdx.x; i < N; i += NT) tw_s[i] = tw[i];
+  float2* plane = V + (size_t)blockIdx.y * N * N;
+  const int c0 = blockIdx.x * B;
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int y = idx / B, b = idx - y * B;
+    buf[idx] = plane[(size_t)y * N + c0 + b];
+  }
+  __syncthreads();
+  fft_lines<N, +1, B, B, NT>(buf, tw_s);
+  const float inv = 1.0f / N;
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int y = idx / B, b = idx - y * B;
+    plane[(size_t)y * N + c0 + b] = cscale(buf[idx], inv);
+  }
+}
+
+template <int N>
+static cudaError_t assemble_n(cpra_plan_s* p) {
+  cudaStream_t st = p->stream;
+  Assembly& a = p->asmb;
+  const int Np = p->Np;
+  cudaError_t e;
+  // rho and its moments, then R2C rows of rho into Hp
+  e = cudaMemsetAsync(a.moments, 0, sizeof(double) * 3 * Np, st);
+  if (e != cudaSuccess) return e;
+  const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  g_launches += 5;  // moments, spectra, gather, rows, columns (+ prime)
+  k_moments<<<dim3(N, Np), threads, 0, st>>>(p->g, p->S, a.moments, N, p->W);
+  CoupleArgs ca{};
+  ca.n_taps = 1;
+  ca.alpha[0] = 1.0f;
+  ca.object = 1;
+  ca.store_g = 0;
+  e = launch_prime(p, 0, Np, p->g, nullptr, p->Hp, ca);
+  if (e != cudaSuccess) return e;
+  p->hp_valid = false;
+  {
+    using T = SpecTile<N>;
+    const size_t smem = sizeof(float2) * (N + N * T::B + N * T::PI + N + 2 * T::B);
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_spectra<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_spectra<N><<<dim3((N / 2) / T::B, Np), T::NT, smem, st>>>(p->Hp, a.moments, a.F, p->tw,
+                                                               p->cfg.com_align);
+  }
+  k_gather<<<dim3((N * N + 255) / 256, N / 8), 256, 0, st>>>(a.F, a.cell_ptr, a.ent_idx, a.ent_w,
+                                                            a.vol, N);
+  {
+    using T = RowTile<N>;
+    const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_c2c_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_c2c_rows<N><<<(unsigned)((size_t)N * N / T::P), T::NT, smem, st>>>(a.vol, p->tw);
+  }
+  {
+    using T = ColTile<N>;
+    const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_c2c_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_c2c_cols<N><<<dim3(N / T::B, N), T::NT, smem, st>>>(a.vol, p->tw);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(cpra_plan_s* p) {
+#define CPRA_CASE(NN) \
+  case NN: return assemble_n<NN>(p);
+  switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+#undef CPRA_CASE
+}
+
+}  // namespace cpra

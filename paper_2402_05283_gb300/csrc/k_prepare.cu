@@ -1,0 +1,161 @@
+// k_prepare.cu - input preparation (Eq. 1-3), support, seeded start, exports.
+#include "cpra_internal.h"
+#include "fft.cuh"
+
+namespace cpra {
+
+std::atomic<long long> g_launches{0};
+
+// One block per (FFT-order row ky, angle).  A(k) = sqrt(I) at the centred
+// index of k; A_sym(k) = (A(k) + A(-k)) / 2 on the half plane kx <= N/2;
+// the full-plane sums of ((A(k) - A(-k))/2)^2 and A(k)^2 go to Cn and sumA2.
+__global__ void k_prepare(const float* __restrict__ I, int N, int first, float* A_main,
+                          float* A_nyq, double* Cn, double* sumA2, int* flag) {
+  const int ky = blockIdx.x;
+  const int n = first + blockIdx.y;
+  const int h = N / 2;
+  const float* In = I + (size_t)blockIdx.y * N * N;
+  const int ry = (ky + h) % N;           // centred row of +ky
+  const int my = (N - ky + h) % N;       // centred row of -ky
+  double c_part = 0.0, a_part = 0.0;
+  int bad = 0;
+  for (int kx = threadIdx.x; kx < N; kx += blockDim.x) {
+    const int rx = (kx + h) % N;
+    const int mx = (N - kx + h) % N;
+    float ip = In[(size_t)ry * N + rx];
+    float im = In[(size_t)my * N + mx];
+    if (!(ip >= 0.0f) || !isfinite(ip)) bad = 1;
+    float ap = sqrtf(fmaxf(ip, 0.0f));
+    float am = sqrtf(fmaxf(im, 0.0f));
+    double d = 0.5 * ((double)ap - (double)am);
+    c_part += d * d;
+    a_part += (double)ap * (double)ap;
+    float as = 0.5f * (ap + am);
+    if (kx < h) A_main[((size_t)n * N + ky) * h + kx] = as;
+    if (kx == h) A_nyq[(size_t)n * N + ky] = as;
+  }
+  if (bad) atomicExch(flag, 1);
+  // block reduction in FP64
+  __shared__ double sc[32], sa[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    c_part += __shfl_down_sync(0xffffffffu, c_part, o);
+    a_part += __shfl_down_sync(0xffffffffu, a_part, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sc[wid] = c_part; sa[wid] = a_part; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    c_part = lane < nw ? sc[lane] : 0.0;
+    a_part = lane < nw ? sa[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      c_part += __shfl_down_sync(0xffffffffu, c_part, o);
+      a_part += __shfl_down_sync(0xffffffffu, a_part, o);
+    }
+    if (lane == 0) {
+      atomicAdd(Cn + n, c_part);
+      atomicAdd(sumA2 + n, a_part);
+    }
+  }
+}
+
+cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count) {
+  cudaError_t e = cudaMemsetAsync(p->Cn + first, 0, sizeof(double) * count, p->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(p->sumA2 + first, 0, sizeof(double) * count, p->stream);
+  if (e != cudaSuccess) return e;
+  dim3 grid(p->N, count);
+  int threads = p->N >= 256 ? 256 : ((p->N + 31) / 32) * 32;
+  g_launches += 1;
+  k_prepare<<<grid, threads, 0, p->stream>>>(I, p->N, first, p->A_main, p->A_nyq, p->Cn,
+                                             p->sumA2, p->flag);
+  return cudaGetLastError();
+}
+
+// Support bits from the padded bounding box [N/4, 3N/4)^2 (or from bytes).
+__global__ void k_support(uint32_t* S, int N, int W, const uint8_t* src, int per_angle) {
+  const int y = blockIdx.x, n = blockIdx.y;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int x = w * 32 + b;
+      if (x >= N) break;
+      bool in;
+      if (src) {
+        const size_t off = (per_angle ? (size_t)n * N * N : 0) + (size_t)y * N + x;
+        in = src[off] != 0;
+      } else {
+        in = (y >= N / 4) && (y < N / 4 + N / 2) && (x >= N / 4) && (x < N / 4 + N / 2);
+      }
+      if (in) bits |= 1u << b;
+    }
+    S[((size_t)n * N + y) * W + w] = bits;
+  }
+}
+
+cudaError_t launch_support_box(cpra_plan_s* p) {
+  g_launches += 1;
+  k_support<<<dim3(p->N, p->Np), 32, 0, p->stream>>>(p->S, p->N, p->W, nullptr, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_support_u8(cpra_plan_s* p, const uint8_t* S, int per_angle) {
+  g_launches += 1;
+  k_support<<<dim3(p->N, p->Np), 32, 0, p->stream>>>(p->S, p->N, p->W, S, per_angle);
+  return cudaGetLastError();
+}
+
+// Seeded start g0 = u * [x in S], u = (splitmix64(key) >> 40) * 2^-24,
+// key = ((seed * Np + n) * N + y) * N + x (mod 2^64).
+__global__ void k_init_guess(float* g, const uint32_t* S, int N, int Np, int W,
+                             unsigned long long seed) {
+  const int y = blockIdx.x, n = blockIdx.y;
+  const size_t srow = ((size_t)n * N + y) * W;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const uint64_t key = ((seed * (uint64_t)Np + (uint64_t)n) * (uint64_t)N + (uint64_t)y) *
+                             (uint64_t)N + (uint64_t)x;
+    const float u = (float)(splitmix64(key) >> 40) * (1.0f / 16777216.0f);
+    g[((size_t)n * N + y) * N + x] = sbit(S, srow, x) ? u : 0.0f;
+  }
+}
+
+cudaError_t launch_init_guess(cpra_plan_s* p) {
+  int threads = p->N >= 256 ? 256 : p->N;
+  g_launches += 1;
+  k_init_guess<<<dim3(p->N, p->Np), threads, 0, p->stream>>>(p->g, p->S, p->N, p->Np, p->W,
+                                                             (unsigned long long)p->cfg.seed);
+  return cudaGetLastError();
+}
+
+__global__ void k_export_po(const float* g, const uint32_t* S, float* out, int N, int W) {
+  const int y = blockIdx.x, n = blockIdx.y;
+  const size_t srow = ((size_t)n * N + y) * W;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const size_t i = ((size_t)n * N + y) * N + x;
+    const float v = g[i];
+    out[i] = (sbit(S, srow, x) && v >= 0.0f) ? v : 0.0f;
+  }
+}
+
+cudaError_t launch_export_po(cpra_plan_s* p, float* out) {
+  int threads = p->N >= 256 ? 256 : p->N;
+  g_launches += 1;
+  k_export_po<<<dim3(p->N, p->Np), threads, 0, p->stream>>>(p->g, p->S, out, p->N, p->W);
+  return cudaGetLastError();
+}
+
+__global__ void k_export_support(const uint32_t* S, uint8_t* out, int N, int W) {
+  const int y = blockIdx.x, n = blockIdx.y;
+  const size_t srow = ((size_t)n * N + y) * W;
+  for (int x = threadIdx.x; x < N; x += blockDim.x)
+    out[((size_t)n * N + y) * N + x] = sbit(S, srow, x) ? 1 : 0;
+}
+
+cudaError_t launch_export_support(cpra_plan_s* p, uint8_t* out) {
+  int threads = p->N >= 256 ? 256 : p->N;
+  g_launches += 1;
+  k_export_support<<<dim3(p->N, p->Np), threads, 0, p->stream>>>(p->S, out, p->N, p->W);
+  return cudaGetLastError();
+}
+
+}  // namespace cpra

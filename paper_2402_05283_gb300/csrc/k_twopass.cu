@@ -1,0 +1,319 @@
+// k_twopass.cu - the two-pass HBM iteration for any supported N.
+//
+// One conventional 2D iteration (Step B inner loop) of every angle:
+//   column pass  Hp -> FFT_y -> modulus projection onto A_sym + Fourier error
+//                -> IFFT_y -> Hp                                   (k_colpass)
+//   row pass     Hp -> C2R rows -> HIO/ER support+positivity update of g
+//                -> R2C rows of the new g -> Hp                    (k_rowpass)
+// Two real rows travel as one complex line (z = row0 + i row1); the half
+// spectrum is packed so every array has N x N/2 complex entries (column 0
+// carries the real kx = 0 and kx = N/2 values).  k_prime makes Hp from g and
+// applies the carousel coupling of Eq. 4 at episode starts.
+#include "cpra_internal.h"
+#include "fft.cuh"
+#include "tiling.cuh"
+
+namespace cpra {
+
+// ---------------------------------------------------------------- helpers
+// Unpack the R2C result of a row pair from the complex line Z in smem and
+// store the packed half spectra of both rows.
+template <int N, int P, int PI, int NT>
+__device__ __forceinline__ void store_row_pair_spectra(const float2* buf, float2* Hp_rows) {
+  constexpr int H = N / 2;
+  for (int idx = threadIdx.x; idx < P * H; idx += NT) {
+    const int p = idx / H, k = idx - p * H;
+    float2 h0, h1;
+    if (k == 0) {
+      const float2 z0 = buf[p], zn = buf[H * PI + p];
+      h0 = make_float2(z0.x, zn.x);
+      h1 = make_float2(z0.y, zn.y);
+    } else {
+      const float2 z = buf[k * PI + p], zm = buf[(N - k) * PI + p];
+      h0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      h1 = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+    Hp_rows[(size_t)(2 * p) * H + k] = h0;
+    Hp_rows[(size_t)(2 * p + 1) * H + k] = h1;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_twiddles(float2* tw_s, const float2* tw) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw_s[i] = tw[i];
+}
+
+// ---------------------------------------------------------------- prime
+// Rows y0..y0+2P of angle n: v = sum_k alpha_k src[(n+k) mod Np] (optionally
+// P_{S+} of it, optionally u-mirrored across the seam), stored to g_dst when
+// asked, then R2C of each row pair into Hp.
+template <int N>
+__global__ void __launch_bounds__(RowTile<N>::NT)
+k_prime(const float* __restrict__ g_src, float* g_dst, float2* Hp, const uint32_t* __restrict__ S,
+        const float2* __restrict__ tw, int Np, int first, int W, CoupleArgs ca) {
+  using T = RowTile<N>;
+  constexpr int P = T::P, PI = T::PI, NT = T::NT;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* buf = smem + N;
+  const int n = first + blockIdx.y;
+  const int y0 = blockIdx.x * 2 * P;
+  load_twiddles<N>(tw_s, tw);
+  const int r = ca.n_taps / 2;
+  for (int idx = threadIdx.x; idx < P * N; idx += NT) {
+    const int p = idx / N, x = idx - p * N;
+    float v[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int y = y0 + 2 * p + s;
+      float acc = 0.0f;
+      for (int k = -r; k <= r; ++k) {
+        const int j = n + k;
+        const int jm = ((j % Np) + Np) % Np;
+        const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
+        const bool mir = ca.mirror && (wraps & 1);
+        const int xs = mir ? (N - x) % N : x;
+        float val = g_src[((size_t)jm * N + y) * N + xs];
+        if (ca.object) {
+          const bool in = sbit(S, ((size_t)jm * N + y) * W, xs);
+          val = (in && val >= 0.0f) ? val : 0.0f;
+        }
+        acc = (ca.n_taps == 1) ? val : fmaf(ca.alpha[k + r], val, acc);
+      }
+      v[s] = acc;
+      if (ca.store_g) g_dst[((size_t)n * N + y) * N + x] = acc;
+    }
+    buf[x * PI + p] = make_float2(v[0], v[1]);
+  }
+  __syncthreads();
+  fft_lines<N, -1, P, PI, NT>(buf, tw_s);
+  store_row_pair_spectra<N, P, PI, NT>(buf, Hp + ((size_t)n * N + y0) * (N / 2));
+}
+
+// ---------------------------------------------------------------- column pass
+__device__ __forceinline__ float2 project(float2 G, float a, double& err, double w) {
+  const float m = sqrtf(G.x * G.x + G.y * G.y);
+  const double d = (double)m - (double)a;
+  err += w * d * d;
+  if (m > 0.0f) {
+    const float s = a / m;
+    return make_float2(G.x * s, G.y * s);
+  }
+  return make_float2(a, 0.0f);
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
+template <int N>
+__global__ void __launch_bounds__(ColTile<N>::NT)
+k_colpass(float2* Hp, const float* __restrict__ A_main, const float* __restrict__ A_nyq,
+          double* err_acc, const float2* __restrict__ tw, int first) {
+  using T = ColTile<N>;
+  constexpr int B = T::B, NT = T::NT, H = N / 2;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* buf = smem + N;
+  __shared__ double red[32];
+  const int n = first + blockIdx.y;
+  const int c0 = blockIdx.x * B;
+  float2* Hn = Hp + (size_t)n * N * H;
+  load_twiddles<N>(tw_s, tw);
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int y = idx / B, b = idx - y * B;
+    buf[idx] = Hn[(size_t)y * H + c0 + b];
+  }
+  __syncthreads();
+  fft_lines<N, -1, B, B, NT>(buf, tw_s);
+  double err = 0.0;
+  const float* An = A_main + (size_t)n * N * H;
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int ky = idx / B, b = idx - ky * B;
+    const int c = c0 + b;
+    if (c == 0) continue;
+    buf[idx] = project(buf[idx], An[(size_t)ky * H + c], err, 2.0);
+  }
+  if (c0 == 0) {
+    // packed column: Z = G(.,0) + i G(.,N/2), both Hermitian along ky
+    for (int ky = threadIdx.x; ky <= H; ky += NT) {
+      const int km = (N - ky) % N;
+      const float2 z = buf[ky * B], zm = buf[km * B];
+      const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+      const double w = (ky == 0 || ky == H) ? 1.0 : 2.0;
+      const float2 p0 = project(g0, An[(size_t)ky * H], err, w);
+      const float2 pn = project(gn, A_nyq[(size_t)n * N + ky], err, w);
+      buf[ky * B] = make_float2(p0.x - pn.y, p0.y + pn.x);
+      if (km != ky) buf[km * B] = make_float2(p0.x + pn.y, pn.x - p0.y);
+    }
+  }
+  __syncthreads();
+  fft_lines<N, +1, B, B, NT>(buf, tw_s);
+  const float inv = 1.0f / N;
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int y = idx / B, b = idx - y * B;
+    Hn[(size_t)y * H + c0 + b] = cscale(buf[idx], inv);
+  }
+  const double s = block_sum<NT>(err, red);
+  if (threadIdx.x == 0) atomicAdd(err_acc + n, s);
+}
+
+// ---------------------------------------------------------------- row pass
+template <int N>
+__global__ void __launch_bounds__(RowTile<N>::NT)
+k_rowpass(float* g, float2* Hp, const uint32_t* __restrict__ S, double* err_acc,
+          const double* __restrict__ Cn, const double* __restrict__ sumA2, double* err_hist,
+          long long err_slot, const float2* __restrict__ tw, int Np, int first, int W, float beta,
+          int algo, int forward) {
+  using T = RowTile<N>;
+  constexpr int P = T::P, PI = T::PI, NT = T::NT, H = N / 2;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* buf = smem + N;
+  const int n = first + blockIdx.y;
+  const int y0 = blockIdx.x * 2 * P;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // the column pass of this iteration is complete: publish E_F, reset
+    if (err_slot >= 0) {
+      const double den = sumA2[n];
+      err_hist[(size_t)err_slot * Np + n] = den > 0.0 ? sqrt((err_acc[n] + Cn[n]) / den) : 0.0;
+    }
+    err_acc[n] = 0.0;
+  }
+  load_twiddles<N>(tw_s, tw);
+  float2* Hrows = Hp + ((size_t)n * N + y0) * H;
+  for (int idx = threadIdx.x; idx < P * H; idx += NT) {
+    const int p = idx / H, k = idx - p * H;
+    const float2 h0 = Hrows[(size_t)(2 * p) * H + k];
+    const float2 h1 = Hrows[(size_t)(2 * p + 1) * H + k];
+    if (k == 0) {
+      buf[p] = make_float2(h0.x, h1.x);
+      buf[H * PI + p] = make_float2(h0.y, h1.y);
+    } else {
+      buf[k * PI + p] = make_float2(h0.x - h1.y, h0.y + h1.x);
+      buf[(N - k) * PI + p] = make_float2(h0.x + h1.y, h1.x - h0.y);
+    }
+  }
+  __syncthreads();
+  fft_lines<N, +1, P, PI, NT>(buf, tw_s);
+  const float inv = 1.0f / N;
+  for (int idx = threadIdx.x; idx < P * N; idx += NT) {
+    const int p = idx / N, x = idx - p * N;
+    const float2 z = buf[x * PI + p];
+    float out[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int y = y0 + 2 * p + s;
+      const size_t gi = ((size_t)n * N + y) * N + x;
+      const float gp = (s ? z.y : z.x) * inv;
+      const bool valid = sbit(S, ((size_t)n * N + y) * W, x) && gp >= 0.0f;
+      const float gold = g[gi];
+      const float gn = valid ? gp : (algo == kHIO ? fmaf(-beta, gp, gold) : 0.0f);
+      g[gi] = gn;
+      out[s] = gn;
+    }
+    buf[x * PI + p] = make_float2(out[0], out[1]);
+  }
+  if (!forward) return;
+  __syncthreads();
+  fft_lines<N, -1, P, PI, NT>(buf, tw_s);
+  store_row_pair_spectra<N, P, PI, NT>(buf, Hrows);
+}
+
+// ---------------------------------------------------------------- launchers
+template <int N>
+static cudaError_t prime_n(cpra_plan_s* p, int first, int count, const float* src, float* dst,
+                           float2* Hp, const CoupleArgs& ca) {
+  using T = RowTile<N>;
+  const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_prime<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(N / (2 * T::P), count);
+  g_launches += 1;
+  k_prime<N><<<grid, T::NT, smem, p->stream>>>(src, dst, Hp, p->S, p->tw, p->Np, first, p->W, ca);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t colpass_n(cpra_plan_s* p, int first, int count) {
+  using T = ColTile<N>;
+  const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_colpass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((N / 2) / T::B, count);
+  g_launches += 1;
+  k_colpass<N><<<grid, T::NT, smem, p->stream>>>(p->Hp, p->A_main, p->A_nyq, p->err_acc, p->tw,
+                                                 first);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t rowpass_n(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
+                             int forward) {
+  using T = RowTile<N>;
+  const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_rowpass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(N / (2 * T::P), count);
+  g_launches += 1;
+  k_rowpass<N><<<grid, T::NT, smem, p->stream>>>(p->g, p->Hp, p->S, p->err_acc, p->Cn, p->sumA2,
+                                                 p->err_hist, (long long)slot, p->tw, p->Np, first,
+                                                 p->W, p->cfg.beta, algo, forward);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prime(cpra_plan_s* p, int first, int count, const float* src, float* dst,
+                         float2* Hp, const CoupleArgs& ca) {
+#define CPRA_CASE(NN) \
+  case NN: return prime_n<NN>(p, first, count, src, dst, Hp, ca);
+  switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+#undef CPRA_CASE
+}
+
+cudaError_t launch_colpass(cpra_plan_s* p, int first, int count) {
+#define CPRA_CASE(NN) \
+  case NN: return colpass_n<NN>(p, first, count);
+  switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+#undef CPRA_CASE
+}
+
+cudaError_t launch_rowpass(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
+                           int forward) {
+#define CPRA_CASE(NN) \
+  case NN: return rowpass_n<NN>(p, first, count, algo, slot, forward);
+  switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+#undef CPRA_CASE
+}
+
+bool n_supported(int N) {
+#define CPRA_CASE(NN) \
+  case NN: return true;
+  switch (N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return false; }
+#undef CPRA_CASE
+}
+
+}  // namespace cpra

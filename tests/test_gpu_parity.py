@@ -1,0 +1,387 @@
+"""GPU vs FP64 oracle parity, through the C ABI.
+
+Tolerance (TOL = 1e-4): the iterate of every angle within 1e-4 relative L2 of
+the oracle, the per-iteration Fourier errors within 1e-4 relative, the
+assembled volume within 1e-4 relative L2.
+
+How far trajectories can be compared is set by the method, not the kernels:
+HIO is designed to be unstable.  On the cfg 1 workload the FP64 oracle's own
+response to a 1e-7 relative perturbation of its start exceeds 1e-4 by
+iteration 9 and 10 % by iteration 18, and the HIO sign test (g' >= 0 inside
+the support) meets pixels within 1e-6 of zero every few iterations; a flip
+there moves the pixel by |g| (HIO jumps between g' and g - beta g').
+So the suite checks
+  * the 1e-4-per-iterate bar over all 50 first iterations of every angle on
+    the cfg 1 workload with the ER update (continuous in the sign test) on the
+    support of the true projections, with carousel coupling;
+  * every kind of HIO step (HIO, ER, coupling, the HIO -> ER switch) one step
+    at a time from states the oracle produced along the full cfg 1 schedule;
+    an angle may differ only at pixels whose sign test the oracle decided
+    within 1e-5 (relative) of zero, and must match to 1e-4 elsewhere;
+  * the final cfg 1 reconstructions of both sides agree in Fourier error and
+    in real-space error against the phantom projections (stated bounds).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+KNIFE = 1e-5  # |g'| / max|g'| below which FP32 and FP64 may take the sign test differently
+
+
+@pytest.fixture(scope="module")
+def cp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_05283_gb300 as pkg
+    return pkg
+
+
+def _rel(a, b):
+    a = a.reshape(a.shape[0], -1).astype(np.float64)
+    b = b.reshape(b.shape[0], -1).astype(np.float64)
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+
+
+def _ocfg(cfg):
+    return O.OracleConfig(
+        N=cfg.N, Np=cfg.Np, n_ei=cfg.n_ei, alpha=tuple(cfg.alpha[:cfg.n_taps]),
+        beta=float(np.float32(cfg.beta)), wrap=cfg.wrap_mode, blend=cfg.blend_target,
+        hio_iters=cfg.hio_iters, er_iters=cfg.er_iters, shrinkwrap_every=cfg.shrinkwrap_every,
+        sw_sigma=float(np.float32(cfg.sw_sigma)), sw_tau=float(np.float32(cfg.sw_tau)),
+        n_pre=cfg.n_pre, com_align=bool(cfg.com_align), seed=cfg.seed)
+
+
+def _plan(cp, cfg, d, S):
+    plan = cp.Plan(cfg)
+    plan.load_intensities(d["I"], 0, d["thetas"])
+    plan.load_support(S)
+    return plan
+
+
+def _check_traj(cp, d, cfg, iters, S):
+    """Run GPU and oracle side by side from the seeded start; every iterate."""
+    plan = _plan(cp, cfg, d, S)
+    run = O.OracleRun.start(_ocfg(cfg), d["I"], S)
+    worst = 0.0
+    errs = []
+    for i in range(iters):
+        errs.append(plan.iterate(1, errors=True)[0])
+        run.step()
+        r = _rel(plan.result(cp.RESULT_STATE), run.g).max()
+        worst = max(worst, r)
+        assert r < TOL, f"iteration {i + 1}: rel-L2 {r:.3e}"
+    e_ref = np.array(run.errors)
+    erel = np.abs(np.array(errs) - e_ref) / np.maximum(e_ref, 1e-300)
+    assert erel.max() < TOL, f"error history rel {erel.max():.3e}"
+    plan.close()
+    return worst, run
+
+
+def _one_step(cp, d, cfg, S, g, t):
+    """GPU: load the oracle state g at iteration t and run one iteration; the
+    oracle runs the same iteration from g.  An angle passes when it is within
+    TOL, or when it is within TOL after removing the pixels whose sign test
+    the oracle decided within KNIFE of zero (a legitimate FP32/FP64 flip moves
+    only those pixels in one step).  Returns (per-angle rel-L2, error rel,
+    number of angles that needed the knife-edge allowance)."""
+    plan = _plan(cp, cfg, d, S)
+    plan.load_state(g.astype(np.float32), t)
+    e = plan.iterate(1, errors=True)[0]
+    out = plan.result(cp.RESULT_STATE).astype(np.float64)
+    plan.close()
+    oc = _ocfg(cfg)
+    run = O.OracleRun.start(oc, d["I"], S, g0=g)
+    gin = O.couple(g, oc.alpha, oc.wrap, oc.blend, run.S) if t % oc.n_ei == 0 else g
+    algo = O.HIO if t < oc.hio_iters else O.ER
+    ref, num, den, gp = O.iterate_2d(gin, run.A, run.S, oc.beta, algo, return_gp=True)
+    rel = _rel(out, ref)
+    mx = np.abs(gp).reshape(gp.shape[0], -1).max(1)[:, None, None]
+    knife = run.S & (np.abs(gp) < KNIFE * mx)
+    rel_k = _rel(np.where(knife, 0, out), np.where(knife, 0, ref))
+    ok = (rel < TOL) | (rel_k < TOL)
+    erel = np.abs(e - np.sqrt(num / den)) / np.sqrt(num / den)
+    assert np.all(ok), f"t={t}: rel-L2 {rel.max():.3e} (knife-edge removed {rel_k.max():.3e})"
+    return rel, erel, int((rel >= TOL).sum())
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    d = synth.make_case("cfg1")
+    d["true_support"] = (d["proj"].numpy() > 1e-9).astype(np.uint8)
+    return d
+
+
+def test_cfg1_er_all_50_iterates(cp, cfg1):
+    """The 1e-4 bar on every one of the first 50 iterates of all 32 angles."""
+    cfg = cp.make_config(64, 32, seed=1, hio_iters=0, er_iters=50, n_ei=10)
+    worst, _ = _check_traj(cp, cfg1, cfg, 50, cfg1["true_support"])
+    print(f"cfg1 ER 50 iterations: worst rel-L2 {worst:.2e}")
+
+
+def test_cfg1_er_variants(cp, cfg1):
+    cfg = cp.make_config(64, 32, seed=2, hio_iters=0, er_iters=20, n_ei=4,
+                         alpha=(0.1, 0.2, 0.4, 0.2, 0.1), wrap_mode=cp.WRAP_MIRROR,
+                         blend_target=cp.BLEND_OBJECT)
+    _check_traj(cp, cfg1, cfg, 20, cfg1["true_support"])
+
+
+def test_cfg1_hio_steps_along_schedule(cp, cfg1):
+    """One GPU iteration from oracle states along the full 220-iteration schedule."""
+    cfg = cp.make_config(64, 32, seed=1)  # 200 HIO + 20 ER, coupling every 10
+    ocfg = _ocfg(cfg)
+    run = O.OracleRun.start(ocfg, cfg1["I"], cfg1["support"])
+    checkpoints = {0, 1, 9, 10, 11, 57, 120, 199, 200, 210, 219}
+    states = {}
+    for t in range(220):
+        if t in checkpoints:
+            states[t] = run.g.copy()
+        run.step()
+    flips = 0
+    for t in sorted(states):
+        rel, erel, nflip = _one_step(cp, cfg1, cfg, cfg1["support"], states[t], t)
+        flips += nflip
+        assert erel.max() < TOL, f"t={t}: error rel {erel.max():.3e}"
+    print(f"{flips} of {len(states) * 32} angle-steps differed only at knife-edge pixels")
+
+
+def test_cfg1_final_reconstruction_quality(cp, cfg1):
+    """Full cfg 1 schedule on both sides: final quality agrees (bounds stated)."""
+    cfg = cp.make_config(64, 32, seed=1)
+    plan = _plan(cp, cfg, cfg1, cfg1["support"])
+    e_gpu = plan.iterate(220, errors=True)[-1]
+    po_gpu = plan.result(cp.RESULT_PO)
+    plan.close()
+    run = O.OracleRun.start(_ocfg(cfg), cfg1["I"], cfg1["support"]).run(220)
+    e_ref = run.errors[-1]
+    P = cfg1["proj"].numpy()
+    rs_gpu = np.mean([O.real_space_error(po_gpu[n], P[n]) for n in range(32)])
+    rs_ref = np.mean([O.real_space_error(run.po()[n], P[n]) for n in range(32)])
+    # final Fourier error within 25 % and mean real-space error within 0.05
+    assert abs(e_gpu.mean() - e_ref.mean()) <= 0.25 * e_ref.mean(), (e_gpu.mean(), e_ref.mean())
+    assert abs(rs_gpu - rs_ref) <= 0.05, (rs_gpu, rs_ref)
+    r_gpu = O.r_factor(po_gpu.astype(np.float64), run.A).mean()
+    r_ref = O.r_factor(run.po(), run.A).mean()
+    assert abs(r_gpu - r_ref) <= 0.25 * r_ref, (r_gpu, r_ref)
+
+
+@pytest.mark.parametrize("N,Np", [(16, 3), (32, 5), (48, 4), (64, 3), (96, 3), (128, 2),
+                                  (192, 2), (256, 2), (384, 2), (512, 2), (768, 1), (1024, 1)])
+def test_sizes_and_radices(cp, N, Np):
+    """Every supported radix chain and tile shape: HIO step with coupling, then ER."""
+    d = synth.make_case("tiny", N=N, Np=Np)
+    S = d["support"]
+    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=1, er_iters=5)
+    g0 = O.initial_guess(7, Np, N, np.broadcast_to(S.astype(bool), (Np, N, N)))
+    rel, erel, _ = _one_step(cp, d, cfg, S, g0, 0)
+    assert erel.max() < TOL, erel
+    # ER steps 1..5 from the seeded start (continuous, so compare the trajectory)
+    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=0, er_iters=6)
+    _check_traj(cp, d, cfg, 6, S)
+
+
+def test_single_angle_and_wide_taps(cp):
+    d = synth.make_case("tiny", N=32, Np=1)
+    cfg = cp.make_config(32, 1, n_ei=2, seed=5, alpha=(0.25, 0.5, 0.25), hio_iters=0, er_iters=6)
+    _check_traj(cp, d, cfg, 6, d["support"])
+    d = synth.make_case("tiny", N=32, Np=2)
+    cfg = cp.make_config(32, 2, n_ei=2, seed=5, alpha=(0.1, 0.15, 0.5, 0.15, 0.1),
+                         wrap_mode=cp.WRAP_MIRROR, hio_iters=0, er_iters=6)
+    _check_traj(cp, d, cfg, 6, d["support"])
+
+
+def test_pre_reconstruction(cp):
+    """Step A: n_pre HIO iterations on angle 0 before the episodes."""
+    d = synth.make_case("tiny", N=32, Np=4)
+    cfg = cp.make_config(32, 4, n_pre=3, n_ei=3, seed=6, hio_iters=0, er_iters=4)
+    _check_traj(cp, d, cfg, 4, d["support"])
+
+
+def test_shrinkwrap(cp):
+    d = synth.make_case("tiny", N=64, Np=4)
+    S = d["support"]
+    cfg = cp.make_config(64, 4, n_ei=5, shrinkwrap_every=5, seed=7, hio_iters=0, er_iters=10)
+    plan = _plan(cp, cfg, d, S)
+    run = O.OracleRun.start(_ocfg(cfg), d["I"], S)
+    for k in range(2):
+        plan.iterate(5)
+        run.run(4)
+        S_before = run.S.copy()
+        run.step()  # iteration whose end runs the shrink-wrap
+        sup = plan.result(cp.RESULT_SUPPORT).astype(bool)
+        # pixels whose blurred value sits within 1e-5 (relative) of the threshold
+        b = O.blur(O.object_estimate(run.g, S_before), 2.0)
+        mx = b.reshape(4, -1).max(1)[:, None, None]
+        edge = np.abs(b - 0.1 * mx) <= 1e-5 * mx
+        diff = sup != run.S
+        assert not np.any(diff & ~edge), f"{int((diff & ~edge).sum())} support pixels differ"
+        assert _rel(plan.result(cp.RESULT_STATE), run.g).max() < TOL
+    assert run.S.sum() < run.S.size  # the support did shrink
+    plan.close()
+
+
+def test_assembly_matches_oracle(cp):
+    d = synth.make_case("tiny", N=32, Np=8)
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal((8, 32, 32)).astype(np.float32)
+    S = np.broadcast_to(d["support"].astype(bool), (8, 32, 32))
+    for com, th in ((1, d["thetas"]), (0, np.sort(rng.uniform(0, math.pi, 8)))):
+        cfg = cp.make_config(32, 8, com_align=com)
+        plan = cp.Plan(cfg)
+        plan.load_intensities(d["I"], 0, th)
+        plan.load_support(d["support"])
+        plan.load_state(g, 0)
+        vol = np.empty((32, 32, 32), np.complex64)
+        plan.assemble_3d(vol)
+        ref = O.assemble(g.astype(np.float64), S, th, com_align=bool(com))
+        rel = np.linalg.norm(vol - ref) / np.linalg.norm(ref)
+        assert rel < TOL, rel
+        assert np.array_equal(plan.result(cp.RESULT_VOLUME), vol)
+        plan.close()
+
+
+@pytest.mark.parametrize("N,Np", [(48, 5), (96, 3)])
+def test_assembly_sizes(cp, N, Np):
+    d = synth.make_case("tiny", N=N, Np=Np)
+    rng = np.random.default_rng(N)
+    g = rng.standard_normal((Np, N, N)).astype(np.float32)
+    plan = _plan(cp, cp.make_config(N, Np), d, d["support"])
+    plan.load_state(g, 0)
+    vol = np.empty((N, N, N), np.complex64)
+    plan.assemble_3d(vol)
+    S = np.broadcast_to(d["support"].astype(bool), (Np, N, N))
+    ref = O.assemble(g.astype(np.float64), S, d["thetas"])
+    assert np.linalg.norm(vol - ref) / np.linalg.norm(ref) < TOL
+
+
+def test_assembly_recovers_phantom(cp):
+    """Exact projections in, volume out: the Fourier-slice assembly reproduces
+    the phantom's central slab to the accuracy the oracle itself reaches."""
+    N, Np = 32, 48
+    obj = synth.ellipsoid_phantom(16, 3, 21)
+    vol = synth.pad_volume(obj, N)
+    th = synth.angles(Np)
+    P = synth.project(vol, th, r_max=8).numpy().astype(np.float32)
+    I = np.fft.fftshift(np.abs(np.fft.fft2(P)) ** 2, axes=(-2, -1)).astype(np.float32)
+    S = np.ones((N, N), np.uint8)
+    plan = cp.Plan(cp.make_config(N, Np, com_align=0))
+    plan.load_intensities(I, 0, th)
+    plan.load_support(S)
+    plan.load_state(P, 0)
+    out = np.empty((N, N, N), np.complex64)
+    plan.assemble_3d(out)
+    ref = O.assemble(P.astype(np.float64), np.ones((Np, N, N), bool), th, com_align=False)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < TOL
+    corr = np.corrcoef(out.real.ravel(), vol.ravel())[0, 1]
+    assert corr > 0.9, corr
+
+
+def test_invalid_inputs(cp):
+    plan = cp.Plan(cp.make_config(32, 2))
+    with pytest.raises(cp.CpraError) as e:
+        plan.iterate(1)
+    assert e.value.status == cp.ERR_NOT_READY
+    bad = np.ones((2, 32, 32), np.float32)
+    bad[1, 3, 4] = -1.0
+    with pytest.raises(cp.CpraError) as e:
+        plan.load_intensities(bad)
+    assert e.value.status == cp.ERR_INVALID_ARG
+    bad[1, 3, 4] = np.nan
+    with pytest.raises(cp.CpraError) as e:
+        plan.load_intensities(bad)
+    assert e.value.status == cp.ERR_INVALID_ARG
+    with pytest.raises(cp.CpraError) as e:
+        plan.result(cp.RESULT_VOLUME)
+    assert e.value.status == cp.ERR_NOT_READY
+    with pytest.raises(cp.CpraError) as e:
+        plan.assemble_3d()
+    assert e.value.status == cp.ERR_NOT_READY
+    # zero patterns are legal; errors are then reported as 0
+    plan.load_intensities(np.zeros((2, 32, 32), np.float32))
+    e = plan.iterate(2, errors=True)
+    assert np.all(np.isfinite(e))
+    plan.close()
+
+
+def test_device_pointers_checkpoint_and_reset(cp):
+    import torch
+    d = synth.make_case("tiny", N=32, Np=4)
+    cfg = cp.make_config(32, 4, seed=9, n_ei=3)
+    plan = cp.Plan(cfg)
+    plan.load_intensities(torch.from_numpy(d["I"]).cuda(), 0, d["thetas"])
+    plan.load_support(torch.from_numpy(d["support"]).cuda())
+    plan.iterate(5)
+    g5 = plan.result(cp.RESULT_STATE)
+    plan.iterate(4)
+    g9 = plan.result(cp.RESULT_STATE)
+    hist = plan.result(cp.RESULT_ERRORS)
+    assert hist.shape == (9, 4) and np.all(hist > 0)
+    plan2 = cp.Plan(cp.make_config(32, 4, seed=9, n_ei=3))
+    plan2.load_intensities(d["I"], 0, d["thetas"])
+    plan2.load_support(d["support"])
+    plan2.load_state(torch.from_numpy(g5).cuda(), 5)
+    plan2.iterate(4)
+    assert np.array_equal(plan2.result(cp.RESULT_STATE), g9)
+    # reset replays the run bit for bit
+    plan.reset()
+    plan.load_support(d["support"])
+    plan.iterate(9)
+    assert np.array_equal(plan.result(cp.RESULT_STATE), g9)
+    # results into device memory
+    dst = torch.empty((4, 32, 32), dtype=torch.float32, device="cuda")
+    cp.cpra_result(plan.h, cp.RESULT_STATE, dst, dst.numel() * 4)
+    assert np.array_equal(dst.cpu().numpy(), g9)
+    plan.close()
+    plan2.close()
+
+
+def test_incremental_angle_loading(cp):
+    d = synth.make_case("tiny", N=32, Np=6)
+    cfg = cp.make_config(32, 6, seed=3, hio_iters=0, er_iters=3)
+    plan = cp.Plan(cfg)
+    plan.load_intensities(d["I"][:4], 0, d["thetas"][:4])
+    with pytest.raises(cp.CpraError):
+        plan.iterate(1)
+    plan.load_intensities(d["I"][4:], 4, d["thetas"][4:])
+    plan.load_support(d["support"])
+    plan.iterate(3)
+    run = O.OracleRun.start(_ocfg(cfg), d["I"], d["support"]).run(3)
+    assert _rel(plan.result(cp.RESULT_STATE), run.g).max() < TOL
+    plan.close()
+
+
+def test_metric_size_sampled(cp):
+    """N = 512, Np = 360 in the bench launch shape; sampled angles one by one."""
+    import torch
+    N, Np = 512, 360
+    rng = np.random.default_rng(10)
+    I = (rng.random((Np, N, N), dtype=np.float32) * 100.0) ** 2
+    g0 = np.zeros((Np, N, N), np.float32)
+    g0[:, N // 4:3 * N // 4, N // 4:3 * N // 4] = rng.random((Np, N // 2, N // 2), dtype=np.float32)
+    plan = cp.Plan(cp.make_config(N, Np))
+    plan.load_intensities(torch.from_numpy(I).cuda(), 0, None)
+    plan.load_support(None)
+    plan.load_state(g0, 0)
+    errs = plan.iterate(1, errors=True)
+    g = plan.result(cp.RESULT_STATE)
+    plan.close()
+    S = synth.padded_box_support(N).astype(bool)[None]
+    for n in (0, 1, 180, 359):
+        idx = [(n - 1) % Np, n, (n + 1) % Np]
+        nb = g0[idx].astype(np.float64)
+        x = (0.2 * nb[0] + 0.6 * nb[1] + 0.2 * nb[2])[None]
+        A = O.amplitudes(I[n])[None]
+        x, num, den, gp = O.iterate_2d(x, A, S, float(np.float32(0.9)), O.HIO, return_gp=True)
+        if O.positivity_margin(gp, S)[0] < KNIFE:
+            continue
+        assert _rel(g[n:n + 1], x)[0] < TOL
+        assert abs(errs[0, n] - np.sqrt(num / den)[0]) < TOL * np.sqrt(num / den)[0]
