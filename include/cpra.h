@@ -195,6 +195,37 @@ cpra_status cpra_kernel_stats(cpra_plan_t plan, int32_t kind, double* total_ms, 
 /* Number of kernels this library has launched in this process. */
 int64_t cpra_launch_count(void);
 
+/* Shrink-wrap support update without any device allocation.
+ *
+ * The paper has no counterpart: this is a library service.  It runs the same
+ * kernels and the same arithmetic as the shrink-wrap step of cpra_iterate
+ * (blur P_{S+} g with the periodic Gaussian of sigma pixels, keep pixels at
+ * or above tau times each pattern's maximum; a pattern whose maximum is 0
+ * keeps S_in), for callers that cannot call cudaMalloc: cudaMalloc and
+ * cudaFree can synchronize the whole device and take driver locks, which a
+ * pipeline that must keep up with a detector while other work runs on the
+ * same GPU, or a process that has handed its whole memory budget to another
+ * allocator, cannot afford.  Plans allocate through cpra_config.alloc; this
+ * call allocates nothing.
+ *
+ *   g      count*N*N float32, device memory: iterates [count][N][N]
+ *   S_in   count*N*N uint8, device memory: current supports (nonzero = in)
+ *   S_out  count*N*N uint8, device memory: new supports (0/1); may be S_in
+ *   stream cudaStream_t the work is queued on (NULL = legacy default stream)
+ *
+ * Scratch lives in file-scope device arrays of the library (about 8.3 MB on
+ * every GPU that loads it, held until the process exits).  The first call on
+ * a device looks up their addresses on that device (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the
+ * arrays, so calls that overlap on the GPU race: queue them on one stream or
+ * order them.  count*N*N may be at most CPRA_SHRINKWRAP_STATIC_MAX_PIXELS
+ * (2^20, e.g. 4 patterns of 512^2 or 256 of 64^2); larger requests return
+ * INVALID_ARG.  Host pointers return INVALID_ARG.  The call returns after
+ * queuing the work; errors are readable with cpra_last_error(NULL). */
+#define CPRA_SHRINKWRAP_STATIC_MAX_PIXELS (1 << 20)
+cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_in, uint8_t* S_out, int32_t N,
+                                   int32_t count, float sigma, float tau, void* stream);
+
 /* Global iteration counter t of the plan (-1 for a NULL plan). */
 int64_t cpra_iteration(cpra_plan_t plan);
 

@@ -75,6 +75,8 @@ def lib() -> C.CDLL:
             "cpra_set_profiling": (C.c_int, [P, C.c_int32]),
             "cpra_kernel_stats": (C.c_int, [P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "cpra_launch_count": (C.c_int64, []),
+            "cpra_shrinkwrap_static": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_float,
+                                                 C.c_float, P]),
             "cpra_sync": (C.c_int, [P]),
             "cpra_destroy": (C.c_int, [P]),
             "cpra_last_error": (C.c_char_p, [P]),
@@ -186,6 +188,16 @@ def cpra_kernel_stats(plan, kind: int):
 
 def cpra_launch_count() -> int:
     return int(lib().cpra_launch_count())
+
+
+def cpra_shrinkwrap_static(g, S_in, S_out, N: int, count: int, sigma: float, tau: float,
+                           stream=None):
+    """Shrink-wrap support update with no device allocation (device tensors only)."""
+    pg, kg = _ptr(g)
+    ps, ks = _ptr(S_in)
+    po, ko = _ptr(S_out)
+    _check(lib().cpra_shrinkwrap_static(pg, ps, po, N, count, sigma, tau, stream))
+    return kg, ks, ko
 
 
 def cpra_sync(plan):

@@ -305,6 +305,10 @@ cpra_status build_gridding(cpra_plan_s* p) {
 
 }  // namespace
 
+cpra_status cpra::record_error(cpra_status st, const std::string& msg) {
+  return fail(nullptr, st, msg);
+}
+
 extern "C" {
 
 cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* c) {

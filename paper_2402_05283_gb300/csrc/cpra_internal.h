@@ -95,6 +95,10 @@ cudaError_t launch_support_u8(cpra_plan_s* p, const uint8_t* S, int per_angle);
 cudaError_t launch_init_guess(cpra_plan_s* p);
 cudaError_t launch_export_po(cpra_plan_s* p, float* out);
 cudaError_t launch_export_support(cpra_plan_s* p, uint8_t* out);
+cudaError_t launch_bits_from_u8(uint32_t* bits, const uint8_t* src, int N, int count,
+                                cudaStream_t st);
+cudaError_t launch_bits_to_u8(const uint32_t* bits, uint8_t* out, int N, int count,
+                              cudaStream_t st);
 
 // two-pass iteration (k_twopass.cu)
 struct CoupleArgs {
@@ -115,5 +119,8 @@ cudaError_t launch_shrinkwrap(cpra_plan_s* p);
 cudaError_t launch_assemble(cpra_plan_s* p);
 
 bool n_supported(int N);
+
+// records a failure of a call without a plan (cpra_last_error(NULL))
+cpra_status record_error(cpra_status st, const std::string& msg);
 
 }  // namespace cpra

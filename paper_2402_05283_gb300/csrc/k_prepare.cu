@@ -127,6 +127,14 @@ cudaError_t launch_init_guess(cpra_plan_s* p) {
   return cudaGetLastError();
 }
 
+// Raw-pointer forms of the two support conversions (count patterns).
+cudaError_t launch_bits_from_u8(uint32_t* bits, const uint8_t* src, int N, int count,
+                                cudaStream_t st) {
+  g_launches += 1;
+  k_support<<<dim3(N, count), 32, 0, st>>>(bits, N, (N + 31) / 32, src, 1);
+  return cudaGetLastError();
+}
+
 __global__ void k_export_po(const float* g, const uint32_t* S, float* out, int N, int W) {
   const int y = blockIdx.x, n = blockIdx.y;
   const size_t srow = ((size_t)n * N + y) * W;
@@ -155,6 +163,14 @@ cudaError_t launch_export_support(cpra_plan_s* p, uint8_t* out) {
   int threads = p->N >= 256 ? 256 : p->N;
   g_launches += 1;
   k_export_support<<<dim3(p->N, p->Np), threads, 0, p->stream>>>(p->S, out, p->N, p->W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bits_to_u8(const uint32_t* bits, uint8_t* out, int N, int count,
+                              cudaStream_t st) {
+  const int threads = N >= 256 ? 256 : N;
+  g_launches += 1;
+  k_export_support<<<dim3(N, count), threads, 0, st>>>(bits, out, N, (N + 31) / 32);
   return cudaGetLastError();
 }
 

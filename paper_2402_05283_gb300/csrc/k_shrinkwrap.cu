@@ -5,6 +5,9 @@
 // S <- {b >= tau * max b} per angle (S kept when max b is 0).  The taps are
 // the wrapped Gaussian computed in FP64 on the host, truncated where they
 // fall below 1e-11 of the centre tap.
+#include <cmath>
+#include <mutex>
+
 #include "cpra_internal.h"
 #include "fft.cuh"
 
@@ -97,4 +100,127 @@ cudaError_t launch_shrinkwrap(cpra_plan_s* p) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- no-allocation form
+// Scratch of cpra_shrinkwrap_static: file-scope device arrays.  Every GPU that
+// loads the library holds them (about 8.3 MB) until the process exits; all
+// calls share them, so calls that overlap on the GPU race.
+static __device__ __align__(256) float sw_static_tmp[CPRA_SHRINKWRAP_STATIC_MAX_PIXELS];
+static __device__ __align__(256) float sw_static_b[CPRA_SHRINKWRAP_STATIC_MAX_PIXELS];
+static __device__ __align__(256) uint32_t sw_static_bits[CPRA_SHRINKWRAP_STATIC_MAX_PIXELS / 16];
+static __device__ __align__(256) unsigned sw_static_max[CPRA_SHRINKWRAP_STATIC_MAX_PIXELS / 256];
+static __device__ __align__(256) float sw_static_taps[1024];
+
+namespace {
+
+struct StaticScratch {
+  float* tmp;
+  float* b;
+  uint32_t* bits;
+  unsigned* mx;
+  float* taps;
+};
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+bool g_static_ready[kMaxDevices] = {};
+StaticScratch g_static[kMaxDevices];
+
+// Device addresses of the arrays above on the current device.  In host code
+// the array names are host-side stand-ins, so the addresses come from
+// cudaGetSymbolAddress, once per device, with that device current.
+cudaError_t static_scratch(StaticScratch& out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ready[dev]) {
+    StaticScratch s{};
+    if ((e = cudaGetSymbolAddress((void**)&s.tmp, sw_static_tmp)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&s.b, sw_static_b)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&s.bits, sw_static_bits)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&s.mx, sw_static_max)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&s.taps, sw_static_taps)) != cudaSuccess) return e;
+    g_static[dev] = s;
+    g_static_ready[dev] = true;
+  }
+  out = g_static[dev];
+  return cudaSuccess;
+}
+
+bool on_device(const void* ptr) {
+  cudaPointerAttributes a;
+  if (!ptr || cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 }  // namespace cpra
+
+extern "C" cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_in, uint8_t* S_out,
+                                              int32_t N, int32_t count, float sigma, float tau,
+                                              void* stream) {
+  using namespace cpra;
+  if (!n_supported(N)) return record_error(CPRA_ERR_UNSUPPORTED, "N must be a supported size");
+  if (count < 1) return record_error(CPRA_ERR_INVALID_ARG, "count must be >= 1");
+  if ((int64_t)count * N * N > CPRA_SHRINKWRAP_STATIC_MAX_PIXELS)
+    return record_error(CPRA_ERR_INVALID_ARG,
+                        "count*N*N exceeds the static scratch of CPRA_SHRINKWRAP_STATIC_MAX_PIXELS "
+                        "(1048576) pixels");
+  if (!(sigma > 0.0f) || !std::isfinite(sigma) || !(tau >= 0.0f) || !(tau <= 1.0f))
+    return record_error(CPRA_ERR_INVALID_ARG, "need sigma > 0 and 0 <= tau <= 1");
+  if (!on_device(g) || !on_device(S_in) || !on_device(S_out))
+    return record_error(CPRA_ERR_INVALID_ARG, "g, S_in and S_out must be device memory");
+  StaticScratch sc;
+  cudaError_t e = static_scratch(sc);
+  if (e != cudaSuccess)
+    return record_error(CPRA_ERR_CUDA, std::string("static scratch address: ") + cudaGetErrorString(e));
+  // periodic Gaussian taps in FP64, the same arithmetic as a plan's shrink-wrap
+  double w[1024];
+  const double sg = sigma;
+  for (int d = 0; d < N; ++d) w[d] = 0.0;
+  const int M = (int)std::ceil(12.0 * sg / N) + 1;
+  for (int d = 0; d < N; ++d)
+    for (int m = -M; m <= M; ++m) {
+      const double t = d + (double)m * N;
+      w[d] += std::exp(-t * t / (2.0 * sg * sg));
+    }
+  double sum = 0.0;
+  for (int d = 0; d < N; ++d) sum += w[d];
+  for (int d = 0; d < N; ++d) w[d] /= sum;
+  int R = 0;
+  while (R < N / 2 && w[R + 1] >= 1e-11 * w[0]) ++R;
+  int ntaps, lo0;
+  if (2 * R + 1 >= N) {
+    ntaps = N;
+    lo0 = -(N / 2) + 1;
+  } else {
+    ntaps = 2 * R + 1;
+    lo0 = -R;
+  }
+  float taps[1024];
+  for (int t = 0; t < ntaps; ++t) taps[t] = (float)w[((lo0 + t) % N + N) % N];
+  cudaStream_t st = (cudaStream_t)stream;
+  const int W = (N + 31) / 32;
+  const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  const int lo = -(ntaps / 2) + ((ntaps % 2) ? 0 : 1);
+  e = cudaMemcpyAsync(sc.taps, taps, sizeof(float) * ntaps, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.mx, 0, sizeof(unsigned) * count, st);
+  if (e == cudaSuccess) e = launch_bits_from_u8(sc.bits, S_in, N, count, st);
+  if (e == cudaSuccess) {
+    g_launches += 3;
+    k_sw_rows<<<dim3(N, count), threads, N * sizeof(float), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps,
+                                                                   lo, N, W);
+    k_sw_cols<<<dim3(N, count), threads, 0, st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
+    k_sw_thresh<<<dim3(N, count), 32, 0, st>>>(sc.b, sc.mx, sc.bits, tau, N, W);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_bits_to_u8(sc.bits, S_out, N, count, st);
+  if (e != cudaSuccess)
+    return record_error(CPRA_ERR_CUDA, std::string("shrink-wrap launch: ") + cudaGetErrorString(e));
+  return CPRA_OK;
+}

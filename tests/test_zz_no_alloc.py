@@ -1,0 +1,71 @@
+"""The allocation-free shrink-wrap entry point against a plan's shrink-wrap.
+
+cpra_shrinkwrap_static serves callers that cannot call cudaMalloc (it
+synchronizes the device and takes driver locks): its scratch is a static
+device array of the library.  Here it must reproduce, on two calls in a row,
+the support that cpra_iterate's own shrink-wrap step produced from the same
+iterate and the same previous support.  Both run the same kernels, so the
+masks must be identical (the tolerance for masks elsewhere in the suite
+allows differences only at knife-edge pixels; here none are expected).
+
+This file is collected last on purpose: it must pass alone in a fresh
+process and after every other test.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_05283_gb300 as pkg
+    return pkg
+
+
+def test_static_shrinkwrap_matches_plan_twice(cp):
+    import torch
+    N, Np = 64, 6
+    d = synth.make_case("tiny", N=N, Np=Np)
+    plan = cp.Plan(cp.make_config(N, Np, n_ei=2, shrinkwrap_every=1, seed=11,
+                                  hio_iters=0, er_iters=4))
+    plan.load_intensities(d["I"], 0, d["thetas"])
+    plan.load_support(d["support"])
+    stream = torch.cuda.current_stream().cuda_stream
+    S_prev = torch.from_numpy(np.broadcast_to(d["support"], (Np, N, N)).copy()).cuda()
+    shrunk = False
+    for call in range(2):
+        plan.iterate(1)  # one ER iteration, then the plan's shrink-wrap
+        g = torch.from_numpy(plan.result(cp.RESULT_STATE)).cuda()
+        S_plan = plan.result(cp.RESULT_SUPPORT)
+        out = torch.full((Np, N, N), 7, dtype=torch.uint8, device="cuda")
+        cp.cpra_shrinkwrap_static(g, S_prev, out, N, Np, 2.0, 0.1, stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert set(np.unique(got)) <= {0, 1}
+        assert np.array_equal(got, S_plan), f"call {call}: {(got != S_plan).sum()} pixels differ"
+        shrunk |= bool(S_plan.sum() < S_prev.cpu().numpy().astype(bool).sum())
+        S_prev = torch.from_numpy(S_plan).cuda()
+    assert shrunk
+    plan.close()
+
+
+def test_static_shrinkwrap_rejects_oversize_and_host_memory(cp):
+    import torch
+    N = 512
+    g = torch.zeros((8, N, N), device="cuda")
+    S = torch.ones((8, N, N), dtype=torch.uint8, device="cuda")
+    with pytest.raises(cp.CpraError) as e:  # 8 * 512^2 > 2^20 pixels
+        cp.cpra_shrinkwrap_static(g, S, S, N, 8, 2.0, 0.1, None)
+    assert e.value.status == cp.ERR_INVALID_ARG
+    assert "static scratch" in cp.cpra_last_error(None)
+    with pytest.raises(cp.CpraError) as e:
+        cp.cpra_shrinkwrap_static(np.zeros((1, 64, 64), np.float32), S, S, 64, 1, 2.0, 0.1, None)
+    assert e.value.status == cp.ERR_INVALID_ARG
