@@ -295,7 +295,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"CPRA N={N} Np={NP}: {T_HIO} HIO + {T_ER} ER iterations, "
                                    "coupling alpha=(0.2,0.6,0.2) every 10, 512^3 assembly",
-                       "N": N, "Np": NP, "iterations": ITERS, "engine": "two-pass",
+                       "N": N, "Np": NP, "iterations": ITERS,
+                       "engine": "two-pass, warp-resident FFTs",
                        "l2": "inputs larger than L2 (state 0.75 GB, intensities 0.38 GB)",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": round(float(qs[0]), 3), "p99_ms": round(float(qs[1]), 3),

@@ -49,7 +49,7 @@ typedef enum {
 enum { CPRA_WRAP_LITERAL = 0, CPRA_WRAP_MIRROR = 1 };
 enum { CPRA_BLEND_STATE = 0, CPRA_BLEND_OBJECT = 1 };
 enum { CPRA_FP32 = 0, CPRA_BF16_TC = 1, CPRA_FP16_TC = 2 };
-enum { CPRA_ENGINE_AUTO = 0, CPRA_ENGINE_TWO_PASS = 1, CPRA_ENGINE_FUSED = 2 };
+enum { CPRA_ENGINE_AUTO = 0, CPRA_ENGINE_TWO_PASS = 1, CPRA_ENGINE_FUSED = 2, CPRA_ENGINE_WARP = 3 };
 enum {
   CPRA_RESULT_PO = 0,      /* Np*N*N float: P_{S+} g (iterate on its valid set)  */
   CPRA_RESULT_STATE = 1,   /* Np*N*N float: the iterate g itself                 */
@@ -83,8 +83,11 @@ enum {
  *   precision      CPRA_FP32 (default) or tensor-core FFT stages.
  *   com_align      1: move each PO's mass centre to the origin before
  *                  assembly (Step C); 0: use the frame centre.
- *   engine         kernel family; AUTO picks the fused cluster-resident
- *                  iteration where it fits on chip, TWO_PASS otherwise.
+ *   engine         kernel family.  TWO_PASS: row and column passes with
+ *                  block-wide shared-memory FFTs (every supported N).  WARP:
+ *                  the same passes with warp-resident two-level FFTs
+ *                  (N = 64, 128, 256, 512, 1024).  AUTO: WARP where
+ *                  available, else TWO_PASS.  FUSED is reserved.
  *   seed           seeds the random initial guess (SplitMix64 per pixel).
  *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
  */

@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_READY, ERR_TIMEOUT, ER
 WRAP_LITERAL, WRAP_MIRROR = 0, 1
 BLEND_STATE, BLEND_OBJECT = 0, 1
 FP32, BF16_TC, FP16_TC = 0, 1, 2
-ENGINE_AUTO, ENGINE_TWO_PASS, ENGINE_FUSED = 0, 1, 2
+ENGINE_AUTO, ENGINE_TWO_PASS, ENGINE_FUSED, ENGINE_WARP = 0, 1, 2, 3
 RESULT_PO, RESULT_STATE, RESULT_SUPPORT, RESULT_ERRORS, RESULT_VOLUME = range(5)
 (KERNEL_COLPASS, KERNEL_ROWPASS, KERNEL_PRIME, KERNEL_SHRINKWRAP, KERNEL_ASSEMBLE, KERNEL_FUSED,
  KERNEL_PREPARE, KERNEL_KINDS) = range(8)

@@ -78,7 +78,7 @@ Sizes plan_sizes(const cpra_config& c) {
            + Np * N * (N / 2) * 4 + Np * N * 4  // A_main, A_nyq
            + 3 * Np * 8         // Cn, sumA2, err_acc
            + Np * N * W * 4     // S
-           + N * 8              // twiddles
+           + 2 * N * 8          // twiddles
            + Np * NN * 4        // staging
            + 256 * Np * 8;      // initial error history
   if (c.shrinkwrap_every > 0) s.iter += Np * NN * 4 + Np * 4 + N * 4;
@@ -127,11 +127,16 @@ cpra_status validate(const cpra_config* c, std::string& why) {
     return CPRA_ERR_INVALID_ARG;
   }
   if (c->precision != CPRA_FP32) { why = "tensor-core precision not built into this engine"; return CPRA_ERR_UNSUPPORTED; }
-  if (c->engine != CPRA_ENGINE_AUTO && c->engine != CPRA_ENGINE_TWO_PASS && c->engine != CPRA_ENGINE_FUSED) {
+  if (c->engine != CPRA_ENGINE_AUTO && c->engine != CPRA_ENGINE_TWO_PASS &&
+      c->engine != CPRA_ENGINE_FUSED && c->engine != CPRA_ENGINE_WARP) {
     why = "bad engine";
     return CPRA_ERR_INVALID_ARG;
   }
   if (c->engine == CPRA_ENGINE_FUSED) { why = "fused engine not available for this N"; return CPRA_ERR_UNSUPPORTED; }
+  if (c->engine == CPRA_ENGINE_WARP && !fast_supported(c->N)) {
+    why = "warp engine needs N in {64, 128, 256, 512, 1024}";
+    return CPRA_ERR_UNSUPPORTED;
+  }
   if ((c->alloc == nullptr) != (c->free == nullptr)) {
     why = "alloc and free must be given together";
     return CPRA_ERR_INVALID_ARG;
@@ -231,7 +236,7 @@ cpra_status prime_plain(cpra_plan_s* p, int first, int count) {
   CoupleArgs ca{};
   ca.n_taps = 1;
   ca.alpha[0] = 1.0f;
-  CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(p, first, count, p->g, p->g, p->Hp, ca); }),
+  CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(p, first, count, p->g, nullptr, p->Hp, ca); }),
      "prime");
   return CPRA_OK;
 }
@@ -360,7 +365,10 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   p->N = cfg->N;
   p->Np = cfg->Np;
   p->W = (cfg->N + 31) / 32;
-  p->engine = CPRA_ENGINE_TWO_PASS;
+  p->engine = (cfg->engine == CPRA_ENGINE_WARP ||
+               (cfg->engine == CPRA_ENGINE_AUTO && fast_supported(cfg->N)))
+                  ? CPRA_ENGINE_WARP
+                  : CPRA_ENGINE_TWO_PASS;
   p->loaded.assign(p->Np, 0);
   p->theta.resize(p->Np);
   for (int n = 0; n < p->Np; ++n) p->theta[n] = n * M_PI / p->Np;
@@ -381,6 +389,7 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   p->err_acc = (double*)A(Np * 8);
   p->S = (uint32_t*)A(Np * N * p->W * 4);
   p->tw = (float2*)A(N * 8);
+  p->xtw = (float2*)A(N * 8);
   p->stage = (float*)A(Np * NN * 4);
   p->flag = (int*)A(sizeof(int) * 4);
   if (ok && cfg->shrinkwrap_every > 0) {
@@ -402,7 +411,18 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
     const double a = -2.0 * M_PI * (double)k / (double)N;
     tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
+  // cross twiddles of the warp FFT, [k1][l] = exp(-2 pi i (l k1 mod N) / N), FP64 then FP32
+  std::vector<float2> xtw(N, make_float2(1.0f, 0.0f));
+  int E1 = 0, E2 = 0;
+  if (fast_dims(p->N, &E1, &E2))
+    for (int k1 = 0; k1 < E1; ++k1)
+      for (int l = 0; l < E2; ++l) {
+        const double a = -2.0 * M_PI * (double)((l * k1) % p->N) / (double)N;
+        xtw[k1 * E2 + l] = make_float2((float)std::cos(a), (float)std::sin(a));
+      }
   cudaError_t e = cudaMemcpyAsync(p->tw, tw.data(), N * 8, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->xtw, xtw.data(), N * 8, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->err_acc, 0, Np * 8, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->g, 0, Np * NN * 4, p->stream);
   if (e == cudaSuccess) e = launch_support_box(p);

@@ -5,7 +5,8 @@
 //   Hp         [Np][N][N/2]  float2  row spectra of g, packed: column 0 holds
 //                                    (Re H(y,0), Re H(y,N/2)); the two-pass
 //                                    engine keeps it between its passes
-//   A_main     [Np][N][N/2]  float   Hermitian-symmetrised amplitude, kx < N/2
+//   A_main     [Np][N/2][N]  float   Hermitian-symmetrised amplitude, kx < N/2,
+//                                    column-major ([kx][ky])
 //   A_nyq      [Np][N]       float   the same at kx = N/2
 //   Cn, sumA2  [Np]          double  antisymmetric-part energy, sum A^2
 //   S          [Np][N][W]    uint32  support bits, W = ceil(N/32) words a row
@@ -60,6 +61,7 @@ struct cpra_plan_s {
   double* err_hist = nullptr;
   int64_t err_cap = 0;
   float2* tw = nullptr;        // forward twiddles exp(-2 pi i k/N)
+  float2* xtw = nullptr;       // warp-FFT cross twiddles, [k1][l] = exp(-2 pi i l k1/N)
   float* stage = nullptr;      // staging for host inputs, Np*N*N floats
   int* flag = nullptr;         // device status word
   float* sw_tmp = nullptr;     // shrink-wrap scratch, Np*N*N floats
@@ -119,6 +121,15 @@ cudaError_t launch_shrinkwrap(cpra_plan_s* p);
 cudaError_t launch_assemble(cpra_plan_s* p);
 
 bool n_supported(int N);
+
+// two-pass engine with warp-resident FFTs (k_fast.cu)
+bool fast_supported(int N);
+bool fast_dims(int N, int* E1, int* E2);
+cudaError_t launch_rowpass_fast(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
+                                int forward);
+cudaError_t launch_prime_fast(cpra_plan_s* p, int first, int count, const float* src, float* dst,
+                              float2* Hp, const CoupleArgs& ca);
+cudaError_t launch_colpass_fast(cpra_plan_s* p, int first, int count);
 
 // records a failure of a call without a plan (cpra_last_error(NULL))
 cpra_status record_error(cpra_status st, const std::string& msg);

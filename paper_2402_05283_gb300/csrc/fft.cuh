@@ -157,6 +157,18 @@ __device__ __forceinline__ void fft_lines(float2* buf, const float2* tw) {
   stockham<N, 1, DIR, B, PI, NT>(buf, tw);
 }
 
+// Asynchronous global -> shared copies (LDGSTS); completion by wait_all.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // support bit x of the row whose first word is at S[row_off]
 __device__ __forceinline__ bool sbit(const uint32_t* S, size_t row_off, int x) {
   return (S[row_off + (x >> 5)] >> (x & 31)) & 1u;

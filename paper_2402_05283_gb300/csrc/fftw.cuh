@@ -1,0 +1,195 @@
+// fftw.cuh - warp-resident two-level FFTs of length N = E1 * E2.
+//
+// A warp transforms L lines at once.  With n = l + E2 m and k = k1 + E1 k2,
+//   X[k1 + E1 k2] = sum_l W_N^(l k1) W_E2^(l k2) [ sum_m x[l + E2 m] W_E1^(m k1) ]
+// so a forward transform is: E1-point DFTs in registers (step A, one per
+// (line, l)), the cross twiddle W_N^(l k1), one transpose through the warp's
+// shared-memory tile, E2-point DFTs in registers (step B, one per
+// (line, k1)).  The inverse runs the same steps backwards.  Only __syncwarp
+// is needed: a warp owns its lines and its tile.
+//
+// Register layouts (lane = threadIdx.x % 32, i = task slot of the lane):
+//   A layout  a[i][m] = x_line[l + E2 m],      task t = lane + 32 i:
+//             line = t / E2, l = t % E2
+//   B layout  b[i][k2] = X_line[k1 + E1 k2],   task t = lane + 32 i:
+//             line = t / E1, k1 = t % E1
+// Twiddles inside the register DFTs are compile-time constants (cos and sin
+// evaluated from their Taylor series at compile time in FP64, exact at
+// multiples of pi/2); the cross twiddles come from a table
+// xtw[k1 * E2 + l] = exp(-2 pi i l k1 / N) built in FP64 on the host.
+#pragma once
+#include <type_traits>
+
+#include "fft.cuh"
+
+namespace cpra {
+
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+
+constexpr double cx_series_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int n = 1; n < 30; ++n) {
+    t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    s += t;
+  }
+  return s;
+}
+constexpr double cx_series_sin(double x) {
+  double t = x, s = x;
+  for (int n = 1; n < 30; ++n) {
+    t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    s += t;
+  }
+  return s;
+}
+// cos(2 pi q / M), sin(2 pi q / M)
+constexpr double cx_cos2pi(int q, int M) {
+  q = ((q % M) + M) % M;
+  if (q == 0) return 1.0;
+  if (2 * q == M) return -1.0;
+  if (4 * q == M || 4 * q == 3 * M) return 0.0;
+  double x = 2.0 * kPiD * q / M;
+  if (x > kPiD) x -= 2.0 * kPiD;
+  return cx_series_cos(x);
+}
+constexpr double cx_sin2pi(int q, int M) {
+  q = ((q % M) + M) % M;
+  if (q == 0 || 2 * q == M) return 0.0;
+  if (4 * q == M) return 1.0;
+  if (4 * q == 3 * M) return -1.0;
+  double x = 2.0 * kPiD * q / M;
+  if (x > kPiD) x -= 2.0 * kPiD;
+  return cx_series_sin(x);
+}
+
+// exp(DIR * 2 pi i Q / M) as compile-time constants
+template <int M, int Q, int DIR> struct TwC {
+  static constexpr float re = (float)cx_cos2pi(Q, M);
+  static constexpr float im = (float)(DIR * cx_sin2pi(Q, M));
+};
+
+template <int I, int End, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < End) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, End>(f);
+  }
+}
+
+// In-register E-point DFT, y_k = sum_j v_j exp(DIR 2 pi i jk / E), as
+// self-sorting Stockham passes over compile-time indices.
+template <int E, int DIR, int NS = 1>
+__device__ __forceinline__ void reg_fft(float2 (&v)[E]) {
+  if constexpr (NS < E) {
+    constexpr int R = pick_radix(E / NS);
+    constexpr int NB = E / R;
+    float2 out[E];
+    static_for<0, NB>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int k = j % NS;
+      float2 x[R];
+      static_for<0, R>([&](auto RR) {
+        constexpr int r = decltype(RR)::value;
+        float2 t = v[j + r * NB];
+        if constexpr (NS > 1 && r > 0 && k > 0) {
+          constexpr float wr = TwC<NS * R, k * r, DIR>::re;
+          constexpr float wi = TwC<NS * R, k * r, DIR>::im;
+          t = make_float2(fmaf(t.x, wr, -t.y * wi), fmaf(t.x, wi, t.y * wr));
+        }
+        x[r] = t;
+      });
+      Dft<R, DIR>::run(x);
+      constexpr int base = (j / NS) * NS * R + k;
+      static_for<0, R>([&](auto RR) {
+        constexpr int r = decltype(RR)::value;
+        out[base + r * NS] = x[r];
+      });
+    });
+    static_for<0, E>([&](auto I) { v[decltype(I)::value] = out[decltype(I)::value]; });
+    reg_fft<E, DIR, NS * R>(v);
+  }
+}
+
+template <int N> struct WarpPlan;
+template <> struct WarpPlan<64> { static constexpr int E1 = 8, E2 = 8, L = 4; };
+template <> struct WarpPlan<128> { static constexpr int E1 = 8, E2 = 16, L = 4; };
+template <> struct WarpPlan<256> { static constexpr int E1 = 16, E2 = 16, L = 2; };
+template <> struct WarpPlan<512> { static constexpr int E1 = 16, E2 = 32, L = 2; };
+template <> struct WarpPlan<1024> { static constexpr int E1 = 32, E2 = 32, L = 1; };
+
+template <int N> struct WP {
+  static constexpr int E1 = WarpPlan<N>::E1, E2 = WarpPlan<N>::E2, L = WarpPlan<N>::L;
+  static constexpr int TA = L * E2 / 32;  // step-A tasks per lane
+  static constexpr int TB = L * E1 / 32;  // step-B tasks per lane
+  static constexpr int TP = E2 + 1;       // odd pitch of the transpose tile
+  static constexpr int TSIZE = (L * E1 * TP > L * N) ? L * E1 * TP : L * N;  // float2 per warp
+  static_assert(E1 * E2 == N && TA * 32 == L * E2 && TB * 32 == L * E1, "warp plan");
+};
+
+template <int N> constexpr bool kHasWarpPlan = (N == 64 || N == 128 || N == 256 || N == 512 || N == 1024);
+
+// A layout -> B layout (forward, unnormalised)
+template <int N>
+__device__ __forceinline__ void warp_fft_fwd(float2 (&a)[WP<N>::TA][WP<N>::E1],
+                                             float2 (&b)[WP<N>::TB][WP<N>::E2], float2* T,
+                                             const float2* xtw, int lane) {
+  using P = WP<N>;
+  static_for<0, P::TA>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
+    const int line = t / P::E2, l = t % P::E2;
+    reg_fft<P::E1, -1>(a[i]);
+    static_for<0, P::E1>([&](auto KK) {
+      constexpr int k1 = decltype(KK)::value;
+      float2 v = a[i][k1];
+      if constexpr (k1 > 0) v = cmul(v, xtw[k1 * P::E2 + l]);
+      T[(line * P::E1 + k1) * P::TP + l] = v;
+    });
+  });
+  __syncwarp();
+  static_for<0, P::TB>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
+    const int line = t / P::E1, k1 = t % P::E1;
+    static_for<0, P::E2>([&](auto LL) {
+      constexpr int l = decltype(LL)::value;
+      b[i][l] = T[(line * P::E1 + k1) * P::TP + l];
+    });
+    reg_fft<P::E2, -1>(b[i]);
+  });
+  __syncwarp();
+}
+
+// B layout -> A layout (inverse, unnormalised)
+template <int N>
+__device__ __forceinline__ void warp_fft_inv(float2 (&b)[WP<N>::TB][WP<N>::E2],
+                                             float2 (&a)[WP<N>::TA][WP<N>::E1], float2* T,
+                                             const float2* xtw, int lane) {
+  using P = WP<N>;
+  static_for<0, P::TB>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
+    const int line = t / P::E1, k1 = t % P::E1;
+    reg_fft<P::E2, +1>(b[i]);
+    static_for<0, P::E2>([&](auto LL) {
+      constexpr int l = decltype(LL)::value;
+      T[(line * P::E1 + k1) * P::TP + l] = b[i][l];
+    });
+  });
+  __syncwarp();
+  static_for<0, P::TA>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
+    const int line = t / P::E2, l = t % P::E2;
+    static_for<0, P::E1>([&](auto KK) {
+      constexpr int k1 = decltype(KK)::value;
+      float2 v = T[(line * P::E1 + k1) * P::TP + l];
+      if constexpr (k1 > 0) v = cmul(v, cconj(xtw[k1 * P::E2 + l]));
+      a[i][k1] = v;
+    });
+    reg_fft<P::E1, +1>(a[i]);
+  });
+  __syncwarp();
+}
+
+}  // namespace cpra

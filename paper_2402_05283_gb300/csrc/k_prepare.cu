@@ -9,7 +9,7 @@ std::atomic<long long> g_launches{0};
 // One block per (FFT-order row ky, angle).  A(k) = sqrt(I) at the centred
 // index of k; A_sym(k) = (A(k) + A(-k)) / 2 on the half plane kx <= N/2;
 // the full-plane sums of ((A(k) - A(-k))/2)^2 and A(k)^2 go to Cn and sumA2.
-__global__ void k_prepare(const float* __restrict__ I, int N, int first, float* A_main,
+__global__ void k_prepare(const float* __restrict__ I, int N, int first, float* A_rows,
                           float* A_nyq, double* Cn, double* sumA2, int* flag) {
   const int ky = blockIdx.x;
   const int n = first + blockIdx.y;
@@ -31,7 +31,7 @@ __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* 
     c_part += d * d;
     a_part += (double)ap * (double)ap;
     float as = 0.5f * (ap + am);
-    if (kx < h) A_main[((size_t)n * N + ky) * h + kx] = as;
+    if (kx < h) A_rows[((size_t)blockIdx.y * N + ky) * h + kx] = as;
     if (kx == h) A_nyq[(size_t)n * N + ky] = as;
   }
   if (bad) atomicExch(flag, 1);
@@ -59,6 +59,25 @@ __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* 
   }
 }
 
+// A_rows[c][ky][kx] (kx < N/2) -> A_main[n][kx][ky], 32 x 32 tiles through smem
+__global__ void k_transpose_amp(const float* __restrict__ A_rows, float* A_main, int N, int first) {
+  __shared__ float tile[32][33];
+  const int h = N / 2;
+  const int c = blockIdx.z;
+  const int kx0 = blockIdx.x * 32, ky0 = blockIdx.y * 32;
+  const float* src = A_rows + (size_t)c * N * h;
+  float* dst = A_main + (size_t)(first + c) * h * N;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int ky = ky0 + j, kx = kx0 + threadIdx.x;
+    if (ky < N && kx < h) tile[j][threadIdx.x] = src[(size_t)ky * h + kx];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int kx = kx0 + j, ky = ky0 + threadIdx.x;
+    if (ky < N && kx < h) dst[(size_t)kx * N + ky] = tile[threadIdx.x][j];
+  }
+}
+
 cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count) {
   cudaError_t e = cudaMemsetAsync(p->Cn + first, 0, sizeof(double) * count, p->stream);
   if (e != cudaSuccess) return e;
@@ -66,9 +85,14 @@ cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count)
   if (e != cudaSuccess) return e;
   dim3 grid(p->N, count);
   int threads = p->N >= 256 ? 256 : ((p->N + 31) / 32) * 32;
-  g_launches += 1;
-  k_prepare<<<grid, threads, 0, p->stream>>>(I, p->N, first, p->A_main, p->A_nyq, p->Cn,
-                                             p->sumA2, p->flag);
+  // g_alt is free outside cpra_iterate: it holds the row-major amplitudes
+  float* rows = p->g_alt;
+  g_launches += 2;
+  k_prepare<<<grid, threads, 0, p->stream>>>(I, p->N, first, rows, p->A_nyq, p->Cn, p->sumA2,
+                                             p->flag);
+  const int h = p->N / 2;
+  dim3 tg((h + 31) / 32, (p->N + 31) / 32, count);
+  k_transpose_amp<<<tg, dim3(32, 8), 0, p->stream>>>(rows, p->A_main, p->N, first);
   return cudaGetLastError();
 }
 

@@ -135,12 +135,12 @@ k_colpass(float2* Hp, const float* __restrict__ A_main, const float* __restrict_
   __syncthreads();
   fft_lines<N, -1, B, B, NT>(buf, tw_s);
   double err = 0.0;
-  const float* An = A_main + (size_t)n * N * H;
+  const float* An = A_main + (size_t)n * N * H;  // [kx][ky]
   for (int idx = threadIdx.x; idx < N * B; idx += NT) {
     const int ky = idx / B, b = idx - ky * B;
     const int c = c0 + b;
     if (c == 0) continue;
-    buf[idx] = project(buf[idx], An[(size_t)ky * H + c], err, 2.0);
+    buf[idx] = project(buf[idx], An[(size_t)c * N + ky], err, 2.0);
   }
   if (c0 == 0) {
     // packed column: Z = G(.,0) + i G(.,N/2), both Hermitian along ky
@@ -150,7 +150,7 @@ k_colpass(float2* Hp, const float* __restrict__ A_main, const float* __restrict_
       const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
       const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
       const double w = (ky == 0 || ky == H) ? 1.0 : 2.0;
-      const float2 p0 = project(g0, An[(size_t)ky * H], err, w);
+      const float2 p0 = project(g0, An[ky], err, w);
       const float2 pn = project(gn, A_nyq[(size_t)n * N + ky], err, w);
       buf[ky * B] = make_float2(p0.x - pn.y, p0.y + pn.x);
       if (km != ky) buf[km * B] = make_float2(p0.x + pn.y, pn.x - p0.y);
@@ -288,6 +288,7 @@ static cudaError_t rowpass_n(cpra_plan_s* p, int first, int count, int algo, int
 
 cudaError_t launch_prime(cpra_plan_s* p, int first, int count, const float* src, float* dst,
                          float2* Hp, const CoupleArgs& ca) {
+  if (p->engine == CPRA_ENGINE_WARP) return launch_prime_fast(p, first, count, src, dst, Hp, ca);
 #define CPRA_CASE(NN) \
   case NN: return prime_n<NN>(p, first, count, src, dst, Hp, ca);
   switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
@@ -295,6 +296,7 @@ cudaError_t launch_prime(cpra_plan_s* p, int first, int count, const float* src,
 }
 
 cudaError_t launch_colpass(cpra_plan_s* p, int first, int count) {
+  if (p->engine == CPRA_ENGINE_WARP) return launch_colpass_fast(p, first, count);
 #define CPRA_CASE(NN) \
   case NN: return colpass_n<NN>(p, first, count);
   switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
@@ -303,6 +305,7 @@ cudaError_t launch_colpass(cpra_plan_s* p, int first, int count) {
 
 cudaError_t launch_rowpass(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
                            int forward) {
+  if (p->engine == CPRA_ENGINE_WARP) return launch_rowpass_fast(p, first, count, algo, slot, forward);
 #define CPRA_CASE(NN) \
   case NN: return rowpass_n<NN>(p, first, count, algo, slot, forward);
   switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }

@@ -121,9 +121,11 @@ def cfg1():
     return d
 
 
-def test_cfg1_er_all_50_iterates(cp, cfg1):
+@pytest.mark.parametrize("engine", ["auto", "two_pass"])
+def test_cfg1_er_all_50_iterates(cp, cfg1, engine):
     """The 1e-4 bar on every one of the first 50 iterates of all 32 angles."""
-    cfg = cp.make_config(64, 32, seed=1, hio_iters=0, er_iters=50, n_ei=10)
+    cfg = cp.make_config(64, 32, seed=1, hio_iters=0, er_iters=50, n_ei=10,
+                         engine=cp.ENGINE_AUTO if engine == "auto" else cp.ENGINE_TWO_PASS)
     worst, _ = _check_traj(cp, cfg1, cfg, 50, cfg1["true_support"])
     print(f"cfg1 ER 50 iterations: worst rel-L2 {worst:.2e}")
 
@@ -174,18 +176,21 @@ def test_cfg1_final_reconstruction_quality(cp, cfg1):
     assert abs(r_gpu - r_ref) <= 0.25 * r_ref, (r_gpu, r_ref)
 
 
-@pytest.mark.parametrize("N,Np", [(16, 3), (32, 5), (48, 4), (64, 3), (96, 3), (128, 2),
-                                  (192, 2), (256, 2), (384, 2), (512, 2), (768, 1), (1024, 1)])
-def test_sizes_and_radices(cp, N, Np):
-    """Every supported radix chain and tile shape: HIO step with coupling, then ER."""
+@pytest.mark.parametrize("N,Np,engine", [
+    (16, 3, 1), (32, 5, 1), (48, 4, 1), (64, 3, 1), (96, 3, 1), (128, 2, 1), (192, 2, 1),
+    (256, 2, 1), (384, 2, 1), (512, 2, 1), (768, 1, 1), (1024, 1, 1),
+    (64, 3, 3), (128, 2, 3), (256, 2, 3), (512, 2, 3), (1024, 1, 3)])
+def test_sizes_and_radices(cp, N, Np, engine):
+    """Every supported radix chain and tile shape of both engines (1 = block-wide
+    Stockham passes, 3 = warp-resident FFTs): HIO step with coupling, then ER."""
     d = synth.make_case("tiny", N=N, Np=Np)
     S = d["support"]
-    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=1, er_iters=5)
+    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=1, er_iters=5, engine=engine)
     g0 = O.initial_guess(7, Np, N, np.broadcast_to(S.astype(bool), (Np, N, N)))
     rel, erel, _ = _one_step(cp, d, cfg, S, g0, 0)
     assert erel.max() < TOL, erel
     # ER steps 1..5 from the seeded start (continuous, so compare the trajectory)
-    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=0, er_iters=6)
+    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=0, er_iters=6, engine=engine)
     _check_traj(cp, d, cfg, 6, S)
 
 
