@@ -49,7 +49,13 @@ typedef enum {
 enum { CPRA_WRAP_LITERAL = 0, CPRA_WRAP_MIRROR = 1 };
 enum { CPRA_BLEND_STATE = 0, CPRA_BLEND_OBJECT = 1 };
 enum { CPRA_FP32 = 0, CPRA_BF16_TC = 1, CPRA_FP16_TC = 2 };
-enum { CPRA_ENGINE_AUTO = 0, CPRA_ENGINE_TWO_PASS = 1, CPRA_ENGINE_FUSED = 2, CPRA_ENGINE_WARP = 3 };
+enum {
+  CPRA_ENGINE_AUTO = 0,
+  CPRA_ENGINE_TWO_PASS = 1,
+  CPRA_ENGINE_FUSED = 2,
+  CPRA_ENGINE_WARP = 3,
+  CPRA_ENGINE_TUNED = 4
+};
 enum {
   CPRA_RESULT_PO = 0,      /* Np*N*N float: P_{S+} g (iterate on its valid set)  */
   CPRA_RESULT_STATE = 1,   /* Np*N*N float: the iterate g itself                 */
@@ -87,7 +93,9 @@ enum {
  *                  block-wide shared-memory FFTs (every supported N).  WARP:
  *                  the same passes with warp-resident two-level FFTs
  *                  (N = 64, 128, 256, 512, 1024).  AUTO: WARP where
- *                  available, else TWO_PASS.  FUSED is reserved.
+ *                  available, else TWO_PASS.  TUNED: the fastest engine for
+ *                  this N on this GPU according to cpra_autotune (its
+ *                  default cache).  FUSED is reserved.
  *   seed           seeds the random initial guess (SplitMix64 per pixel).
  *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
  */
@@ -228,6 +236,122 @@ int64_t cpra_launch_count(void);
 #define CPRA_SHRINKWRAP_STATIC_MAX_PIXELS (1 << 20)
 cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_in, uint8_t* S_out, int32_t N,
                                    int32_t count, float sigma, float tau, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batching (many reconstructions per launch) and the engine autotuner.
+ *
+ * A batch iterates several plans together: for every group of plans with
+ * the same N and engine, each kernel of an iteration runs as ONE launch
+ * whose tiles are the (plan, angle) pairs of the whole group; each plan
+ * keeps its own schedule (its own t, episode boundaries, HIO/ER switch), so
+ * every plan computes exactly what cpra_iterate would (bit-identical).  With
+ * use_graph = 1 the launches of one cpra_batch_iterate call are captured
+ * once into a CUDA graph and replayed while the call pattern repeats.
+ * Paper: the reconstructions are independent (Steps A-B per guess and per
+ * object); this is a throughput form, not a step of the method.
+ * ------------------------------------------------------------------------ */
+typedef struct cpra_batch_s* cpra_batch_t;
+
+/* plans: n plans (n >= 1) on the same device, all using plans[0]'s stream.
+ * Plans must not use shrink-wrap (UNSUPPORTED) and must stay alive until
+ * cpra_batch_destroy.  The batch holds device tables only (a few KB). */
+cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_graph,
+                              cpra_batch_t* out);
+
+/* Advance every plan of the batch by n_iters iterations (NOT_READY if a plan
+ * lacks intensities).  Error histories are kept per plan. */
+cpra_status cpra_batch_iterate(cpra_batch_t batch, int32_t n_iters);
+
+/* Number of kernel launches one cpra_batch_iterate(n_iters) issues (or the
+ * graph holds); -1 for a NULL batch. */
+int64_t cpra_batch_launches(cpra_batch_t batch, int32_t n_iters);
+
+cpra_status cpra_batch_destroy(cpra_batch_t batch);
+
+/* Autotuner: time each engine available for N (TWO_PASS, WARP) on a sample
+ * of 64 random patterns with CUDA events on a private stream, and keep the
+ * fastest per (N, precision, SM count, device name) in a JSON cache file.
+ * cache_path NULL = $CPRA_TUNE_CACHE or $HOME/.cache/cpra_tune.json.  A
+ * cached entry is returned without timing.  *engine_out receives the engine,
+ * *ms_out (nullable) the measured or cached milliseconds per iteration of the
+ * sample. */
+cpra_status cpra_autotune(int32_t N, int32_t precision, const char* cache_path,
+                          int32_t* engine_out, double* ms_out);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of reconstructions while patterns stream in.
+ *
+ * A library-owned host thread admits submitted requests in order while the
+ * device's free memory minus the request's footprint (cpra_plan_bytes:
+ * iteration state + assembly) stays above hbm_reserve_bytes; prepares the
+ * patterns pushed for resident requests as they arrive; and advances every
+ * request whose angles have all arrived in rounds of iters_per_round
+ * iterations, all running requests together through one batch (see
+ * cpra_batch_create), so requests arriving while others run join at the
+ * next round.  After its first episode (n_ei iterations) a request gets a
+ * first 3D estimate (cpra_assemble_3d), after hio_iters + er_iters
+ * iterations its final volume.  Each request computes exactly what a
+ * standalone plan would.  The paper motivates this by reconstructing while
+ * the experiment runs ("concurrent partial reconstructions", concluding
+ * section); the serving loop itself has no counterpart in the paper.
+ * Times are seconds since cpra_server_start.
+ * ------------------------------------------------------------------------ */
+typedef struct cpra_server_s* cpra_server_t;
+
+typedef struct {
+  size_t hbm_reserve_bytes;  /* device memory left free (default 2 GiB)        */
+  int32_t max_active;        /* resident requests at most (0 = no limit)        */
+  int32_t iters_per_round;   /* iterations per batched round (default 10)       */
+  int32_t use_graph;         /* capture each round's launches in a CUDA graph   */
+  void* stream;              /* cudaStream_t of the serving thread (NULL = own) */
+} cpra_server_config;
+
+enum { CPRA_EVENT_FIRST_ESTIMATE = 1, CPRA_EVENT_FINAL = 2, CPRA_EVENT_FAILED = 3 };
+
+typedef struct {
+  int64_t id;
+  int32_t kind;            /* CPRA_EVENT_*                                 */
+  double t_event;          /* when it happened                             */
+  double t_submit;         /* when the request was submitted               */
+  double t_last_pattern;   /* when its latest pattern push arrived         */
+} cpra_server_event;
+
+typedef struct {
+  int32_t state;           /* 0 queued, 1 resident, 2 running, 3 done, 4 failed */
+  int64_t iterations_done;
+  int32_t angles_arrived;
+  double t_submit, t_admit, t_last_pattern, t_first_estimate, t_final;  /* -1 = not yet */
+} cpra_server_request;
+
+typedef struct {
+  int64_t submitted, admitted, completed, rounds, max_batch, angle_iterations;
+} cpra_server_stats;
+
+cpra_status cpra_server_default_config(cpra_server_config* cfg);
+/* Start the serving thread on the current device. */
+cpra_status cpra_server_start(const cpra_server_config* cfg, cpra_server_t* out);
+/* Queue a request (cfg is copied; shrink-wrap unsupported; the serving
+ * thread allocates with cudaMalloc, cfg->alloc is ignored). */
+cpra_status cpra_server_submit(cpra_server_t s, const cpra_config* cfg, int64_t* request_id);
+/* Stream count patterns [count][N][N] (host or device float32, centred) for
+ * angles first..first+count-1, with optional angles theta (host).  The data
+ * are copied before the call returns. */
+cpra_status cpra_server_push(cpra_server_t s, int64_t request_id, const float* I, int32_t first,
+                             int32_t count, const double* theta);
+/* Take up to max_events finished events (non-blocking); *got = how many. */
+cpra_status cpra_server_poll(cpra_server_t s, cpra_server_event* ev, int32_t max_events,
+                             int32_t* got);
+/* Block until the request is done (TIMEOUT after timeout_s seconds). */
+cpra_status cpra_server_wait(cpra_server_t s, int64_t request_id, double timeout_s);
+cpra_status cpra_server_request_info(cpra_server_t s, int64_t request_id, cpra_server_request* info);
+/* cpra_result of a finished request (NOT_READY before). */
+cpra_status cpra_server_result(cpra_server_t s, int64_t request_id, int32_t what, void* dst,
+                               size_t bytes);
+/* Free a finished request's device memory. */
+cpra_status cpra_server_release(cpra_server_t s, int64_t request_id);
+cpra_status cpra_server_get_stats(cpra_server_t s, cpra_server_stats* out);
+/* Stop the thread and free every request. */
+cpra_status cpra_server_stop(cpra_server_t s);
 
 /* Global iteration counter t of the plan (-1 for a NULL plan). */
 int64_t cpra_iteration(cpra_plan_t plan);

@@ -4,4 +4,4 @@ The compute lives in ``libcpra.so`` (hand-written sm_103a CUDA kernels behind
 the C ABI of ``include/cpra.h``); this package is its ctypes binding.
 """
 from .binding import *  # noqa: F401,F403
-from .binding import Plan, make_config, lib, CpraError  # noqa: F401
+from .binding import Plan, Batch, Server, make_config, lib, CpraError  # noqa: F401

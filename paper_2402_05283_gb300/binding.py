@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_READY, ERR_TIMEOUT, ER
 WRAP_LITERAL, WRAP_MIRROR = 0, 1
 BLEND_STATE, BLEND_OBJECT = 0, 1
 FP32, BF16_TC, FP16_TC = 0, 1, 2
-ENGINE_AUTO, ENGINE_TWO_PASS, ENGINE_FUSED, ENGINE_WARP = 0, 1, 2, 3
+ENGINE_AUTO, ENGINE_TWO_PASS, ENGINE_FUSED, ENGINE_WARP, ENGINE_TUNED = 0, 1, 2, 3, 4
 RESULT_PO, RESULT_STATE, RESULT_SUPPORT, RESULT_ERRORS, RESULT_VOLUME = range(5)
 (KERNEL_COLPASS, KERNEL_ROWPASS, KERNEL_PRIME, KERNEL_SHRINKWRAP, KERNEL_ASSEMBLE, KERNEL_FUSED,
  KERNEL_PREPARE, KERNEL_KINDS) = range(8)
@@ -40,6 +40,30 @@ class cpra_config(C.Structure):
         ("engine", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
         ("alloc_ctx", C.c_void_p),
     ]
+
+
+class cpra_server_config(C.Structure):
+    _fields_ = [("hbm_reserve_bytes", C.c_size_t), ("max_active", C.c_int32),
+                ("iters_per_round", C.c_int32), ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+
+
+class cpra_server_event(C.Structure):
+    _fields_ = [("id", C.c_int64), ("kind", C.c_int32), ("t_event", C.c_double),
+                ("t_submit", C.c_double), ("t_last_pattern", C.c_double)]
+
+
+class cpra_server_request(C.Structure):
+    _fields_ = [("state", C.c_int32), ("iterations_done", C.c_int64), ("angles_arrived", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_last_pattern", C.c_double),
+                ("t_first_estimate", C.c_double), ("t_final", C.c_double)]
+
+
+class cpra_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rounds", C.c_int64), ("max_batch", C.c_int64), ("angle_iterations", C.c_int64)]
+
+
+EVENT_FIRST_ESTIMATE, EVENT_FINAL, EVENT_FAILED = 1, 2, 3
 
 
 class CpraError(RuntimeError):
@@ -77,6 +101,24 @@ def lib() -> C.CDLL:
             "cpra_launch_count": (C.c_int64, []),
             "cpra_shrinkwrap_static": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_float,
                                                  C.c_float, P]),
+            "cpra_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]),
+            "cpra_batch_iterate": (C.c_int, [P, C.c_int32]),
+            "cpra_batch_launches": (C.c_int64, [P, C.c_int32]),
+            "cpra_batch_destroy": (C.c_int, [P]),
+            "cpra_autotune": (C.c_int, [C.c_int32, C.c_int32, C.c_char_p, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_double)]),
+            "cpra_server_default_config": (C.c_int, [C.POINTER(cpra_server_config)]),
+            "cpra_server_start": (C.c_int, [C.POINTER(cpra_server_config), C.POINTER(P)]),
+            "cpra_server_submit": (C.c_int, [P, C.POINTER(cpra_config), C.POINTER(C.c_int64)]),
+            "cpra_server_push": (C.c_int, [P, C.c_int64, P, C.c_int32, C.c_int32, P]),
+            "cpra_server_poll": (C.c_int, [P, C.POINTER(cpra_server_event), C.c_int32,
+                                           C.POINTER(C.c_int32)]),
+            "cpra_server_wait": (C.c_int, [P, C.c_int64, C.c_double]),
+            "cpra_server_request_info": (C.c_int, [P, C.c_int64, C.POINTER(cpra_server_request)]),
+            "cpra_server_result": (C.c_int, [P, C.c_int64, C.c_int32, P, C.c_size_t]),
+            "cpra_server_release": (C.c_int, [P, C.c_int64]),
+            "cpra_server_get_stats": (C.c_int, [P, C.POINTER(cpra_server_stats)]),
+            "cpra_server_stop": (C.c_int, [P]),
             "cpra_sync": (C.c_int, [P]),
             "cpra_destroy": (C.c_int, [P]),
             "cpra_last_error": (C.c_char_p, [P]),
@@ -198,6 +240,33 @@ def cpra_shrinkwrap_static(g, S_in, S_out, N: int, count: int, sigma: float, tau
     po, ko = _ptr(S_out)
     _check(lib().cpra_shrinkwrap_static(pg, ps, po, N, count, sigma, tau, stream))
     return kg, ks, ko
+
+
+def cpra_batch_create(plans, use_graph: bool = True):
+    hs = [p.h if isinstance(p, Plan) else p for p in plans]
+    arr = (C.c_void_p * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    out = C.c_void_p()
+    _check(lib().cpra_batch_create(arr, len(hs), int(bool(use_graph)), C.byref(out)))
+    return out
+
+
+def cpra_batch_iterate(batch, n_iters: int):
+    _check(lib().cpra_batch_iterate(batch, n_iters))
+
+
+def cpra_batch_launches(batch, n_iters: int) -> int:
+    return int(lib().cpra_batch_launches(batch, n_iters))
+
+
+def cpra_batch_destroy(batch):
+    _check(lib().cpra_batch_destroy(batch))
+
+
+def cpra_autotune(N: int, precision: int = FP32, cache_path: str | None = None):
+    eng, ms = C.c_int32(), C.c_double()
+    _check(lib().cpra_autotune(N, precision, cache_path.encode() if cache_path else None,
+                               C.byref(eng), C.byref(ms)))
+    return eng.value, ms.value
 
 
 def cpra_sync(plan):
@@ -337,5 +406,107 @@ class Plan:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several plans iterated together (one launch per kernel and size group)."""
+
+    def __init__(self, plans, use_graph: bool = True):
+        self.plans = list(plans)  # keep the plans alive
+        self.h = cpra_batch_create(self.plans, use_graph)
+
+    def iterate(self, n: int):
+        cpra_batch_iterate(self.h, n)
+
+    def launches(self, n: int) -> int:
+        return cpra_batch_launches(self.h, n)
+
+    def close(self):
+        if self.h:
+            cpra_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The library's serving thread (continuous batching of reconstructions)."""
+
+    def __init__(self, hbm_reserve_bytes=None, max_active=0, iters_per_round=10, use_graph=True):
+        cfg = cpra_server_config()
+        _check(lib().cpra_server_default_config(C.byref(cfg)))
+        if hbm_reserve_bytes is not None:
+            cfg.hbm_reserve_bytes = int(hbm_reserve_bytes)
+        cfg.max_active = max_active
+        cfg.iters_per_round = iters_per_round
+        cfg.use_graph = int(bool(use_graph))
+        self.h = C.c_void_p()
+        _check(lib().cpra_server_start(C.byref(cfg), C.byref(self.h)))
+        self.cfgs = {}
+
+    def submit(self, cfg: cpra_config) -> int:
+        rid = C.c_int64()
+        _check(lib().cpra_server_submit(self.h, C.byref(cfg), C.byref(rid)))
+        self.cfgs[rid.value] = (cfg.N, cfg.Np)
+        return rid.value
+
+    def push(self, rid: int, I, first: int, thetas=None):
+        p, keep = _ptr(I)
+        count = I.shape[0]
+        th = None if thetas is None else np.ascontiguousarray(thetas, dtype=np.float64)
+        _check(lib().cpra_server_push(self.h, rid, p, first, count,
+                                      None if th is None else th.ctypes.data))
+        del keep
+
+    def poll(self, max_events: int = 64):
+        evs = (cpra_server_event * max_events)()
+        got = C.c_int32()
+        _check(lib().cpra_server_poll(self.h, evs, max_events, C.byref(got)))
+        return [dict(id=e.id, kind=e.kind, t_event=e.t_event, t_submit=e.t_submit,
+                     t_last_pattern=e.t_last_pattern) for e in evs[:got.value]]
+
+    def wait(self, rid: int, timeout_s: float = 60.0):
+        _check(lib().cpra_server_wait(self.h, rid, timeout_s))
+
+    def info(self, rid: int) -> dict:
+        r = cpra_server_request()
+        _check(lib().cpra_server_request_info(self.h, rid, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in cpra_server_request._fields_}
+
+    def result(self, rid: int, what: int):
+        N, Np = self.cfgs[rid]
+        if what in (RESULT_PO, RESULT_STATE):
+            a = np.empty((Np, N, N), np.float32)
+        elif what == RESULT_VOLUME:
+            a = np.empty((N, N, N), np.complex64)
+        elif what == RESULT_SUPPORT:
+            a = np.empty((Np, N, N), np.uint8)
+        else:
+            raise ValueError(what)
+        _check(lib().cpra_server_result(self.h, rid, what, a.ctypes.data, a.nbytes))
+        return a
+
+    def release(self, rid: int):
+        _check(lib().cpra_server_release(self.h, rid))
+
+    def stats(self) -> dict:
+        st = cpra_server_stats()
+        _check(lib().cpra_server_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in cpra_server_stats._fields_}
+
+    def stop(self):
+        if self.h:
+            _check(lib().cpra_server_stop(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass

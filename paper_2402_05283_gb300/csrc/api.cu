@@ -2,8 +2,13 @@
 // schedule of Steps A and B, assembly (Step D) and results.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
+#include <string>
+#include <sys/stat.h>
 #include <vector>
 
 #include "cpra_internal.h"
@@ -128,7 +133,8 @@ cpra_status validate(const cpra_config* c, std::string& why) {
   }
   if (c->precision != CPRA_FP32) { why = "tensor-core precision not built into this engine"; return CPRA_ERR_UNSUPPORTED; }
   if (c->engine != CPRA_ENGINE_AUTO && c->engine != CPRA_ENGINE_TWO_PASS &&
-      c->engine != CPRA_ENGINE_FUSED && c->engine != CPRA_ENGINE_WARP) {
+      c->engine != CPRA_ENGINE_FUSED && c->engine != CPRA_ENGINE_WARP &&
+      c->engine != CPRA_ENGINE_TUNED) {
     why = "bad engine";
     return CPRA_ERR_INVALID_ARG;
   }
@@ -171,6 +177,8 @@ std::vector<float> gaussian_taps(int N, double sigma, int& ntaps) {
   return taps;
 }
 
+cpra_status upload_static(cpra_plan_s* p);
+
 cpra_status ensure_err_cap(cpra_plan_s* p, int64_t need) {
   if (need <= p->err_cap) return CPRA_OK;
   int64_t cap = p->err_cap > 0 ? p->err_cap : 256;
@@ -184,7 +192,7 @@ cpra_status ensure_err_cap(cpra_plan_s* p, int64_t need) {
   dev_free(p, p->err_hist);
   p->err_hist = nh;
   p->err_cap = cap;
-  return CPRA_OK;
+  return upload_static(p);
 }
 
 cpra_status copy_out(cpra_plan_s* p, void* dst, const void* src, size_t bytes) {
@@ -231,14 +239,76 @@ cudaError_t drain_timings(cpra_plan_s* p) {
   return cudaSuccess;
 }
 
-// Steps A/B scheduling helpers
-cpra_status prime_plain(cpra_plan_s* p, int first, int count) {
+// ---------------------------------------------------------------- job tables
+JobStatic job_static(const cpra_plan_s* p) {
+  JobStatic j{};
+  j.Hp = p->Hp;
+  j.A_main = p->A_main;
+  j.A_nyq = p->A_nyq;
+  j.Cn = p->Cn;
+  j.sumA2 = p->sumA2;
+  j.err_acc = p->err_acc;
+  j.S = p->S;
+  j.err_hist = p->err_hist;
+  j.tw = p->tw;
+  j.xtw = p->xtw;
+  j.Np = p->Np;
+  j.W = p->W;
+  j.beta = p->cfg.beta;
+  return j;
+}
+
+cpra_status upload_static(cpra_plan_s* p) {
+  JobStatic j = job_static(p);
+  CK(cudaMemcpyAsync(p->d_js, &j, sizeof(j), cudaMemcpyHostToDevice, p->stream), "job table");
+  return CPRA_OK;
+}
+
+CoupleArgs plain_args() {
   CoupleArgs ca{};
   ca.n_taps = 1;
   ca.alpha[0] = 1.0f;
-  CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(p, first, count, p->g, nullptr, p->Hp, ca); }),
-     "prime");
+  return ca;
+}
+
+CoupleArgs coupling_args(const cpra_config& c) {
+  CoupleArgs ca{};
+  ca.n_taps = c.n_taps;
+  for (int k = 0; k < c.n_taps; ++k) ca.alpha[k] = (float)c.alpha[k];
+  ca.mirror = c.wrap_mode == CPRA_WRAP_MIRROR;
+  ca.object = c.blend_target == CPRA_BLEND_OBJECT;
+  ca.store_g = 1;
+  return ca;
+}
+
+// Upload steps[] into the plan's step table (grown as needed).
+cpra_status upload_steps(cpra_plan_s* p, const std::vector<JobStep>& steps) {
+  if ((int64_t)steps.size() > p->steps_cap) {
+    int64_t cap = p->steps_cap > 0 ? p->steps_cap : 256;
+    while (cap < (int64_t)steps.size()) cap *= 2;
+    JobStep* ns = (JobStep*)dev_alloc(p, sizeof(JobStep) * cap);
+    if (!ns) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "step table allocation failed");
+    CK(cudaStreamSynchronize(p->stream), "step table sync");
+    dev_free(p, p->d_steps);
+    p->d_steps = ns;
+    p->steps_cap = cap;
+  }
+  if (!steps.empty())
+    CK(cudaMemcpyAsync(p->d_steps, steps.data(), sizeof(JobStep) * steps.size(),
+                       cudaMemcpyHostToDevice, p->stream), "step upload");
   return CPRA_OK;
+}
+
+Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles) {
+  Launch L;
+  L.N = p->N;
+  L.engine = p->engine;
+  L.stream = p->stream;
+  L.js = p->d_js;
+  L.st = p->d_steps + step;
+  L.tiles = p->d_tiles;
+  L.ntiles = ntiles;
+  return L;
 }
 
 cpra_status build_gridding(cpra_plan_s* p) {
@@ -369,6 +439,15 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
                (cfg->engine == CPRA_ENGINE_AUTO && fast_supported(cfg->N)))
                   ? CPRA_ENGINE_WARP
                   : CPRA_ENGINE_TWO_PASS;
+  if (cfg->engine == CPRA_ENGINE_TUNED) {
+    int32_t e = 0;
+    cpra_status ts = cpra_autotune(cfg->N, cfg->precision, nullptr, &e, nullptr);
+    if (ts != CPRA_OK) {
+      delete p;
+      return ts;
+    }
+    p->engine = e;
+  }
   p->loaded.assign(p->Np, 0);
   p->theta.resize(p->Np);
   for (int n = 0; n < p->Np; ++n) p->theta[n] = n * M_PI / p->Np;
@@ -392,6 +471,8 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   p->xtw = (float2*)A(N * 8);
   p->stage = (float*)A(Np * NN * 4);
   p->flag = (int*)A(sizeof(int) * 4);
+  p->d_js = (JobStatic*)A(sizeof(JobStatic));
+  p->d_tiles = (int2*)A(sizeof(int2) * Np);
   if (ok && cfg->shrinkwrap_every > 0) {
     std::vector<float> taps = gaussian_taps(p->N, cfg->sw_sigma, p->sw_ntaps);
     p->sw_tmp = (float*)A(Np * NN * 4);
@@ -425,6 +506,14 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
     e = cudaMemcpyAsync(p->xtw, xtw.data(), N * 8, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->err_acc, 0, Np * 8, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->g, 0, Np * NN * 4, p->stream);
+  std::vector<int2> tiles(Np);
+  for (size_t n = 0; n < Np; ++n) tiles[n] = make_int2(0, (int)n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * Np, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) {
+    JobStatic j = job_static(p);
+    e = cudaMemcpyAsync(p->d_js, &j, sizeof(j), cudaMemcpyHostToDevice, p->stream);
+  }
   if (e == cudaSuccess) e = launch_support_box(p);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) {
@@ -507,49 +596,72 @@ cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
   if (n_iters < 0) return fail(p, CPRA_ERR_INVALID_ARG, "n_iters < 0");
   if (p->n_loaded < p->Np) return fail(p, CPRA_ERR_NOT_READY, "not every angle has intensities");
   const cpra_config& c = p->cfg;
+  cpra_status st = ensure_err_cap(p, p->t + n_iters);
+  if (st != CPRA_OK) return st;
+  // the schedule of Steps A and B as one step-table row per iteration
+  std::vector<JobStep> steps;
+  const int n_pre = p->state_ready ? 0 : c.n_pre;
+  for (int i = 0; i < n_pre; ++i) {  // Step A: HIO on angle 0 alone
+    JobStep s{};
+    s.prime = 1;
+    s.ca = plain_args();
+    s.g_src = p->g;
+    s.g = p->g;
+    s.err_slot = -1;
+    s.algo = kHIO;
+    s.forward = 0;
+    s.active = 1;
+    steps.push_back(s);
+  }
+  float* gcur = p->g;
+  float* galt = p->g_alt;
+  bool hp = p->state_ready && p->hp_valid;
+  for (int i = 0; i < n_iters; ++i) {
+    const int64_t t = p->t + i;
+    JobStep s{};
+    if (t % c.n_ei == 0) {  // Eq. 4 at the episode start, Jacobi into the other buffer
+      s.prime = 1;
+      s.ca = coupling_args(c);
+      s.g_src = gcur;
+      s.g_dst = galt;
+      std::swap(gcur, galt);
+    } else if (!hp) {
+      s.prime = 1;
+      s.ca = plain_args();
+      s.g_src = gcur;
+    }
+    s.g = gcur;
+    s.err_slot = t;
+    s.algo = t < c.hio_iters ? kHIO : kER;
+    s.forward = ((t + 1) % c.n_ei) != 0;
+    s.active = 1;
+    hp = s.forward != 0;
+    steps.push_back(s);
+  }
+  st = upload_steps(p, steps);
+  if (st != CPRA_OK) return st;
   if (!p->state_ready) {
     CK(launch_init_guess(p), "initial guess");
-    for (int i = 0; i < c.n_pre; ++i) {  // Step A on angle 0
-      cpra_status st = prime_plain(p, 0, 1);
-      if (st != CPRA_OK) return st;
-      CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(p, 0, 1); }), "colpass");
-      CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(p, 0, 1, kHIO, -1, 0); }),
-         "rowpass");
+    for (int i = 0; i < n_pre; ++i) {
+      CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(plan_launch(p, i, 1)); }), "prime");
+      CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(plan_launch(p, i, 1)); }), "colpass");
+      CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(plan_launch(p, i, 1)); }), "rowpass");
     }
     p->state_ready = true;
     p->hp_valid = false;
   }
-  cpra_status st = ensure_err_cap(p, p->t + n_iters);
-  if (st != CPRA_OK) return st;
   const int64_t t0 = p->t;
-  const int r = c.n_taps / 2;
   for (int i = 0; i < n_iters; ++i) {
-    const int64_t t = p->t;
-    if (t % c.n_ei == 0) {
-      CoupleArgs ca{};
-      ca.n_taps = c.n_taps;
-      for (int k = 0; k < c.n_taps; ++k) ca.alpha[k] = (float)c.alpha[k];
-      ca.mirror = c.wrap_mode == CPRA_WRAP_MIRROR;
-      ca.object = c.blend_target == CPRA_BLEND_OBJECT;
-      ca.store_g = 1;
-      (void)r;
-      CK(timed(p, CPRA_KERNEL_PRIME,
-               [&] { return launch_prime(p, 0, p->Np, p->g, p->g_alt, p->Hp, ca); }),
-         "couple");
-      std::swap(p->g, p->g_alt);
-      p->hp_valid = true;
-    } else if (!p->hp_valid) {
-      st = prime_plain(p, 0, p->Np);
-      if (st != CPRA_OK) return st;
-      p->hp_valid = true;
+    const int64_t k = n_pre + i;
+    const JobStep& s = steps[k];
+    if (s.prime) {
+      CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(plan_launch(p, k, p->Np)); }), "prime");
+      if (s.ca.store_g) std::swap(p->g, p->g_alt);
     }
-    CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(p, 0, p->Np); }), "colpass");
-    const int algo = t < c.hio_iters ? kHIO : kER;
-    const int forward = ((t + 1) % c.n_ei) != 0;
-    CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(p, 0, p->Np, algo, t, forward); }),
-       "rowpass");
-    p->hp_valid = forward != 0;
-    if (c.shrinkwrap_every > 0 && (t + 1) % c.shrinkwrap_every == 0)
+    CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(plan_launch(p, k, p->Np)); }), "colpass");
+    CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(plan_launch(p, k, p->Np)); }), "rowpass");
+    p->hp_valid = s.forward != 0;
+    if (c.shrinkwrap_every > 0 && (p->t + 1) % c.shrinkwrap_every == 0)
       CK(timed(p, CPRA_KERNEL_SHRINKWRAP, [&] { return launch_shrinkwrap(p); }), "shrinkwrap");
     p->t++;
   }
@@ -578,7 +690,21 @@ cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
     cpra_status st = build_gridding(p);
     if (st != CPRA_OK) return st;
   }
-  CK(timed(p, CPRA_KERNEL_ASSEMBLE, [&] { return launch_assemble(p); }), "assemble");
+  {
+    JobStep s{};
+    s.prime = 1;
+    s.ca = plain_args();
+    s.ca.object = 1;  // R2C rows of rho = P_{S+} g
+    s.g_src = p->g;
+    s.g = p->g;
+    s.active = 1;
+    cpra_status st = upload_steps(p, std::vector<JobStep>{s});
+    if (st != CPRA_OK) return st;
+  }
+  CK(timed(p, CPRA_KERNEL_ASSEMBLE, [&] {
+       cudaError_t e = launch_prime(plan_launch(p, 0, p->Np));
+       return e == cudaSuccess ? launch_assemble(p) : e;
+     }), "assemble");
   p->asmb.ready = true;
   p->hp_valid = false;
   if (out) return copy_out(p, out, a.vol, N * NN * 8);
@@ -679,6 +805,426 @@ cpra_status cpra_destroy(cpra_plan_t p) {
 
 const char* cpra_last_error(cpra_plan_t p) {
   return p ? p->err.c_str() : g_last_error.c_str();
+}
+
+}  // extern "C"
+
+// ========================================================================
+// Batching: one launch per kernel and size group over all (plan, angle)
+// tiles, optionally captured into a CUDA graph.
+// ========================================================================
+struct cpra_batch_s {
+  struct Group {
+    int N = 0, engine = 0;
+    std::vector<int> members;
+    JobStatic* d_js = nullptr;
+    int2* d_tiles = nullptr;
+    int ntiles = 0;
+    JobStep* d_steps = nullptr;
+    int64_t steps_cap = 0;
+  };
+  std::vector<cpra_plan_s*> plans;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream the graph is captured on
+  bool use_graph = false;
+  std::vector<Group> groups;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<char> graph_sig;
+  int64_t graph_kernels = 0;
+  std::vector<void*> owned;
+  std::string err;
+};
+
+namespace {
+
+cpra_status bfail(cpra_batch_s* b, cpra_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  g_last_error = msg;
+  return st;
+}
+
+void* balloc(cpra_batch_s* b, size_t bytes) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  b->owned.push_back(q);
+  return q;
+}
+
+// One row of the step table for plan p at its current iteration; advances
+// the plan's host-side schedule state (t, coupling buffers, Hp validity).
+JobStep next_step(cpra_plan_s* p) {
+  const cpra_config& c = p->cfg;
+  const int64_t t = p->t;
+  JobStep s{};
+  if (t % c.n_ei == 0) {
+    s.prime = 1;
+    s.ca = coupling_args(c);
+    s.g_src = p->g;
+    s.g_dst = p->g_alt;
+    std::swap(p->g, p->g_alt);
+  } else if (!p->hp_valid) {
+    s.prime = 1;
+    s.ca = plain_args();
+    s.g_src = p->g;
+  }
+  s.g = p->g;
+  s.err_slot = t;
+  s.algo = t < c.hio_iters ? kHIO : kER;
+  s.forward = ((t + 1) % c.n_ei) != 0;
+  s.active = 1;
+  p->hp_valid = s.forward != 0;
+  p->t = t + 1;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_graph,
+                              cpra_batch_t* out) {
+  if (!out) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!plans || n < 1) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "need at least one plan");
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "NULL plan in batch");
+    if (plans[i]->cfg.shrinkwrap_every > 0)
+      return bfail(nullptr, CPRA_ERR_UNSUPPORTED, "batches run plans without shrink-wrap");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "plan listed twice");
+  }
+  cpra_batch_s* b = new (std::nothrow) cpra_batch_s();
+  if (!b) return bfail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "host allocation failed");
+  b->plans.assign(plans, plans + n);
+  b->stream = plans[0]->stream;
+  b->use_graph = use_graph != 0;
+  if (b->use_graph && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return bfail(nullptr, CPRA_ERR_CUDA, "batch capture stream");
+  }
+  for (int i = 0; i < n; ++i) {
+    cpra_plan_s* p = plans[i];
+    size_t gi = 0;
+    for (; gi < b->groups.size(); ++gi)
+      if (b->groups[gi].N == p->N && b->groups[gi].engine == p->engine) break;
+    if (gi == b->groups.size()) {
+      cpra_batch_s::Group g;
+      g.N = p->N;
+      g.engine = p->engine;
+      b->groups.push_back(g);
+    }
+    b->groups[gi].members.push_back(i);
+  }
+  for (auto& g : b->groups) {
+    std::vector<int2> tiles;
+    for (size_t j = 0; j < g.members.size(); ++j)
+      for (int a = 0; a < b->plans[g.members[j]]->Np; ++a) tiles.push_back(make_int2((int)j, a));
+    g.ntiles = (int)tiles.size();
+    g.d_js = (JobStatic*)balloc(b, sizeof(JobStatic) * g.members.size());
+    g.d_tiles = (int2*)balloc(b, sizeof(int2) * tiles.size());
+    if (!g.d_js || !g.d_tiles) {
+      cpra_batch_destroy(b);
+      return bfail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "batch tables");
+    }
+    cudaError_t e = cudaMemcpy(g.d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = prepare_kernels(g.N, g.engine);
+    if (e != cudaSuccess) {
+      cpra_batch_destroy(b);
+      return bfail(nullptr, CPRA_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+    }
+  }
+  *out = b;
+  return CPRA_OK;
+}
+
+cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
+  if (!b) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "batch is NULL");
+  if (n_iters < 0) return bfail(b, CPRA_ERR_INVALID_ARG, "n_iters < 0");
+  for (cpra_plan_s* p : b->plans)
+    if (p->n_loaded < p->Np) return bfail(b, CPRA_ERR_NOT_READY, "a plan lacks intensities");
+  for (cpra_plan_s* p : b->plans) {
+    if (!p->state_ready) {  // seeded start and Step A through the plan itself
+      cpra_status st = cpra_iterate(p, 0, nullptr);
+      if (st != CPRA_OK) return bfail(b, st, p->err);
+    }
+    cpra_status st = ensure_err_cap(p, p->t + n_iters);
+    if (st != CPRA_OK) return bfail(b, st, p->err);
+  }
+  if (n_iters == 0) return CPRA_OK;
+  cudaStream_t stream = b->stream;
+  // step tables (and the launch pattern) of every group for this call
+  const size_t G = b->groups.size();
+  std::vector<char> sig((size_t)n_iters * G, 0);
+  std::vector<std::vector<JobStep>> steps(G);
+  for (size_t gi = 0; gi < G; ++gi) steps[gi].resize((size_t)n_iters * b->groups[gi].members.size());
+  for (int i = 0; i < n_iters; ++i)
+    for (size_t gi = 0; gi < G; ++gi) {
+      auto& g = b->groups[gi];
+      const size_t m = g.members.size();
+      for (size_t j = 0; j < m; ++j) {
+        JobStep s = next_step(b->plans[g.members[j]]);
+        if (s.prime) sig[(size_t)i * G + gi] = 1;
+        steps[gi][(size_t)i * m + j] = s;
+      }
+    }
+  for (size_t gi = 0; gi < G; ++gi) {
+    auto& g = b->groups[gi];
+    std::vector<JobStatic> js;
+    for (int mi : g.members) js.push_back(job_static(b->plans[mi]));
+    cudaError_t e = cudaMemcpyAsync(g.d_js, js.data(), sizeof(JobStatic) * js.size(),
+                                    cudaMemcpyHostToDevice, stream);
+    const int64_t need = (int64_t)steps[gi].size();
+    if (e == cudaSuccess && need > g.steps_cap) {
+      e = cudaStreamSynchronize(stream);
+      if (e == cudaSuccess && g.d_steps) {
+        for (size_t k = 0; k < b->owned.size(); ++k)
+          if (b->owned[k] == g.d_steps) {
+            b->owned.erase(b->owned.begin() + k);
+            break;
+          }
+        cudaFree(g.d_steps);
+        g.d_steps = nullptr;
+        if (b->exec) {  // the graph points at the old table
+          cudaGraphExecDestroy(b->exec);
+          cudaGraphDestroy(b->graph);
+          b->exec = nullptr;
+          b->graph = nullptr;
+          b->graph_sig.clear();
+        }
+      }
+      g.d_steps = (JobStep*)balloc(b, sizeof(JobStep) * need);
+      if (!g.d_steps) return bfail(b, CPRA_ERR_OUT_OF_MEMORY, "batch step table");
+      g.steps_cap = need;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.d_steps, steps[gi].data(), sizeof(JobStep) * need,
+                          cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+  }
+  auto issue = [&](cudaStream_t on) -> cudaError_t {
+    int64_t kernels = 0;
+    for (int i = 0; i < n_iters; ++i)
+      for (size_t gi = 0; gi < G; ++gi) {
+        auto& g = b->groups[gi];
+        Launch L;
+        L.N = g.N;
+        L.engine = g.engine;
+        L.stream = on;
+        L.js = g.d_js;
+        L.st = g.d_steps + (size_t)i * g.members.size();
+        L.tiles = g.d_tiles;
+        L.ntiles = g.ntiles;
+        cudaError_t e = cudaSuccess;
+        if (sig[(size_t)i * G + gi]) {
+          e = launch_prime(L);
+          ++kernels;
+        }
+        if (e == cudaSuccess) e = launch_colpass(L);
+        if (e == cudaSuccess) e = launch_rowpass(L);
+        kernels += 2;
+        if (e != cudaSuccess) return e;
+      }
+    b->graph_kernels = kernels;
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  if (!b->use_graph) {
+    e = issue(stream);
+  } else {
+    if (!b->exec || b->graph_sig != sig) {
+      if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+      }
+      // captured on a private stream (the plans' stream may be the legacy
+      // default stream, which cannot be captured); launched on the plans' stream
+      e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t ei = issue(b->cap);
+        e = cudaStreamEndCapture(b->cap, &b->graph);
+        if (ei != cudaSuccess) e = ei;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, CPRA_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+      }
+      b->graph_sig = sig;
+    } else {
+      g_launches += b->graph_kernels;
+    }
+    e = cudaGraphLaunch(b->exec, stream);
+  }
+  if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  return CPRA_OK;
+}
+
+int64_t cpra_batch_launches(cpra_batch_t b, int32_t n_iters) {
+  if (!b) return -1;
+  int64_t k = 0;
+  for (auto& g : b->groups) {
+    (void)g;
+    k += 2 * (int64_t)n_iters;
+  }
+  // coupling launches: one per group at every iteration where a member primes
+  for (auto& g : b->groups) {
+    for (int i = 0; i < n_iters; ++i) {
+      bool any = false;
+      for (int mi : g.members) {
+        const cpra_plan_s* p = b->plans[mi];
+        const int64_t t = p->t + i;
+        if (t % p->cfg.n_ei == 0) any = true;
+      }
+      k += any ? 1 : 0;
+    }
+  }
+  return k;
+}
+
+cpra_status cpra_batch_destroy(cpra_batch_t b) {
+  if (!b) return CPRA_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (void* q : b->owned) cudaFree(q);
+  delete b;
+  return CPRA_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+
+std::string tune_path(const char* given) {
+  if (given && *given) return given;
+  const char* env = std::getenv("CPRA_TUNE_CACHE");
+  if (env && *env) return env;
+  const char* home = std::getenv("HOME");
+  std::string dir = std::string(home && *home ? home : "/tmp") + "/.cache";
+  mkdir(dir.c_str(), 0755);
+  return dir + "/cpra_tune.json";
+}
+
+std::vector<std::string> read_lines(const std::string& path) {
+  std::vector<std::string> out;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) out.push_back(line);
+  return out;
+}
+
+// time one engine: ms per iteration on 64 random patterns
+cpra_status time_engine(int N, int engine, double* ms) {
+  const int Np = 64;
+  cpra_config c;
+  cpra_default_config(N, Np, &c);
+  c.engine = engine;
+  c.hio_iters = 1 << 20;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "tune stream");
+  cpra_plan_t p = nullptr;
+  cpra_status s = cpra_plan(&c, st, &p);
+  std::vector<float> I((size_t)Np * N * N);
+  for (size_t i = 0; i < I.size(); ++i) {
+    uint64_t z = (uint64_t)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    I[i] = (float)((z >> 40) * (1.0 / 16777216.0)) * 100.0f;
+  }
+  cudaEvent_t a = nullptr, bq = nullptr;
+  if (s == CPRA_OK) s = cpra_load_intensities(p, I.data(), 0, Np, nullptr);
+  if (s == CPRA_OK) s = cpra_iterate(p, 3, nullptr);
+  if (s == CPRA_OK) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&bq);
+    cudaEventRecord(a, st);
+    s = cpra_iterate(p, 10, nullptr);
+    cudaEventRecord(bq, st);
+    cudaEventSynchronize(bq);
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, a, bq);
+    *ms = t / 10.0;
+  }
+  if (a) cudaEventDestroy(a);
+  if (bq) cudaEventDestroy(bq);
+  cpra_destroy(p);
+  cudaStreamDestroy(st);
+  return s;
+}
+
+}  // namespace
+
+cpra_status cpra_autotune(int32_t N, int32_t precision, const char* cache_path,
+                          int32_t* engine_out, double* ms_out) {
+  if (!engine_out) return fail(nullptr, CPRA_ERR_INVALID_ARG, "engine_out is NULL");
+  if (!n_supported(N)) return fail(nullptr, CPRA_ERR_UNSUPPORTED, "N not supported");
+  if (precision != CPRA_FP32) return fail(nullptr, CPRA_ERR_UNSUPPORTED, "tuning covers FP32 engines");
+  int dev = 0;
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
+  char key[512];
+  std::snprintf(key, sizeof(key), "N=%d,prec=%d,sms=%d,dev=%s", N, precision,
+                prop.multiProcessorCount, prop.name);
+  const std::string path = tune_path(cache_path);
+  std::vector<std::string> lines = read_lines(path);
+  const std::string needle = std::string("{\"key\": \"") + key + "\"";
+  for (const std::string& l : lines) {
+    if (l.rfind(needle, 0) == 0) {
+      int eng = 0;
+      double ms = 0.0;
+      const char* q = std::strstr(l.c_str(), "\"engine\": ");
+      const char* r = std::strstr(l.c_str(), "\"ms\": ");
+      if (q && std::sscanf(q, "\"engine\": %d", &eng) == 1) {
+        if (r) std::sscanf(r, "\"ms\": %lf", &ms);
+        *engine_out = eng;
+        if (ms_out) *ms_out = ms;
+        return CPRA_OK;
+      }
+    }
+  }
+  int best = CPRA_ENGINE_TWO_PASS;
+  double best_ms = 1e30;
+  std::ostringstream detail;
+  const int cands[2] = {CPRA_ENGINE_TWO_PASS, CPRA_ENGINE_WARP};
+  for (int cand : cands) {
+    if (cand == CPRA_ENGINE_WARP && !fast_supported(N)) continue;
+    double ms = 0.0;
+    cpra_status s = time_engine(N, cand, &ms);
+    if (s != CPRA_OK) return s;
+    detail << ", \"ms_engine_" << cand << "\": " << ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand;
+    }
+  }
+  std::ostringstream entry;
+  entry << needle << ", \"engine\": " << best << ", \"ms\": " << best_ms << detail.str() << "}";
+  std::vector<std::string> entries;
+  for (const std::string& l : lines)
+    if (l.rfind("{\"key\": ", 0) == 0) entries.push_back(l.back() == ',' ? l.substr(0, l.size() - 1) : l);
+  entries.push_back(entry.str());
+  std::ofstream f(path, std::ios::trunc);
+  if (f) {
+    f << "{\"cpra_tune_cache\": 1, \"entries\": [\n";
+    for (size_t i = 0; i < entries.size(); ++i)
+      f << entries[i] << (i + 1 < entries.size() ? ",\n" : "\n");
+    f << "]}\n";
+  }
+  *engine_out = best;
+  if (ms_out) *ms_out = best_ms;
+  return CPRA_OK;
 }
 
 }  // extern "C"

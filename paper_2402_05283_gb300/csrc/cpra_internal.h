@@ -24,6 +24,9 @@
 
 namespace cpra {
 
+struct JobStatic;
+struct JobStep;
+
 struct Assembly {
   float2* F = nullptr;        // [Np][N][N] z-transformed spectra, [n][ku][z]
   float2* vol = nullptr;      // [N][N][N] grid, then the centred volume
@@ -70,6 +73,11 @@ struct cpra_plan_s {
   int sw_ntaps = 0;
   float* po_tmp = nullptr;
   cpra::Assembly asmb;
+  // kernel tables of this plan as a one-job launch
+  cpra::JobStatic* d_js = nullptr;
+  int2* d_tiles = nullptr;
+  cpra::JobStep* d_steps = nullptr;
+  int64_t steps_cap = 0;
 
   // device-time profiling of launches (cpra_set_profiling)
   struct Timed { int kind; cudaEvent_t a, b; };
@@ -102,7 +110,7 @@ cudaError_t launch_bits_from_u8(uint32_t* bits, const uint8_t* src, int N, int c
 cudaError_t launch_bits_to_u8(const uint32_t* bits, uint8_t* out, int N, int count,
                               cudaStream_t st);
 
-// two-pass iteration (k_twopass.cu)
+// two-pass iteration (k_twopass.cu, k_fast.cu)
 struct CoupleArgs {
   int n_taps;        // 1 = no coupling
   float alpha[CPRA_MAX_TAPS];
@@ -110,11 +118,54 @@ struct CoupleArgs {
   int object;        // blend P_{S+} g instead of g
   int store_g;       // write the coupled rows to g_dst
 };
-cudaError_t launch_prime(cpra_plan_s* p, int first, int count, const float* g_src, float* g_dst,
-                         float2* Hp, const CoupleArgs& ca);
-cudaError_t launch_colpass(cpra_plan_s* p, int first, int count);
-cudaError_t launch_rowpass(cpra_plan_s* p, int first, int count, int algo, int64_t err_slot,
-                           int forward);
+
+// Per-reconstruction pointers and constants, read by the kernels from a
+// device table so that one launch can serve many reconstructions.
+struct JobStatic {
+  float2* Hp;
+  const float* A_main;
+  const float* A_nyq;
+  const double* Cn;
+  const double* sumA2;
+  double* err_acc;
+  const uint32_t* S;
+  double* err_hist;
+  const float2* tw;
+  const float2* xtw;
+  int Np, W;
+  float beta;
+  int pad;
+};
+
+// What one reconstruction does in one iteration (device table, one entry
+// per job per iteration).
+struct JobStep {
+  const float* g_src;  // prime: source stack (coupling reads the neighbours here)
+  float* g_dst;        // prime: coupled stack, written when ca.store_g
+  float* g;            // the iterate the row pass updates in place
+  long long err_slot;  // error-history row, -1 = none
+  int prime;           // run the prime kernel (coupling and/or row R2C)
+  int algo;            // kHIO / kER
+  int forward;         // row pass also computes the next row spectra
+  int active;          // 0: the column and row passes skip this job
+  CoupleArgs ca;
+};
+
+// One launch over ntiles (job, angle) tiles.
+struct Launch {
+  int N;
+  int engine;
+  cudaStream_t stream;
+  const JobStatic* js;
+  const JobStep* st;
+  const int2* tiles;
+  int ntiles;
+};
+
+cudaError_t prepare_kernels(int N, int engine);  // shared-memory attributes, before capture
+cudaError_t launch_prime(const Launch& L);
+cudaError_t launch_colpass(const Launch& L);
+cudaError_t launch_rowpass(const Launch& L);
 cudaError_t launch_shrinkwrap(cpra_plan_s* p);
 
 // assembly (k_assemble.cu)
@@ -125,11 +176,10 @@ bool n_supported(int N);
 // two-pass engine with warp-resident FFTs (k_fast.cu)
 bool fast_supported(int N);
 bool fast_dims(int N, int* E1, int* E2);
-cudaError_t launch_rowpass_fast(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
-                                int forward);
-cudaError_t launch_prime_fast(cpra_plan_s* p, int first, int count, const float* src, float* dst,
-                              float2* Hp, const CoupleArgs& ca);
-cudaError_t launch_colpass_fast(cpra_plan_s* p, int first, int count);
+cudaError_t prepare_kernels_fast(int N);
+cudaError_t launch_rowpass_fast(const Launch& L);
+cudaError_t launch_prime_fast(const Launch& L);
+cudaError_t launch_colpass_fast(const Launch& L);
 
 // records a failure of a call without a plan (cpra_last_error(NULL))
 cpra_status record_error(cpra_status st, const std::string& msg);

@@ -217,20 +217,12 @@ static cudaError_t assemble_n(cpra_plan_s* p) {
   Assembly& a = p->asmb;
   const int Np = p->Np;
   cudaError_t e;
-  // rho and its moments, then R2C rows of rho into Hp
+  // moments of rho; the caller has put the R2C rows of rho into Hp
   e = cudaMemsetAsync(a.moments, 0, sizeof(double) * 3 * Np, st);
   if (e != cudaSuccess) return e;
   const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
-  g_launches += 5;  // moments, spectra, gather, rows, columns (+ prime)
+  g_launches += 5;  // moments, spectra, gather, rows, columns
   k_moments<<<dim3(N, Np), threads, 0, st>>>(p->g, p->S, a.moments, N, p->W);
-  CoupleArgs ca{};
-  ca.n_taps = 1;
-  ca.alpha[0] = 1.0f;
-  ca.object = 1;
-  ca.store_g = 0;
-  e = launch_prime(p, 0, Np, p->g, nullptr, p->Hp, ca);
-  if (e != cudaSuccess) return e;
-  p->hp_valid = false;
   {
     using T = SpecTile<N>;
     const size_t smem = sizeof(float2) * (N + N * T::B + N * T::PI + N + 2 * T::B);

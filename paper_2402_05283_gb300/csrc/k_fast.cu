@@ -76,19 +76,33 @@ __device__ __forceinline__ void store_pairs_w(float2 (&b)[WP<N>::TB][WP<N>::E2],
 // ---------------------------------------------------------------- row pass
 template <int N>
 __global__ void __launch_bounds__(kRowWarps * 32, 3)
-k_rowpass_w(float* g, float2* Hp, const uint32_t* __restrict__ S, double* err_acc,
-            const double* __restrict__ Cn, const double* __restrict__ sumA2, double* err_hist,
-            long long err_slot, const float2* __restrict__ xtw, int Np, int first, int W,
-            float beta, int algo, int forward) {
+k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+            const int2* __restrict__ tiles) {
   using P = WP<N>;
   using RW = RowW<N>;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
+  const int2 tl = tiles[blockIdx.y];
+  const JobStatic* J = js + tl.x;
+  const JobStep* Z = st + tl.x;
+  if (!Z->active) return;
+  float* g = Z->g;
+  float2* Hp = J->Hp;
+  const uint32_t* __restrict__ S = J->S;
+  double* err_acc = J->err_acc;
+  const double* __restrict__ Cn = J->Cn;
+  const double* __restrict__ sumA2 = J->sumA2;
+  double* err_hist = J->err_hist;
+  const long long err_slot = Z->err_slot;
+  const float2* __restrict__ xtw = J->xtw;
+  const int Np = J->Np, W = J->W;
+  const float beta = J->beta;
+  const int algo = Z->algo, forward = Z->forward;
   float2* xs = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* T = smem + N + warp * RW::WARP_F2;
   float* Gs = reinterpret_cast<float*>(T + P::TSIZE);  // this warp's 2L rows of g
-  const int n = first + blockIdx.y;
+  const int n = tl.y;
   const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
   float* grow = g + ((size_t)n * N + 2 * pair0) * N;  // 2L contiguous rows
   // prefetch the old iterate; it is needed only after the inverse FFT
@@ -168,17 +182,27 @@ k_rowpass_w(float* g, float2* Hp, const uint32_t* __restrict__ S, double* err_ac
 // ---------------------------------------------------------------- prime
 template <int N>
 __global__ void __launch_bounds__(kRowWarps * 32, 3)
-k_prime_w(const float* __restrict__ g_src, float* __restrict__ g_dst, float2* Hp,
-          const uint32_t* __restrict__ S, const float2* __restrict__ xtw, int Np, int first, int W,
-          CoupleArgs ca) {
+k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+          const int2* __restrict__ tiles) {
   using P = WP<N>;
   using RW = RowW<N>;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
+  const int2 tl = tiles[blockIdx.y];
+  const JobStatic* J = js + tl.x;
+  const JobStep* Z = st + tl.x;
+  if (!Z->prime) return;
+  const float* __restrict__ g_src = Z->g_src;
+  float* __restrict__ g_dst = Z->ca.store_g ? Z->g_dst : nullptr;
+  float2* Hp = J->Hp;
+  const uint32_t* __restrict__ S = J->S;
+  const float2* __restrict__ xtw = J->xtw;
+  const int Np = J->Np, W = J->W;
+  const CoupleArgs& ca = Z->ca;
   float2* xs = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* T = smem + N + warp * RW::WARP_F2;
-  const int n = first + blockIdx.y;
+  const int n = tl.y;
   const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
   __shared__ const float* tap_src[CPRA_MAX_TAPS];
   __shared__ const uint32_t* tap_s[CPRA_MAX_TAPS];
@@ -279,19 +303,27 @@ __device__ __forceinline__ float2 project_w(float2 G, float a, float& err, float
 
 template <int N>
 __global__ void __launch_bounds__(ColW<N>::NT, ColW<N>::NT <= 256 ? 2 : 1)
-k_colpass_w(float2* Hp, const float* __restrict__ A_T, const float* __restrict__ A_nyq,
-            double* err_acc, const float2* __restrict__ xtw, int first) {
+k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+            const int2* __restrict__ tiles) {
   using P = WP<N>;
   using C = ColW<N>;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
+  const int2 tl = tiles[blockIdx.y];
+  const JobStatic* J = js + tl.x;
+  if (!st[tl.x].active) return;
+  float2* Hp = J->Hp;
+  const float* __restrict__ A_T = J->A_main;
+  const float* __restrict__ A_nyq = J->A_nyq;
+  double* err_acc = J->err_acc;
+  const float2* __restrict__ xtw = J->xtw;
   float2* xs = smem;
   float2* buf = smem + N;  // staging, then the warps' transpose tiles
   __shared__ double red[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* As = reinterpret_cast<float*>(buf + C::BUF);  // A_sym of the block, [c][ky]
   float2* T = buf + warp * P::TSIZE;
-  const int n = first + blockIdx.y;
+  const int n = tl.y;
   const int c0 = blockIdx.x * kColB;
   float2* Hn = Hp + (size_t)n * N * H;
   for (int idx = threadIdx.x; idx < N * kColB; idx += C::NT) {
@@ -405,55 +437,49 @@ static cudaError_t smem_attr(K kernel, size_t bytes) {
 }
 
 template <int N>
-static cudaError_t rowpass_w(cpra_plan_s* p, int first, int count, int algo, int64_t slot, int fwd) {
+static cudaError_t prepare_w() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = smem_attr(k_rowpass_w<N>, RowW<N>::SMEM);
+  if (e == cudaSuccess) e = smem_attr(k_prime_w<N>, RowW<N>::SMEM);
+  if (e == cudaSuccess) e = smem_attr(k_colpass_w<N>, ColW<N>::SMEM);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int N>
+static cudaError_t rowpass_w(const Launch& L) {
   using P = WP<N>;
   const size_t smem = RowW<N>::SMEM;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = smem_attr(k_rowpass_w<N>, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  dim3 grid((N / 2) / (kRowWarps * P::L), count);
+  cudaError_t e = prepare_w<N>();
+  if (e != cudaSuccess) return e;
+  dim3 grid((N / 2) / (kRowWarps * P::L), L.ntiles);
   g_launches += 1;
-  k_rowpass_w<N><<<grid, kRowWarps * 32, smem, p->stream>>>(
-      p->g, p->Hp, p->S, p->err_acc, p->Cn, p->sumA2, p->err_hist, (long long)slot, p->xtw, p->Np,
-      first, p->W, p->cfg.beta, algo, fwd);
+  k_rowpass_w<N><<<grid, kRowWarps * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 
 template <int N>
-static cudaError_t prime_w(cpra_plan_s* p, int first, int count, const float* src, float* dst,
-                           float2* Hp, const CoupleArgs& ca) {
+static cudaError_t prime_w(const Launch& L) {
   using P = WP<N>;
   const size_t smem = RowW<N>::SMEM;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = smem_attr(k_prime_w<N>, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  dim3 grid((N / 2) / (kRowWarps * P::L), count);
+  cudaError_t e = prepare_w<N>();
+  if (e != cudaSuccess) return e;
+  dim3 grid((N / 2) / (kRowWarps * P::L), L.ntiles);
   g_launches += 1;
-  k_prime_w<N><<<grid, kRowWarps * 32, smem, p->stream>>>(src, ca.store_g ? dst : nullptr, Hp, p->S,
-                                                          p->xtw, p->Np, first, p->W, ca);
+  k_prime_w<N><<<grid, kRowWarps * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 
 template <int N>
-static cudaError_t colpass_w(cpra_plan_s* p, int first, int count) {
+static cudaError_t colpass_w(const Launch& L) {
   using C = ColW<N>;
   const size_t smem = C::SMEM;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = smem_attr(k_colpass_w<N>, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  dim3 grid((N / 2) / kColB, count);
+  cudaError_t e = prepare_w<N>();
+  if (e != cudaSuccess) return e;
+  dim3 grid((N / 2) / kColB, L.ntiles);
   g_launches += 1;
-  k_colpass_w<N><<<grid, C::NT, smem, p->stream>>>(p->Hp, p->A_main, p->A_nyq, p->err_acc, p->xtw,
-                                                   first);
+  k_colpass_w<N><<<grid, C::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 
@@ -484,11 +510,10 @@ bool fast_dims(int N, int* E1, int* E2) {
   }
 }
 
-cudaError_t launch_rowpass_fast(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
-                                int fwd) {
-  switch (p->N) {
+cudaError_t prepare_kernels_fast(int N) {
+  switch (N) {
 #define CPRA_CASE(NN) \
-  case NN: return rowpass_w<NN>(p, first, count, algo, slot, fwd);
+  case NN: return prepare_w<NN>();
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
@@ -496,11 +521,10 @@ cudaError_t launch_rowpass_fast(cpra_plan_s* p, int first, int count, int algo, 
   }
 }
 
-cudaError_t launch_prime_fast(cpra_plan_s* p, int first, int count, const float* src, float* dst,
-                              float2* Hp, const CoupleArgs& ca) {
-  switch (p->N) {
+cudaError_t launch_rowpass_fast(const Launch& L) {
+  switch (L.N) {
 #define CPRA_CASE(NN) \
-  case NN: return prime_w<NN>(p, first, count, src, dst, Hp, ca);
+  case NN: return rowpass_w<NN>(L);
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
@@ -508,10 +532,21 @@ cudaError_t launch_prime_fast(cpra_plan_s* p, int first, int count, const float*
   }
 }
 
-cudaError_t launch_colpass_fast(cpra_plan_s* p, int first, int count) {
-  switch (p->N) {
+cudaError_t launch_prime_fast(const Launch& L) {
+  switch (L.N) {
 #define CPRA_CASE(NN) \
-  case NN: return colpass_w<NN>(p, first, count);
+  case NN: return prime_w<NN>(L);
+    CPRA_FOR_EACH_FAST_N(CPRA_CASE)
+#undef CPRA_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_colpass_fast(const Launch& L) {
+  switch (L.N) {
+#define CPRA_CASE(NN) \
+  case NN: return colpass_w<NN>(L);
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
 #undef CPRA_CASE
     default:

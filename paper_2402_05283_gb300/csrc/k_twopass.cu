@@ -49,14 +49,25 @@ __device__ __forceinline__ void load_twiddles(float2* tw_s, const float2* tw) {
 // asked, then R2C of each row pair into Hp.
 template <int N>
 __global__ void __launch_bounds__(RowTile<N>::NT)
-k_prime(const float* __restrict__ g_src, float* g_dst, float2* Hp, const uint32_t* __restrict__ S,
-        const float2* __restrict__ tw, int Np, int first, int W, CoupleArgs ca) {
+k_prime(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+        const int2* __restrict__ tiles) {
   using T = RowTile<N>;
   constexpr int P = T::P, PI = T::PI, NT = T::NT;
   extern __shared__ float2 smem[];
+  const int2 tl = tiles[blockIdx.y];
+  const JobStatic* J = js + tl.x;
+  const JobStep* Z = st + tl.x;
+  if (!Z->prime) return;
+  const float* __restrict__ g_src = Z->g_src;
+  float* g_dst = Z->g_dst;
+  float2* Hp = J->Hp;
+  const uint32_t* __restrict__ S = J->S;
+  const float2* __restrict__ tw = J->tw;
+  const int Np = J->Np, W = J->W;
+  const CoupleArgs ca = Z->ca;
   float2* tw_s = smem;
   float2* buf = smem + N;
-  const int n = first + blockIdx.y;
+  const int n = tl.y;
   const int y0 = blockIdx.x * 2 * P;
   load_twiddles<N>(tw_s, tw);
   const int r = ca.n_taps / 2;
@@ -116,15 +127,23 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 template <int N>
 __global__ void __launch_bounds__(ColTile<N>::NT)
-k_colpass(float2* Hp, const float* __restrict__ A_main, const float* __restrict__ A_nyq,
-          double* err_acc, const float2* __restrict__ tw, int first) {
+k_colpass(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+          const int2* __restrict__ tiles) {
   using T = ColTile<N>;
   constexpr int B = T::B, NT = T::NT, H = N / 2;
   extern __shared__ float2 smem[];
+  const int2 tl = tiles[blockIdx.y];
+  const JobStatic* J = js + tl.x;
+  if (!st[tl.x].active) return;
+  float2* Hp = J->Hp;
+  const float* __restrict__ A_main = J->A_main;
+  const float* __restrict__ A_nyq = J->A_nyq;
+  double* err_acc = J->err_acc;
+  const float2* __restrict__ tw = J->tw;
   float2* tw_s = smem;
   float2* buf = smem + N;
   __shared__ double red[32];
-  const int n = first + blockIdx.y;
+  const int n = tl.y;
   const int c0 = blockIdx.x * B;
   float2* Hn = Hp + (size_t)n * N * H;
   load_twiddles<N>(tw_s, tw);
@@ -170,16 +189,30 @@ k_colpass(float2* Hp, const float* __restrict__ A_main, const float* __restrict_
 // ---------------------------------------------------------------- row pass
 template <int N>
 __global__ void __launch_bounds__(RowTile<N>::NT)
-k_rowpass(float* g, float2* Hp, const uint32_t* __restrict__ S, double* err_acc,
-          const double* __restrict__ Cn, const double* __restrict__ sumA2, double* err_hist,
-          long long err_slot, const float2* __restrict__ tw, int Np, int first, int W, float beta,
-          int algo, int forward) {
+k_rowpass(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+          const int2* __restrict__ tiles) {
   using T = RowTile<N>;
   constexpr int P = T::P, PI = T::PI, NT = T::NT, H = N / 2;
   extern __shared__ float2 smem[];
+  const int2 tl = tiles[blockIdx.y];
+  const JobStatic* J = js + tl.x;
+  const JobStep* Z = st + tl.x;
+  if (!Z->active) return;
+  float* g = Z->g;
+  float2* Hp = J->Hp;
+  const uint32_t* __restrict__ S = J->S;
+  double* err_acc = J->err_acc;
+  const double* __restrict__ Cn = J->Cn;
+  const double* __restrict__ sumA2 = J->sumA2;
+  double* err_hist = J->err_hist;
+  const long long err_slot = Z->err_slot;
+  const float2* __restrict__ tw = J->tw;
+  const int Np = J->Np, W = J->W;
+  const float beta = J->beta;
+  const int algo = Z->algo, forward = Z->forward;
   float2* tw_s = smem;
   float2* buf = smem + N;
-  const int n = first + blockIdx.y;
+  const int n = tl.y;
   const int y0 = blockIdx.x * 2 * P;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // the column pass of this iteration is complete: publish E_F, reset
@@ -230,85 +263,88 @@ k_rowpass(float* g, float2* Hp, const uint32_t* __restrict__ S, double* err_acc,
 }
 
 // ---------------------------------------------------------------- launchers
+template <class K>
+static cudaError_t set_smem_once(K kernel, size_t bytes, bool& done) {
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 template <int N>
-static cudaError_t prime_n(cpra_plan_s* p, int first, int count, const float* src, float* dst,
-                           float2* Hp, const CoupleArgs& ca) {
+static cudaError_t prepare_n();
+
+template <int N>
+static cudaError_t prime_n(const Launch& L) {
   using T = RowTile<N>;
   const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_prime<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  dim3 grid(N / (2 * T::P), count);
+  cudaError_t e = prepare_n<N>();
+  if (e != cudaSuccess) return e;
   g_launches += 1;
-  k_prime<N><<<grid, T::NT, smem, p->stream>>>(src, dst, Hp, p->S, p->tw, p->Np, first, p->W, ca);
+  k_prime<N><<<dim3(N / (2 * T::P), L.ntiles), T::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 
 template <int N>
-static cudaError_t colpass_n(cpra_plan_s* p, int first, int count) {
+static cudaError_t colpass_n(const Launch& L) {
   using T = ColTile<N>;
   const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_colpass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  dim3 grid((N / 2) / T::B, count);
+  cudaError_t e = prepare_n<N>();
+  if (e != cudaSuccess) return e;
   g_launches += 1;
-  k_colpass<N><<<grid, T::NT, smem, p->stream>>>(p->Hp, p->A_main, p->A_nyq, p->err_acc, p->tw,
-                                                 first);
+  k_colpass<N><<<dim3((N / 2) / T::B, L.ntiles), T::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 
 template <int N>
-static cudaError_t rowpass_n(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
-                             int forward) {
+static cudaError_t rowpass_n(const Launch& L) {
   using T = RowTile<N>;
   const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_rowpass<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  dim3 grid(N / (2 * T::P), count);
+  cudaError_t e = prepare_n<N>();
+  if (e != cudaSuccess) return e;
   g_launches += 1;
-  k_rowpass<N><<<grid, T::NT, smem, p->stream>>>(p->g, p->Hp, p->S, p->err_acc, p->Cn, p->sumA2,
-                                                 p->err_hist, (long long)slot, p->tw, p->Np, first,
-                                                 p->W, p->cfg.beta, algo, forward);
+  k_rowpass<N><<<dim3(N / (2 * T::P), L.ntiles), T::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prime(cpra_plan_s* p, int first, int count, const float* src, float* dst,
-                         float2* Hp, const CoupleArgs& ca) {
-  if (p->engine == CPRA_ENGINE_WARP) return launch_prime_fast(p, first, count, src, dst, Hp, ca);
+template <int N>
+static cudaError_t prepare_n() {
+  static bool a1 = false, a2 = false, a3 = false;
+  cudaError_t e = set_smem_once(k_prime<N>, sizeof(float2) * (N + RowTile<N>::SMEM_LINES), a1);
+  if (e == cudaSuccess) e = set_smem_once(k_colpass<N>, sizeof(float2) * (N + ColTile<N>::SMEM_LINES), a2);
+  if (e == cudaSuccess) e = set_smem_once(k_rowpass<N>, sizeof(float2) * (N + RowTile<N>::SMEM_LINES), a3);
+  return e;
+}
+
+cudaError_t prepare_kernels(int N, int engine) {
+  if (engine == CPRA_ENGINE_WARP) return prepare_kernels_fast(N);
 #define CPRA_CASE(NN) \
-  case NN: return prime_n<NN>(p, first, count, src, dst, Hp, ca);
-  switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+  case NN: return prepare_n<NN>();
+  switch (N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
 #undef CPRA_CASE
 }
 
-cudaError_t launch_colpass(cpra_plan_s* p, int first, int count) {
-  if (p->engine == CPRA_ENGINE_WARP) return launch_colpass_fast(p, first, count);
+cudaError_t launch_prime(const Launch& L) {
+  if (L.engine == CPRA_ENGINE_WARP) return launch_prime_fast(L);
 #define CPRA_CASE(NN) \
-  case NN: return colpass_n<NN>(p, first, count);
-  switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+  case NN: return prime_n<NN>(L);
+  switch (L.N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
 #undef CPRA_CASE
 }
 
-cudaError_t launch_rowpass(cpra_plan_s* p, int first, int count, int algo, int64_t slot,
-                           int forward) {
-  if (p->engine == CPRA_ENGINE_WARP) return launch_rowpass_fast(p, first, count, algo, slot, forward);
+cudaError_t launch_colpass(const Launch& L) {
+  if (L.engine == CPRA_ENGINE_WARP) return launch_colpass_fast(L);
 #define CPRA_CASE(NN) \
-  case NN: return rowpass_n<NN>(p, first, count, algo, slot, forward);
-  switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+  case NN: return colpass_n<NN>(L);
+  switch (L.N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+#undef CPRA_CASE
+}
+
+cudaError_t launch_rowpass(const Launch& L) {
+  if (L.engine == CPRA_ENGINE_WARP) return launch_rowpass_fast(L);
+#define CPRA_CASE(NN) \
+  case NN: return rowpass_n<NN>(L);
+  switch (L.N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
 #undef CPRA_CASE
 }
 
