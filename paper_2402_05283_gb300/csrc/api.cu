@@ -11,6 +11,9 @@
 #include <sys/stat.h>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "cpra_internal.h"
 #include "tiling.cuh"
 
@@ -131,7 +134,11 @@ cpra_status validate(const cpra_config* c, std::string& why) {
     why = "bad precision";
     return CPRA_ERR_INVALID_ARG;
   }
-  if (c->precision != CPRA_FP32) { why = "tensor-core precision not built into this engine"; return CPRA_ERR_UNSUPPORTED; }
+  if (c->precision != CPRA_FP32 &&
+      !(fast_supported(c->N) && (c->engine == CPRA_ENGINE_AUTO || c->engine == CPRA_ENGINE_WARP))) {
+    why = "tensor-core precision runs on the warp engine (N in {64, 128, 256, 512, 1024})";
+    return CPRA_ERR_UNSUPPORTED;
+  }
   if (c->engine != CPRA_ENGINE_AUTO && c->engine != CPRA_ENGINE_TWO_PASS &&
       c->engine != CPRA_ENGINE_FUSED && c->engine != CPRA_ENGINE_WARP &&
       c->engine != CPRA_ENGINE_TUNED) {
@@ -252,6 +259,7 @@ JobStatic job_static(const cpra_plan_s* p) {
   j.err_hist = p->err_hist;
   j.tw = p->tw;
   j.xtw = p->xtw;
+  j.tcw = p->tcw;
   j.Np = p->Np;
   j.W = p->W;
   j.beta = p->cfg.beta;
@@ -303,6 +311,7 @@ Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles) {
   Launch L;
   L.N = p->N;
   L.engine = p->engine;
+  L.prec = p->cfg.precision;
   L.stream = p->stream;
   L.js = p->d_js;
   L.st = p->d_steps + step;
@@ -504,6 +513,47 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   cudaError_t e = cudaMemcpyAsync(p->tw, tw.data(), N * 8, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->xtw, xtw.data(), N * 8, cudaMemcpyHostToDevice, p->stream);
+  std::vector<uint16_t> tcw;
+  if (cfg->precision != CPRA_FP32) {
+    // block DFT matrices [[Re W, Im W], [-Im W, Re W]] of the E1- and
+    // E2-point DFTs, forward and inverse, stored [n][k] with pitch 2E + 8,
+    // FP64 then rounded once to BF16 / FP16
+    for (int which = 0; which < 2; ++which)
+      for (int dir = -1; dir <= 1; dir += 2) {
+        const int E = which == 0 ? E1 : E2;
+        const int K = 2 * E, P = 2 * E + 8;
+        std::vector<uint16_t> m((size_t)K * P, 0);
+        for (int j = 0; j < E; ++j)
+          for (int k = 0; k < E; ++k) {
+            const double a = dir * 2.0 * M_PI * (double)((j * k) % E) / (double)E;
+            const double wr = std::cos(a), wi = std::sin(a);
+            const double B[2][2] = {{wr, wi}, {-wi, wr}};  // [input half][output half]
+            for (int hi = 0; hi < 2; ++hi)
+              for (int ho = 0; ho < 2; ++ho) {
+                const int kk = hi * E + j;  // GEMM depth index
+                const int nn = ho * E + k;  // GEMM column index
+                const float v = (float)B[hi][ho];
+                uint16_t bits;
+                if (cfg->precision == CPRA_BF16_TC) {
+                  __nv_bfloat16 h = __float2bfloat16_rn(v);
+                  std::memcpy(&bits, &h, 2);
+                } else {
+                  __half h = __float2half_rn(v);
+                  std::memcpy(&bits, &h, 2);
+                }
+                m[(size_t)nn * P + kk] = bits;
+              }
+          }
+        tcw.insert(tcw.end(), m.begin(), m.end());
+      }
+    p->tcw = (uint16_t*)dev_alloc(p, tcw.size() * 2);
+    if (!p->tcw) {
+      cpra_destroy(p);
+      return fail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "device allocation failed");
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->tcw, tcw.data(), tcw.size() * 2, cudaMemcpyHostToDevice, p->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(p->err_acc, 0, Np * 8, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->g, 0, Np * NN * 4, p->stream);
   std::vector<int2> tiles(Np);
@@ -815,7 +865,7 @@ const char* cpra_last_error(cpra_plan_t p) {
 // ========================================================================
 struct cpra_batch_s {
   struct Group {
-    int N = 0, engine = 0;
+    int N = 0, engine = 0, prec = 0;
     std::vector<int> members;
     JobStatic* d_js = nullptr;
     int2* d_tiles = nullptr;
@@ -911,11 +961,14 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
     cpra_plan_s* p = plans[i];
     size_t gi = 0;
     for (; gi < b->groups.size(); ++gi)
-      if (b->groups[gi].N == p->N && b->groups[gi].engine == p->engine) break;
+      if (b->groups[gi].N == p->N && b->groups[gi].engine == p->engine &&
+          b->groups[gi].prec == p->cfg.precision)
+        break;
     if (gi == b->groups.size()) {
       cpra_batch_s::Group g;
       g.N = p->N;
       g.engine = p->engine;
+      g.prec = p->cfg.precision;
       b->groups.push_back(g);
     }
     b->groups[gi].members.push_back(i);
@@ -933,7 +986,7 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
     }
     cudaError_t e = cudaMemcpy(g.d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
                                cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = prepare_kernels(g.N, g.engine);
+    if (e == cudaSuccess) e = prepare_kernels(g.N, g.engine, g.prec);
     if (e != cudaSuccess) {
       cpra_batch_destroy(b);
       return bfail(nullptr, CPRA_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
@@ -1015,6 +1068,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
         Launch L;
         L.N = g.N;
         L.engine = g.engine;
+        L.prec = g.prec;
         L.stream = on;
         L.js = g.d_js;
         L.st = g.d_steps + (size_t)i * g.members.size();

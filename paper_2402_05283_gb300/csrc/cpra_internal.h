@@ -65,6 +65,7 @@ struct cpra_plan_s {
   int64_t err_cap = 0;
   float2* tw = nullptr;        // forward twiddles exp(-2 pi i k/N)
   float2* xtw = nullptr;       // warp-FFT cross twiddles, [k1][l] = exp(-2 pi i l k1/N)
+  uint16_t* tcw = nullptr;     // tensor-core DFT matrices (BF16 / FP16 precision)
   float* stage = nullptr;      // staging for host inputs, Np*N*N floats
   int* flag = nullptr;         // device status word
   float* sw_tmp = nullptr;     // shrink-wrap scratch, Np*N*N floats
@@ -132,6 +133,7 @@ struct JobStatic {
   double* err_hist;
   const float2* tw;
   const float2* xtw;
+  const uint16_t* tcw;  // 16-bit block DFT matrices (tensor-core precision)
   int Np, W;
   float beta;
   int pad;
@@ -155,6 +157,7 @@ struct JobStep {
 struct Launch {
   int N;
   int engine;
+  int prec;  // CPRA_FP32 / CPRA_BF16_TC / CPRA_FP16_TC
   cudaStream_t stream;
   const JobStatic* js;
   const JobStep* st;
@@ -162,7 +165,7 @@ struct Launch {
   int ntiles;
 };
 
-cudaError_t prepare_kernels(int N, int engine);  // shared-memory attributes, before capture
+cudaError_t prepare_kernels(int N, int engine, int prec);  // shared-memory attributes, before capture
 cudaError_t launch_prime(const Launch& L);
 cudaError_t launch_colpass(const Launch& L);
 cudaError_t launch_rowpass(const Launch& L);
@@ -177,6 +180,10 @@ bool n_supported(int N);
 bool fast_supported(int N);
 bool fast_dims(int N, int* E1, int* E2);
 cudaError_t prepare_kernels_fast(int N);
+cudaError_t prepare_kernels_fast_tc(int N, int prec);
+cudaError_t launch_rowpass_fast_tc(const Launch& L);
+cudaError_t launch_prime_fast_tc(const Launch& L);
+cudaError_t launch_colpass_fast_tc(const Launch& L);
 cudaError_t launch_rowpass_fast(const Launch& L);
 cudaError_t launch_prime_fast(const Launch& L);
 cudaError_t launch_colpass_fast(const Launch& L);

@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "fft.cuh"
+#include "fftw_tc.cuh"
 
 namespace cpra {
 
@@ -122,23 +123,59 @@ template <int N> struct WP {
   static constexpr int TA = L * E2 / 32;  // step-A tasks per lane
   static constexpr int TB = L * E1 / 32;  // step-B tasks per lane
   static constexpr int TP = E2 + 1;       // odd pitch of the transpose tile
-  static constexpr int TSIZE = (L * E1 * TP > L * N) ? L * E1 * TP : L * N;  // float2 per warp
+  static constexpr int AP = E1 + 1;       // step-A staging pitch (tensor-core path)
+  static constexpr int T0 = (L * E1 * TP > L * N) ? L * E1 * TP : L * N;
+  static constexpr int TSIZE = (L * E2 * AP > T0) ? L * E2 * AP : T0;  // float2 per warp
   static_assert(E1 * E2 == N && TA * 32 == L * E2 && TB * 32 == L * E1, "warp plan");
 };
 
 template <int N> constexpr bool kHasWarpPlan = (N == 64 || N == 128 || N == 256 || N == 512 || N == 1024);
 
-// A layout -> B layout (forward, unnormalised)
-template <int N>
-__device__ __forceinline__ void warp_fft_fwd(float2 (&a)[WP<N>::TA][WP<N>::E1],
-                                             float2 (&b)[WP<N>::TB][WP<N>::E2], float2* T,
-                                             const float2* xtw, int lane) {
+// Tensor-core scratch of one warp and the block DFT matrices (16-bit).
+struct TcCtx {
+  uint16_t* A16;
+  float* R;
+  const uint16_t* W1f;  // E1-point forward / inverse
+  const uint16_t* W1i;
+  const uint16_t* W2f;  // E2-point forward / inverse
+  const uint16_t* W2i;
+};
+
+// step-A DFTs of every task of this warp through the tensor cores; a[][]
+// goes through the warp tile T with pitch E1 + 1
+template <int N, int PREC, int DIR>
+__device__ __forceinline__ void tc_step_a(float2 (&a)[WP<N>::TA][WP<N>::E1], float2* T,
+                                          const TcCtx& tc, int lane) {
   using P = WP<N>;
   static_for<0, P::TA>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
+    static_for<0, P::E1>([&](auto MM) { T[t * P::AP + decltype(MM)::value] = a[i][decltype(MM)::value]; });
+  });
+  __syncwarp();
+  for (int c = 0; c < P::TA; ++c)
+    warp_tc_dft<P::E1, PREC>(T + c * 32 * P::AP, P::AP, tc.A16, tc.R, DIR < 0 ? tc.W1f : tc.W1i, lane);
+  static_for<0, P::TA>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
+    static_for<0, P::E1>([&](auto MM) { a[i][decltype(MM)::value] = T[t * P::AP + decltype(MM)::value]; });
+  });
+  __syncwarp();
+}
+
+// A layout -> B layout (forward, unnormalised)
+template <int N, int PREC = kPrecFP32>
+__device__ __forceinline__ void warp_fft_fwd(float2 (&a)[WP<N>::TA][WP<N>::E1],
+                                             float2 (&b)[WP<N>::TB][WP<N>::E2], float2* T,
+                                             const float2* xtw, int lane,
+                                             const TcCtx* tc = nullptr) {
+  using P = WP<N>;
+  if constexpr (PREC != kPrecFP32) tc_step_a<N, PREC, -1>(a, T, *tc, lane);
+  static_for<0, P::TA>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
     const int line = t / P::E2, l = t % P::E2;
-    reg_fft<P::E1, -1>(a[i]);
+    if constexpr (PREC == kPrecFP32) reg_fft<P::E1, -1>(a[i]);
     static_for<0, P::E1>([&](auto KK) {
       constexpr int k1 = decltype(KK)::value;
       float2 v = a[i][k1];
@@ -147,6 +184,11 @@ __device__ __forceinline__ void warp_fft_fwd(float2 (&a)[WP<N>::TA][WP<N>::E1],
     });
   });
   __syncwarp();
+  if constexpr (PREC != kPrecFP32) {
+    // rows of T are the step-B tasks (line * E1 + k1 = t)
+    for (int c = 0; c < P::TB; ++c)
+      warp_tc_dft<P::E2, PREC>(T + c * 32 * P::TP, P::TP, tc->A16, tc->R, tc->W2f, lane);
+  }
   static_for<0, P::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
@@ -155,28 +197,33 @@ __device__ __forceinline__ void warp_fft_fwd(float2 (&a)[WP<N>::TA][WP<N>::E1],
       constexpr int l = decltype(LL)::value;
       b[i][l] = T[(line * P::E1 + k1) * P::TP + l];
     });
-    reg_fft<P::E2, -1>(b[i]);
+    if constexpr (PREC == kPrecFP32) reg_fft<P::E2, -1>(b[i]);
   });
   __syncwarp();
 }
 
 // B layout -> A layout (inverse, unnormalised)
-template <int N>
+template <int N, int PREC = kPrecFP32>
 __device__ __forceinline__ void warp_fft_inv(float2 (&b)[WP<N>::TB][WP<N>::E2],
                                              float2 (&a)[WP<N>::TA][WP<N>::E1], float2* T,
-                                             const float2* xtw, int lane) {
+                                             const float2* xtw, int lane,
+                                             const TcCtx* tc = nullptr) {
   using P = WP<N>;
   static_for<0, P::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
     const int line = t / P::E1, k1 = t % P::E1;
-    reg_fft<P::E2, +1>(b[i]);
+    if constexpr (PREC == kPrecFP32) reg_fft<P::E2, +1>(b[i]);
     static_for<0, P::E2>([&](auto LL) {
       constexpr int l = decltype(LL)::value;
       T[(line * P::E1 + k1) * P::TP + l] = b[i][l];
     });
   });
   __syncwarp();
+  if constexpr (PREC != kPrecFP32) {
+    for (int c = 0; c < P::TB; ++c)
+      warp_tc_dft<P::E2, PREC>(T + c * 32 * P::TP, P::TP, tc->A16, tc->R, tc->W2i, lane);
+  }
   static_for<0, P::TA>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
@@ -187,9 +234,10 @@ __device__ __forceinline__ void warp_fft_inv(float2 (&b)[WP<N>::TB][WP<N>::E2],
       if constexpr (k1 > 0) v = cmul(v, cconj(xtw[k1 * P::E2 + l]));
       a[i][k1] = v;
     });
-    reg_fft<P::E1, +1>(a[i]);
+    if constexpr (PREC == kPrecFP32) reg_fft<P::E1, +1>(a[i]);
   });
   __syncwarp();
+  if constexpr (PREC != kPrecFP32) tc_step_a<N, PREC, +1>(a, T, *tc, lane);
 }
 
 }  // namespace cpra

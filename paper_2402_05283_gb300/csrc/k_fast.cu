@@ -1,489 +1,9 @@
-// k_fast.cu - two-pass iteration with warp-resident FFTs, N in {64,...,1024}.
-//
-// Same dataflow and the same packed half spectrum Hp as k_twopass.cu, but
-// every line transform is the two-level register FFT of fftw.cuh: one
-// warp-local transpose per transform instead of one block-wide shared-memory
-// round trip per radix pass, and no block barriers inside a transform.
-//   k_rowpass_w  Hp rows -> C2R -> HIO/ER update of g -> R2C -> Hp rows
-//   k_prime_w    Eq. 4 coupling of g (optional) -> R2C -> Hp rows
-//   k_colpass_w  Hp column block -> FFT_y -> modulus projection onto A_sym
-//                with the FP64 Fourier error -> IFFT_y -> Hp column block
-// A_sym is read column-major (A_T[n][kx][ky]) so a warp's B-layout reads
-// are coalesced.
-#include "cpra_internal.h"
-#include "fft.cuh"
-#include "fftw.cuh"
+// k_fast.cu - FP32 instances and dispatch of the warp-FFT engine kernels
+// (fast_kernels.cuh); the BF16 / FP16 instances live in k_fast_tc.cu.
+#include "fast_kernels.cuh"
 
 namespace cpra {
 
-constexpr int kRowWarps = 4;
-
-// per-warp shared memory of the row kernels: transpose tile + the warp's g rows
-template <int N> struct RowW {
-  using P = WP<N>;
-  static constexpr int GROWS = 2 * P::L;                  // image rows per warp
-  static constexpr int GFLOATS = GROWS * N;
-  static constexpr int WARP_F2 = P::TSIZE + GFLOATS / 2;  // float2 per warp
-  static constexpr size_t SMEM = sizeof(float2) * (N + kRowWarps * WARP_F2);
-};
-
-template <int N>
-__device__ __forceinline__ void load_xtw(float2* xs, const float2* xtw, int nthreads) {
-  for (int i = threadIdx.x; i < N; i += nthreads) xs[i] = xtw[i];
-}
-
-// Z (B layout) of the row pairs of this warp -> packed half spectra of both
-// rows of every pair, stored to Hp.  Z goes through the warp tile so each
-// output index k can meet its partner N - k.
-template <int N>
-__device__ __forceinline__ void store_pairs_w(float2 (&b)[WP<N>::TB][WP<N>::E2], float2* T,
-                                              float2* Hn, int pair0, int lane) {
-  using P = WP<N>;
-  constexpr int H = N / 2;
-  static_for<0, P::TB>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E1, k1 = t % P::E1;
-    static_for<0, P::E2>([&](auto KK) {
-      constexpr int k2 = decltype(KK)::value;
-      T[line * N + k1 + P::E1 * k2] = b[i][k2];
-    });
-  });
-  __syncwarp();
-#pragma unroll
-  for (int line = 0; line < P::L; ++line) {
-    const float2* Z = T + line * N;
-    float2* r0 = Hn + (size_t)(2 * (pair0 + line)) * H;
-    float2* r1 = r0 + H;
-    for (int k = lane; k < H; k += 32) {
-      float2 h0, h1;
-      if (k == 0) {
-        const float2 z0 = Z[0], zn = Z[H];
-        h0 = make_float2(z0.x, zn.x);
-        h1 = make_float2(z0.y, zn.y);
-      } else {
-        const float2 z = Z[k], zm = Z[N - k];
-        h0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-        h1 = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-      }
-      r0[k] = h0;
-      r1[k] = h1;
-    }
-  }
-  __syncwarp();
-}
-
-// ---------------------------------------------------------------- row pass
-template <int N>
-__global__ void __launch_bounds__(kRowWarps * 32, 3)
-k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
-            const int2* __restrict__ tiles) {
-  using P = WP<N>;
-  using RW = RowW<N>;
-  constexpr int H = N / 2;
-  extern __shared__ float2 smem[];
-  const int2 tl = tiles[blockIdx.y];
-  const JobStatic* J = js + tl.x;
-  const JobStep* Z = st + tl.x;
-  if (!Z->active) return;
-  float* g = Z->g;
-  float2* Hp = J->Hp;
-  const uint32_t* __restrict__ S = J->S;
-  double* err_acc = J->err_acc;
-  const double* __restrict__ Cn = J->Cn;
-  const double* __restrict__ sumA2 = J->sumA2;
-  double* err_hist = J->err_hist;
-  const long long err_slot = Z->err_slot;
-  const float2* __restrict__ xtw = J->xtw;
-  const int Np = J->Np, W = J->W;
-  const float beta = J->beta;
-  const int algo = Z->algo, forward = Z->forward;
-  float2* xs = smem;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* T = smem + N + warp * RW::WARP_F2;
-  float* Gs = reinterpret_cast<float*>(T + P::TSIZE);  // this warp's 2L rows of g
-  const int n = tl.y;
-  const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
-  float* grow = g + ((size_t)n * N + 2 * pair0) * N;  // 2L contiguous rows
-  // prefetch the old iterate; it is needed only after the inverse FFT
-  for (int q = lane; q < RW::GFLOATS / 4; q += 32) cp_async16(Gs + 4 * q, grow + 4 * q);
-  cp_async_commit();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (err_slot >= 0) {
-      const double den = sumA2[n];
-      err_hist[(size_t)err_slot * Np + n] = den > 0.0 ? sqrt((err_acc[n] + Cn[n]) / den) : 0.0;
-    }
-    err_acc[n] = 0.0;
-  }
-  load_xtw<N>(xs, xtw, kRowWarps * 32);
-  __syncthreads();
-  float2* Hn = Hp + (size_t)n * N * H;
-  // packed row spectra -> Z = H(row 2p) + i H(row 2p+1), B layout
-  float2 b[P::TB][P::E2];
-  static_for<0, P::TB>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E1, k1 = t % P::E1;
-    const float2* r0 = Hn + (size_t)(2 * (pair0 + line)) * H;
-    const float2* r1 = r0 + H;
-    static_for<0, P::E2>([&](auto KK) {
-      constexpr int k2 = decltype(KK)::value;
-      const int k = k1 + P::E1 * k2;
-      float2 z;
-      if (k == 0) {
-        z = make_float2(r0[0].x, r1[0].x);
-      } else if (k == H) {
-        z = make_float2(r0[0].y, r1[0].y);
-      } else if (k < H) {
-        const float2 h0 = r0[k], h1 = r1[k];
-        z = make_float2(h0.x - h1.y, h0.y + h1.x);
-      } else {
-        const float2 h0 = r0[N - k], h1 = r1[N - k];
-        z = make_float2(h0.x + h1.y, h1.x - h0.y);
-      }
-      b[i][k2] = z;
-    });
-  });
-  float2 a[P::TA][P::E1];
-  warp_fft_inv<N>(b, a, T, xs, lane);
-  cp_async_wait_all();
-  __syncwarp();
-  const float inv = 1.0f / N;
-  static_for<0, P::TA>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
-    const int y0 = 2 * (pair0 + line);
-    float* g0 = g + ((size_t)n * N + y0) * N;
-    float* g1 = g0 + N;
-    const float* o0s = Gs + (2 * line) * N;
-    const float* o1s = o0s + N;
-    const uint32_t* s0 = S + ((size_t)n * N + y0) * W;
-    const uint32_t* s1 = s0 + W;
-    static_for<0, P::E1>([&](auto MM) {
-      constexpr int m = decltype(MM)::value;
-      const int x = l + P::E2 * m;
-      const float2 z = a[i][m];
-      const float gp0 = z.x * inv, gp1 = z.y * inv;
-      const bool v0 = ((__ldg(s0 + (x >> 5)) >> (x & 31)) & 1u) && gp0 >= 0.0f;
-      const bool v1 = ((__ldg(s1 + (x >> 5)) >> (x & 31)) & 1u) && gp1 >= 0.0f;
-      const float n0 = v0 ? gp0 : (algo == kHIO ? fmaf(-beta, gp0, o0s[x]) : 0.0f);
-      const float n1 = v1 ? gp1 : (algo == kHIO ? fmaf(-beta, gp1, o1s[x]) : 0.0f);
-      g0[x] = n0;
-      g1[x] = n1;
-      a[i][m] = make_float2(n0, n1);
-    });
-  });
-  if (!forward) return;
-  warp_fft_fwd<N>(a, b, T, xs, lane);
-  store_pairs_w<N>(b, T, Hn, pair0, lane);
-}
-
-// ---------------------------------------------------------------- prime
-template <int N>
-__global__ void __launch_bounds__(kRowWarps * 32, 3)
-k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
-          const int2* __restrict__ tiles) {
-  using P = WP<N>;
-  using RW = RowW<N>;
-  constexpr int H = N / 2;
-  extern __shared__ float2 smem[];
-  const int2 tl = tiles[blockIdx.y];
-  const JobStatic* J = js + tl.x;
-  const JobStep* Z = st + tl.x;
-  if (!Z->prime) return;
-  const float* __restrict__ g_src = Z->g_src;
-  float* __restrict__ g_dst = Z->ca.store_g ? Z->g_dst : nullptr;
-  float2* Hp = J->Hp;
-  const uint32_t* __restrict__ S = J->S;
-  const float2* __restrict__ xtw = J->xtw;
-  const int Np = J->Np, W = J->W;
-  const CoupleArgs& ca = Z->ca;
-  float2* xs = smem;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* T = smem + N + warp * RW::WARP_F2;
-  const int n = tl.y;
-  const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
-  __shared__ const float* tap_src[CPRA_MAX_TAPS];
-  __shared__ const uint32_t* tap_s[CPRA_MAX_TAPS];
-  __shared__ int tap_mir[CPRA_MAX_TAPS];
-  load_xtw<N>(xs, xtw, kRowWarps * 32);
-  if (threadIdx.x < ca.n_taps) {
-    // angle (n + k) mod Np and whether the seam was crossed an odd number of times
-    const int k = (int)threadIdx.x - ca.n_taps / 2;
-    const int j = n + k;
-    const int jm = ((j % Np) + Np) % Np;
-    const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
-    tap_src[threadIdx.x] = g_src + (size_t)jm * N * N;
-    tap_s[threadIdx.x] = S + (size_t)jm * N * W;
-    tap_mir[threadIdx.x] = ca.mirror && (wraps & 1);
-  }
-  __syncthreads();
-  const int ntaps = ca.n_taps;
-  float2 a[P::TA][P::E1];
-  static_for<0, P::TA>([&](auto II) {
-    static_for<0, P::E1>([&](auto MM) { a[decltype(II)::value][decltype(MM)::value] = make_float2(0.f, 0.f); });
-  });
-  // taps outermost: every load of one tap is independent, so a warp keeps
-  // 2 * TA * E1 loads in flight per tap
-  for (int k = 0; k < ntaps; ++k) {
-    const float* src = tap_src[k];
-    const uint32_t* sk = tap_s[k];
-    const bool mir = tap_mir[k] != 0;
-    const float alpha = ntaps == 1 ? 1.0f : ca.alpha[k];
-    static_for<0, P::TA>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      const int t = lane + 32 * i;
-      const int line = t / P::E2, l = t % P::E2;
-      const int y0 = 2 * (pair0 + line);
-      static_for<0, P::E1>([&](auto MM) {
-        constexpr int m = decltype(MM)::value;
-        const int x = l + P::E2 * m;
-        const int xs_ = mir ? ((N - x) & (N - 1)) : x;
-        float v0 = __ldg(src + (size_t)y0 * N + xs_);
-        float v1 = __ldg(src + (size_t)(y0 + 1) * N + xs_);
-        if (ca.object) {
-          const bool in0 = (__ldg(sk + (size_t)y0 * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
-          const bool in1 = (__ldg(sk + (size_t)(y0 + 1) * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
-          v0 = (in0 && v0 >= 0.0f) ? v0 : 0.0f;
-          v1 = (in1 && v1 >= 0.0f) ? v1 : 0.0f;
-        }
-        a[i][m].x = fmaf(alpha, v0, a[i][m].x);
-        a[i][m].y = fmaf(alpha, v1, a[i][m].y);
-      });
-    });
-  }
-  if (ca.store_g) {
-    static_for<0, P::TA>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      const int t = lane + 32 * i;
-      const int line = t / P::E2, l = t % P::E2;
-      float* d0 = g_dst + ((size_t)n * N + 2 * (pair0 + line)) * N;
-      static_for<0, P::E1>([&](auto MM) {
-        constexpr int m = decltype(MM)::value;
-        d0[l + P::E2 * m] = a[i][m].x;
-        d0[N + l + P::E2 * m] = a[i][m].y;
-      });
-    });
-  }
-  float2 b[P::TB][P::E2];
-  warp_fft_fwd<N>(a, b, T, xs, lane);
-  store_pairs_w<N>(b, T, Hp + (size_t)n * N * H, pair0, lane);
-}
-
-// ---------------------------------------------------------------- column pass
-constexpr int kColB = 16;  // packed columns per CTA (128 B of each row)
-
-template <int N> struct ColW {
-  using P = WP<N>;
-  static constexpr int WARPS = kColB / P::L;
-  static constexpr int NT = WARPS * 32;
-  static constexpr int SP = kColB + 1;  // staging pitch
-  static constexpr int STAGE = N * SP;
-  static constexpr int TILES = WARPS * P::TSIZE;
-  static constexpr int BUF = STAGE > TILES ? STAGE : TILES;
-  static constexpr size_t SMEM = sizeof(float2) * (N + BUF) + sizeof(float) * kColB * N;
-};
-
-// G' = a G / |G| (a where G = 0); err += w (|G| - a)^2.  The per-thread
-// partial sum stays in FP32 (at most a few hundred terms); the reduction
-// across threads, blocks and columns is FP64.
-__device__ __forceinline__ float2 project_w(float2 G, float a, float& err, float w) {
-  const float r2 = fmaf(G.x, G.x, G.y * G.y);
-  if (r2 > 0.0f) {
-    const float inv = rsqrtf(r2);
-    const float d = fmaf(r2, inv, -a);
-    err = fmaf(w * d, d, err);
-    const float s = a * inv;
-    return make_float2(G.x * s, G.y * s);
-  }
-  err = fmaf(w * a, a, err);
-  return make_float2(a, 0.0f);
-}
-
-template <int N>
-__global__ void __launch_bounds__(ColW<N>::NT, ColW<N>::NT <= 256 ? 2 : 1)
-k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
-            const int2* __restrict__ tiles) {
-  using P = WP<N>;
-  using C = ColW<N>;
-  constexpr int H = N / 2;
-  extern __shared__ float2 smem[];
-  const int2 tl = tiles[blockIdx.y];
-  const JobStatic* J = js + tl.x;
-  if (!st[tl.x].active) return;
-  float2* Hp = J->Hp;
-  const float* __restrict__ A_T = J->A_main;
-  const float* __restrict__ A_nyq = J->A_nyq;
-  double* err_acc = J->err_acc;
-  const float2* __restrict__ xtw = J->xtw;
-  float2* xs = smem;
-  float2* buf = smem + N;  // staging, then the warps' transpose tiles
-  __shared__ double red[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* As = reinterpret_cast<float*>(buf + C::BUF);  // A_sym of the block, [c][ky]
-  float2* T = buf + warp * P::TSIZE;
-  const int n = tl.y;
-  const int c0 = blockIdx.x * kColB;
-  float2* Hn = Hp + (size_t)n * N * H;
-  for (int idx = threadIdx.x; idx < N * kColB; idx += C::NT) {
-    const int y = idx / kColB, c = idx - y * kColB;
-    cp_async8(buf + y * C::SP + c, Hn + (size_t)y * H + c0 + c);
-  }
-  const float* Ablk = A_T + ((size_t)n * H + c0) * N;  // kColB contiguous columns
-  for (int q = threadIdx.x; q < kColB * N / 4; q += C::NT) cp_async16(As + 4 * q, Ablk + 4 * q);
-  cp_async_commit();
-  load_xtw<N>(xs, xtw, C::NT);
-  cp_async_wait_all();
-  __syncthreads();
-  float2 a[P::TA][P::E1];
-  static_for<0, P::TA>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
-    const int col = warp * P::L + line;
-    static_for<0, P::E1>([&](auto MM) {
-      constexpr int m = decltype(MM)::value;
-      a[i][m] = buf[(l + P::E2 * m) * C::SP + col];
-    });
-  });
-  __syncthreads();
-  float2 b[P::TB][P::E2];
-  warp_fft_fwd<N>(a, b, T, xs, lane);
-  float err = 0.0f;
-  const bool warp_packed = (c0 == 0 && warp == 0);  // line 0 of warp 0 holds column 0
-  static_for<0, P::TB>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E1, k1 = t % P::E1;
-    const int col = warp * P::L + line;
-    if (c0 + col != 0) {
-      const float* Ac = As + col * N;
-      static_for<0, P::E2>([&](auto KK) {
-        constexpr int k2 = decltype(KK)::value;
-        const int ky = k1 + P::E1 * k2;
-        b[i][k2] = project_w(b[i][k2], Ac[ky], err, 2.0f);
-      });
-    }
-  });
-  if (warp_packed) {
-    // column 0 packs G(., 0) + i G(., N/2); both are Hermitian along ky
-    static_for<0, P::TB>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      const int t = lane + 32 * i;
-      const int line = t / P::E1, k1 = t % P::E1;
-      if (line == 0) {
-        static_for<0, P::E2>([&](auto KK) {
-          constexpr int k2 = decltype(KK)::value;
-          T[k1 + P::E1 * k2] = b[i][k2];
-        });
-      }
-    });
-    __syncwarp();
-    static_for<0, P::TB>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      const int t = lane + 32 * i;
-      const int line = t / P::E1, k1 = t % P::E1;
-      if (line == 0) {
-        const float* A0 = As;  // column 0 of the block
-        const float* An = A_nyq + (size_t)n * N;
-        static_for<0, P::E2>([&](auto KK) {
-          constexpr int k2 = decltype(KK)::value;
-          const int ky = k1 + P::E1 * k2;
-          const float2 z = T[ky], zm = T[(N - ky) % N];
-          const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-          const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-          const float2 p0 = project_w(g0, A0[ky], err, 1.0f);
-          const float2 pn = project_w(gn, __ldg(An + ky), err, 1.0f);
-          b[i][k2] = make_float2(p0.x - pn.y, p0.y + pn.x);
-        });
-      }
-    });
-    __syncwarp();
-  }
-  warp_fft_inv<N>(b, a, T, xs, lane);
-  __syncthreads();
-  const float inv = 1.0f / N;
-  static_for<0, P::TA>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
-    const int col = warp * P::L + line;
-    static_for<0, P::E1>([&](auto MM) {
-      constexpr int m = decltype(MM)::value;
-      buf[(l + P::E2 * m) * C::SP + col] = cscale(a[i][m], inv);
-    });
-  });
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < N * kColB; idx += C::NT) {
-    const int y = idx / kColB, c = idx - y * kColB;
-    Hn[(size_t)y * H + c0 + c] = buf[y * C::SP + c];
-  }
-  double errd = (double)err;
-  for (int o = 16; o > 0; o >>= 1) errd += __shfl_down_sync(0xffffffffu, errd, o);
-  if (lane == 0) red[warp] = errd;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < C::WARPS; ++w) s += red[w];
-    atomicAdd(err_acc + n, s);
-  }
-}
-
-// ---------------------------------------------------------------- launchers
-template <class K>
-static cudaError_t smem_attr(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int N>
-static cudaError_t prepare_w() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = smem_attr(k_rowpass_w<N>, RowW<N>::SMEM);
-  if (e == cudaSuccess) e = smem_attr(k_prime_w<N>, RowW<N>::SMEM);
-  if (e == cudaSuccess) e = smem_attr(k_colpass_w<N>, ColW<N>::SMEM);
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-
-template <int N>
-static cudaError_t rowpass_w(const Launch& L) {
-  using P = WP<N>;
-  const size_t smem = RowW<N>::SMEM;
-  cudaError_t e = prepare_w<N>();
-  if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / (kRowWarps * P::L), L.ntiles);
-  g_launches += 1;
-  k_rowpass_w<N><<<grid, kRowWarps * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
-  return cudaGetLastError();
-}
-
-template <int N>
-static cudaError_t prime_w(const Launch& L) {
-  using P = WP<N>;
-  const size_t smem = RowW<N>::SMEM;
-  cudaError_t e = prepare_w<N>();
-  if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / (kRowWarps * P::L), L.ntiles);
-  g_launches += 1;
-  k_prime_w<N><<<grid, kRowWarps * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
-  return cudaGetLastError();
-}
-
-template <int N>
-static cudaError_t colpass_w(const Launch& L) {
-  using C = ColW<N>;
-  const size_t smem = C::SMEM;
-  cudaError_t e = prepare_w<N>();
-  if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / kColB, L.ntiles);
-  g_launches += 1;
-  k_colpass_w<N><<<grid, C::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
-  return cudaGetLastError();
-}
-
-#define CPRA_FOR_EACH_FAST_N(X) X(64) X(128) X(256) X(512) X(1024)
 
 bool fast_supported(int N) {
   switch (N) {
@@ -513,7 +33,7 @@ bool fast_dims(int N, int* E1, int* E2) {
 cudaError_t prepare_kernels_fast(int N) {
   switch (N) {
 #define CPRA_CASE(NN) \
-  case NN: return prepare_w<NN>();
+  case NN: return prepare_w<NN, kPrecFP32>();
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
@@ -522,9 +42,10 @@ cudaError_t prepare_kernels_fast(int N) {
 }
 
 cudaError_t launch_rowpass_fast(const Launch& L) {
+  if (L.prec != kPrecFP32) return launch_rowpass_fast_tc(L);
   switch (L.N) {
 #define CPRA_CASE(NN) \
-  case NN: return rowpass_w<NN>(L);
+  case NN: return rowpass_w<NN, kPrecFP32>(L);
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
@@ -533,9 +54,10 @@ cudaError_t launch_rowpass_fast(const Launch& L) {
 }
 
 cudaError_t launch_prime_fast(const Launch& L) {
+  if (L.prec != kPrecFP32) return launch_prime_fast_tc(L);
   switch (L.N) {
 #define CPRA_CASE(NN) \
-  case NN: return prime_w<NN>(L);
+  case NN: return prime_w<NN, kPrecFP32>(L);
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
@@ -544,9 +66,10 @@ cudaError_t launch_prime_fast(const Launch& L) {
 }
 
 cudaError_t launch_colpass_fast(const Launch& L) {
+  if (L.prec != kPrecFP32) return launch_colpass_fast_tc(L);
   switch (L.N) {
 #define CPRA_CASE(NN) \
-  case NN: return colpass_w<NN>(L);
+  case NN: return colpass_w<NN, kPrecFP32>(L);
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
 #undef CPRA_CASE
     default:

@@ -316,8 +316,9 @@ static cudaError_t prepare_n() {
   return e;
 }
 
-cudaError_t prepare_kernels(int N, int engine) {
-  if (engine == CPRA_ENGINE_WARP) return prepare_kernels_fast(N);
+cudaError_t prepare_kernels(int N, int engine, int prec) {
+  if (engine == CPRA_ENGINE_WARP)
+    return prec == CPRA_FP32 ? prepare_kernels_fast(N) : prepare_kernels_fast_tc(N, prec);
 #define CPRA_CASE(NN) \
   case NN: return prepare_n<NN>();
   switch (N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
