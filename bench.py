@@ -163,6 +163,178 @@ def cpu_baseline(I, S, seconds: float = 12.0):
                       f"{it} iterations ({dt:.1f} s), dense-DFT matmuls on {cores} host threads"}
 
 
+# ---------------------------------------------------------------- systems forms
+_SERVE_POOL = {}
+
+def form_batch(cp, torch, seed=3):
+    """cfg 3: 16 reconstructions of uneven N and Np, 300 iterations each, run
+    one at a time (plain plans, no graph) and as one batch (one launch per
+    kernel and size group, CUDA graph, autotuned engines).  Results must be
+    bit-identical between the two."""
+    import synth
+    rng = np.random.default_rng(seed)
+    Ns = rng.choice([128, 192, 256, 384], size=16)
+    Nps = rng.choice([90, 180, 360], size=16)
+    iters = 300
+    cases = {}
+    for i in range(16):
+        key = (int(Ns[i]), int(Nps[i]))
+        if key not in cases:
+            d = synth.make_case("cfg1", device="cuda", N=key[0], Np=key[1], request=i)
+            cases[key] = (d["I"].contiguous(), d["thetas"])
+
+    def plans(engine):
+        out = []
+        for i in range(16):
+            I, th = cases[(int(Ns[i]), int(Nps[i]))]
+            p = cp.Plan(cp.make_config(int(Ns[i]), int(Nps[i]), seed=i, hio_iters=280, er_iters=20,
+                                       engine=engine))
+            p.load_intensities(I, 0, th)
+            out.append(p)
+        return out
+
+    work = int(sum(int(n) for n in Nps)) * iters
+    alone = plans(cp.ENGINE_AUTO)
+    for p in alone:
+        p.iterate(1)
+        p.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p in alone:
+        p.iterate(iters)
+        p.sync()
+    t_alone = time.perf_counter() - t0
+    tuned = {int(n): cp.cpra_autotune(int(n))[0] for n in set(Ns.tolist())}
+    mixed = plans(cp.ENGINE_TUNED)
+    b = cp.Batch(mixed, use_graph=True)
+    b.iterate(30)  # capture the 30-iteration graph
+    for p in mixed:
+        p.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters // 30):
+        b.iterate(30)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    # plans whose tuned engine is the one AUTO picks must agree bit for bit
+    auto = {n: (cp.ENGINE_WARP if n in (64, 128, 256, 512, 1024) else cp.ENGINE_TWO_PASS) for n in tuned}
+    pairs = [(a, m) for a, m in zip(alone, mixed) if tuned[a.N] == auto[a.N]]
+    same = all(np.array_equal(a.result(cp.RESULT_STATE), m.result(cp.RESULT_STATE)) for a, m in pairs)
+    b.close()
+    for p in alone + mixed:
+        p.close()
+    return {"workload": "16 reconstructions, N in {128,192,256,384}, Np in {90,180,360}, "
+                        "280 HIO + 20 ER", "angle_iterations": work,
+            "one_at_a_time": {"value": round(work / t_alone, 1), "seconds": round(t_alone, 3)},
+            "batched_graph": {"value": round(work / t_batch, 1), "seconds": round(t_batch, 3)},
+            "speedup": round(t_alone / t_batch, 3), "tuned_engines": tuned,
+            "bit_identical": bool(same), "compared": len(pairs)}
+
+
+def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0):
+    """cfg 4 with time compressed by `compress`: Poisson arrivals at 4/s,
+    each request streams its Np patterns at 10 patterns/s (both x compress),
+    N in {256, 512}, Np in {180, 360}, 220 iterations; continuous batching
+    (max_active 0) or one request at a time (max_active 1)."""
+    import synth
+    rng = np.random.default_rng(seed)
+    combos = [(256, 180), (256, 360), (512, 180), (512, 360)]
+    pool = _SERVE_POOL
+    for N_, Np_ in combos:
+        if (N_, Np_) not in pool:
+            d = synth.make_case("cfg1", device="cuda", N=N_, Np=Np_, request=N_ + Np_)
+            pool[(N_, Np_)] = (d["I"].cpu().numpy(), d["thetas"])
+    arrivals = np.cumsum(rng.exponential(1.0 / (4.0 * compress), size=n_req))
+    picks = [combos[i] for i in rng.integers(0, 4, size=n_req)]
+    rate = 10.0 * compress  # patterns per second
+    chunk = 10
+    srv = cp.Server(hbm_reserve_bytes=8 << 30, max_active=max_active, iters_per_round=10)
+    sched = []  # (time, kind, request index, first)
+    for r in range(n_req):
+        sched.append((arrivals[r], 0, r, 0))
+        Np_ = picks[r][1]
+        for f in range(0, Np_, chunk):
+            sched.append((arrivals[r] + (f + chunk) / rate, 1, r, f))
+    sched.sort()
+    ids = [None] * n_req
+    t0 = time.perf_counter()
+    for t_ev, kind, r, f in sched:
+        dt = t_ev - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        N_, Np_ = picks[r]
+        if kind == 0:
+            ids[r] = srv.submit(cp.make_config(N_, Np_, seed=r, hio_iters=200, er_iters=20))
+        else:
+            I, th = pool[(N_, Np_)]
+            k = min(chunk, Np_ - f)
+            srv.push(ids[r], I[f:f + k], f, th[f:f + k])
+    for rid in ids:
+        srv.wait(rid, 600.0)
+    wall = time.perf_counter() - t0
+    first, final, first_sub, final_sub = [], [], [], []
+    for rid in ids:
+        info = srv.info(rid)
+        first.append(info["t_first_estimate"] - info["t_last_pattern"])
+        final.append(info["t_final"] - info["t_last_pattern"])
+        first_sub.append(info["t_first_estimate"] - info["t_submit"])
+        final_sub.append(info["t_final"] - info["t_submit"])
+    st = srv.stats()
+    srv.stop()
+    q = lambda a: [round(float(x), 4) for x in np.percentile(a, [50, 99])]  # noqa: E731
+    return {"requests": n_req, "time_compression": compress, "max_active": max_active,
+            "p50_p99_s_first_estimate_after_last_pattern": q(first),
+            "p50_p99_s_final_after_last_pattern": q(final),
+            "p50_p99_s_first_estimate_after_submit": q(first_sub),
+            "p50_p99_s_final_after_submit": q(final_sub),
+            "angle_iterations": int(st["angle_iterations"]),
+            "value": round(st["angle_iterations"] / wall, 1), "wall_s": round(wall, 3),
+            "max_batch": int(st["max_batch"]), "rounds": int(st["rounds"])}
+
+
+def form_precision(cp, torch, I_dev, thetas, S_box, n_angles=NP, N_=N, sample=(0, 1), iters=5):
+    """Throughput of the FP32 / BF16 / FP16 forms on the bench workload and
+    their iterate error against the FP64 oracle after `iters` ER iterations
+    from a seeded state, on sampled angles (neighbours coupled at t = 0)."""
+    import oracle as O
+    rng = np.random.default_rng(11)
+    S = np.zeros((N_, N_), bool)
+    S[N_ // 4:3 * N_ // 4, N_ // 4:3 * N_ // 4] = True
+    g0 = (rng.random((n_angles, N_, N_), dtype=np.float32) * S).astype(np.float32)
+    out = {}
+    ref = {}
+    I_host = None
+    for n in sample:
+        if I_host is None:
+            I_host = I_dev.cpu().numpy()
+        idx = [(n - 1) % n_angles, n, (n + 1) % n_angles]
+        x = 0.2 * g0[idx[0]].astype(np.float64) + 0.6 * g0[idx[1]] + 0.2 * g0[idx[2]]
+        A = O.amplitudes(I_host[n])[None]
+        x = x[None]
+        for _ in range(iters):
+            x, _, _ = O.iterate_2d(x, A, S[None], 0.9, O.ER)
+        ref[n] = x[0]
+    for name, prec in (("fp32", cp.FP32), ("bf16", cp.BF16_TC), ("fp16", cp.FP16_TC)):
+        plan = cp.Plan(cp.make_config(N_, n_angles, precision=prec, hio_iters=0, er_iters=iters))
+        plan.load_intensities(I_dev, 0, thetas)
+        plan.load_support(S_box)
+        plan.load_state(g0, 0)
+        plan.iterate(iters)
+        g = plan.result(cp.RESULT_STATE)
+        errs = [float(np.linalg.norm(g[n] - ref[n]) / np.linalg.norm(ref[n])) for n in sample]
+        plan.load_state(g0, 0)
+        plan.iterate(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.iterate(20)
+        plan.sync()
+        dt = time.perf_counter() - t0
+        plan.close()
+        out[name] = {"value": round(n_angles * 20 / dt, 1), "unit": "angle-iterations/s",
+                     "rel_l2_vs_fp64_after_%d_er" % iters: [float("%.3e" % e) for e in errs]}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -285,6 +457,12 @@ def run_gpu(args):
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_value = world * NPa * IT / float(e2e_t.item())
 
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        forms = {"precision": form_precision(cp, torch, I_dev, thetas, S_box),
+                 "batching": form_batch(cp, torch),
+                 "serving_continuous": form_serving(cp, torch, max_active=0),
+                 "serving_one_at_a_time": form_serving(cp, torch, max_active=1)}
     if rank == 0:
         cb = cpu_baseline(I_dev[:8].cpu().numpy(), d["support"]) if world == 1 else None
         qs = np.percentile(step_ms, [50, 99])
@@ -309,6 +487,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": int(vol_host.numel() * 4)},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -327,6 +506,8 @@ def main():
     ap.add_argument("--iters", type=int, default=ITERS, help=PROFILE_NOTE)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e and CPU-baseline legs (profiler captures)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batching / serving / precision measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
