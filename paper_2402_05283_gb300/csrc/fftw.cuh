@@ -93,9 +93,18 @@ __device__ __forceinline__ void reg_fft(float2 (&v)[E]) {
         constexpr int r = decltype(RR)::value;
         float2 t = v[j + r * NB];
         if constexpr (NS > 1 && r > 0 && k > 0) {
-          constexpr float wr = TwC<NS * R, k * r, DIR>::re;
-          constexpr float wi = TwC<NS * R, k * r, DIR>::im;
-          t = make_float2(fmaf(t.x, wr, -t.y * wi), fmaf(t.x, wi, t.y * wr));
+          constexpr int M = NS * R, Q = (k * r) % (NS * R);
+          if constexpr ((4 * Q) % M == 0) {
+            // a multiple of pi/2: exact sign changes and swaps
+            constexpr int quarter = (4 * Q) / M;  // exp(DIR * i * pi/2 * quarter)
+            if constexpr (quarter == 1) t = mul_i<DIR>(t);
+            else if constexpr (quarter == 2) t = make_float2(-t.x, -t.y);
+            else if constexpr (quarter == 3) t = mul_i<-DIR>(t);
+          } else {
+            constexpr float wr = TwC<M, Q, DIR>::re;
+            constexpr float wi = TwC<M, Q, DIR>::im;
+            t = make_float2(fmaf(t.x, wr, -t.y * wi), fmaf(t.x, wi, t.y * wr));
+          }
         }
         x[r] = t;
       });
@@ -171,16 +180,23 @@ __device__ __forceinline__ void warp_fft_fwd(float2 (&a)[WP<N>::TA][WP<N>::E1],
                                              const TcCtx* tc = nullptr) {
   using P = WP<N>;
   if constexpr (PREC != kPrecFP32) tc_step_a<N, PREC, -1>(a, T, *tc, lane);
-  static_for<0, P::TA>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
-    if constexpr (PREC == kPrecFP32) reg_fft<P::E1, -1>(a[i]);
-    static_for<0, P::E1>([&](auto KK) {
-      constexpr int k1 = decltype(KK)::value;
-      float2 v = a[i][k1];
-      if constexpr (k1 > 0) v = cmul(v, xtw[k1 * P::E2 + l]);
-      T[(line * P::E1 + k1) * P::TP + l] = v;
+  if constexpr (PREC == kPrecFP32)
+    static_for<0, P::TA>([&](auto II) { reg_fft<P::E1, -1>(a[decltype(II)::value]); });
+  // cross twiddles: k1 outermost so tasks of a lane that share l share the load
+  static_for<0, P::E1>([&](auto KK) {
+    constexpr int k1 = decltype(KK)::value;
+    float2 v[P::TA];
+    static_for<0, P::TA>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      const int l = (lane + 32 * i) % P::E2;
+      v[i] = a[i][k1];
+      if constexpr (k1 > 0) v[i] = cmul(v[i], xtw[k1 * P::E2 + l]);
+    });
+    static_for<0, P::TA>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      const int t = lane + 32 * i;
+      const int line = t / P::E2, l = t % P::E2;
+      T[(line * P::E1 + k1) * P::TP + l] = v[i];
     });
   });
   __syncwarp();
@@ -224,18 +240,22 @@ __device__ __forceinline__ void warp_fft_inv(float2 (&b)[WP<N>::TB][WP<N>::E2],
     for (int c = 0; c < P::TB; ++c)
       warp_tc_dft<P::E2, PREC>(T + c * 32 * P::TP, P::TP, tc->A16, tc->R, tc->W2i, lane);
   }
-  static_for<0, P::TA>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
-    static_for<0, P::E1>([&](auto KK) {
-      constexpr int k1 = decltype(KK)::value;
-      float2 v = T[(line * P::E1 + k1) * P::TP + l];
-      if constexpr (k1 > 0) v = cmul(v, cconj(xtw[k1 * P::E2 + l]));
-      a[i][k1] = v;
+  static_for<0, P::E1>([&](auto KK) {
+    constexpr int k1 = decltype(KK)::value;
+    static_for<0, P::TA>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      const int t = lane + 32 * i;
+      const int line = t / P::E2, l = t % P::E2;
+      a[i][k1] = T[(line * P::E1 + k1) * P::TP + l];
     });
-    if constexpr (PREC == kPrecFP32) reg_fft<P::E1, +1>(a[i]);
+    static_for<0, P::TA>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      const int l = (lane + 32 * i) % P::E2;
+      if constexpr (k1 > 0) a[i][k1] = cmul(a[i][k1], cconj(xtw[k1 * P::E2 + l]));
+    });
   });
+  if constexpr (PREC == kPrecFP32)
+    static_for<0, P::TA>([&](auto II) { reg_fft<P::E1, +1>(a[decltype(II)::value]); });
   __syncwarp();
   if constexpr (PREC != kPrecFP32) tc_step_a<N, PREC, +1>(a, T, *tc, lane);
 }
