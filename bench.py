@@ -100,7 +100,7 @@ def make_inputs(device, n_angles=NP):
     return synth.make_case("metric", device=device, Np=n_angles)
 
 
-def roofline_figures(plan, cp, peaks, Np_total):
+def roofline_figures(plan, cp, peaks, Np_total, angle_iters):
     """Dominant kernel's algorithmic bytes / its mean CUDA-event duration."""
     stats = {k: plan.kernel_stats(k) for k in range(cp.KERNEL_KINDS)}
     total = sum(v[0] for v in stats.values()) or 1.0
@@ -120,12 +120,14 @@ def roofline_figures(plan, cp, peaks, Np_total):
              cp.KERNEL_PREPARE: "k_prepare"}
     if per_angle is None or launches == 0:
         return None, stats
-    bytes_launch = per_angle * Np_total
+    # units of one launch: Np angles, times the iterations it runs (fused)
+    units = Np_total * (angle_iters / Np_total / launches if kind == cp.KERNEL_FUSED else 1)
+    bytes_launch = per_angle * units
     achieved = bytes_launch / (ms / launches * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "kernel": names[kind], "achieved": round(achieved, 1),
             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": None, "bytes_per_launch": bytes_launch,
+            "traffic": None, "bytes_per_launch": int(bytes_launch),
             "mean_launch_ms": round(ms / launches, 4),
             "share_of_kernel_time": round(ms / total, 3),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}, stats
@@ -217,7 +219,8 @@ def form_batch(cp, torch, seed=3):
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     # plans whose tuned engine is the one AUTO picks must agree bit for bit
-    auto = {n: (cp.ENGINE_WARP if n in (64, 128, 256, 512, 1024) else cp.ENGINE_TWO_PASS) for n in tuned}
+    auto = {n: (cp.ENGINE_FUSED if n in (64, 128, 256) else
+                cp.ENGINE_WARP if n in (512, 1024) else cp.ENGINE_TWO_PASS) for n in tuned}
     pairs = [(a, m) for a, m in zip(alone, mixed) if tuned[a.N] == auto[a.N]]
     same = all(np.array_equal(a.result(cp.RESULT_STATE), m.result(cp.RESULT_STATE)) for a, m in pairs)
     b.close()
@@ -387,7 +390,9 @@ def run_gpu(args):
     S_box = torch.from_numpy(d["support"]).cuda()
     stream = torch.cuda.current_stream()
     hio = min(T_HIO, IT)
-    cfg = cp.make_config(N, NPa, hio_iters=hio, er_iters=IT - hio, seed=rank)
+    engine = {"auto": cp.ENGINE_AUTO, "warp": cp.ENGINE_WARP, "fused": cp.ENGINE_FUSED,
+              "two_pass": cp.ENGINE_TWO_PASS}[args.engine]
+    cfg = cp.make_config(N, NPa, hio_iters=hio, er_iters=IT - hio, seed=rank, engine=engine)
     plan = cp.Plan(cfg, stream=stream.cuda_stream)
     vol = torch.empty((N, N, N, 2), dtype=torch.float32, device=f"cuda:{local}")
 
@@ -419,7 +424,7 @@ def run_gpu(args):
     launches = cp.cpra_launch_count() - launches0
     step_ms = [a.elapsed_time(b_) for a, b_ in evs]
     total_ms = sum(step_ms)
-    roof, kstats = roofline_figures(plan, cp, peaks, NPa)
+    roof, kstats = roofline_figures(plan, cp, peaks, NPa, NPa * IT * args.steps)
     plan.set_profiling(False)
     t_dev = torch.tensor([total_ms], device=f"cuda:{local}")
     if dist:
@@ -506,6 +511,8 @@ def main():
     ap.add_argument("--iters", type=int, default=ITERS, help=PROFILE_NOTE)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e and CPU-baseline legs (profiler captures)")
+    ap.add_argument("--engine", default="auto", choices=["auto", "warp", "fused", "two_pass"],
+                    help="iteration engine of the plain path")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batching / serving / precision measurements")
     args = ap.parse_args()

@@ -145,7 +145,10 @@ cpra_status validate(const cpra_config* c, std::string& why) {
     why = "bad engine";
     return CPRA_ERR_INVALID_ARG;
   }
-  if (c->engine == CPRA_ENGINE_FUSED) { why = "fused engine not available for this N"; return CPRA_ERR_UNSUPPORTED; }
+  if (c->engine == CPRA_ENGINE_FUSED && !fused_supported(c->N)) {
+    why = "fused engine needs N in {64, 128, 256, 512}";
+    return CPRA_ERR_UNSUPPORTED;
+  }
   if (c->engine == CPRA_ENGINE_WARP && !fast_supported(c->N)) {
     why = "warp engine needs N in {64, 128, 256, 512, 1024}";
     return CPRA_ERR_UNSUPPORTED;
@@ -393,6 +396,77 @@ cpra_status cpra::record_error(cpra_status st, const std::string& msg) {
   return fail(nullptr, st, msg);
 }
 
+// The fused engine: one launch per window of iterations that no coupling
+// step (Eq. 4, at t % n_ei == 0) and no shrink-wrap interrupts.  Every
+// launch primes from g (coupled into the other buffer at an episode start)
+// and runs the window's iterations with the spectra resident on chip.
+static cpra_status iterate_fused(cpra_plan_s* p, int32_t n_iters) {
+  const cpra_config& c = p->cfg;
+  std::vector<JobStep> steps;
+  std::vector<int> sw_after;  // shrink-wrap after window k
+  const int n_pre = p->state_ready ? 0 : c.n_pre;
+  if (n_pre > 0) {  // Step A: HIO on angle 0 alone, one launch
+    JobStep s{};
+    s.prime = 1;
+    s.ca = plain_args();
+    s.g_src = p->g;
+    s.g = p->g;
+    s.err_slot = -1;
+    s.algo = kHIO;
+    s.active = 1;
+    s.n_iters = n_pre;
+    s.hio_left = n_pre;
+    steps.push_back(s);
+  }
+  const size_t first_win = steps.size();
+  float* gcur = p->g;
+  float* galt = p->g_alt;
+  for (int64_t t = p->t, end = p->t + n_iters; t < end;) {
+    int64_t tb = std::min<int64_t>(end, (t / c.n_ei + 1) * c.n_ei);
+    if (c.shrinkwrap_every > 0)
+      tb = std::min<int64_t>(tb, (t / c.shrinkwrap_every + 1) * c.shrinkwrap_every);
+    JobStep s{};
+    s.prime = 1;
+    if (t % c.n_ei == 0) {
+      s.ca = coupling_args(c);
+      s.g_src = gcur;
+      s.g_dst = galt;
+      std::swap(gcur, galt);
+    } else {
+      s.ca = plain_args();
+      s.g_src = gcur;
+    }
+    s.g = gcur;
+    s.err_slot = t;
+    s.algo = t < c.hio_iters ? kHIO : kER;
+    s.active = 1;
+    s.n_iters = (int)(tb - t);
+    s.hio_left = (int)std::max<int64_t>(0, std::min<int64_t>(tb - t, (int64_t)c.hio_iters - t));
+    steps.push_back(s);
+    sw_after.push_back(c.shrinkwrap_every > 0 && tb % c.shrinkwrap_every == 0);
+    t = tb;
+  }
+  cpra_status st = upload_steps(p, steps);
+  if (st != CPRA_OK) return st;
+  if (!p->state_ready) {
+    CK(launch_init_guess(p), "initial guess");
+    if (n_pre > 0)
+      CK(timed(p, CPRA_KERNEL_FUSED, [&] { return launch_fused(plan_launch(p, 0, 1)); }), "fused");
+    p->state_ready = true;
+  }
+  for (size_t k = first_win; k < steps.size(); ++k) {
+    const JobStep& s = steps[k];
+    CK(timed(p, CPRA_KERNEL_FUSED, [&] { return launch_fused(plan_launch(p, (int64_t)k, p->Np)); }),
+       "fused");
+    if (s.ca.store_g) std::swap(p->g, p->g_alt);
+    p->t += s.n_iters;
+    if (sw_after[k - first_win])
+      CK(timed(p, CPRA_KERNEL_SHRINKWRAP, [&] { return launch_shrinkwrap(p); }), "shrinkwrap");
+  }
+  p->hp_valid = false;
+  return CPRA_OK;
+}
+
 extern "C" {
 
 cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* c) {
@@ -456,6 +530,24 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
       return ts;
     }
     p->engine = e;
+  }
+  // AUTO: the fused engine where it is the faster one (N <= 256, FP32) and
+  // this device can hold its clusters, else the warp engine
+  const bool auto_fused = cfg->engine == CPRA_ENGINE_AUTO && cfg->precision == CPRA_FP32 &&
+                          fused_supported(cfg->N) && cfg->N <= 256 &&
+                          prepare_kernels(cfg->N, CPRA_ENGINE_FUSED, CPRA_FP32) == cudaSuccess;
+  cudaGetLastError();
+  if (auto_fused) p->engine = CPRA_ENGINE_FUSED;
+  if (cfg->engine == CPRA_ENGINE_FUSED) {
+    p->engine = CPRA_ENGINE_FUSED;
+    // a cluster of N/64 CTAs with its shared memory must fit on this device
+    cudaError_t e = prepare_kernels(p->N, CPRA_ENGINE_FUSED, CPRA_FP32);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete p;
+      return fail(nullptr, CPRA_ERR_UNSUPPORTED,
+                  std::string("fused engine cannot run here: ") + cudaGetErrorString(e));
+    }
   }
   p->loaded.assign(p->Np, 0);
   p->theta.resize(p->Np);
@@ -648,6 +740,17 @@ cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
   const cpra_config& c = p->cfg;
   cpra_status st = ensure_err_cap(p, p->t + n_iters);
   if (st != CPRA_OK) return st;
+  if (p->engine == CPRA_ENGINE_FUSED) {
+    const int64_t t0 = p->t;
+    st = iterate_fused(p, n_iters);
+    if (st != CPRA_OK) return st;
+    if (err_out && n_iters > 0) {
+      st = copy_out(p, err_out, p->err_hist + t0 * p->Np, sizeof(double) * n_iters * p->Np);
+      if (st != CPRA_OK) return st;
+    }
+    CK(cudaGetLastError(), "iterate");
+    return CPRA_OK;
+  }
   // the schedule of Steps A and B as one step-table row per iteration
   std::vector<JobStep> steps;
   const int n_pre = p->state_ready ? 0 : c.n_pre;
@@ -931,6 +1034,47 @@ JobStep next_step(cpra_plan_s* p) {
   return s;
 }
 
+// The step-table row of the fused engine for plan p's next window: at most
+// max_iters iterations from p->t, ending at the next coupling step.
+// Advances the plan's host-side schedule state like next_step.
+JobStep next_window(cpra_plan_s* p, int64_t max_iters) {
+  const cpra_config& c = p->cfg;
+  const int64_t t = p->t;
+  const int64_t tb = std::min<int64_t>(t + max_iters, (t / c.n_ei + 1) * c.n_ei);
+  JobStep s{};
+  s.prime = 1;
+  if (t % c.n_ei == 0) {  // Eq. 4 at the episode start, Jacobi into the other buffer
+    s.ca = coupling_args(c);
+    s.g_src = p->g;
+    s.g_dst = p->g_alt;
+    std::swap(p->g, p->g_alt);
+  } else {
+    s.ca = plain_args();
+    s.g_src = p->g;
+  }
+  s.g = p->g;
+  s.err_slot = t;
+  s.algo = t < c.hio_iters ? kHIO : kER;
+  s.active = 1;
+  s.n_iters = (int)(tb - t);
+  s.hio_left = (int)std::max<int64_t>(0, std::min<int64_t>(tb - t, (int64_t)c.hio_iters - t));
+  p->t = tb;
+  p->hp_valid = false;
+  return s;
+}
+
+// windows the fused engine needs for n iterations from iteration t
+int64_t fused_windows(int64_t t, int64_t n, int n_ei) {
+  int64_t w = 0;
+  while (n > 0) {
+    const int64_t tb = std::min<int64_t>(t + n, (t / n_ei + 1) * n_ei);
+    n -= tb - t;
+    t = tb;
+    ++w;
+  }
+  return w;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1015,10 +1159,38 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
   const size_t G = b->groups.size();
   std::vector<char> sig((size_t)n_iters * G, 0);
   std::vector<std::vector<JobStep>> steps(G);
-  for (size_t gi = 0; gi < G; ++gi) steps[gi].resize((size_t)n_iters * b->groups[gi].members.size());
+  for (size_t gi = 0; gi < G; ++gi) {
+    auto& g = b->groups[gi];
+    const size_t m = g.members.size();
+    if (g.engine == CPRA_ENGINE_FUSED) {
+      // rounds of windows: round r launches every member's r-th window
+      // (members with none left sit the round out)
+      std::vector<int64_t> left(m, n_iters);
+      for (int r = 0; r < n_iters; ++r) {
+        bool any = false;
+        for (size_t j = 0; j < m; ++j) {
+          JobStep s{};
+          if (left[j] > 0) {
+            s = next_window(b->plans[g.members[j]], left[j]);
+            left[j] -= s.n_iters;
+            any = true;
+          }
+          steps[gi].push_back(s);
+        }
+        if (!any) {
+          steps[gi].resize((size_t)r * m);
+          break;
+        }
+        sig[(size_t)r * G + gi] = 2;
+      }
+    } else {
+      steps[gi].resize((size_t)n_iters * m);
+    }
+  }
   for (int i = 0; i < n_iters; ++i)
     for (size_t gi = 0; gi < G; ++gi) {
       auto& g = b->groups[gi];
+      if (g.engine == CPRA_ENGINE_FUSED) continue;
       const size_t m = g.members.size();
       for (size_t j = 0; j < m; ++j) {
         JobStep s = next_step(b->plans[g.members[j]]);
@@ -1075,6 +1247,14 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
         L.tiles = g.d_tiles;
         L.ntiles = g.ntiles;
         cudaError_t e = cudaSuccess;
+        if (g.engine == CPRA_ENGINE_FUSED) {
+          if (sig[(size_t)i * G + gi] == 2) {
+            e = launch_fused(L);
+            ++kernels;
+          }
+          if (e != cudaSuccess) return e;
+          continue;
+        }
         if (sig[(size_t)i * G + gi]) {
           e = launch_prime(L);
           ++kernels;
@@ -1125,11 +1305,20 @@ int64_t cpra_batch_launches(cpra_batch_t b, int32_t n_iters) {
   if (!b) return -1;
   int64_t k = 0;
   for (auto& g : b->groups) {
-    (void)g;
+    if (g.engine == CPRA_ENGINE_FUSED) {  // one launch per round of windows
+      int64_t rounds = 0;
+      for (int mi : g.members) {
+        const cpra_plan_s* p = b->plans[mi];
+        rounds = std::max(rounds, fused_windows(p->t, n_iters, p->cfg.n_ei));
+      }
+      k += rounds;
+      continue;
+    }
     k += 2 * (int64_t)n_iters;
   }
   // coupling launches: one per group at every iteration where a member primes
   for (auto& g : b->groups) {
+    if (g.engine == CPRA_ENGINE_FUSED) continue;
     for (int i = 0; i < n_iters; ++i) {
       bool any = false;
       for (int mi : g.members) {
@@ -1251,9 +1440,10 @@ cpra_status cpra_autotune(int32_t N, int32_t precision, const char* cache_path,
   int best = CPRA_ENGINE_TWO_PASS;
   double best_ms = 1e30;
   std::ostringstream detail;
-  const int cands[2] = {CPRA_ENGINE_TWO_PASS, CPRA_ENGINE_WARP};
+  const int cands[3] = {CPRA_ENGINE_TWO_PASS, CPRA_ENGINE_WARP, CPRA_ENGINE_FUSED};
   for (int cand : cands) {
     if (cand == CPRA_ENGINE_WARP && !fast_supported(N)) continue;
+    if (cand == CPRA_ENGINE_FUSED && !fused_supported(N)) continue;
     double ms = 0.0;
     cpra_status s = time_engine(N, cand, &ms);
     if (s != CPRA_OK) return s;

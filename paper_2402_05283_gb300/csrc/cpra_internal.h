@@ -151,6 +151,8 @@ struct JobStep {
   int forward;         // row pass also computes the next row spectra
   int active;          // 0: the column and row passes skip this job
   CoupleArgs ca;
+  int n_iters;         // fused engine: iterations of this launch (prime first)
+  int hio_left;        // fused engine: how many of them are HIO (the rest ER)
 };
 
 // One launch over ntiles (job, angle) tiles.
@@ -187,6 +189,13 @@ cudaError_t launch_colpass_fast_tc(const Launch& L);
 cudaError_t launch_rowpass_fast(const Launch& L);
 cudaError_t launch_prime_fast(const Launch& L);
 cudaError_t launch_colpass_fast(const Launch& L);
+
+// cluster-resident fused engine (k_fused.cu): one launch = prime + n_iters
+// iterations of every tile, the angle's spectrum held in distributed shared
+// memory
+bool fused_supported(int N);
+cudaError_t prepare_kernels_fused(int N);
+cudaError_t launch_fused(const Launch& L);
 
 // records a failure of a call without a plan (cpra_last_error(NULL))
 cpra_status record_error(cpra_status st, const std::string& msg);

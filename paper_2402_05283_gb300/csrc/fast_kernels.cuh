@@ -211,6 +211,85 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   store_pairs_w<N>(b, T, Hn, pair0, lane);
 }
 
+// ---------------------------------------------------------------- Eq. 4 taps
+// Source image, support rows and seam mirroring of each coupling tap of
+// angle n: tap k reads angle (n + k - n_taps/2) mod Np, mirrored in u when
+// the seam was crossed an odd number of times (MIRROR wrap).
+struct TapTab {
+  const float* src[CPRA_MAX_TAPS];
+  const uint32_t* s[CPRA_MAX_TAPS];
+  int mir[CPRA_MAX_TAPS];
+};
+
+template <int N>
+__device__ __forceinline__ void fill_taps(TapTab& tt, const CoupleArgs& ca, const float* g_src,
+                                          const uint32_t* S, int n, int Np, int W) {
+  if (threadIdx.x < ca.n_taps) {
+    const int k = (int)threadIdx.x - ca.n_taps / 2;
+    const int j = n + k;
+    const int jm = ((j % Np) + Np) % Np;
+    const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
+    tt.src[threadIdx.x] = g_src + (size_t)jm * N * N;
+    tt.s[threadIdx.x] = S + (size_t)jm * N * W;
+    tt.mir[threadIdx.x] = ca.mirror && (wraps & 1);
+  }
+}
+
+// a (A layout) of this warp's row pairs = sum_k alpha_k tap_k (Eq. 4), or
+// the image itself for a single tap.  Taps outermost: every load of one tap
+// is independent, so a warp keeps 2 * TA * E1 loads in flight per tap.
+template <int N, class FL = WarpLines<N>>
+__device__ __forceinline__ void blend_rows(float2 (&a)[FL::TA][FL::E1], const TapTab& tt,
+                                           const CoupleArgs& ca, int W, int pair0, int lane) {
+  const int ntaps = ca.n_taps;
+  static_for<0, FL::TA>([&](auto II) {
+    static_for<0, FL::E1>([&](auto MM) { a[decltype(II)::value][decltype(MM)::value] = make_float2(0.f, 0.f); });
+  });
+  for (int k = 0; k < ntaps; ++k) {
+    const float* src = tt.src[k];
+    const uint32_t* sk = tt.s[k];
+    const bool mir = tt.mir[k] != 0;
+    const float alpha = ntaps == 1 ? 1.0f : ca.alpha[k];
+    static_for<0, FL::TA>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      const int t = lane + 32 * i;
+      const int y0 = 2 * (pair0 + FL::a_line(t));
+      static_for<0, FL::E1>([&](auto MM) {
+        constexpr int m = decltype(MM)::value;
+        const int x = FL::a_x(t, m);
+        const int xs_ = mir ? ((N - x) & (N - 1)) : x;
+        float v0 = __ldg(src + (size_t)y0 * N + xs_);
+        float v1 = __ldg(src + (size_t)(y0 + 1) * N + xs_);
+        if (ca.object) {
+          const bool in0 = (__ldg(sk + (size_t)y0 * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
+          const bool in1 = (__ldg(sk + (size_t)(y0 + 1) * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
+          v0 = (in0 && v0 >= 0.0f) ? v0 : 0.0f;
+          v1 = (in1 && v1 >= 0.0f) ? v1 : 0.0f;
+        }
+        a[i][m].x = fmaf(alpha, v0, a[i][m].x);
+        a[i][m].y = fmaf(alpha, v1, a[i][m].y);
+      });
+    });
+  }
+}
+
+// a (A layout) of this warp's row pairs -> rows of one image
+template <int N, class FL = WarpLines<N>>
+__device__ __forceinline__ void store_rows(const float2 (&a)[FL::TA][FL::E1], float* img, int pair0,
+                                           int lane) {
+  static_for<0, FL::TA>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
+    float* d0 = img + (size_t)(2 * (pair0 + FL::a_line(t))) * N;
+    static_for<0, FL::E1>([&](auto MM) {
+      constexpr int m = decltype(MM)::value;
+      const int x = FL::a_x(t, m);
+      d0[x] = a[i][m].x;
+      d0[N + x] = a[i][m].y;
+    });
+  });
+}
+
 // ---------------------------------------------------------------- prime
 template <int N, int PREC>
 __global__ void __launch_bounds__(kRowWarps * 32, 3)
@@ -238,68 +317,13 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
                                      J->tcw, warp);
   const int n = tl.y;
   const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
-  __shared__ const float* tap_src[CPRA_MAX_TAPS];
-  __shared__ const uint32_t* tap_s[CPRA_MAX_TAPS];
-  __shared__ int tap_mir[CPRA_MAX_TAPS];
+  __shared__ TapTab tt;
   load_xtw<N>(xs, xtw, kRowWarps * 32);
-  if (threadIdx.x < ca.n_taps) {
-    // angle (n + k) mod Np and whether the seam was crossed an odd number of times
-    const int k = (int)threadIdx.x - ca.n_taps / 2;
-    const int j = n + k;
-    const int jm = ((j % Np) + Np) % Np;
-    const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
-    tap_src[threadIdx.x] = g_src + (size_t)jm * N * N;
-    tap_s[threadIdx.x] = S + (size_t)jm * N * W;
-    tap_mir[threadIdx.x] = ca.mirror && (wraps & 1);
-  }
+  fill_taps<N>(tt, ca, g_src, S, n, Np, W);
   __syncthreads();
-  const int ntaps = ca.n_taps;
   float2 a[P::TA][P::E1];
-  static_for<0, P::TA>([&](auto II) {
-    static_for<0, P::E1>([&](auto MM) { a[decltype(II)::value][decltype(MM)::value] = make_float2(0.f, 0.f); });
-  });
-  // taps outermost: every load of one tap is independent, so a warp keeps
-  // 2 * TA * E1 loads in flight per tap
-  for (int k = 0; k < ntaps; ++k) {
-    const float* src = tap_src[k];
-    const uint32_t* sk = tap_s[k];
-    const bool mir = tap_mir[k] != 0;
-    const float alpha = ntaps == 1 ? 1.0f : ca.alpha[k];
-    static_for<0, P::TA>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      const int t = lane + 32 * i;
-      const int line = t / P::E2, l = t % P::E2;
-      const int y0 = 2 * (pair0 + line);
-      static_for<0, P::E1>([&](auto MM) {
-        constexpr int m = decltype(MM)::value;
-        const int x = l + P::E2 * m;
-        const int xs_ = mir ? ((N - x) & (N - 1)) : x;
-        float v0 = __ldg(src + (size_t)y0 * N + xs_);
-        float v1 = __ldg(src + (size_t)(y0 + 1) * N + xs_);
-        if (ca.object) {
-          const bool in0 = (__ldg(sk + (size_t)y0 * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
-          const bool in1 = (__ldg(sk + (size_t)(y0 + 1) * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
-          v0 = (in0 && v0 >= 0.0f) ? v0 : 0.0f;
-          v1 = (in1 && v1 >= 0.0f) ? v1 : 0.0f;
-        }
-        a[i][m].x = fmaf(alpha, v0, a[i][m].x);
-        a[i][m].y = fmaf(alpha, v1, a[i][m].y);
-      });
-    });
-  }
-  if (ca.store_g) {
-    static_for<0, P::TA>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      const int t = lane + 32 * i;
-      const int line = t / P::E2, l = t % P::E2;
-      float* d0 = g_dst + ((size_t)n * N + 2 * (pair0 + line)) * N;
-      static_for<0, P::E1>([&](auto MM) {
-        constexpr int m = decltype(MM)::value;
-        d0[l + P::E2 * m] = a[i][m].x;
-        d0[N + l + P::E2 * m] = a[i][m].y;
-      });
-    });
-  }
+  blend_rows<N>(a, tt, ca, W, pair0, lane);
+  if (ca.store_g) store_rows<N>(a, g_dst + (size_t)n * N * N, pair0, lane);
   float2 b[P::TB][P::E2];
   warp_fft_fwd<N, PREC>(a, b, T, xs, lane, &tc);
   store_pairs_w<N>(b, T, Hp + (size_t)n * N * H, pair0, lane);

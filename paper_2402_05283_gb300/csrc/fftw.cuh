@@ -260,4 +260,24 @@ __device__ __forceinline__ void warp_fft_inv(float2 (&b)[WP<N>::TB][WP<N>::E2],
   if constexpr (PREC != kPrecFP32) tc_step_a<N, PREC, +1>(a, T, *tc, lane);
 }
 
+// The L-line plan of N as a line-transform policy: task t = lane + 32 i of
+// a layout covers
+//   A layout: line a_line(t), points a_x(t, m), m < E1;
+//   B layout: line b_line(t), frequencies b_k(t, j), j < E2.
+template <int N> struct WarpLines {
+  using P = WP<N>;
+  static constexpr int L = P::L, TA = P::TA, E1 = P::E1, TB = P::TB, E2 = P::E2, TSIZE = P::TSIZE;
+  static __device__ __forceinline__ int a_line(int t) { return t / E2; }
+  static __device__ __forceinline__ int a_x(int t, int m) { return t % E2 + E2 * m; }
+  static __device__ __forceinline__ int b_line(int t) { return t / E1; }
+  static __device__ __forceinline__ int b_k(int t, int j) { return t % E1 + E1 * j; }
+  static __device__ __forceinline__ void fwd(float2 (&a)[TA][E1], float2 (&b)[TB][E2], float2* T,
+                                             const float2* xs, int lane) {
+    warp_fft_fwd<N>(a, b, T, xs, lane);
+  }
+  static __device__ __forceinline__ void inv(float2 (&b)[TB][E2], float2 (&a)[TA][E1], float2* T,
+                                             const float2* xs, int lane) {
+    warp_fft_inv<N>(b, a, T, xs, lane);
+  }
+};
 }  // namespace cpra

@@ -317,6 +317,11 @@ static cudaError_t prepare_n() {
 }
 
 cudaError_t prepare_kernels(int N, int engine, int prec) {
+  if (engine == CPRA_ENGINE_FUSED) {
+    // the fused engine's plans also run the warp kernels (assembly, batches)
+    cudaError_t e = prepare_kernels_fused(N);
+    return e == cudaSuccess ? prepare_kernels_fast(N) : e;
+  }
   if (engine == CPRA_ENGINE_WARP)
     return prec == CPRA_FP32 ? prepare_kernels_fast(N) : prepare_kernels_fast_tc(N, prec);
 #define CPRA_CASE(NN) \
@@ -326,7 +331,7 @@ cudaError_t prepare_kernels(int N, int engine, int prec) {
 }
 
 cudaError_t launch_prime(const Launch& L) {
-  if (L.engine == CPRA_ENGINE_WARP) return launch_prime_fast(L);
+  if (L.engine == CPRA_ENGINE_WARP || L.engine == CPRA_ENGINE_FUSED) return launch_prime_fast(L);
 #define CPRA_CASE(NN) \
   case NN: return prime_n<NN>(L);
   switch (L.N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
@@ -334,7 +339,7 @@ cudaError_t launch_prime(const Launch& L) {
 }
 
 cudaError_t launch_colpass(const Launch& L) {
-  if (L.engine == CPRA_ENGINE_WARP) return launch_colpass_fast(L);
+  if (L.engine == CPRA_ENGINE_WARP || L.engine == CPRA_ENGINE_FUSED) return launch_colpass_fast(L);
 #define CPRA_CASE(NN) \
   case NN: return colpass_n<NN>(L);
   switch (L.N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
@@ -342,7 +347,7 @@ cudaError_t launch_colpass(const Launch& L) {
 }
 
 cudaError_t launch_rowpass(const Launch& L) {
-  if (L.engine == CPRA_ENGINE_WARP) return launch_rowpass_fast(L);
+  if (L.engine == CPRA_ENGINE_WARP || L.engine == CPRA_ENGINE_FUSED) return launch_rowpass_fast(L);
 #define CPRA_CASE(NN) \
   case NN: return rowpass_n<NN>(L);
   switch (L.N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }

@@ -87,7 +87,7 @@ def test_batch_rejects_shrinkwrap_and_unloaded(cp):
 def test_autotune_cache(cp, tmp_path):
     path = str(tmp_path / "tune.json")
     eng, ms = cp.cpra_autotune(128, cp.FP32, path)
-    assert eng in (cp.ENGINE_TWO_PASS, cp.ENGINE_WARP) and ms > 0
+    assert eng in (cp.ENGINE_TWO_PASS, cp.ENGINE_WARP, cp.ENGINE_FUSED) and ms > 0
     doc = json.load(open(path))
     assert len(doc["entries"]) == 1 and doc["entries"][0]["engine"] == eng
     assert cp.cpra_autotune(128, cp.FP32, path) == (eng, pytest.approx(ms))

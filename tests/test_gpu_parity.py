@@ -121,11 +121,12 @@ def cfg1():
     return d
 
 
-@pytest.mark.parametrize("engine", ["auto", "two_pass"])
+@pytest.mark.parametrize("engine", ["auto", "two_pass", "warp", "fused"])
 def test_cfg1_er_all_50_iterates(cp, cfg1, engine):
     """The 1e-4 bar on every one of the first 50 iterates of all 32 angles."""
-    cfg = cp.make_config(64, 32, seed=1, hio_iters=0, er_iters=50, n_ei=10,
-                         engine=cp.ENGINE_AUTO if engine == "auto" else cp.ENGINE_TWO_PASS)
+    eng = {"auto": cp.ENGINE_AUTO, "two_pass": cp.ENGINE_TWO_PASS, "warp": cp.ENGINE_WARP,
+           "fused": cp.ENGINE_FUSED}[engine]
+    cfg = cp.make_config(64, 32, seed=1, hio_iters=0, er_iters=50, n_ei=10, engine=eng)
     worst, _ = _check_traj(cp, cfg1, cfg, 50, cfg1["true_support"])
     print(f"cfg1 ER 50 iterations: worst rel-L2 {worst:.2e}")
 
