@@ -234,7 +234,7 @@ def form_batch(cp, torch, seed=3):
             "bit_identical": bool(same), "compared": len(pairs)}
 
 
-def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0):
+def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0, early_start=False):
     """cfg 4 with time compressed by `compress`: Poisson arrivals at 4/s,
     each request streams its Np patterns at 10 patterns/s (both x compress),
     N in {256, 512}, Np in {180, 360}, 220 iterations; continuous batching
@@ -251,7 +251,8 @@ def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0):
     picks = [combos[i] for i in rng.integers(0, 4, size=n_req)]
     rate = 10.0 * compress  # patterns per second
     chunk = 10
-    srv = cp.Server(hbm_reserve_bytes=8 << 30, max_active=max_active, iters_per_round=10)
+    srv = cp.Server(hbm_reserve_bytes=8 << 30, max_active=max_active, iters_per_round=10,
+                    early_start=early_start)
     sched = []  # (time, kind, request index, first)
     for r in range(n_req):
         sched.append((arrivals[r], 0, r, 0))
@@ -275,9 +276,10 @@ def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0):
     for rid in ids:
         srv.wait(rid, 600.0)
     wall = time.perf_counter() - t0
-    first, final, first_sub, final_sub = [], [], [], []
+    first, final, first_sub, final_sub, ferr = [], [], [], [], []
     for rid in ids:
         info = srv.info(rid)
+        ferr.append(float(srv.result(rid, cp.RESULT_ERRORS)[-1].mean()))
         first.append(info["t_first_estimate"] - info["t_last_pattern"])
         final.append(info["t_final"] - info["t_last_pattern"])
         first_sub.append(info["t_first_estimate"] - info["t_submit"])
@@ -292,7 +294,45 @@ def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0):
             "p50_p99_s_final_after_submit": q(final_sub),
             "angle_iterations": int(st["angle_iterations"]),
             "value": round(st["angle_iterations"] / wall, 1), "wall_s": round(wall, 3),
-            "max_batch": int(st["max_batch"]), "rounds": int(st["rounds"])}
+            "max_batch": int(st["max_batch"]), "rounds": int(st["rounds"]),
+            "early_start": bool(early_start),
+            "mean_final_fourier_error": round(float(np.mean(ferr)), 5)}
+
+
+def form_p0(torch, I_dev, S_box, iters=20, beta=0.9, n_ei=10):
+    """The comparison path P0: the same iteration (HIO on the support with
+    positivity, Eq. 4 coupling alpha = (0.2, 0.6, 0.2) every n_ei) written as
+    cuFFT transforms (torch.fft) plus separate elementwise kernels on a
+    complex FP32 spectrum, on the workload of the plain path.  Timed only;
+    never on the product path."""
+    Np_, N_, _ = I_dev.shape
+    A = torch.fft.ifftshift(torch.sqrt(torch.clamp(I_dev, min=0.0)), dim=(-2, -1))
+    S = S_box.bool().expand(Np_, N_, N_) if S_box.dim() == 2 else S_box.bool()
+    g = torch.rand((Np_, N_, N_), device=I_dev.device) * S
+
+    def step(t, g):
+        if t % n_ei == 0:
+            g = 0.2 * torch.roll(g, 1, 0) + 0.6 * g + 0.2 * torch.roll(g, -1, 0)
+        G = torch.fft.fft2(g)
+        mag = torch.abs(G)
+        Gp = torch.where(mag > 0, A * G / torch.clamp(mag, min=1e-30), A.to(G.dtype))
+        gp = torch.fft.ifft2(Gp).real
+        v = S & (gp >= 0)
+        return torch.where(v, gp, g - beta * gp)
+
+    for t in range(3):
+        g = step(t, g)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(iters):
+        g = step(t, g)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": round(Np_ * iters / (ms * 1e-3), 1), "unit": "angle-iterations/s",
+            "what": "cuFFT (torch.fft) + separate elementwise kernels, complex64 spectrum, "
+                    f"N={N_}, Np={Np_}, {iters} HIO iterations with coupling every {n_ei}"}
 
 
 def form_precision(cp, torch, I_dev, thetas, S_box, n_angles=NP, N_=N, sample=(0, 1), iters=5):
@@ -464,10 +504,12 @@ def run_gpu(args):
 
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
-        forms = {"precision": form_precision(cp, torch, I_dev, thetas, S_box),
+        forms = {"p0_cufft_pointwise": form_p0(torch, I_dev, S_box),
+                 "precision": form_precision(cp, torch, I_dev, thetas, S_box),
                  "batching": form_batch(cp, torch),
                  "serving_continuous": form_serving(cp, torch, max_active=0),
-                 "serving_one_at_a_time": form_serving(cp, torch, max_active=1)}
+                 "serving_one_at_a_time": form_serving(cp, torch, max_active=1),
+                 "serving_early_start": form_serving(cp, torch, max_active=0, early_start=True)}
     if rank == 0:
         cb = cpu_baseline(I_dev[:8].cpu().numpy(), d["support"]) if world == 1 else None
         qs = np.percentile(step_ms, [50, 99])

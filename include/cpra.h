@@ -92,10 +92,16 @@ enum {
  *   engine         kernel family.  TWO_PASS: row and column passes with
  *                  block-wide shared-memory FFTs (every supported N).  WARP:
  *                  the same passes with warp-resident two-level FFTs
- *                  (N = 64, 128, 256, 512, 1024).  AUTO: WARP where
- *                  available, else TWO_PASS.  TUNED: the fastest engine for
- *                  this N on this GPU according to cpra_autotune (its
- *                  default cache).  FUSED is reserved.
+ *                  (N = 64, 128, 256, 512, 1024).  FUSED: one launch per
+ *                  run of iterations between coupling steps, each angle's
+ *                  spectrum held in the distributed shared memory of a
+ *                  thread-block cluster (N = 64, 128, 256, 512; FP32; needs a
+ *                  GPU that can hold an N/32-CTA cluster at N = 512, an
+ *                  N/64-CTA cluster below, else UNSUPPORTED at cpra_plan).
+ *                  AUTO: FUSED for N <= 256 in FP32 where the device holds
+ *                  its clusters, else WARP where available, else TWO_PASS.
+ *                  TUNED: the fastest engine for this N on this GPU
+ *                  according to cpra_autotune (its default cache).
  *   seed           seeds the random initial guess (SplitMix64 per pixel).
  *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
  */
@@ -163,8 +169,21 @@ cpra_status cpra_load_state(cpra_plan_t plan, const float* g, int64_t t);
  * FFT -> HIO/ER update for every angle, shrink-wrap on schedule.  If err_out
  * is not NULL it receives the Fourier error of every angle and iteration,
  * err_out[i*Np + n] (double, host or device).  Returns NOT_READY until every
- * angle has intensities. */
+ * iterating angle (every angle unless cpra_set_present restricted them) has
+ * intensities. */
 cpra_status cpra_iterate(cpra_plan_t plan, int32_t n_iters, double* err_out);
+
+/* Let only the angles with mask[n] != 0 iterate (mask: host memory, Np
+ * bytes, read during the call; NULL = every angle), so that a reconstruction
+ * can start while its patterns are still arriving.  Reading of the paper's
+ * concurrent partial reconstruction: the iterating angles run Step B as
+ * usual, and Eq. 4 couples each of them with its present neighbours only,
+ * the alpha_k of the present taps divided by their sum; absent angles keep
+ * their state (the seeded start until they join) and their error entries
+ * stay 0.  INVALID_ARG when no angle is present, UNSUPPORTED with
+ * shrink-wrap on; cpra_assemble_3d returns NOT_READY while an angle is
+ * absent.  Batches follow a member's mask from their next iterate call. */
+cpra_status cpra_set_present(cpra_plan_t plan, const uint8_t* mask);
 
 /* Step D: spectra of P_{S+} g with the centre-of-mass phase ramp, Fourier
  * slice gridding (bilinear in kx, ky; exact kz) into an N^3 grid, inverse 3D
@@ -190,7 +209,7 @@ enum {
   CPRA_KERNEL_PRIME = 2,     /* coupling (Eq. 4) + R2C rows                        */
   CPRA_KERNEL_SHRINKWRAP = 3,
   CPRA_KERNEL_ASSEMBLE = 4,
-  CPRA_KERNEL_FUSED = 5,     /* fused engine: one whole iteration                  */
+  CPRA_KERNEL_FUSED = 5,     /* fused engine: prime + a run of whole iterations    */
   CPRA_KERNEL_PREPARE = 6,
   CPRA_KERNEL_KINDS = 7
 };
@@ -242,7 +261,9 @@ cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_in, uint8_t*
  *
  * A batch iterates several plans together: for every group of plans with
  * the same N and engine, each kernel of an iteration runs as ONE launch
- * whose tiles are the (plan, angle) pairs of the whole group; each plan
+ * whose tiles are the (plan, angle) pairs of the whole group (for the FUSED
+ * engine: one launch per round, round r running every member's r-th run of
+ * iterations between its coupling steps); each plan
  * keeps its own schedule (its own t, episode boundaries, HIO/ER switch), so
  * every plan computes exactly what cpra_iterate would (bit-identical).  With
  * use_graph = 1 the launches of one cpra_batch_iterate call are captured
@@ -268,7 +289,7 @@ int64_t cpra_batch_launches(cpra_batch_t batch, int32_t n_iters);
 
 cpra_status cpra_batch_destroy(cpra_batch_t batch);
 
-/* Autotuner: time each engine available for N (TWO_PASS, WARP) on a sample
+/* Autotuner: time each engine available for N (TWO_PASS, WARP, FUSED) on a sample
  * of 64 random patterns with CUDA events on a private stream, and keep the
  * fastest per (N, precision, SM count, device name) in a JSON cache file.
  * cache_path NULL = $CPRA_TUNE_CACHE or $HOME/.cache/cpra_tune.json.  A
@@ -285,13 +306,15 @@ cpra_status cpra_autotune(int32_t N, int32_t precision, const char* cache_path,
  * device's free memory minus the request's footprint (cpra_plan_bytes:
  * iteration state + assembly) stays above hbm_reserve_bytes; prepares the
  * patterns pushed for resident requests as they arrive; and advances every
- * request whose angles have all arrived in rounds of iters_per_round
- * iterations, all running requests together through one batch (see
- * cpra_batch_create), so requests arriving while others run join at the
- * next round.  After its first episode (n_ei iterations) a request gets a
+ * request whose angles have all arrived (with early_start: whose first
+ * angles have arrived) in rounds of iters_per_round iterations, all running
+ * requests together through one batch (see cpra_batch_create), so requests
+ * arriving while others run join at the next round.  After its first
+ * episode with every angle present (n_ei iterations) a request gets a
  * first 3D estimate (cpra_assemble_3d), after hio_iters + er_iters
- * iterations its final volume.  Each request computes exactly what a
- * standalone plan would.  The paper motivates this by reconstructing while
+ * iterations its final volume.  Without early_start each request computes
+ * exactly what a standalone plan would; with it, what a plan computes whose
+ * present mask follows the arrivals round by round.  The paper motivates this by reconstructing while
  * the experiment runs ("concurrent partial reconstructions", concluding
  * section); the serving loop itself has no counterpart in the paper.
  * Times are seconds since cpra_server_start.
@@ -304,6 +327,14 @@ typedef struct {
   int32_t iters_per_round;   /* iterations per batched round (default 10)       */
   int32_t use_graph;         /* capture each round's launches in a CUDA graph   */
   void* stream;              /* cudaStream_t of the serving thread (NULL = own) */
+  int32_t early_start;       /* 1: a request iterates its arrived angles while the
+                                others stream in (cpra_set_present), holding its
+                                last early_tail iterations until every angle is
+                                there; 0 (default): it starts once every angle
+                                arrived                                         */
+  int32_t early_tail;        /* iterations kept for after the last pattern with
+                                early_start (0 = half the schedule, rounded up
+                                to whole episodes; at least one episode)        */
 } cpra_server_config;
 
 enum { CPRA_EVENT_FIRST_ESTIMATE = 1, CPRA_EVENT_FINAL = 2, CPRA_EVENT_FAILED = 3 };

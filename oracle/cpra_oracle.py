@@ -50,6 +50,11 @@ design notes):
       weight < 1e-12 are 0.  Volume = fftshift(IDFT3(V)).
   R12 FFT conventions: forward unnormalised with exp(-2 pi i jk/N), inverse
       carries 1/N per axis; intensities arrive centred and are ifftshifted.
+  R13 Partial presence (serving while patterns still arrive, the concluding
+      section's concurrent partial reconstruction): only angles marked
+      present iterate; Eq. 4 couples each present angle with its present
+      neighbours, the alpha_k of the present taps divided by their sum (all
+      taps present: the alpha_k as given); absent angles keep their state.
 """
 from __future__ import annotations
 
@@ -239,20 +244,29 @@ def object_estimate(g, S):
     return np.where(S.astype(bool) & (g >= 0), g, 0.0)
 
 
-def couple(g, alpha, wrap=WRAP_LITERAL, blend=BLEND_STATE, S=None):
-    """O_n <- sum_{k=-r..r} alpha_k O_{(n+k) mod Np}, all n from the old stack."""
+def couple(g, alpha, wrap=WRAP_LITERAL, blend=BLEND_STATE, S=None, present=None):
+    """O_n <- sum_{k=-r..r} alpha_k O_{(n+k) mod Np}, all n from the old stack
+    (Eq. 4, R1).  With a present mask (R13) an absent n keeps its g, and a
+    present n sums its present taps only, with weights alpha_k / sum of the
+    present taps' alpha."""
     Np = g.shape[0]
     alpha = np.asarray(alpha, dtype=np.float64)
     r = len(alpha) // 2
+    on = np.ones(Np, dtype=bool) if present is None else np.asarray(present).astype(bool)
     src = g if blend == BLEND_STATE else object_estimate(g, S)
     out = np.zeros_like(g, dtype=np.float64)
     for n in range(Np):
-        for k in range(-r, r + 1):
+        if not on[n]:
+            out[n] = g[n]
+            continue
+        taps = [k for k in range(-r, r + 1) if on[(n + k) % Np]]
+        norm = 1.0 if len(taps) == 2 * r + 1 else sum(alpha[k + r] for k in taps)
+        for k in taps:
             j = n + k
             img = src[j % Np]
             if wrap == WRAP_MIRROR and (j // Np) % 2 != 0:
                 img = _mirror_u(img)
-            out[n] += alpha[k + r] * img
+            out[n] += (alpha[k + r] / norm) * img
     return out
 
 
@@ -389,6 +403,7 @@ class OracleRun:
     t: int = 0
     errors: list = field(default_factory=list)
     margins: list = field(default_factory=list)
+    present: np.ndarray = None  # R13: angles that iterate (None = all)
 
     @classmethod
     def start(cls, cfg: OracleConfig, I_centred, S0=None, g0=None):
@@ -409,10 +424,16 @@ class OracleRun:
         """One global iteration t (coupling first at episode starts)."""
         c = self.cfg
         if self.t % c.n_ei == 0:
-            self.g = couple(self.g, c.alpha, c.wrap, c.blend, self.S)
+            self.g = couple(self.g, c.alpha, c.wrap, c.blend, self.S, self.present)
         algo = HIO if self.t < c.hio_iters else ER
-        self.g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True)
-        self.errors.append(np.sqrt(num / den))
+        g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True)
+        err = np.sqrt(num / den)
+        if self.present is not None:  # absent angles keep their state (R13)
+            on = np.asarray(self.present).astype(bool)
+            g = np.where(on[:, None, None], g, self.g)
+            err = np.where(on, err, 0.0)
+        self.g = g
+        self.errors.append(err)
         self.margins.append(positivity_margin(gp, self.S))
         if c.shrinkwrap_every > 0 and (self.t + 1) % c.shrinkwrap_every == 0:
             self.S = shrinkwrap(self.g, self.S, c.sw_sigma, c.sw_tau)

@@ -44,7 +44,8 @@ class cpra_config(C.Structure):
 
 class cpra_server_config(C.Structure):
     _fields_ = [("hbm_reserve_bytes", C.c_size_t), ("max_active", C.c_int32),
-                ("iters_per_round", C.c_int32), ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+                ("iters_per_round", C.c_int32), ("use_graph", C.c_int32), ("stream", C.c_void_p),
+                ("early_start", C.c_int32), ("early_tail", C.c_int32)]
 
 
 class cpra_server_event(C.Structure):
@@ -96,6 +97,7 @@ def lib() -> C.CDLL:
             "cpra_result": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
             "cpra_iteration": (C.c_int64, [P]),
             "cpra_reset": (C.c_int, [P]),
+            "cpra_set_present": (C.c_int, [P, P]),
             "cpra_set_profiling": (C.c_int, [P, C.c_int32]),
             "cpra_kernel_stats": (C.c_int, [P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "cpra_launch_count": (C.c_int64, []),
@@ -216,6 +218,12 @@ def cpra_iteration(plan) -> int:
 
 def cpra_reset(plan):
     _check(lib().cpra_reset(plan), plan)
+
+
+def cpra_set_present(plan, mask):
+    """mask: None or a host uint8 array of Np entries."""
+    p = None if mask is None else mask.ctypes.data_as(C.c_void_p)
+    _check(lib().cpra_set_present(plan, p), plan)
 
 
 def cpra_set_profiling(plan, on: bool):
@@ -385,6 +393,14 @@ class Plan:
     def reset(self):
         cpra_reset(self.h)
 
+    def set_present(self, mask=None):
+        """Let only the angles with mask[n] != 0 iterate (None: every angle)."""
+        if mask is not None:
+            mask = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+            if mask.shape != (self.Np,):
+                raise ValueError("mask must hold Np entries")
+        cpra_set_present(self.h, mask)
+
     def set_profiling(self, on: bool = True):
         cpra_set_profiling(self.h, on)
 
@@ -438,7 +454,8 @@ class Batch:
 class Server:
     """The library's serving thread (continuous batching of reconstructions)."""
 
-    def __init__(self, hbm_reserve_bytes=None, max_active=0, iters_per_round=10, use_graph=True):
+    def __init__(self, hbm_reserve_bytes=None, max_active=0, iters_per_round=10, use_graph=True,
+                 early_start=False, early_tail=0):
         cfg = cpra_server_config()
         _check(lib().cpra_server_default_config(C.byref(cfg)))
         if hbm_reserve_bytes is not None:
@@ -446,6 +463,8 @@ class Server:
         cfg.max_active = max_active
         cfg.iters_per_round = iters_per_round
         cfg.use_graph = int(bool(use_graph))
+        cfg.early_start = int(bool(early_start))
+        cfg.early_tail = int(early_tail)
         self.h = C.c_void_p()
         _check(lib().cpra_server_start(C.byref(cfg), C.byref(self.h)))
         self.cfgs = {}
@@ -487,6 +506,8 @@ class Server:
             a = np.empty((N, N, N), np.complex64)
         elif what == RESULT_SUPPORT:
             a = np.empty((Np, N, N), np.uint8)
+        elif what == RESULT_ERRORS:
+            a = np.empty((self.info(rid)["iterations_done"], Np), np.float64)
         else:
             raise ValueError(what)
         _check(lib().cpra_server_result(self.h, rid, what, a.ctypes.data, a.nbytes))

@@ -198,6 +198,9 @@ cpra_status ensure_err_cap(cpra_plan_s* p, int64_t need) {
   if (p->err_hist && p->t > 0)
     CK(cudaMemcpyAsync(nh, p->err_hist, sizeof(double) * p->t * p->Np, cudaMemcpyDeviceToDevice,
                        p->stream), "err_hist copy");
+  // angles outside a present mask leave their entries 0
+  CK(cudaMemsetAsync(nh + p->t * p->Np, 0, sizeof(double) * (cap - p->t) * p->Np, p->stream),
+     "err_hist clear");
   CK(cudaStreamSynchronize(p->stream), "err_hist sync");
   dev_free(p, p->err_hist);
   p->err_hist = nh;
@@ -263,6 +266,7 @@ JobStatic job_static(const cpra_plan_s* p) {
   j.tw = p->tw;
   j.xtw = p->xtw;
   j.tcw = p->tcw;
+  j.present = p->partial ? p->present : nullptr;
   j.Np = p->Np;
   j.W = p->W;
   j.beta = p->cfg.beta;
@@ -390,6 +394,13 @@ cpra_status build_gridding(cpra_plan_s* p) {
   return CPRA_OK;
 }
 
+// every angle that iterates has intensities
+bool present_loaded(const cpra_plan_s* p) {
+  for (int n = 0; n < p->Np; ++n)
+    if (p->present_h[n] && !p->loaded[n]) return false;
+  return true;
+}
+
 }  // namespace
 
 cpra_status cpra::record_error(cpra_status st, const std::string& msg) {
@@ -456,7 +467,7 @@ static cpra_status iterate_fused(cpra_plan_s* p, int32_t n_iters) {
   }
   for (size_t k = first_win; k < steps.size(); ++k) {
     const JobStep& s = steps[k];
-    CK(timed(p, CPRA_KERNEL_FUSED, [&] { return launch_fused(plan_launch(p, (int64_t)k, p->Np)); }),
+    CK(timed(p, CPRA_KERNEL_FUSED, [&] { return launch_fused(plan_launch(p, (int64_t)k, p->n_present)); }),
        "fused");
     if (s.ca.store_g) std::swap(p->g, p->g_alt);
     p->t += s.n_iters;
@@ -651,6 +662,8 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   std::vector<int2> tiles(Np);
   for (size_t n = 0; n < Np; ++n) tiles[n] = make_int2(0, (int)n);
   if (e == cudaSuccess)
+    p->n_present = (int)Np;
+    p->present_h.assign(Np, 1);
     e = cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * Np, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) {
     JobStatic j = job_static(p);
@@ -723,6 +736,8 @@ cpra_status cpra_load_state(cpra_plan_t p, const float* g, int64_t t) {
   const size_t bytes = sizeof(float) * p->Np * p->N * p->N;
   CK(cudaMemcpyAsync(p->g, g, bytes, is_device_ptr(g) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      p->stream), "state upload");
+  // both Jacobi buffers, so that angles outside a present mask keep it
+  CK(cudaMemcpyAsync(p->g_alt, p->g, bytes, cudaMemcpyDeviceToDevice, p->stream), "state copy");
   CK(cudaStreamSynchronize(p->stream), "state sync");
   cpra_status st = ensure_err_cap(p, t);
   if (st != CPRA_OK) return st;
@@ -736,7 +751,9 @@ cpra_status cpra_load_state(cpra_plan_t p, const float* g, int64_t t) {
 cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
   if (n_iters < 0) return fail(p, CPRA_ERR_INVALID_ARG, "n_iters < 0");
-  if (p->n_loaded < p->Np) return fail(p, CPRA_ERR_NOT_READY, "not every angle has intensities");
+  if (!present_loaded(p)) return fail(p, CPRA_ERR_NOT_READY, "an iterating angle has no intensities");
+  if (!p->state_ready && p->cfg.n_pre > 0 && !p->present_h[0])
+    return fail(p, CPRA_ERR_NOT_READY, "Step A needs angle 0");
   const cpra_config& c = p->cfg;
   cpra_status st = ensure_err_cap(p, p->t + n_iters);
   if (st != CPRA_OK) return st;
@@ -808,11 +825,11 @@ cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
     const int64_t k = n_pre + i;
     const JobStep& s = steps[k];
     if (s.prime) {
-      CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(plan_launch(p, k, p->Np)); }), "prime");
+      CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(plan_launch(p, k, p->n_present)); }), "prime");
       if (s.ca.store_g) std::swap(p->g, p->g_alt);
     }
-    CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(plan_launch(p, k, p->Np)); }), "colpass");
-    CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(plan_launch(p, k, p->Np)); }), "rowpass");
+    CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(plan_launch(p, k, p->n_present)); }), "colpass");
+    CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(plan_launch(p, k, p->n_present)); }), "rowpass");
     p->hp_valid = s.forward != 0;
     if (c.shrinkwrap_every > 0 && (p->t + 1) % c.shrinkwrap_every == 0)
       CK(timed(p, CPRA_KERNEL_SHRINKWRAP, [&] { return launch_shrinkwrap(p); }), "shrinkwrap");
@@ -829,6 +846,7 @@ cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
 cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
   if (!p->state_ready) return fail(p, CPRA_ERR_NOT_READY, "no iterate to assemble");
+  if (p->partial) return fail(p, CPRA_ERR_NOT_READY, "assembly needs every angle present");
   const size_t N = p->N, Np = p->Np, NN = N * N;
   Assembly& a = p->asmb;
   if (!a.F) {
@@ -905,6 +923,35 @@ cpra_status cpra_result(cpra_plan_t p, int32_t what, void* dst, size_t bytes) {
 
 int64_t cpra_iteration(cpra_plan_t p) { return p ? p->t : -1; }
 
+cpra_status cpra_set_present(cpra_plan_t p, const uint8_t* mask) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  std::vector<uint8_t> m(p->Np, 1);
+  if (mask)
+    for (int n = 0; n < p->Np; ++n) m[n] = mask[n] != 0;
+  std::vector<int2> tiles;
+  for (int n = 0; n < p->Np; ++n)
+    if (m[n]) tiles.push_back(make_int2(0, n));
+  if (tiles.empty()) return fail(p, CPRA_ERR_INVALID_ARG, "no angle present");
+  const bool all = (int)tiles.size() == p->Np;
+  if (!all && p->cfg.shrinkwrap_every > 0)
+    return fail(p, CPRA_ERR_UNSUPPORTED, "a present mask runs without shrink-wrap");
+  if (m == p->present_h) return CPRA_OK;
+  if (!p->present) {
+    p->present = (uint8_t*)dev_alloc(p, (size_t)p->Np);
+    if (!p->present) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "present mask allocation failed");
+  }
+  CK(cudaMemcpyAsync(p->present, m.data(), (size_t)p->Np, cudaMemcpyHostToDevice, p->stream), "mask");
+  CK(cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice,
+                     p->stream), "tiles");
+  CK(cudaStreamSynchronize(p->stream), "mask sync");
+  p->present_h = m;
+  p->n_present = (int)tiles.size();
+  p->partial = !all;
+  p->present_version++;
+  p->hp_valid = false;
+  return upload_static(p);
+}
+
 cpra_status cpra_reset(cpra_plan_t p) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
   p->t = 0;
@@ -971,8 +1018,9 @@ struct cpra_batch_s {
     int N = 0, engine = 0, prec = 0;
     std::vector<int> members;
     JobStatic* d_js = nullptr;
-    int2* d_tiles = nullptr;
+    int2* d_tiles = nullptr;   // room for every angle of every member
     int ntiles = 0;
+    std::vector<int64_t> versions;  // members' present-mask versions the tiles follow
     JobStep* d_steps = nullptr;
     int64_t steps_cap = 0;
   };
@@ -995,6 +1043,21 @@ cpra_status bfail(cpra_batch_s* b, cpra_status st, const std::string& msg) {
   if (b) b->err = msg;
   g_last_error = msg;
   return st;
+}
+
+// (member, angle) tiles of a group: every iterating angle of every member
+cudaError_t group_tiles(cpra_batch_s* b, cpra_batch_s::Group& g) {
+  std::vector<int2> tiles;
+  g.versions.clear();
+  for (size_t j = 0; j < g.members.size(); ++j) {
+    const cpra_plan_s* p = b->plans[g.members[j]];
+    for (int a = 0; a < p->Np; ++a)
+      if (p->present_h[a]) tiles.push_back(make_int2((int)j, a));
+    g.versions.push_back(p->present_version);
+  }
+  g.ntiles = (int)tiles.size();
+  return cudaMemcpyAsync(g.d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
+                         cudaMemcpyHostToDevice, b->stream);
 }
 
 void* balloc(cpra_batch_s* b, size_t bytes) {
@@ -1118,18 +1181,16 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
     b->groups[gi].members.push_back(i);
   }
   for (auto& g : b->groups) {
-    std::vector<int2> tiles;
-    for (size_t j = 0; j < g.members.size(); ++j)
-      for (int a = 0; a < b->plans[g.members[j]]->Np; ++a) tiles.push_back(make_int2((int)j, a));
-    g.ntiles = (int)tiles.size();
+    size_t room = 0;
+    for (int mi : g.members) room += (size_t)b->plans[mi]->Np;
     g.d_js = (JobStatic*)balloc(b, sizeof(JobStatic) * g.members.size());
-    g.d_tiles = (int2*)balloc(b, sizeof(int2) * tiles.size());
+    g.d_tiles = (int2*)balloc(b, sizeof(int2) * room);
     if (!g.d_js || !g.d_tiles) {
       cpra_batch_destroy(b);
       return bfail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "batch tables");
     }
-    cudaError_t e = cudaMemcpy(g.d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
-                               cudaMemcpyHostToDevice);
+    cudaError_t e = group_tiles(b, g);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess) e = prepare_kernels(g.N, g.engine, g.prec);
     if (e != cudaSuccess) {
       cpra_batch_destroy(b);
@@ -1144,7 +1205,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
   if (!b) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "batch is NULL");
   if (n_iters < 0) return bfail(b, CPRA_ERR_INVALID_ARG, "n_iters < 0");
   for (cpra_plan_s* p : b->plans)
-    if (p->n_loaded < p->Np) return bfail(b, CPRA_ERR_NOT_READY, "a plan lacks intensities");
+    if (!present_loaded(p)) return bfail(b, CPRA_ERR_NOT_READY, "a plan lacks intensities");
   for (cpra_plan_s* p : b->plans) {
     if (!p->state_ready) {  // seeded start and Step A through the plan itself
       cpra_status st = cpra_iterate(p, 0, nullptr);
@@ -1155,6 +1216,22 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
   }
   if (n_iters == 0) return CPRA_OK;
   cudaStream_t stream = b->stream;
+  for (auto& g : b->groups) {  // present masks changed since the tiles were built
+    bool stale = false;
+    for (size_t j = 0; j < g.members.size(); ++j)
+      stale = stale || b->plans[g.members[j]]->present_version != g.versions[j];
+    if (!stale) continue;
+    cudaError_t e = group_tiles(b, g);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch tiles: ") + cudaGetErrorString(e));
+    if (b->exec) {  // the graph holds the old tile counts
+      cudaGraphExecDestroy(b->exec);
+      cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      b->graph_sig.clear();
+    }
+  }
   // step tables (and the launch pattern) of every group for this call
   const size_t G = b->groups.size();
   std::vector<char> sig((size_t)n_iters * G, 0);

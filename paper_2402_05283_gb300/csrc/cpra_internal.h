@@ -76,7 +76,13 @@ struct cpra_plan_s {
   cpra::Assembly asmb;
   // kernel tables of this plan as a one-job launch
   cpra::JobStatic* d_js = nullptr;
-  int2* d_tiles = nullptr;
+  int2* d_tiles = nullptr;     // (0, angle) of every iterating angle, ascending
+  // angles that iterate (cpra_set_present); all of them unless partial
+  uint8_t* present = nullptr;  // device, Np bytes
+  std::vector<uint8_t> present_h;
+  int n_present = 0;
+  bool partial = false;
+  int64_t present_version = 0;
   cpra::JobStep* d_steps = nullptr;
   int64_t steps_cap = 0;
 
@@ -134,6 +140,7 @@ struct JobStatic {
   const float2* tw;
   const float2* xtw;
   const uint16_t* tcw;  // 16-bit block DFT matrices (tensor-core precision)
+  const uint8_t* present;  // angles that iterate (coupling renormalises), NULL = all
   int Np, W;
   float beta;
   int pad;

@@ -15,6 +15,7 @@
 #include "cpra_internal.h"
 #include "fft.cuh"
 #include "fftw.cuh"
+#include "taps.cuh"
 
 namespace cpra {
 
@@ -212,29 +213,6 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 }
 
 // ---------------------------------------------------------------- Eq. 4 taps
-// Source image, support rows and seam mirroring of each coupling tap of
-// angle n: tap k reads angle (n + k - n_taps/2) mod Np, mirrored in u when
-// the seam was crossed an odd number of times (MIRROR wrap).
-struct TapTab {
-  const float* src[CPRA_MAX_TAPS];
-  const uint32_t* s[CPRA_MAX_TAPS];
-  int mir[CPRA_MAX_TAPS];
-};
-
-template <int N>
-__device__ __forceinline__ void fill_taps(TapTab& tt, const CoupleArgs& ca, const float* g_src,
-                                          const uint32_t* S, int n, int Np, int W) {
-  if (threadIdx.x < ca.n_taps) {
-    const int k = (int)threadIdx.x - ca.n_taps / 2;
-    const int j = n + k;
-    const int jm = ((j % Np) + Np) % Np;
-    const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
-    tt.src[threadIdx.x] = g_src + (size_t)jm * N * N;
-    tt.s[threadIdx.x] = S + (size_t)jm * N * W;
-    tt.mir[threadIdx.x] = ca.mirror && (wraps & 1);
-  }
-}
-
 // a (A layout) of this warp's row pairs = sum_k alpha_k tap_k (Eq. 4), or
 // the image itself for a single tap.  Taps outermost: every load of one tap
 // is independent, so a warp keeps 2 * TA * E1 loads in flight per tap.
@@ -246,10 +224,11 @@ __device__ __forceinline__ void blend_rows(float2 (&a)[FL::TA][FL::E1], const Ta
     static_for<0, FL::E1>([&](auto MM) { a[decltype(II)::value][decltype(MM)::value] = make_float2(0.f, 0.f); });
   });
   for (int k = 0; k < ntaps; ++k) {
+    const float alpha = tt.w[k];
+    if (alpha == 0.0f) continue;  // a tap on an absent angle
     const float* src = tt.src[k];
     const uint32_t* sk = tt.s[k];
     const bool mir = tt.mir[k] != 0;
-    const float alpha = ntaps == 1 ? 1.0f : ca.alpha[k];
     static_for<0, FL::TA>([&](auto II) {
       constexpr int i = decltype(II)::value;
       const int t = lane + 32 * i;
@@ -319,7 +298,7 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
   __shared__ TapTab tt;
   load_xtw<N>(xs, xtw, kRowWarps * 32);
-  fill_taps<N>(tt, ca, g_src, S, n, Np, W);
+  fill_taps<N>(tt, ca, g_src, S, n, Np, W, J->present);
   __syncthreads();
   float2 a[P::TA][P::E1];
   blend_rows<N>(a, tt, ca, W, pair0, lane);

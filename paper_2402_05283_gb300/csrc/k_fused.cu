@@ -1,26 +1,27 @@
 // k_fused.cu - cluster-resident fused iteration, N in {64, 128, 256, 512}.
 //
-// One thread-block cluster of C = N/64 CTAs owns one angle for a whole
-// launch: the prime (Eq. 4 coupling, or a plain read of g, then the row
-// R2C) and n_iters iterations of
+// One thread-block cluster of C CTAs owns one angle for a whole launch: the
+// prime (Eq. 4 coupling, or a plain read of g, then the row R2C) and
+// n_iters iterations of
 //   column FFT -> modulus projection onto A_sym (FP64 Fourier error) ->
 //   column IFFT -> row C2R -> HIO / ER update -> row R2C,
 // with the packed half spectrum (N x N/2 complex, column 0 holding
 // (Re H(y,0), Re H(y,N/2)) as in the two-pass engine) never leaving the
 // cluster's distributed shared memory.  CTA r keeps packed columns
-// [32r, 32r + 32) of all N rows (its slab) and does the row work of image
-// rows [64r, 64r + 64):
-//   column phase  local to the CTA: its 32 columns, two tasks of L columns
-//                 per warp;
+// [CW r, CW (r + 1)) of all N rows (its slab; CW = 32, or 16 at N = 512)
+// and does the row work of image rows [2 CW r, 2 CW (r + 1)):
+//   column phase  local to the CTA: its CW columns, two tasks per warp;
 //   row phase     each row pair gathered from the C slabs over DSMEM,
 //                 inverted, updated against g in global memory, transformed
 //                 again and scattered back to the same slab places.
-// Two cluster barriers per iteration separate the phases.  Global memory
-// per angle-iteration: g read (HIO needs the old iterate) and written,
-// A_sym and the support bits read; within one launch all of it stays in L2.
-// The line transforms are the warp-resident FFTs of fftw.cuh with the same
-// task-to-lane maps as the two-pass warp engine, so both engines run the
-// same FP32 arithmetic on every value.
+// Two cluster barriers per iteration separate the phases; loads that do not
+// depend on other CTAs (A_sym, the old iterate) are issued between the
+// arrive and the wait.  Global memory per angle-iteration: g read (HIO
+// needs the old iterate) and written, A_sym read; within one launch these
+// stay in L2, and the support bits are read once per launch into registers.
+// Up to N = 256 the line transforms are the warp-resident FFTs of fftw.cuh
+// with the same task-to-lane maps as the two-pass warp engine (bit-identical
+// iterates); N = 512 uses the one-line FFT of fftw_pair.cuh.
 #include <cooperative_groups.h>
 
 #include "fast_kernels.cuh"
@@ -227,7 +228,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const long long err_slot = Z->err_slot;
 
   load_xtw<N>(xs, J->xtw, F::NT);
-  fill_taps<N>(tt, ca, Z->g_src, J->S, n, Np, W);
+  fill_taps<N>(tt, ca, Z->g_src, J->S, n, Np, W, J->present);
   // the support is fixed during a launch: each lane keeps its pixels' bits
   uint32_t mask[2][F::MASKW];
   static_for<0, 2>([&](auto QQ) {

@@ -131,7 +131,9 @@ cudaError_t launch_support_u8(cpra_plan_s* p, const uint8_t* S, int per_angle) {
 
 // Seeded start g0 = u * [x in S], u = (splitmix64(key) >> 40) * 2^-24,
 // key = ((seed * Np + n) * N + y) * N + x (mod 2^64).
-__global__ void k_init_guess(float* g, const uint32_t* S, int N, int Np, int W,
+// the seeded start into both Jacobi buffers (angles outside a present mask
+// keep it whichever buffer is current)
+__global__ void k_init_guess(float* g, float* g2, const uint32_t* S, int N, int Np, int W,
                              unsigned long long seed) {
   const int y = blockIdx.x, n = blockIdx.y;
   const size_t srow = ((size_t)n * N + y) * W;
@@ -139,15 +141,17 @@ __global__ void k_init_guess(float* g, const uint32_t* S, int N, int Np, int W,
     const uint64_t key = ((seed * (uint64_t)Np + (uint64_t)n) * (uint64_t)N + (uint64_t)y) *
                              (uint64_t)N + (uint64_t)x;
     const float u = (float)(splitmix64(key) >> 40) * (1.0f / 16777216.0f);
-    g[((size_t)n * N + y) * N + x] = sbit(S, srow, x) ? u : 0.0f;
+    const float v = sbit(S, srow, x) ? u : 0.0f;
+    g[((size_t)n * N + y) * N + x] = v;
+    g2[((size_t)n * N + y) * N + x] = v;
   }
 }
 
 cudaError_t launch_init_guess(cpra_plan_s* p) {
   int threads = p->N >= 256 ? 256 : p->N;
   g_launches += 1;
-  k_init_guess<<<dim3(p->N, p->Np), threads, 0, p->stream>>>(p->g, p->S, p->N, p->Np, p->W,
-                                                             (unsigned long long)p->cfg.seed);
+  k_init_guess<<<dim3(p->N, p->Np), threads, 0, p->stream>>>(p->g, p->g_alt, p->S, p->N, p->Np,
+                                                             p->W, (unsigned long long)p->cfg.seed);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 // applies the carousel coupling of Eq. 4 at episode starts.
 #include "cpra_internal.h"
 #include "fft.cuh"
+#include "taps.cuh"
 #include "tiling.cuh"
 
 namespace cpra {
@@ -69,8 +70,10 @@ k_prime(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   float2* buf = smem + N;
   const int n = tl.y;
   const int y0 = blockIdx.x * 2 * P;
+  __shared__ TapTab tt;
   load_twiddles<N>(tw_s, tw);
-  const int r = ca.n_taps / 2;
+  fill_taps<N>(tt, ca, g_src, S, n, Np, W, J->present);
+  __syncthreads();
   for (int idx = threadIdx.x; idx < P * N; idx += NT) {
     const int p = idx / N, x = idx - p * N;
     float v[2];
@@ -78,18 +81,15 @@ k_prime(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     for (int s = 0; s < 2; ++s) {
       const int y = y0 + 2 * p + s;
       float acc = 0.0f;
-      for (int k = -r; k <= r; ++k) {
-        const int j = n + k;
-        const int jm = ((j % Np) + Np) % Np;
-        const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
-        const bool mir = ca.mirror && (wraps & 1);
-        const int xs = mir ? (N - x) % N : x;
-        float val = g_src[((size_t)jm * N + y) * N + xs];
+      for (int k = 0; k < ca.n_taps; ++k) {
+        if (tt.w[k] == 0.0f) continue;  // a tap on an absent angle
+        const int xs = tt.mir[k] ? (N - x) % N : x;
+        float val = tt.src[k][(size_t)y * N + xs];
         if (ca.object) {
-          const bool in = sbit(S, ((size_t)jm * N + y) * W, xs);
+          const bool in = sbit(tt.s[k], (size_t)y * W, xs);
           val = (in && val >= 0.0f) ? val : 0.0f;
         }
-        acc = (ca.n_taps == 1) ? val : fmaf(ca.alpha[k + r], val, acc);
+        acc = (ca.n_taps == 1) ? val : fmaf(tt.w[k], val, acc);
       }
       v[s] = acc;
       if (ca.store_g) g_dst[((size_t)n * N + y) * N + x] = acc;

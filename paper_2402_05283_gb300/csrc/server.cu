@@ -50,6 +50,7 @@ struct Request {
   int n_arrived = 0;
   int64_t total = 0, done = 0;
   bool first_done = false;
+  int n_masked = -1;  // arrivals the plan's present mask follows (early start)
   double t_submit = 0, t_last_push = 0, t_admit = 0, t_first = -1, t_final = -1;
   std::string err;
 };
@@ -99,6 +100,15 @@ void fail_request(cpra_server_s* s, Request* r, const std::string& why) {
   emit(s, r, CPRA_EVENT_FAILED, now_s(s->t0));
 }
 
+// Early start: iterations a request may run before every angle arrived
+// (the rest, at least one episode, wait for the last pattern)
+int64_t hold_at(const cpra_server_s* s, const Request* r) {
+  const int64_t e = r->cfg.n_ei;
+  int64_t tail = s->cfg.early_tail > 0 ? s->cfg.early_tail : (r->total + 1) / 2;
+  tail = std::max<int64_t>(e, (tail + e - 1) / e * e);
+  return std::max<int64_t>(0, r->total - tail);
+}
+
 // One round of the loop; returns true when it did GPU work.
 bool round(cpra_server_s* s) {
   std::vector<Request*> admit, resident, fresh_running;
@@ -131,8 +141,11 @@ bool round(cpra_server_s* s) {
       r->t_admit = now_s(s->t0);
       s->stats.admitted++;
     }
+    // (a running request with early start still receives patterns)
     for (auto& kv : s->reqs)
-      if (kv.second->state == kResident && !kv.second->inbox.empty()) resident.push_back(kv.second);
+      if ((kv.second->state == kResident || kv.second->state == kRunning) &&
+          !kv.second->inbox.empty())
+        resident.push_back(kv.second);
   }
   bool worked = false;
   // streaming: prepare the patterns that arrived for resident requests
@@ -158,7 +171,8 @@ bool round(cpra_server_s* s) {
         }
     }
     std::lock_guard<std::mutex> lk(s->mu);
-    if (r->state == kResident && r->n_arrived == r->cfg.Np) {
+    if (r->state == kResident &&
+        (r->n_arrived == r->cfg.Np || (s->cfg.early_start && r->n_arrived > 0))) {
       r->state = kRunning;
       s->running.push_back(r->id);
     }
@@ -166,7 +180,34 @@ bool round(cpra_server_s* s) {
   std::vector<Request*> run;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    for (int64_t id : s->running) run.push_back(s->reqs[id]);
+    for (int64_t id : s->running) {
+      Request* r = s->reqs[id];
+      // early start: the tail of the schedule waits for every angle
+      if (r->n_arrived < r->cfg.Np && r->done >= hold_at(s, r)) continue;
+      run.push_back(r);
+    }
+  }
+  // early start: each plan's present mask follows its arrivals
+  for (Request* r : run) {
+    if (r->n_masked == r->n_arrived) continue;
+    const bool all = r->n_arrived == r->cfg.Np;
+    if (all && r->n_masked < 0) {
+      r->n_masked = r->n_arrived;
+      continue;
+    }
+    cpra_status st = cpra_set_present(r->plan, all ? nullptr : r->arrived.data());
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (st != CPRA_OK) {
+      fail_request(s, r, cpra_last_error(r->plan));
+      continue;
+    }
+    r->n_masked = r->n_arrived;
+  }
+  {
+    std::vector<Request*> ok;
+    for (Request* r : run)
+      if (r->state == kRunning) ok.push_back(r);
+    run.swap(ok);
   }
   if (run.empty()) return worked;
   // continuous batching: the batch follows the running set
@@ -190,7 +231,9 @@ bool round(cpra_server_s* s) {
   int64_t n = s->cfg.iters_per_round > 0 ? s->cfg.iters_per_round : 10;
   for (Request* r : run) {
     n = std::min<int64_t>(n, r->total - r->done);
-    if (!r->first_done) n = std::min<int64_t>(n, r->cfg.n_ei - r->done);
+    const bool all = r->n_arrived == r->cfg.Np;
+    if (!all) n = std::min<int64_t>(n, hold_at(s, r) - r->done);
+    if (!r->first_done && all && r->done < r->cfg.n_ei) n = std::min<int64_t>(n, r->cfg.n_ei - r->done);
   }
   if (n < 1) n = 1;
   cpra_status st = cpra_batch_iterate(s->batch, (int32_t)n);
@@ -206,14 +249,14 @@ bool round(cpra_server_s* s) {
     }
     for (Request* r : run) {
       r->done += n;
-      s->stats.angle_iterations += n * r->cfg.Np;
+      s->stats.angle_iterations += n * r->n_masked;
     }
   }
   // first 3D estimates and final volumes
-  std::vector<int64_t> still;
   for (Request* r : run) {
+    const bool all = r->n_arrived == r->cfg.Np;
     const bool final = r->done >= r->total;
-    const bool first = !r->first_done && (r->done >= r->cfg.n_ei || final);
+    const bool first = all && !r->first_done && (r->done >= r->cfg.n_ei || final);
     if (first || final) {
       cpra_status as = cpra_assemble_3d(r->plan, nullptr);
       if (as == CPRA_OK) as = cpra_sync(r->plan);
@@ -236,10 +279,13 @@ bool round(cpra_server_s* s) {
         continue;
       }
     }
-    still.push_back(r->id);
   }
   {
+    // requests held back this round stay in the running set
     std::lock_guard<std::mutex> lk(s->mu);
+    std::vector<int64_t> still;
+    for (int64_t id : s->running)
+      if (s->reqs[id]->state == kRunning) still.push_back(id);
     s->running = still;
   }
   s->cv.notify_all();
@@ -287,7 +333,7 @@ cpra_status cpra_server_default_config(cpra_server_config* c) {
 cpra_status cpra_server_start(const cpra_server_config* cfg, cpra_server_t* out) {
   if (!cfg || !out) return cpra::record_error(CPRA_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
-  if (cfg->iters_per_round < 0 || cfg->max_active < 0)
+  if (cfg->iters_per_round < 0 || cfg->max_active < 0 || cfg->early_tail < 0)
     return cpra::record_error(CPRA_ERR_INVALID_ARG, "negative limits");
   cpra_server_s* s = new (std::nothrow) cpra_server_s();
   if (!s) return cpra::record_error(CPRA_ERR_OUT_OF_MEMORY, "host allocation failed");

@@ -94,3 +94,38 @@ def test_admission_waits_for_memory(cp):
         srv.wait(rid, 0.1)
     assert e.value.status == cp.ERR_TIMEOUT
     srv.stop()
+
+
+def test_early_start_iterates_while_streaming(cp):
+    """early_start: a request iterates its arrived angles while the rest
+    stream in, holds the tail of its schedule (by default half of it, in
+    whole episodes: 40 of 70 iterations here) until every angle is there, and
+    reaches the quality of a standalone reconstruction within a factor 2."""
+    N, Np, seed = 64, 16, 9
+    d = synth.make_case("tiny", N=N, Np=Np, request=seed)
+    cfg = cp.make_config(N, Np, seed=seed, hio_iters=50, er_iters=20, n_ei=10)
+    srv = cp.Server(hbm_reserve_bytes=1 << 30, iters_per_round=5, early_start=True)
+    rid = srv.submit(cfg)
+    done_while_streaming = 0
+    for f in range(0, Np, 4):
+        if f + 4 >= Np:  # before the last patterns arrive
+            done_while_streaming = srv.info(rid)["iterations_done"]
+        srv.push(rid, d["I"][f:f + 4], f, d["thetas"][f:f + 4])
+        time.sleep(0.05)
+    srv.wait(rid, 120.0)
+    info = srv.info(rid)
+    assert info["iterations_done"] == 70 and info["t_final"] >= info["t_first_estimate"] >= 0
+    assert 0 < done_while_streaming <= 30  # started early, held the tail
+    po = srv.result(rid, cp.RESULT_PO)
+    e_srv = srv.result(rid, cp.RESULT_ERRORS)[-1]
+    srv.release(rid)
+    srv.stop()
+    p = cp.Plan(cfg)
+    p.load_intensities(d["I"], 0, d["thetas"])
+    p.iterate(70)
+    e_alone = p.result(cp.RESULT_ERRORS)[-1]
+    p.close()
+    assert np.all(np.isfinite(po))
+    print(f"early start: {done_while_streaming} iterations before the last patterns, "
+          f"final error {e_srv.mean():.4f} vs {e_alone.mean():.4f} alone")
+    assert e_srv.mean() <= 2.0 * e_alone.mean(), (e_srv.mean(), e_alone.mean())

@@ -200,6 +200,50 @@ def test_coupling_identity_constant_and_linearity():
     assert np.allclose(O.couple(np.roll(g, 2, axis=0), a), np.roll(O.couple(g, a), 2, axis=0))
 
 
+def test_coupling_present_mask_hand_case():
+    """R13 on Np = 3 with angle 2 absent and alpha = (0.2, 0.6, 0.2), constant
+    images 1, 10, 100: angle 0 keeps taps 0 (0.6) and 1 (0.2), renormalised by
+    0.8: (0.6 * 1 + 0.2 * 10) / 0.8 = 3.25; angle 1 keeps taps 0 (0.2) and 1
+    (0.6): (0.2 * 1 + 0.6 * 10) / 0.8 = 7.75; angle 2 is left as it is."""
+    x = np.array([1.0, 10.0, 100.0])[:, None, None] * np.ones((3, 4, 4))
+    out = O.couple(x, [0.2, 0.6, 0.2], present=[1, 1, 0])
+    assert np.allclose(out[:, 0, 0], [3.25, 7.75, 100.0], rtol=0, atol=1e-13)
+
+
+def test_coupling_present_mask_invariants():
+    g = _rand(7, 6, 6)
+    a = [0.1, 0.2, 0.4, 0.2, 0.1]
+    # every angle present: exactly the plain coupling
+    assert np.array_equal(O.couple(g, a, present=np.ones(7)), O.couple(g, a))
+    # one constant image everywhere stays that constant at every present angle
+    # (the present weights sum to 1); absent angles keep their own image
+    rng = np.random.default_rng(5)
+    c = np.broadcast_to(_rand(1, 6, 6), (7, 6, 6)).copy()
+    for _ in range(5):
+        m = rng.integers(0, 2, size=7)
+        m[rng.integers(0, 7)] = 1
+        h = np.where(m[:, None, None] == 1, c, g)
+        out = O.couple(h, a, wrap=O.WRAP_LITERAL, present=m)
+        on = m == 1
+        assert np.allclose(out[on], c[on], atol=1e-14)
+        assert np.array_equal(out[~on], h[~on])
+
+
+def test_oracle_run_present_mask():
+    """Absent angles keep their state and error 0 through coupling steps."""
+    N, Np = 16, 4
+    rng = np.random.default_rng(9)
+    I = rng.uniform(0.0, 50.0, size=(Np, N, N))
+    cfg = O.OracleConfig(N=N, Np=Np, n_ei=2, hio_iters=2, er_iters=3, seed=4)
+    run = O.OracleRun.start(cfg, I)
+    g0 = run.g.copy()
+    run.present = np.array([1, 0, 1, 1])
+    run.run(5)
+    assert np.array_equal(run.g[1], g0[1])
+    assert all(e[1] == 0.0 for e in run.errors)
+    assert all(e[0] > 0.0 for e in run.errors)
+
+
 def test_coupling_mirror_seam():
     Np, N = 4, 6
     g = _rand(Np, N, N)
