@@ -66,7 +66,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
         objs = list(ex.map(one, srcs))
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [cc, *ARCH, "-shared", "--cudart", "static", "-o", LIB, *objs]
+        cmd = [cc, *ARCH, "-shared", "--cudart", "static", "-o", LIB, *objs, "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -9,6 +9,8 @@
 #include <sstream>
 #include <string>
 #include <sys/stat.h>
+
+#include <nvtx3/nvToolsExt.h>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -217,8 +219,20 @@ cpra_status copy_out(cpra_plan_s* p, void* dst, const void* src, size_t bytes) {
 }
 
 // Records CUDA events around a launch when the plan profiles its kernels.
+// NVTX range of every kernel class (free when no tool listens)
+struct Range {
+  explicit Range(int kind) {
+    static const char* names[CPRA_KERNEL_KINDS] = {"cpra colpass", "cpra rowpass", "cpra prime",
+                                                   "cpra shrinkwrap", "cpra assemble",
+                                                   "cpra fused", "cpra prepare"};
+    nvtxRangePushA(names[kind]);
+  }
+  ~Range() { nvtxRangePop(); }
+};
+
 template <class F>
 cudaError_t timed(cpra_plan_s* p, int kind, F&& launch) {
+  Range range(kind);
   if (!p->profiling) return launch();
   cpra_plan_s::Timed ev;
   if (!p->spare.empty()) {
