@@ -15,19 +15,40 @@
 #include "cpra_internal.h"
 #include "fft.cuh"
 #include "fftw.cuh"
+#include "fftw_pair.cuh"
 #include "taps.cuh"
 
 namespace cpra {
 
-constexpr int kRowWarps = 4;
+// Line transforms of the warp engine: the L-line plans of fftw.cuh, or, at
+// N = 512 in FP32, the one-line plan of fftw_pair.cuh (half the registers a
+// thread, so twice the warps an SM).  The tensor-core forms keep the L-line
+// plans.
+template <int N, int PREC> struct WLines { using type = WarpLines<N>; };
+template <> struct WLines<512, kPrecFP32> { using type = PairLines512; };
 
-// per-warp shared memory of the row kernels: transpose tile + the warp's g rows
-template <int N> struct RowW {
-  using P = WP<N>;
-  static constexpr int GROWS = 2 * P::L;                  // image rows per warp
+template <int N, int PREC, class FL>
+__device__ __forceinline__ void lines_fwd(float2 (&a)[FL::TA][FL::E1], float2 (&b)[FL::TB][FL::E2],
+                                          float2* T, const float2* xs, int lane, const TcCtx* tc) {
+  if constexpr (PREC == kPrecFP32) FL::fwd(a, b, T, xs, lane);
+  else warp_fft_fwd<N, PREC>(a, b, T, xs, lane, tc);
+}
+template <int N, int PREC, class FL>
+__device__ __forceinline__ void lines_inv(float2 (&b)[FL::TB][FL::E2], float2 (&a)[FL::TA][FL::E1],
+                                          float2* T, const float2* xs, int lane, const TcCtx* tc) {
+  if constexpr (PREC == kPrecFP32) FL::inv(b, a, T, xs, lane);
+  else warp_fft_inv<N, PREC>(b, a, T, xs, lane, tc);
+}
+
+// per-warp shared memory of the row kernels: transpose tile + the warp's g
+// rows; 4 warps a block with the L-line plans, 8 with the one-line plan
+template <int N, int PREC> struct RowW {
+  using FL = typename WLines<N, PREC>::type;
+  static constexpr int WARPS = FL::L == 1 ? 8 : 4;
+  static constexpr int GROWS = 2 * FL::L;                  // image rows per warp
   static constexpr int GFLOATS = GROWS * N;
-  static constexpr int WARP_F2 = P::TSIZE + GFLOATS / 2;  // float2 per warp
-  static constexpr size_t SMEM = sizeof(float2) * (N + kRowWarps * WARP_F2);
+  static constexpr int WARP_F2 = FL::TSIZE + GFLOATS / 2;  // float2 per warp
+  static constexpr size_t SMEM = sizeof(float2) * (N + WARPS * WARP_F2);
 };
 
 // extra shared memory of the tensor-core path: one 16-bit A tile and 32
@@ -40,7 +61,7 @@ template <int N, int PREC> struct TcSmem {
   static constexpr size_t bytes(int warps) { return warps * WARP_BYTES; }
 };
 template <int N, int PREC>
-constexpr size_t row_smem() { return RowW<N>::SMEM + TcSmem<N, PREC>::bytes(kRowWarps); }
+constexpr size_t row_smem() { return RowW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(RowW<N, PREC>::WARPS); }
 
 // Tensor-core scratch of this warp; W = the plan's matrices in global memory
 template <int N, int PREC>
@@ -66,23 +87,22 @@ __device__ __forceinline__ void load_xtw(float2* xs, const float2* xtw, int nthr
 // Z (B layout) of the row pairs of this warp -> packed half spectra of both
 // rows of every pair, stored to Hp.  Z goes through the warp tile so each
 // output index k can meet its partner N - k.
-template <int N>
-__device__ __forceinline__ void store_pairs_w(float2 (&b)[WP<N>::TB][WP<N>::E2], float2* T,
-                                              float2* Hn, int pair0, int lane) {
-  using P = WP<N>;
+template <int N, class FL>
+__device__ __forceinline__ void store_pairs_w(float2 (&b)[FL::TB][FL::E2], float2* T, float2* Hn,
+                                              int pair0, int lane) {
   constexpr int H = N / 2;
-  static_for<0, P::TB>([&](auto II) {
+  static_for<0, FL::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
-    const int line = t / P::E1, k1 = t % P::E1;
-    static_for<0, P::E2>([&](auto KK) {
-      constexpr int k2 = decltype(KK)::value;
-      T[line * N + k1 + P::E1 * k2] = b[i][k2];
+    const int line = FL::b_line(t);
+    static_for<0, FL::E2>([&](auto KK) {
+      constexpr int j = decltype(KK)::value;
+      T[line * N + FL::b_k(t, j)] = b[i][j];
     });
   });
   __syncwarp();
 #pragma unroll
-  for (int line = 0; line < P::L; ++line) {
+  for (int line = 0; line < FL::L; ++line) {
     const float2* Z = T + line * N;
     float2* r0 = Hn + (size_t)(2 * (pair0 + line)) * H;
     float2* r1 = r0 + H;
@@ -106,11 +126,11 @@ __device__ __forceinline__ void store_pairs_w(float2 (&b)[WP<N>::TB][WP<N>::E2],
 
 // ---------------------------------------------------------------- row pass
 template <int N, int PREC>
-__global__ void __launch_bounds__(kRowWarps * 32, 3)
+__global__ void __launch_bounds__(RowW<N, PREC>::WARPS * 32, 3)
 k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
             const int2* __restrict__ tiles) {
-  using P = WP<N>;
-  using RW = RowW<N>;
+  using RW = RowW<N, PREC>;
+  using FL = typename RW::FL;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
   const int2 tl = tiles[blockIdx.y];
@@ -132,11 +152,11 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   float2* xs = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* T = smem + N + warp * RW::WARP_F2;
-  float* Gs = reinterpret_cast<float*>(T + P::TSIZE);  // this warp's 2L rows of g
-  const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(smem + N + kRowWarps * RW::WARP_F2),
+  float* Gs = reinterpret_cast<float*>(T + FL::TSIZE);  // this warp's 2L rows of g
+  const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(smem + N + RW::WARPS * RW::WARP_F2),
                                      J->tcw, warp);
   const int n = tl.y;
-  const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
+  const int pair0 = (blockIdx.x * RW::WARPS + warp) * FL::L;
   float* grow = g + ((size_t)n * N + 2 * pair0) * N;  // 2L contiguous rows
   // prefetch the old iterate; it is needed only after the inverse FFT
   for (int q = lane; q < RW::GFLOATS / 4; q += 32) cp_async16(Gs + 4 * q, grow + 4 * q);
@@ -148,20 +168,19 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     }
     err_acc[n] = 0.0;
   }
-  load_xtw<N>(xs, xtw, kRowWarps * 32);
+  load_xtw<N>(xs, xtw, RW::WARPS * 32);
   __syncthreads();
   float2* Hn = Hp + (size_t)n * N * H;
   // packed row spectra -> Z = H(row 2p) + i H(row 2p+1), B layout
-  float2 b[P::TB][P::E2];
-  static_for<0, P::TB>([&](auto II) {
+  float2 b[FL::TB][FL::E2];
+  static_for<0, FL::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
-    const int line = t / P::E1, k1 = t % P::E1;
-    const float2* r0 = Hn + (size_t)(2 * (pair0 + line)) * H;
+    const float2* r0 = Hn + (size_t)(2 * (pair0 + FL::b_line(t))) * H;
     const float2* r1 = r0 + H;
-    static_for<0, P::E2>([&](auto KK) {
-      constexpr int k2 = decltype(KK)::value;
-      const int k = k1 + P::E1 * k2;
+    static_for<0, FL::E2>([&](auto KK) {
+      constexpr int j = decltype(KK)::value;
+      const int k = FL::b_k(t, j);
       float2 z;
       if (k == 0) {
         z = make_float2(r0[0].x, r1[0].x);
@@ -174,18 +193,18 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
         const float2 h0 = r0[N - k], h1 = r1[N - k];
         z = make_float2(h0.x + h1.y, h1.x - h0.y);
       }
-      b[i][k2] = z;
+      b[i][j] = z;
     });
   });
-  float2 a[P::TA][P::E1];
-  warp_fft_inv<N, PREC>(b, a, T, xs, lane, &tc);
+  float2 a[FL::TA][FL::E1];
+  lines_inv<N, PREC, FL>(b, a, T, xs, lane, &tc);
   cp_async_wait_all();
   __syncwarp();
   const float inv = 1.0f / N;
-  static_for<0, P::TA>([&](auto II) {
+  static_for<0, FL::TA>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
+    const int line = FL::a_line(t);
     const int y0 = 2 * (pair0 + line);
     float* g0 = g + ((size_t)n * N + y0) * N;
     float* g1 = g0 + N;
@@ -193,9 +212,9 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     const float* o1s = o0s + N;
     const uint32_t* s0 = S + ((size_t)n * N + y0) * W;
     const uint32_t* s1 = s0 + W;
-    static_for<0, P::E1>([&](auto MM) {
+    static_for<0, FL::E1>([&](auto MM) {
       constexpr int m = decltype(MM)::value;
-      const int x = l + P::E2 * m;
+      const int x = FL::a_x(t, m);
       const float2 z = a[i][m];
       const float gp0 = z.x * inv, gp1 = z.y * inv;
       const bool v0 = ((__ldg(s0 + (x >> 5)) >> (x & 31)) & 1u) && gp0 >= 0.0f;
@@ -208,8 +227,8 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     });
   });
   if (!forward) return;
-  warp_fft_fwd<N, PREC>(a, b, T, xs, lane, &tc);
-  store_pairs_w<N>(b, T, Hn, pair0, lane);
+  lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
+  store_pairs_w<N, FL>(b, T, Hn, pair0, lane);
 }
 
 // ---------------------------------------------------------------- Eq. 4 taps
@@ -271,11 +290,11 @@ __device__ __forceinline__ void store_rows(const float2 (&a)[FL::TA][FL::E1], fl
 
 // ---------------------------------------------------------------- prime
 template <int N, int PREC>
-__global__ void __launch_bounds__(kRowWarps * 32, 3)
+__global__ void __launch_bounds__(RowW<N, PREC>::WARPS * 32, 3)
 k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
           const int2* __restrict__ tiles) {
-  using P = WP<N>;
-  using RW = RowW<N>;
+  using RW = RowW<N, PREC>;
+  using FL = typename RW::FL;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
   const int2 tl = tiles[blockIdx.y];
@@ -292,33 +311,35 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   float2* xs = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* T = smem + N + warp * RW::WARP_F2;
-  const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(smem + N + kRowWarps * RW::WARP_F2),
+  const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(smem + N + RW::WARPS * RW::WARP_F2),
                                      J->tcw, warp);
   const int n = tl.y;
-  const int pair0 = (blockIdx.x * kRowWarps + warp) * P::L;
+  const int pair0 = (blockIdx.x * RW::WARPS + warp) * FL::L;
   __shared__ TapTab tt;
-  load_xtw<N>(xs, xtw, kRowWarps * 32);
+  load_xtw<N>(xs, xtw, RW::WARPS * 32);
   fill_taps<N>(tt, ca, g_src, S, n, Np, W, J->present);
   __syncthreads();
-  float2 a[P::TA][P::E1];
-  blend_rows<N>(a, tt, ca, W, pair0, lane);
-  if (ca.store_g) store_rows<N>(a, g_dst + (size_t)n * N * N, pair0, lane);
-  float2 b[P::TB][P::E2];
-  warp_fft_fwd<N, PREC>(a, b, T, xs, lane, &tc);
-  store_pairs_w<N>(b, T, Hp + (size_t)n * N * H, pair0, lane);
+  float2 a[FL::TA][FL::E1];
+  blend_rows<N, FL>(a, tt, ca, W, pair0, lane);
+  if (ca.store_g) store_rows<N, FL>(a, g_dst + (size_t)n * N * N, pair0, lane);
+  float2 b[FL::TB][FL::E2];
+  lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
+  store_pairs_w<N, FL>(b, T, Hp + (size_t)n * N * H, pair0, lane);
 }
 
 // ---------------------------------------------------------------- column pass
-// packed columns per CTA: 16 (128 B of each row); 8 for the 16-bit path at
-// N = 1024, whose extra per-warp tiles would not fit beside 16 columns
+// packed columns per CTA: 16 (128 B of each row) with the L-line plans; 8
+// with the one-line plan (8 warps, three CTAs an SM) and for the 16-bit path
+// at N = 1024, whose extra per-warp tiles would not fit beside 16 columns
 template <int N, int PREC> struct ColW {
-  using P = WP<N>;
-  static constexpr int CB = (PREC != kPrecFP32 && N >= 1024) ? 8 : 16;
-  static constexpr int WARPS = CB / P::L;
+  using FL = typename WLines<N, PREC>::type;
+  static constexpr int CB = ((PREC != kPrecFP32 && N >= 1024) || FL::L == 1) ? 8 : 16;
+  static constexpr int WARPS = CB / FL::L;
   static constexpr int NT = WARPS * 32;
+  static constexpr int MINB = FL::L == 1 ? 3 : (NT <= 256 ? 2 : 1);
   static constexpr int SP = CB + 1;  // staging pitch
   static constexpr int STAGE = N * SP;
-  static constexpr int TILES = WARPS * P::TSIZE;
+  static constexpr int TILES = WARPS * FL::TSIZE;
   static constexpr int BUF = STAGE > TILES ? STAGE : TILES;
   static constexpr size_t SMEM = sizeof(float2) * (N + BUF) + sizeof(float) * CB * N;
 };
@@ -342,11 +363,11 @@ __device__ __forceinline__ float2 project_w(float2 G, float a, float& err, float
 }
 
 template <int N, int PREC>
-__global__ void __launch_bounds__(ColW<N, PREC>::NT, ColW<N, PREC>::NT <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(ColW<N, PREC>::NT, ColW<N, PREC>::MINB)
 k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
             const int2* __restrict__ tiles) {
-  using P = WP<N>;
   using C = ColW<N, PREC>;
+  using FL = typename C::FL;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
   const int2 tl = tiles[blockIdx.y];
@@ -363,7 +384,7 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* As = reinterpret_cast<float*>(buf + C::BUF);  // A_sym of the block, [c][ky]
   const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(As + C::CB * N), J->tcw, threadIdx.x >> 5);
-  float2* T = buf + warp * P::TSIZE;
+  float2* T = buf + warp * FL::TSIZE;
   const int n = tl.y;
   const int c0 = blockIdx.x * C::CB;
   float2* Hn = Hp + (size_t)n * N * H;
@@ -377,82 +398,76 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   load_xtw<N>(xs, xtw, C::NT);
   cp_async_wait_all();
   __syncthreads();
-  float2 a[P::TA][P::E1];
-  static_for<0, P::TA>([&](auto II) {
+  float2 a[FL::TA][FL::E1];
+  static_for<0, FL::TA>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
-    const int col = warp * P::L + line;
-    static_for<0, P::E1>([&](auto MM) {
+    const int col = warp * FL::L + FL::a_line(t);
+    static_for<0, FL::E1>([&](auto MM) {
       constexpr int m = decltype(MM)::value;
-      a[i][m] = buf[(l + P::E2 * m) * C::SP + col];
+      a[i][m] = buf[FL::a_x(t, m) * C::SP + col];
     });
   });
   __syncthreads();
-  float2 b[P::TB][P::E2];
-  warp_fft_fwd<N, PREC>(a, b, T, xs, lane, &tc);
+  float2 b[FL::TB][FL::E2];
+  lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
   float err = 0.0f;
   const bool warp_packed = (c0 == 0 && warp == 0);  // line 0 of warp 0 holds column 0
-  static_for<0, P::TB>([&](auto II) {
+  static_for<0, FL::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
-    const int line = t / P::E1, k1 = t % P::E1;
-    const int col = warp * P::L + line;
+    const int col = warp * FL::L + FL::b_line(t);
     if (c0 + col != 0) {
       const float* Ac = As + col * N;
-      static_for<0, P::E2>([&](auto KK) {
-        constexpr int k2 = decltype(KK)::value;
-        const int ky = k1 + P::E1 * k2;
-        b[i][k2] = project_w(b[i][k2], Ac[ky], err, 2.0f);
+      static_for<0, FL::E2>([&](auto KK) {
+        constexpr int j = decltype(KK)::value;
+        b[i][j] = project_w(b[i][j], Ac[FL::b_k(t, j)], err, 2.0f);
       });
     }
   });
   if (warp_packed) {
     // column 0 packs G(., 0) + i G(., N/2); both are Hermitian along ky
-    static_for<0, P::TB>([&](auto II) {
+    static_for<0, FL::TB>([&](auto II) {
       constexpr int i = decltype(II)::value;
       const int t = lane + 32 * i;
-      const int line = t / P::E1, k1 = t % P::E1;
-      if (line == 0) {
-        static_for<0, P::E2>([&](auto KK) {
-          constexpr int k2 = decltype(KK)::value;
-          T[k1 + P::E1 * k2] = b[i][k2];
+      if (FL::b_line(t) == 0) {
+        static_for<0, FL::E2>([&](auto KK) {
+          constexpr int j = decltype(KK)::value;
+          T[FL::b_k(t, j)] = b[i][j];
         });
       }
     });
     __syncwarp();
-    static_for<0, P::TB>([&](auto II) {
+    static_for<0, FL::TB>([&](auto II) {
       constexpr int i = decltype(II)::value;
       const int t = lane + 32 * i;
-      const int line = t / P::E1, k1 = t % P::E1;
-      if (line == 0) {
+      if (FL::b_line(t) == 0) {
         const float* A0 = As;  // column 0 of the block
         const float* An = A_nyq + (size_t)n * N;
-        static_for<0, P::E2>([&](auto KK) {
-          constexpr int k2 = decltype(KK)::value;
-          const int ky = k1 + P::E1 * k2;
+        static_for<0, FL::E2>([&](auto KK) {
+          constexpr int j = decltype(KK)::value;
+          const int ky = FL::b_k(t, j);
           const float2 z = T[ky], zm = T[(N - ky) % N];
           const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
           const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
           const float2 p0 = project_w(g0, A0[ky], err, 1.0f);
           const float2 pn = project_w(gn, __ldg(An + ky), err, 1.0f);
-          b[i][k2] = make_float2(p0.x - pn.y, p0.y + pn.x);
+          b[i][j] = make_float2(p0.x - pn.y, p0.y + pn.x);
         });
       }
     });
     __syncwarp();
   }
-  warp_fft_inv<N, PREC>(b, a, T, xs, lane, &tc);
+  lines_inv<N, PREC, FL>(b, a, T, xs, lane, &tc);
   __syncthreads();
   const float inv = 1.0f / N;
-  static_for<0, P::TA>([&](auto II) {
+  static_for<0, FL::TA>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
-    const int line = t / P::E2, l = t % P::E2;
-    const int col = warp * P::L + line;
-    static_for<0, P::E1>([&](auto MM) {
+    const int col = warp * FL::L + FL::a_line(t);
+    static_for<0, FL::E1>([&](auto MM) {
       constexpr int m = decltype(MM)::value;
-      buf[(l + P::E2 * m) * C::SP + col] = cscale(a[i][m], inv);
+      buf[FL::a_x(t, m) * C::SP + col] = cscale(a[i][m], inv);
     });
   });
   __syncthreads();
@@ -490,25 +505,25 @@ static cudaError_t prepare_w() {
 
 template <int N, int PREC>
 static cudaError_t rowpass_w(const Launch& L) {
-  using P = WP<N>;
+  using RW = RowW<N, PREC>;
   const size_t smem = row_smem<N, PREC>();
   cudaError_t e = prepare_w<N, PREC>();
   if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / (kRowWarps * P::L), L.ntiles);
+  dim3 grid((N / 2) / (RW::WARPS * RW::FL::L), L.ntiles);
   g_launches += 1;
-  k_rowpass_w<N, PREC><<<grid, kRowWarps * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
+  k_rowpass_w<N, PREC><<<grid, RW::WARPS * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 
 template <int N, int PREC>
 static cudaError_t prime_w(const Launch& L) {
-  using P = WP<N>;
+  using RW = RowW<N, PREC>;
   const size_t smem = row_smem<N, PREC>();
   cudaError_t e = prepare_w<N, PREC>();
   if (e != cudaSuccess) return e;
-  dim3 grid((N / 2) / (kRowWarps * P::L), L.ntiles);
+  dim3 grid((N / 2) / (RW::WARPS * RW::FL::L), L.ntiles);
   g_launches += 1;
-  k_prime_w<N, PREC><<<grid, kRowWarps * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
+  k_prime_w<N, PREC><<<grid, RW::WARPS * 32, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 

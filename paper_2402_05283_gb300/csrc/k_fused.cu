@@ -25,7 +25,6 @@
 #include <cooperative_groups.h>
 
 #include "fast_kernels.cuh"
-#include "fftw_pair.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -34,8 +33,7 @@ namespace cpra {
 // Line transforms of the fused kernel: the L-line plans of fftw.cuh, or the
 // one-line 512-point plan of fftw_pair.cuh (half the registers, so 16 warps
 // fit beside the slab).
-template <int N> struct FusedLines { using type = WarpLines<N>; };
-template <> struct FusedLines<512> { using type = PairLines512; };
+template <int N> struct FusedLines { using type = typename WLines<N, kPrecFP32>::type; };
 
 // Packed columns per CTA: 32, or 16 at N = 512, where a cluster of 16 CTAs
 // of 108 KB each puts two CTAs of different angles on an SM, so that one
