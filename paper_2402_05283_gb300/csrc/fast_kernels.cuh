@@ -26,6 +26,8 @@ namespace cpra {
 // plans.
 template <int N, int PREC> struct WLines { using type = WarpLines<N>; };
 template <> struct WLines<512, kPrecFP32> { using type = PairLines512; };
+// the one-line plan holds 16 values a lane: small enough for 24 warps an SM
+template <class FL> constexpr bool kSlimLines = FL::L == 1 && FL::E1 <= 16 && FL::E2 <= 16;
 
 template <int N, int PREC, class FL>
 __device__ __forceinline__ void lines_fwd(float2 (&a)[FL::TA][FL::E1], float2 (&b)[FL::TB][FL::E2],
@@ -44,7 +46,7 @@ __device__ __forceinline__ void lines_inv(float2 (&b)[FL::TB][FL::E2], float2 (&
 // rows; 4 warps a block with the L-line plans, 8 with the one-line plan
 template <int N, int PREC> struct RowW {
   using FL = typename WLines<N, PREC>::type;
-  static constexpr int WARPS = FL::L == 1 ? 8 : 4;
+  static constexpr int WARPS = kSlimLines<FL> ? 8 : 4;
   static constexpr int GROWS = 2 * FL::L;                  // image rows per warp
   static constexpr int GFLOATS = GROWS * N;
   static constexpr int WARP_F2 = FL::TSIZE + GFLOATS / 2;  // float2 per warp
@@ -158,7 +160,14 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const int n = tl.y;
   const int pair0 = (blockIdx.x * RW::WARPS + warp) * FL::L;
   float* grow = g + ((size_t)n * N + 2 * pair0) * N;  // 2L contiguous rows
-  // prefetch the old iterate; it is needed only after the inverse FFT
+  float2* Hn = Hp + (size_t)n * N * H;
+  // the warp's 2L packed spectrum rows (contiguous) into its tile, then the
+  // old iterate, which is needed only after the inverse FFT
+  {
+    const float2* hrow = Hn + (size_t)(2 * pair0) * H;
+    for (int q = lane; q < FL::L * N / 2; q += 32) cp_async16(T + 2 * q, hrow + 2 * q);
+    cp_async_commit();
+  }
   for (int q = lane; q < RW::GFLOATS / 4; q += 32) cp_async16(Gs + 4 * q, grow + 4 * q);
   cp_async_commit();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -169,33 +178,29 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     err_acc[n] = 0.0;
   }
   load_xtw<N>(xs, xtw, RW::WARPS * 32);
-  __syncthreads();
-  float2* Hn = Hp + (size_t)n * N * H;
-  // packed row spectra -> Z = H(row 2p) + i H(row 2p+1), B layout
+  cp_async_wait_group<1>();  // this lane's spectrum copies have landed
+  __syncthreads();           // xs, and every lane's copies
+  // packed row spectra -> Z = H(row 2p) + i H(row 2p+1), B layout, without
+  // branches: k < H reads column k, k > H column N - k (sign s = -1)
   float2 b[FL::TB][FL::E2];
   static_for<0, FL::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
-    const float2* r0 = Hn + (size_t)(2 * (pair0 + FL::b_line(t))) * H;
+    const float2* r0 = T + FL::b_line(t) * N;
     const float2* r1 = r0 + H;
     static_for<0, FL::E2>([&](auto KK) {
       constexpr int j = decltype(KK)::value;
       const int k = FL::b_k(t, j);
-      float2 z;
-      if (k == 0) {
-        z = make_float2(r0[0].x, r1[0].x);
-      } else if (k == H) {
-        z = make_float2(r0[0].y, r1[0].y);
-      } else if (k < H) {
-        const float2 h0 = r0[k], h1 = r1[k];
-        z = make_float2(h0.x - h1.y, h0.y + h1.x);
-      } else {
-        const float2 h0 = r0[N - k], h1 = r1[N - k];
-        z = make_float2(h0.x + h1.y, h1.x - h0.y);
-      }
+      const bool up = k > H;
+      const int c = up ? N - k : (k == H ? 0 : k);
+      const float s = up ? -1.0f : 1.0f;
+      const float2 h0 = r0[c], h1 = r1[c];
+      float2 z = make_float2(fmaf(-s, h1.y, h0.x), fmaf(s, h0.y, h1.x));
+      if (c == 0) z = k == 0 ? make_float2(h0.x, h1.x) : make_float2(h0.y, h1.y);
       b[i][j] = z;
     });
   });
+  __syncwarp();  // the tile is the transforms' scratch from here on
   float2 a[FL::TA][FL::E1];
   lines_inv<N, PREC, FL>(b, a, T, xs, lane, &tc);
   cp_async_wait_all();
@@ -333,10 +338,10 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 // at N = 1024, whose extra per-warp tiles would not fit beside 16 columns
 template <int N, int PREC> struct ColW {
   using FL = typename WLines<N, PREC>::type;
-  static constexpr int CB = ((PREC != kPrecFP32 && N >= 1024) || FL::L == 1) ? 8 : 16;
+  static constexpr int CB = ((PREC != kPrecFP32 && N >= 1024) || kSlimLines<FL>) ? 8 : 16;
   static constexpr int WARPS = CB / FL::L;
   static constexpr int NT = WARPS * 32;
-  static constexpr int MINB = FL::L == 1 ? 3 : (NT <= 256 ? 2 : 1);
+  static constexpr int MINB = kSlimLines<FL> ? 3 : (NT <= 256 ? 2 : 1);
   static constexpr int SP = CB + 1;  // staging pitch
   static constexpr int STAGE = N * SP;
   static constexpr int TILES = WARPS * FL::TSIZE;
