@@ -83,12 +83,13 @@ struct PairLines512 {
   template <int DIR>
   static __device__ __forceinline__ void pair_butterfly(float2 (&v)[16], int h) {
     if constexpr (DIR < 0) twiddle_odd<DIR>(v, h);
+    const float sg = h ? -1.0f : 1.0f;  // even lane: partner + mine, odd lane: partner - mine
     static_for<0, 16>([&](auto JJ) {
       constexpr int j = decltype(JJ)::value;
       const float2 mine = v[j];
       const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, 1),
                                    __shfl_xor_sync(0xffffffffu, mine.y, 1));
-      v[j] = h ? csub(p, mine) : cadd(mine, p);
+      v[j] = make_float2(fmaf(sg, mine.x, p.x), fmaf(sg, mine.y, p.y));
     });
     if constexpr (DIR > 0) twiddle_odd<DIR>(v, h);
   }
