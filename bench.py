@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -335,6 +336,62 @@ def form_p0(torch, I_dev, S_box, iters=20, beta=0.9, n_ei=10):
                     f"N={N_}, Np={Np_}, {iters} HIO iterations with coupling every {n_ei}"}
 
 
+def form_precision_large(cp, torch, N_=1024, Np_=720, n_proj=45, iters_acc=20, iters_speed=50,
+                         sample=(0, 361)):
+    """S3 at the sizes of the large configuration (N = 1024, Np = 720).
+    Patterns: the cfg 1 recipe scaled to a 512^3 object (6 ellipsoids; the
+    200-ellipsoid object takes minutes to rasterise on the host) projected at
+    n_proj angles, each pattern serving Np / n_proj consecutive angles.
+    Speed: iters_speed HIO iterations per form.  Accuracy: relative L2 of
+    sampled angles against the FP64 oracle (numpy.fft transforms) after
+    iters_acc ER iterations from one seeded state (no coupling)."""
+    import oracle as O
+    import synth
+    t_gen = time.perf_counter()
+    d = synth.make_case("cfg1", device="cuda", N=N_, Np=n_proj, request=5)
+    rep = Np_ // n_proj
+    I_dev = d["I"].repeat_interleave(rep, dim=0).contiguous()
+    thetas = [n * math.pi / Np_ for n in range(Np_)]
+    t_gen = time.perf_counter() - t_gen
+    rng = np.random.default_rng(12)
+    S = np.zeros((N_, N_), bool)
+    S[N_ // 4:3 * N_ // 4, N_ // 4:3 * N_ // 4] = True
+    g0 = (rng.random((Np_, N_, N_), dtype=np.float32) * S).astype(np.float32)
+    I_host = I_dev[list(sample)].cpu().numpy()
+    ref = {}
+    for i, n in enumerate(sample):
+        x = g0[n][None].astype(np.float64)
+        A = O.amplitudes(I_host[i])[None]
+        for _ in range(iters_acc):
+            x, _, _ = O.iterate_2d(x, A, S[None], 0.9, O.ER, fft=True)
+        ref[n] = x[0]
+    out = {"workload": f"N={N_}, Np={Np_} ({n_proj} projected patterns, each for {rep} angles), "
+                       f"6-ellipsoid 512^3 object, noisy 1e6 photons",
+           "input_seconds": round(t_gen, 1)}
+    for name, prec in (("fp32", cp.FP32), ("bf16", cp.BF16_TC), ("fp16", cp.FP16_TC)):
+        cfg = cp.make_config(N_, Np_, precision=prec, hio_iters=0, er_iters=iters_acc, n_ei=1 << 20)
+        plan = cp.Plan(cfg)
+        plan.load_intensities(I_dev, 0, thetas)
+        plan.load_support(torch.from_numpy(S.astype(np.uint8)).cuda())
+        plan.load_state(g0, 1)  # t = 1: no coupling step inside the run
+        plan.iterate(iters_acc)
+        g = plan.result(cp.RESULT_STATE)
+        errs = [float(np.linalg.norm(g[n] - ref[n]) / np.linalg.norm(ref[n])) for n in sample]
+        plan.close()
+        plan = cp.Plan(cp.make_config(N_, Np_, precision=prec, hio_iters=iters_speed, er_iters=0))
+        plan.load_intensities(I_dev, 0, thetas)
+        plan.iterate(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.iterate(iters_speed)
+        plan.sync()
+        dt = time.perf_counter() - t0
+        plan.close()
+        out[name] = {"value": round(Np_ * iters_speed / dt, 1), "unit": "angle-iterations/s",
+                     "rel_l2_vs_fp64_after_%d_er" % iters_acc: [float("%.3e" % e) for e in errs]}
+    return out
+
+
 def form_precision(cp, torch, I_dev, thetas, S_box, n_angles=NP, N_=N, sample=(0, 1), iters=5):
     """Throughput of the FP32 / BF16 / FP16 forms on the bench workload and
     their iterate error against the FP64 oracle after `iters` ER iterations
@@ -506,6 +563,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_forms:
         forms = {"p0_cufft_pointwise": form_p0(torch, I_dev, S_box),
                  "precision": form_precision(cp, torch, I_dev, thetas, S_box),
+                 "precision_large": form_precision_large(cp, torch),
                  "batching": form_batch(cp, torch),
                  "serving_continuous": form_serving(cp, torch, max_active=0),
                  "serving_one_at_a_time": form_serving(cp, torch, max_active=1),

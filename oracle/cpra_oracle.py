@@ -214,11 +214,18 @@ def support_update(g, gp, S, beta, algo):
     return np.where(valid, gp, 0.0)
 
 
-def iterate_2d(g, A, S, beta, algo, return_gp=False):
-    """One iteration for a stack of POs; returns (g_new, err_num, err_den[, g'])."""
-    G = dft2(g)
+def iterate_2d(g, A, S, beta, algo, return_gp=False, fft=False):
+    """One iteration for a stack of POs; returns (g_new, err_num, err_den[, g']).
+    fft=True takes the transforms from numpy.fft (FP64, the same unnormalised
+    forward / 1/N^2 inverse) instead of the dense DFT matrices: for sizes
+    where the matrices are too slow."""
+    if fft:
+        G = np.fft.fft2(g)
+    else:
+        G = dft2(g)
     num, den = fourier_error_terms(G, A)
-    gp = idft2(modulus_projection(G, A)).real
+    P = modulus_projection(G, A)
+    gp = (np.fft.ifft2(P) if fft else idft2(P)).real
     out = support_update(g, gp, S, beta, algo)
     return (out, num, den, gp) if return_gp else (out, num, den)
 

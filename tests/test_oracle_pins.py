@@ -200,6 +200,21 @@ def test_coupling_identity_constant_and_linearity():
     assert np.allclose(O.couple(np.roll(g, 2, axis=0), a), np.roll(O.couple(g, a), 2, axis=0))
 
 
+def test_iterate_fft_mode_equals_dft_mode():
+    """The numpy.fft transforms used at large N agree with the DFT matrices."""
+    rng = np.random.default_rng(2)
+    N = 24
+    g = rng.random((2, N, N))
+    A = rng.uniform(0.0, 5.0, size=(2, N, N))
+    S = np.zeros((2, N, N), bool)
+    S[:, 6:18, 6:18] = True
+    for algo in (O.HIO, O.ER):
+        a = O.iterate_2d(g, A, S, 0.9, algo, return_gp=True)
+        b = O.iterate_2d(g, A, S, 0.9, algo, return_gp=True, fft=True)
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=1e-11, atol=1e-12)
+
+
 def test_coupling_present_mask_hand_case():
     """R13 on Np = 3 with angle 2 absent and alpha = (0.2, 0.6, 0.2), constant
     images 1, 10, 100: angle 0 keeps taps 0 (0.6) and 1 (0.2), renormalised by
