@@ -44,14 +44,18 @@ __device__ __forceinline__ void lines_inv(float2 (&b)[FL::TB][FL::E2], float2 (&
 
 // per-warp shared memory of the row kernels: transpose tile + the warp's g
 // rows; 4 warps a block with the L-line plans, 8 with the one-line plan
-template <int N, int PREC> struct RowW {
-  using FL = typename WLines<N, PREC>::type;
+template <int N, class FL_> struct RowCfg {
+  using FL = FL_;
   static constexpr int WARPS = kSlimLines<FL> ? 8 : 4;
   static constexpr int GROWS = 2 * FL::L;                  // image rows per warp
   static constexpr int GFLOATS = GROWS * N;
   static constexpr int WARP_F2 = FL::TSIZE + GFLOATS / 2;  // float2 per warp
   static constexpr size_t SMEM = sizeof(float2) * (N + WARPS * WARP_F2);
 };
+template <int N, int PREC> using RowW = RowCfg<N, typename WLines<N, PREC>::type>;
+// the prime keeps the L-line plans: its three taps a pixel are loaded in
+// registers, where the extra warps of the one-line plan do not pay
+template <int N, int PREC> using PrimeW = RowCfg<N, WarpLines<N>>;
 
 // extra shared memory of the tensor-core path: one 16-bit A tile and 32
 // unscale factors per warp (the block DFT matrices are read through L1)
@@ -64,6 +68,8 @@ template <int N, int PREC> struct TcSmem {
 };
 template <int N, int PREC>
 constexpr size_t row_smem() { return RowW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(RowW<N, PREC>::WARPS); }
+template <int N, int PREC>
+constexpr size_t prime_smem() { return PrimeW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(PrimeW<N, PREC>::WARPS); }
 
 // Tensor-core scratch of this warp; W = the plan's matrices in global memory
 template <int N, int PREC>
@@ -295,10 +301,10 @@ __device__ __forceinline__ void store_rows(const float2 (&a)[FL::TA][FL::E1], fl
 
 // ---------------------------------------------------------------- prime
 template <int N, int PREC>
-__global__ void __launch_bounds__(RowW<N, PREC>::WARPS * 32, 3)
+__global__ void __launch_bounds__(PrimeW<N, PREC>::WARPS * 32, 3)
 k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
           const int2* __restrict__ tiles) {
-  using RW = RowW<N, PREC>;
+  using RW = PrimeW<N, PREC>;
   using FL = typename RW::FL;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
@@ -502,7 +508,7 @@ static cudaError_t prepare_w() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = smem_attr(k_rowpass_w<N, PREC>, row_smem<N, PREC>());
-  if (e == cudaSuccess) e = smem_attr(k_prime_w<N, PREC>, row_smem<N, PREC>());
+  if (e == cudaSuccess) e = smem_attr(k_prime_w<N, PREC>, prime_smem<N, PREC>());
   if (e == cudaSuccess) e = smem_attr(k_colpass_w<N, PREC>, col_smem<N, PREC>());
   if (e == cudaSuccess) done = true;
   return e;
@@ -522,8 +528,8 @@ static cudaError_t rowpass_w(const Launch& L) {
 
 template <int N, int PREC>
 static cudaError_t prime_w(const Launch& L) {
-  using RW = RowW<N, PREC>;
-  const size_t smem = row_smem<N, PREC>();
+  using RW = PrimeW<N, PREC>;
+  const size_t smem = prime_smem<N, PREC>();
   cudaError_t e = prepare_w<N, PREC>();
   if (e != cudaSuccess) return e;
   dim3 grid((N / 2) / (RW::WARPS * RW::FL::L), L.ntiles);
