@@ -43,6 +43,20 @@ def _dist():
     return rank, world, local
 
 
+def job_rate(units_per_rank, ms_local, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: every rank processed units_per_rank
+    units; the job took as long as its slowest rank.  Returns (units/s over
+    all ranks, the max-over-ranks milliseconds)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms = float(t.item())
+    return world * units_per_rank / (ms * 1e-3), ms
+
+
 class Clocks:
     """Samples nvidia-smi SM clocks and throttle reasons while running."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -523,11 +537,7 @@ def run_gpu(args):
     total_ms = sum(step_ms)
     roof, kstats = roofline_figures(plan, cp, peaks, NPa, NPa * IT * args.steps)
     plan.set_profiling(False)
-    t_dev = torch.tensor([total_ms], device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
-    total_ms = float(t_dev.item())
-    value = world * NPa * IT * args.steps / (total_ms * 1e-3)
+    value, total_ms = job_rate(NPa * IT * args.steps, total_ms, dist, device=f"cuda:{local}")
     if args.no_extras:
         if rank == 0:
             print(json.dumps({"profile_run": True, "value": value, "N": N, "Np": NPa,
@@ -554,10 +564,7 @@ def run_gpu(args):
         step_host()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / e2e_steps
-    e2e_t = torch.tensor([e2e_s], device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * NPa * IT / float(e2e_t.item())
+    e2e_value, _ = job_rate(NPa * IT, e2e_s * 1e3, dist, device=f"cuda:{local}")
 
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
