@@ -15,10 +15,15 @@ diffraction imaging"):
   * Step B    episodes W_m; each PO runs N_ei conventional 2D iterations
               starting from the Eq. 4 combination of the previous episode.
   * Eq. 4     carousel coupling O_n = sum_k alpha_k O_{n+k}, periodic in n.
-  * Step C    centre-of-mass move Delta r_n = -int O'_n r dv before merging.
+  * Step C    N_r guesses, the N_l of lowest error kept, centre-of-mass move
+              Delta r_n = -int O'_n r dv, twin (central inversion) choice by
+              Euclidean distance to the best episode, average -> E_n; the
+              PRTF of the merged guesses (results section, its ref. 23).
   * Step D    interpolation of the spectra E_n into the 3D E(q); inverse 3D FT.
   * HIO (Fienup, the paper's ref. 22) and ER updates; shrink-wrap (ref. 36)
     with the paper's 0.1 relative threshold.
+  * RAAR (Luke, the paper's ref. 39), the update the paper runs with
+    beta = 0.9 on its S. aureus data (results section).
 
 Readings where the paper is silent or garbled (the same list is kept with the
 design notes):
@@ -55,6 +60,22 @@ design notes):
       present iterate; Eq. 4 couples each present angle with its present
       neighbours, the alpha_k of the present taps divided by their sum (all
       taps present: the alpha_k as given); absent angles keep their state.
+  R14 RAAR with a positivity-constrained support: T = beta/2 (R_S R_M + I)
+      + (1 - beta) P_M, reflections R = 2P - I, P_M g = g' (R6) and
+      P_S = P_{S+}; it replaces HIO for the iterations before hio_iters
+      (and in Step A) when the configuration selects it.
+  R15 Episode reconstruction error (Step C ranks episodes by it, the paper
+      does not define it): the mean over the POs of E_F (R8) in the last
+      recorded iteration.  Ties keep the lower guess index first.
+  R16 Twin choice: the distance is taken on one PO (index twin_ref, default
+      0) after the mass-centre move, and the version chosen there is used for
+      every PO of that episode (inverting the 3D object inverts every
+      projection).  The inverted version of a moved PO rho_m is
+      conj(rho_m(-x)), whose spectrum is conj(E_n); a tie keeps the plain one.
+  R17 The final E_n is the spectrum of the mean of the corrected POs of the
+      kept episodes (equivalently the mean of their spectra).
+  R18 PRTF per PO: |sum_g E'_g| / sum_g |E'_g| over the kept, corrected
+      episodes, averaged on rings s = round(|k|), s < N/2.
 """
 from __future__ import annotations
 
@@ -63,19 +84,20 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-HIO, ER = 0, 1
+HIO, ER, RAAR = 0, 1, 2
 WRAP_LITERAL, WRAP_MIRROR = 0, 1
 BLEND_STATE, BLEND_OBJECT = 0, 1
 
 __all__ = [
-    "HIO", "ER", "WRAP_LITERAL", "WRAP_MIRROR", "BLEND_STATE", "BLEND_OBJECT",
+    "HIO", "ER", "RAAR", "WRAP_LITERAL", "WRAP_MIRROR", "BLEND_STATE", "BLEND_OBJECT",
     "dft_matrix", "dft2", "idft2", "dft3", "idft3", "fftshift2", "ifftshift2",
     "fftshift3", "amplitudes", "a_sym", "splitmix64", "initial_guess",
     "modulus_projection", "fourier_error_terms", "support_update",
     "iterate_2d", "positivity_margin", "couple", "wrapped_gaussian", "blur", "shrinkwrap",
     "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d",
     "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
-    "r_factor",
+    "r_factor", "raar_update", "episode_error", "select_best", "centrally_inverted", "prtf",
+    "merge_episodes", "assemble_spectra",
 ]
 
 
@@ -206,8 +228,18 @@ def fourier_error_terms(G: np.ndarray, A: np.ndarray):
     return (d * d).sum(axis=(-2, -1)), (A * A).sum(axis=(-2, -1))
 
 
+def raar_update(g, gp, S, beta):
+    """RAAR (R14): beta/2 (R_S R_M g + g) + (1 - beta) P_M g, the operator
+    written out with the reflections R = 2P - I of P_M g = g' and P_{S+}."""
+    rm = 2.0 * gp - g                      # R_M g
+    rs = 2.0 * object_estimate(rm, S) - rm  # R_S R_M g
+    return 0.5 * beta * (rs + g) + (1.0 - beta) * gp
+
+
 def support_update(g, gp, S, beta, algo):
-    """HIO or ER real-space step on the valid set V = S and g' >= 0."""
+    """HIO or ER real-space step on the valid set V = S and g' >= 0; RAAR (R14)."""
+    if algo == RAAR:
+        return raar_update(g, gp, S, beta)
     valid = S.astype(bool) & (gp >= 0)
     if algo == HIO:
         return np.where(valid, gp, g - beta * gp)
@@ -379,6 +411,80 @@ def assemble(g, S, thetas, com_align=True):
 
 
 # --------------------------------------------------------------------------
+# Step C: repeating and merging (R15-R18)
+# --------------------------------------------------------------------------
+def episode_error(final_errors) -> float:
+    """R15: reconstruction error of an episode = mean over its POs of the
+    Fourier error E_F (R8) of its last recorded iteration."""
+    return float(np.mean(np.asarray(final_errors, dtype=np.float64)))
+
+
+def select_best(episode_errors, n_l):
+    """The n_l episodes with the lowest error, best first (ties by index)."""
+    e = [float(x) for x in episode_errors]
+    return sorted(range(len(e)), key=lambda i: (e[i], i))[:n_l]
+
+
+def centrally_inverted(img):
+    """img(-x): central inversion about index 0 of the periodic grid."""
+    m = _neg_index(img.shape[-1])
+    return img[..., m[:, None], m[None, :]]
+
+
+def prtf(E_corrected) -> np.ndarray:
+    """R18: phase retrieval transfer function of each PO over the merged
+    episodes: |sum_g E'_g(k)| / sum_g |E'_g(k)| (0 where the denominator is
+    0), averaged over the pixels of each ring s = round(|k|) of signed
+    frequencies, s = 0..N/2-1.  Returns [Np][N/2]."""
+    num = np.abs(np.sum(E_corrected, axis=0))
+    den = np.sum(np.abs(E_corrected), axis=0)
+    ratio = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+    N = ratio.shape[-1]
+    k = signed_freq(N)
+    ring = np.rint(np.sqrt(k[:, None] ** 2 + k[None, :] ** 2)).astype(np.int64)
+    out = np.zeros(ratio.shape[:-2] + (N // 2,))
+    for r in range(N // 2):
+        out[..., r] = ratio[..., ring == r].mean(axis=-1)
+    return out
+
+
+def merge_episodes(gs, Ss, final_errors, n_l, twin_ref=0, com_align=True):
+    """Step C on N_r finished episodes (gs[i], Ss[i]: iterate and support
+    stacks [Np][N][N] of guess i; final_errors[i]: its last E_F per PO).
+
+    1. keep the n_l episodes of lowest error (R15);
+    2. move the mass centre of every PO to the origin (R10's phase ramp) and
+       return to real space: rho_m = IDFT2(E_n);
+    3. twin (R16): compare PO twin_ref of every kept episode with PO twin_ref
+       of the best one, as is and centrally inverted, conj(rho_m(-x)) (the
+       inversion of the real PO; conj keeps it exact where the ramp leaves an
+       imaginary part on the Nyquist lines); the version at the smaller
+       Euclidean distance is used for every PO of that episode;
+    4. average the corrected episodes (R17) and take the spectra of the mean
+       as the final E_n.
+    Returns (selected, inverted flags, E [Np][N][N] complex, PRTF [Np][N/2])."""
+    sel = select_best([episode_error(e) for e in final_errors], n_l)
+    moved = [idft2(spectra(gs[i], Ss[i], com_align)) for i in sel]
+    ref = moved[0][twin_ref]
+    corrected, inverted = [], []
+    for rho in moved:
+        twin = np.conj(centrally_inverted(rho))
+        d_plain = np.linalg.norm(rho[twin_ref] - ref)
+        d_twin = np.linalg.norm(twin[twin_ref] - ref)
+        flip = bool(d_twin < d_plain)
+        inverted.append(flip)
+        corrected.append(twin if flip else rho)
+    mean = np.mean(corrected, axis=0)
+    E_corr = np.array([dft2(c) for c in corrected])
+    return sel, inverted, dft2(mean), prtf(E_corr)
+
+
+def assemble_spectra(E, thetas):
+    """Step D from given spectra E[Np][N][N] (e.g. the merged episode)."""
+    return volume(grid_3d(E, thetas))
+
+
+# --------------------------------------------------------------------------
 # The whole schedule (Steps A, B; R4)
 # --------------------------------------------------------------------------
 @dataclass
@@ -398,6 +504,7 @@ class OracleConfig:
     n_pre: int = 0
     com_align: bool = True
     seed: int = 0
+    update: int = HIO  # the rule before hio_iters: HIO or RAAR (R14)
 
 
 @dataclass
@@ -422,8 +529,8 @@ class OracleRun:
         S = np.broadcast_to(np.asarray(S0).astype(bool), A.shape).copy()
         g = initial_guess(cfg.seed, cfg.Np, cfg.N, S) if g0 is None else np.array(g0, dtype=np.float64)
         run = cls(cfg=cfg, A=A, S=S, g=g)
-        for _ in range(cfg.n_pre):  # Step A: angle 0 alone, HIO
-            g1, _, _ = iterate_2d(run.g[0:1], A[0:1], S[0:1], cfg.beta, HIO)
+        for _ in range(cfg.n_pre):  # Step A: angle 0 alone, the update rule
+            g1, _, _ = iterate_2d(run.g[0:1], A[0:1], S[0:1], cfg.beta, cfg.update)
             run.g[0] = g1[0]
         return run
 
@@ -432,7 +539,7 @@ class OracleRun:
         c = self.cfg
         if self.t % c.n_ei == 0:
             self.g = couple(self.g, c.alpha, c.wrap, c.blend, self.S, self.present)
-        algo = HIO if self.t < c.hio_iters else ER
+        algo = c.update if self.t < c.hio_iters else ER
         g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True)
         err = np.sqrt(num / den)
         if self.present is not None:  # absent angles keep their state (R13)

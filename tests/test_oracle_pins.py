@@ -144,6 +144,76 @@ def test_support_update_cases():
     assert np.all(e[neg] == 0) and np.allclose(h[neg], g[neg] - 0.9 * gp[neg])
 
 
+# ---------------------------------------------------------------- RAAR (R14)
+def _raar_inputs(shape=(2, 16, 16)):
+    g = _rand(*shape)
+    gp = _rand(*shape)
+    S = rng.random(shape) > 0.4
+    return g, gp, S
+
+
+def test_raar_pixel_cases():
+    """The reflection form reduces, pixel by pixel, to: g' where x is in S and
+    2g' - g >= 0 (R_M g lies in the constraint set, so R_S leaves it alone),
+    beta g + (1 - 2 beta) g' elsewhere (R_S negates it).  Derived by hand
+    from R = 2P - I, not from the oracle's expression."""
+    g, gp, S = _raar_inputs()
+    for beta in (0.9, 0.5, 0.3, 1.0):
+        out = O.support_update(g, gp, S, beta, O.RAAR)
+        keep = S & (2 * gp - g >= 0)
+        assert np.allclose(out[keep], gp[keep], atol=1e-15)
+        assert np.allclose(out[~keep], beta * g[~keep] + (1 - 2 * beta) * gp[~keep], atol=1e-14)
+
+
+def test_raar_beta_one_is_douglas_rachford_and_relaxation():
+    """beta = 1 is the averaged alternating reflections (Douglas-Rachford)
+    map (R_S R_M + I) / 2, which outside the support equals HIO with beta = 1
+    (Bauschke, Combettes and Luke); RAAR is the convex combination
+    T_beta = beta T_1 + (1 - beta) P_M (Luke's relaxation)."""
+    g, gp, S = _raar_inputs()
+    t1 = O.support_update(g, gp, S, 1.0, O.RAAR)
+    h1 = O.support_update(g, gp, S, 1.0, O.HIO)
+    assert np.allclose(t1[~S], h1[~S], atol=1e-15)
+    assert np.allclose(t1[~S], g[~S] - gp[~S], atol=1e-15)
+    for beta in (0.9, 0.5, 0.25):
+        tb = O.support_update(g, gp, S, beta, O.RAAR)
+        assert np.allclose(tb, beta * t1 + (1 - beta) * gp, atol=1e-14)
+
+
+def test_raar_is_continuous_where_hio_jumps():
+    """Across the boundary of its valid set RAAR changes by O(eps) (both sides
+    give g' when 2g' = g), while HIO jumps by |g| at g' = 0: the property that
+    makes a wrong valid-set test (g' >= 0 instead of 2g' - g >= 0) visible."""
+    gp = np.abs(_rand(64)) + 0.1
+    S = np.ones(64, bool)
+    eps = 1e-9
+    lo = O.support_update(2 * gp - eps, gp, S, 0.9, O.RAAR)   # 2g' - g = +eps
+    hi = O.support_update(2 * gp + eps, gp, S, 0.9, O.RAAR)   # 2g' - g = -eps
+    assert np.max(np.abs(hi - lo)) < 1e-8
+    g = np.abs(_rand(64)) + 0.5
+    h_pos = O.support_update(g, np.full(64, eps), S, 0.9, O.HIO)
+    h_neg = O.support_update(g, np.full(64, -eps), S, 0.9, O.HIO)
+    assert np.min(np.abs(h_pos - h_neg)) > 0.4
+
+
+def test_schedule_uses_raar_before_switch():
+    P, A_true = _true_case(16, 8)
+    I = np.fft.fftshift(A_true ** 2, axes=(-2, -1))
+    cfg = O.OracleConfig(N=16, Np=2, n_ei=2, hio_iters=3, er_iters=2, seed=4, update=O.RAAR, n_pre=2)
+    run = O.OracleRun.start(cfg, I)
+    g = O.initial_guess(4, 2, 16, run.S)
+    for _ in range(2):  # Step A with the same rule
+        g1, _, _ = O.iterate_2d(g[0:1], run.A[0:1], run.S[0:1], 0.9, O.RAAR)
+        g[0] = g1[0]
+    assert np.array_equal(run.g, g)
+    for t in range(5):
+        if t % 2 == 0:
+            g = O.couple(g, cfg.alpha)
+        g, _, _ = O.iterate_2d(g, run.A, run.S, 0.9, O.RAAR if t < 3 else O.ER)
+        run.step()
+        assert np.array_equal(run.g, g)
+
+
 def _true_case(N=32, seed=3):
     r = np.random.default_rng(seed)
     P = np.zeros((2, N, N))
@@ -155,7 +225,7 @@ def _true_case(N=32, seed=3):
 def test_true_object_is_fixed_point():
     P, A = _true_case()
     S = P > 0
-    for algo in (O.HIO, O.ER):
+    for algo in (O.HIO, O.ER, O.RAAR):
         g, num, den = O.iterate_2d(P, A, S, 0.9, algo)
         assert np.max(np.abs(g - P)) < 1e-12
         assert np.all(num / den < 1e-26)
@@ -400,6 +470,64 @@ def test_assembly_axis_aligned_roundtrip():
     assert np.allclose(V[:, 0, 1:], F3[:, 0, 1:], atol=1e-10)
     assert np.allclose(V[:, 1:, 0], F3[:, 1:, 0], atol=1e-10)
     assert np.allclose(V[:, 0, 0], F3[:, 0, 0], atol=1e-10)
+
+
+# ---------------------------------------------------------------- Step C merge (R15-R18)
+def _po_stack(Np=3, N=16, seed=21):
+    """Positive POs inside the central N/2 box (index 0 never touched)."""
+    r = np.random.default_rng(seed)
+    P = np.zeros((Np, N, N))
+    P[:, N // 4:3 * N // 4, N // 4:3 * N // 4] = r.random((Np, N // 2, N // 2)) + 0.1
+    return P
+
+
+def test_merge_undoes_translation_and_inversion():
+    """Step C names the two ambiguities it removes: a translation of a PO and
+    its central inversion.  A second episode that is the first one inverted
+    and shifted by an integer vector merges back onto the first exactly
+    (flagged as inverted), the mean equals the first episode's moved spectra,
+    and its PRTF is 1 on every ring."""
+    N = 16
+    A = _po_stack(N=N)
+    S = np.ones_like(A, bool)
+    B = np.roll(O.centrally_inverted(A), (2, -3), axis=(-2, -1))
+    C = np.roll(A, (-1, 2), axis=(-2, -1))
+    errs = [np.full(3, 0.1), np.full(3, 0.2), np.full(3, 0.3)]
+    sel, inv, E, pr = O.merge_episodes([A, B, C], [S, S, S], errs, n_l=3)
+    assert sel == [0, 1, 2] and inv == [False, True, False]
+    E_A = O.spectra(A, S)
+    assert np.allclose(E, E_A, rtol=0, atol=1e-10 * np.abs(E_A).max())
+    assert np.allclose(pr, 1.0, atol=1e-12)
+
+
+def test_merge_selects_lowest_errors_and_averages():
+    N = 16
+    A = _po_stack(N=N, seed=5)
+    S = np.ones_like(A, bool)
+    Z = np.zeros_like(A)
+    errs = [np.full(3, 0.3), np.full(3, 0.1), np.array([0.2, 0.2, 0.2])]
+    sel, inv, E, pr = O.merge_episodes([Z, A, 2 * A], [S, S, S], errs, n_l=2)
+    assert sel == [1, 2] and inv == [False, False]
+    # the mean of A and 2A (same mass centres) is 1.5 A
+    assert np.allclose(E, 1.5 * O.spectra(A, S), atol=1e-10 * np.abs(E).max())
+    assert O.select_best([0.5, 0.2, 0.2, 0.1], 3) == [3, 1, 2]  # ties by index
+    assert O.episode_error([[0.1, 0.3], [0.2, 0.4]]) == pytest.approx(0.25)
+
+
+def test_prtf_hand_cases():
+    """|sum E| / sum |E|: 1 for equal phases, 0 for opposite phases, 1/sqrt 2
+    for a quarter turn.  On a 4 x 4 grid (signed k in {-2, -1, 0, 1}) ring
+    s = round(|k|) = 1 holds the 4 pixels at |k| = 1 and the 4 at |k| = sqrt 2,
+    so one pixel with ratio 1 there averages to 1/8."""
+    N = 4
+    E = np.exp(1j * _rand(2, N, N)) * (1 + np.abs(_rand(2, N, N)))
+    assert np.allclose(O.prtf(np.array([E, E])), 1.0)
+    assert np.allclose(O.prtf(np.array([E, -E])), 0.0)
+    assert np.allclose(O.prtf(np.array([E, 1j * E])), 1 / math.sqrt(2))
+    one = np.zeros((1, N, N), complex)
+    one[0, 0, 1] = 1.0  # k = (0, 1): ring 1; the other pixels have 0 / 0 -> 0
+    pr = O.prtf(np.array([one, one]))
+    assert np.allclose(pr[0], [0.0, 0.125])
 
 
 # ---------------------------------------------------------------- schedule
