@@ -49,6 +49,7 @@ typedef enum {
 enum { CPRA_WRAP_LITERAL = 0, CPRA_WRAP_MIRROR = 1 };
 enum { CPRA_BLEND_STATE = 0, CPRA_BLEND_OBJECT = 1 };
 enum { CPRA_FP32 = 0, CPRA_BF16_TC = 1, CPRA_FP16_TC = 2 };
+enum { CPRA_UPDATE_HIO = 0, CPRA_UPDATE_RAAR = 1 };
 enum {
   CPRA_ENGINE_AUTO = 0,
   CPRA_ENGINE_TWO_PASS = 1,
@@ -62,7 +63,11 @@ enum {
   CPRA_RESULT_SUPPORT = 2, /* Np*N*N uint8: support, 1 inside                    */
   CPRA_RESULT_ERRORS = 3,  /* t*Np double: Fourier error of every iteration so far,
                               [iteration][angle]                                 */
-  CPRA_RESULT_VOLUME = 4   /* N*N*N complex64 [z][y][x], centred (after assemble) */
+  CPRA_RESULT_VOLUME = 4,  /* N*N*N complex64 [z][y][x], centred (after assemble
+                              or merge)                                          */
+  CPRA_RESULT_MERGED_SPECTRA = 5 /* Np*N*N complex64 [angle][kz][ku], FFT order: the
+                              merged spectra E_n of the last cpra_merge into this
+                              plan (NOT_READY before)                             */
 };
 
 #define CPRA_MAX_TAPS 15
@@ -75,17 +80,20 @@ enum {
  *   n_ei           conventional 2D iterations per episode, N_ei (Step B).
  *   n_taps, alpha  coupling weights alpha_k, k = -(n_taps/2)..n_taps/2 (Eq. 4);
  *                  n_taps odd, <= CPRA_MAX_TAPS, sum 1 within 1e-12.
- *   beta           HIO feedback (Fienup); the paper uses 0.9.
+ *   beta           feedback of the update rule: HIO's beta (Fienup) or RAAR's
+ *                  relaxation (Luke); the paper uses 0.9 for both.
  *   wrap_mode      180-degree seam: LITERAL couples angle Np-1 with angle 0 as
  *                  is; MIRROR flips u once per wrap.
  *   blend_target   STATE blends the iterate g, OBJECT blends P_{S+} g.
- *   hio_iters, er_iters  global schedule: iteration t runs HIO while
- *                  t < hio_iters, ER afterwards.
+ *   hio_iters, er_iters  global schedule: iteration t runs the update rule
+ *                  (HIO or RAAR, see `update`) while t < hio_iters, ER
+ *                  afterwards.
  *   shrinkwrap_every, sw_sigma, sw_tau   support update after iteration t
  *                  when (t+1) % every == 0 (0 = off): blur P_{S+} g with a
  *                  periodic Gaussian of sw_sigma pixels and keep pixels at or
  *                  above sw_tau times the maximum (the paper's 0.1 threshold).
- *   n_pre          Step A: HIO iterations run on angle 0 alone before t = 0.
+ *   n_pre          Step A: iterations of the update rule run on angle 0
+ *                  alone before t = 0.
  *   precision      CPRA_FP32 (default) or tensor-core FFT stages.
  *   com_align      1: move each PO's mass centre to the origin before
  *                  assembly (Step C); 0: use the frame centre.
@@ -102,6 +110,15 @@ enum {
  *                  its clusters, else WARP where available, else TWO_PASS.
  *                  TUNED: the fastest engine for this N on this GPU
  *                  according to cpra_autotune (its default cache).
+ *   update         real-space rule of the iterations before hio_iters.
+ *                  CPRA_UPDATE_HIO (default): g' on V = {x in S, g'(x) >= 0},
+ *                  g - beta g' elsewhere.  CPRA_UPDATE_RAAR (relaxed averaged
+ *                  alternating reflections, Luke 2005; the paper's rule for
+ *                  its S. aureus data): g' on {x in S, 2 g'(x) - g(x) >= 0},
+ *                  beta g + (1 - 2 beta) g' elsewhere, which is
+ *                  beta/2 (R_S R_M + I) g + (1 - beta) P_M g with the
+ *                  reflections R = 2P - I of the support-positivity and
+ *                  modulus projections.
  *   seed           seeds the random initial guess (SplitMix64 per pixel).
  *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
  */
@@ -120,6 +137,7 @@ typedef struct {
   int32_t precision;
   int32_t com_align;
   int32_t engine;
+  int32_t update;
   uint64_t seed;
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);
@@ -129,7 +147,7 @@ typedef struct {
 /* Fill *cfg with defaults for an N x N, Np-angle problem: n_ei 10, alpha
  * (0.2, 0.6, 0.2) and beta 0.9 (the paper's Eq. 4 example and HIO value),
  * 200 HIO + 20 ER, shrink-wrap off, sigma 2, tau 0.1, LITERAL, STATE, FP32,
- * com_align 1, seed 0, cudaMalloc.  Returns INVALID_ARG for a NULL cfg. */
+ * com_align 1, engine AUTO, update HIO, seed 0, cudaMalloc.  Returns INVALID_ARG for a NULL cfg. */
 cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* cfg);
 
 /* Device bytes a plan for *cfg holds while iterating (iter_bytes) and the
@@ -166,7 +184,7 @@ cpra_status cpra_load_state(cpra_plan_t plan, const float* g, int64_t t);
 
 /* Run n_iters global iterations (Step B): coupling (Eq. 4) before every
  * iteration t with t % n_ei == 0, then FFT -> modulus projection -> inverse
- * FFT -> HIO/ER update for every angle, shrink-wrap on schedule.  If err_out
+ * FFT -> HIO/RAAR/ER update for every angle, shrink-wrap on schedule.  If err_out
  * is not NULL it receives the Fourier error of every angle and iteration,
  * err_out[i*Np + n] (double, host or device).  Returns NOT_READY until every
  * iterating angle (every angle unless cpra_set_present restricted them) has
@@ -191,6 +209,44 @@ cpra_status cpra_set_present(cpra_plan_t plan, const uint8_t* mask);
  * with CPRA_RESULT_VOLUME) and is also copied to out_volume when that is not
  * NULL (N^3 * 8 bytes, host or device). */
 cpra_status cpra_assemble_3d(cpra_plan_t plan, void* out_volume);
+
+/* Step C (repeating and merging): combine n_r finished reconstructions of
+ * the same patterns, each from its own random start (its own seed), into one
+ * episode and assemble it (Step D) into dst's volume.
+ *   1. Keep the n_l guesses of lowest reconstruction error, best first; the
+ *      error of a guess is the mean over its POs of the Fourier error of its
+ *      last iteration.
+ *   2. Move the mass centre of every PO of every kept guess to the origin
+ *      (Delta r_n = -int O'_n r dv, as a phase ramp on its spectrum
+ *      E_n = FFT2(P_{S+} g_n), as in cpra_assemble_3d).
+ *   3. Twin: compare PO twin_ref of each kept guess with PO twin_ref of the
+ *      best one, as is and centrally inverted (spectrum conj(E_n)); the
+ *      version at the smaller Euclidean distance (computed on the spectra,
+ *      Parseval) is used for every PO of that guess.
+ *   4. Average the corrected spectra: the final E_n, readable as
+ *      CPRA_RESULT_MERGED_SPECTRA; gridding and the inverse 3D FFT put the
+ *      volume into dst (CPRA_RESULT_VOLUME).
+ *   guesses   n_r plans with dst's N and Np (dst may be one of them), every
+ *             angle present and at least one iteration run
+ *   twin_ref  the PO compared for the twin choice, 0 <= twin_ref < Np
+ *   dst       receives the merged spectra and volume; its angles grid them
+ *   selected  NULL or host int32[n_l]: the kept guesses, best first
+ *   inverted  NULL or host int32[n_l]: 1 where that guess was inverted
+ *   prtf      NULL or float32[Np][N/2] (host or device): per PO, the phase
+ *             retrieval transfer function |sum_g E'_g| / sum_g |E'_g| over the
+ *             kept, corrected guesses, averaged over rings round(|k|) = s
+ *             (signed k), s = 0..N/2-1 (0 where sum |E'| = 0)
+ * Paper: Step C (N_r random guesses, the N_l best kept, mass-centre move,
+ * twin choice against the best episode, averaging); PRTF as in its results
+ * section (its ref. 23).  The call runs on the guesses' and dst's streams and
+ * returns when the merge is complete.  Besides the assembly buffers, dst
+ * allocates about 8 N^2 Np bytes of scratch on first use (4 N^2 Np more
+ * with prtf).  Each guess's
+ * state is only read; its row spectra buffer is reused.  INVALID_ARG for bad
+ * counts, sizes or pointers, NOT_READY for a guess that has not iterated or
+ * has absent angles. */
+cpra_status cpra_merge(const cpra_plan_t* guesses, int32_t n_r, int32_t n_l, int32_t twin_ref,
+                       cpra_plan_t dst, int32_t* selected, int32_t* inverted, float* prtf);
 
 /* Copy one result (CPRA_RESULT_*) into dst, which holds `bytes` bytes (host
  * or device).  INVALID_ARG if bytes is smaller than the result, NOT_READY for

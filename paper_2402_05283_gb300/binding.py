@@ -20,8 +20,9 @@ OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_READY, ERR_TIMEOUT, ER
 WRAP_LITERAL, WRAP_MIRROR = 0, 1
 BLEND_STATE, BLEND_OBJECT = 0, 1
 FP32, BF16_TC, FP16_TC = 0, 1, 2
+UPDATE_HIO, UPDATE_RAAR = 0, 1
 ENGINE_AUTO, ENGINE_TWO_PASS, ENGINE_FUSED, ENGINE_WARP, ENGINE_TUNED = 0, 1, 2, 3, 4
-RESULT_PO, RESULT_STATE, RESULT_SUPPORT, RESULT_ERRORS, RESULT_VOLUME = range(5)
+RESULT_PO, RESULT_STATE, RESULT_SUPPORT, RESULT_ERRORS, RESULT_VOLUME, RESULT_MERGED_SPECTRA = range(6)
 (KERNEL_COLPASS, KERNEL_ROWPASS, KERNEL_PRIME, KERNEL_SHRINKWRAP, KERNEL_ASSEMBLE, KERNEL_FUSED,
  KERNEL_PREPARE, KERNEL_KINDS) = range(8)
 MAX_TAPS = 15
@@ -37,7 +38,7 @@ class cpra_config(C.Structure):
         ("blend_target", C.c_int32), ("hio_iters", C.c_int32), ("er_iters", C.c_int32),
         ("shrinkwrap_every", C.c_int32), ("sw_sigma", C.c_float), ("sw_tau", C.c_float),
         ("n_pre", C.c_int32), ("precision", C.c_int32), ("com_align", C.c_int32),
-        ("engine", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+        ("engine", C.c_int32), ("update", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
         ("alloc_ctx", C.c_void_p),
     ]
 
@@ -103,6 +104,8 @@ def lib() -> C.CDLL:
             "cpra_launch_count": (C.c_int64, []),
             "cpra_shrinkwrap_static": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_float,
                                                  C.c_float, P]),
+            "cpra_merge": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, P,
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32), P]),
             "cpra_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]),
             "cpra_batch_iterate": (C.c_int, [P, C.c_int32]),
             "cpra_batch_launches": (C.c_int64, [P, C.c_int32]),
@@ -210,6 +213,22 @@ def cpra_result(plan, what: int, dst, nbytes: int):
     p, keep = _ptr(dst)
     _check(lib().cpra_result(plan, what, p, nbytes), plan)
     return keep
+
+
+def cpra_merge(guesses, n_l: int, twin_ref: int, dst, prtf=None):
+    """Step C merge of plan handles `guesses` into plan handle `dst`.
+    Returns (selected, inverted) as lists; prtf: None, or a float32 array /
+    tensor of Np * N/2 elements that receives the PRTF."""
+    hs = [g.h if isinstance(g, Plan) else g for g in guesses]
+    if isinstance(dst, Plan):
+        dst = dst.h
+    n_r = len(hs)
+    arr = (C.c_void_p * n_r)(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    sel = (C.c_int32 * max(n_l, 1))()
+    inv = (C.c_int32 * max(n_l, 1))()
+    p, keep = _ptr(prtf)
+    _check(lib().cpra_merge(arr, n_r, n_l, twin_ref, dst, sel, inv, p), dst)
+    return list(sel)[:n_l], [bool(v) for v in inv][:n_l]
 
 
 def cpra_iteration(plan) -> int:
@@ -384,6 +403,8 @@ class Plan:
             a = np.empty((self.iteration, Np), np.float64)
         elif what == RESULT_VOLUME:
             a = np.empty((N, N, N), np.complex64)
+        elif what == RESULT_MERGED_SPECTRA:
+            a = np.empty((Np, N, N), np.complex64)
         else:
             raise ValueError(what)
         if a.nbytes:
@@ -504,6 +525,8 @@ class Server:
             a = np.empty((Np, N, N), np.float32)
         elif what == RESULT_VOLUME:
             a = np.empty((N, N, N), np.complex64)
+        elif what == RESULT_MERGED_SPECTRA:
+            a = np.empty((Np, N, N), np.complex64)
         elif what == RESULT_SUPPORT:
             a = np.empty((Np, N, N), np.uint8)
         elif what == RESULT_ERRORS:

@@ -1,5 +1,6 @@
 // api.cu - the C ABI (include/cpra.h): plans, loading, the iteration
 // schedule of Steps A and B, assembly (Step D) and results.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -116,6 +117,10 @@ cpra_status validate(const cpra_config* c, std::string& why) {
   }
   if (std::fabs(s - 1.0) > 1e-12) { why = "alpha must sum to 1 (within 1e-12)"; return CPRA_ERR_INVALID_ARG; }
   if (!std::isfinite(c->beta)) { why = "beta not finite"; return CPRA_ERR_INVALID_ARG; }
+  if (c->update != CPRA_UPDATE_HIO && c->update != CPRA_UPDATE_RAAR) {
+    why = "bad update rule";
+    return CPRA_ERR_INVALID_ARG;
+  }
   if (c->wrap_mode != CPRA_WRAP_LITERAL && c->wrap_mode != CPRA_WRAP_MIRROR) {
     why = "bad wrap_mode";
     return CPRA_ERR_INVALID_ARG;
@@ -293,6 +298,9 @@ cpra_status upload_static(cpra_plan_s* p) {
   return CPRA_OK;
 }
 
+// the kernel rule of the iterations before hio_iters (HIO or RAAR)
+int update_rule(const cpra_config& c) { return c.update == CPRA_UPDATE_RAAR ? kRAAR : kHIO; }
+
 CoupleArgs plain_args() {
   CoupleArgs ca{};
   ca.n_taps = 1;
@@ -430,14 +438,14 @@ static cpra_status iterate_fused(cpra_plan_s* p, int32_t n_iters) {
   std::vector<JobStep> steps;
   std::vector<int> sw_after;  // shrink-wrap after window k
   const int n_pre = p->state_ready ? 0 : c.n_pre;
-  if (n_pre > 0) {  // Step A: HIO on angle 0 alone, one launch
+  if (n_pre > 0) {  // Step A: the update rule on angle 0 alone, one launch
     JobStep s{};
     s.prime = 1;
     s.ca = plain_args();
     s.g_src = p->g;
     s.g = p->g;
     s.err_slot = -1;
-    s.algo = kHIO;
+    s.algo = update_rule(c);
     s.active = 1;
     s.n_iters = n_pre;
     s.hio_left = n_pre;
@@ -463,7 +471,7 @@ static cpra_status iterate_fused(cpra_plan_s* p, int32_t n_iters) {
     }
     s.g = gcur;
     s.err_slot = t;
-    s.algo = t < c.hio_iters ? kHIO : kER;
+    s.algo = t < c.hio_iters ? update_rule(c) : kER;
     s.active = 1;
     s.n_iters = (int)(tb - t);
     s.hio_left = (int)std::max<int64_t>(0, std::min<int64_t>(tb - t, (int64_t)c.hio_iters - t));
@@ -516,6 +524,7 @@ cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* c) {
   c->precision = CPRA_FP32;
   c->com_align = 1;
   c->engine = CPRA_ENGINE_AUTO;
+  c->update = CPRA_UPDATE_HIO;
   c->seed = 0;
   return CPRA_OK;
 }
@@ -785,14 +794,14 @@ cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
   // the schedule of Steps A and B as one step-table row per iteration
   std::vector<JobStep> steps;
   const int n_pre = p->state_ready ? 0 : c.n_pre;
-  for (int i = 0; i < n_pre; ++i) {  // Step A: HIO on angle 0 alone
+  for (int i = 0; i < n_pre; ++i) {  // Step A: the update rule on angle 0 alone
     JobStep s{};
     s.prime = 1;
     s.ca = plain_args();
     s.g_src = p->g;
     s.g = p->g;
     s.err_slot = -1;
-    s.algo = kHIO;
+    s.algo = update_rule(c);
     s.forward = 0;
     s.active = 1;
     steps.push_back(s);
@@ -816,7 +825,7 @@ cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
     }
     s.g = gcur;
     s.err_slot = t;
-    s.algo = t < c.hio_iters ? kHIO : kER;
+    s.algo = t < c.hio_iters ? update_rule(c) : kER;
     s.forward = ((t + 1) % c.n_ei) != 0;
     s.active = 1;
     hp = s.forward != 0;
@@ -857,10 +866,8 @@ cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
   return CPRA_OK;
 }
 
-cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
-  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
-  if (!p->state_ready) return fail(p, CPRA_ERR_NOT_READY, "no iterate to assemble");
-  if (p->partial) return fail(p, CPRA_ERR_NOT_READY, "assembly needs every angle present");
+// the assembly buffers and gridding lists of p (allocated on first use)
+static cpra_status ensure_assembly(cpra_plan_s* p) {
   const size_t N = p->N, Np = p->Np, NN = N * N;
   Assembly& a = p->asmb;
   if (!a.F) {
@@ -871,28 +878,145 @@ cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
     if (!a.F || !a.vol || !a.cell_ptr || !a.moments)
       return fail(p, CPRA_ERR_OUT_OF_MEMORY, "assembly allocation failed");
   }
-  if (!a.ready) {
-    cpra_status st = build_gridding(p);
-    if (st != CPRA_OK) return st;
-  }
-  {
-    JobStep s{};
-    s.prime = 1;
-    s.ca = plain_args();
-    s.ca.object = 1;  // R2C rows of rho = P_{S+} g
-    s.g_src = p->g;
-    s.g = p->g;
-    s.active = 1;
-    cpra_status st = upload_steps(p, std::vector<JobStep>{s});
-    if (st != CPRA_OK) return st;
-  }
+  if (!a.ready) return build_gridding(p);
+  return CPRA_OK;
+}
+
+// step-table row 0 of p: the R2C rows of rho = P_{S+} g into Hp (prime kernel)
+static cpra_status upload_rho_rows(cpra_plan_s* p) {
+  JobStep s{};
+  s.prime = 1;
+  s.ca = plain_args();
+  s.ca.object = 1;
+  s.g_src = p->g;
+  s.g = p->g;
+  s.active = 1;
+  return upload_steps(p, std::vector<JobStep>{s});
+}
+
+cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->state_ready) return fail(p, CPRA_ERR_NOT_READY, "no iterate to assemble");
+  if (p->partial) return fail(p, CPRA_ERR_NOT_READY, "assembly needs every angle present");
+  const size_t N = p->N, NN = N * N;
+  cpra_status st = ensure_assembly(p);
+  if (st == CPRA_OK) st = upload_rho_rows(p);
+  if (st != CPRA_OK) return st;
   CK(timed(p, CPRA_KERNEL_ASSEMBLE, [&] {
        cudaError_t e = launch_prime(plan_launch(p, 0, p->Np));
        return e == cudaSuccess ? launch_assemble(p) : e;
      }), "assemble");
   p->asmb.ready = true;
   p->hp_valid = false;
-  if (out) return copy_out(p, out, a.vol, N * NN * 8);
+  p->merged = false;
+  if (out) return copy_out(p, out, p->asmb.vol, N * NN * 8);
+  return CPRA_OK;
+}
+
+cpra_status cpra_merge(const cpra_plan_t* guesses, int32_t n_r, int32_t n_l, int32_t twin_ref,
+                       cpra_plan_t p, int32_t* selected, int32_t* inverted, float* prtf) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "destination plan is NULL");
+  if (!guesses || n_r < 1) return fail(p, CPRA_ERR_INVALID_ARG, "no guesses");
+  if (n_l < 1 || n_l > n_r) return fail(p, CPRA_ERR_INVALID_ARG, "need 1 <= n_l <= n_r");
+  const int N = p->N, Np = p->Np;
+  if (twin_ref < 0 || twin_ref >= Np) return fail(p, CPRA_ERR_INVALID_ARG, "twin_ref outside [0, Np)");
+  if (p->partial) return fail(p, CPRA_ERR_NOT_READY, "the destination has absent angles");
+  for (int i = 0; i < n_r; ++i) {
+    const cpra_plan_s* g = guesses[i];
+    if (!g) return fail(p, CPRA_ERR_INVALID_ARG, "a guess is NULL");
+    if (g->N != N || g->Np != Np) return fail(p, CPRA_ERR_INVALID_ARG, "guesses differ in N or Np");
+    if (!g->state_ready || g->t < 1) return fail(p, CPRA_ERR_NOT_READY, "a guess has not iterated");
+    if (g->partial) return fail(p, CPRA_ERR_NOT_READY, "a guess has absent angles");
+  }
+  CK(cudaStreamSynchronize(p->stream), "merge sync");
+  // R15: episode error = mean over the POs of the last recorded Fourier error
+  std::vector<double> err(n_r), row(Np);
+  for (int i = 0; i < n_r; ++i) {
+    cpra_plan_s* g = guesses[i];
+    CK(cudaStreamSynchronize(g->stream), "merge sync");
+    CK(cudaMemcpy(row.data(), g->err_hist + (size_t)(g->t - 1) * Np, sizeof(double) * Np,
+                  cudaMemcpyDeviceToHost), "merge errors");
+    double s = 0.0;
+    for (double v : row) s += v;
+    err[i] = s / Np;
+  }
+  std::vector<int> order(n_r);
+  for (int i = 0; i < n_r; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return err[a] < err[b]; });
+  cpra_status st = ensure_assembly(p);
+  if (st != CPRA_OK) return st;
+  const size_t NN = (size_t)N * N;
+  if (!p->mg_acc) {
+    p->mg_acc = (float2*)dev_alloc(p, Np * NN * 8);
+    p->mg_ref = (float2*)dev_alloc(p, NN * 8);
+    p->mg_dist = (double*)dev_alloc(p, 2 * 8);
+    if (!p->mg_acc || !p->mg_ref || !p->mg_dist) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "merge scratch");
+  }
+  if (prtf && !p->mg_mag) {
+    p->mg_mag = (float*)dev_alloc(p, Np * NN * 4);
+    if (!p->mg_mag) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "merge scratch");
+  }
+  p->merged = false;
+  CK(cudaMemsetAsync(p->mg_acc, 0, Np * NN * 8, p->stream), "merge clear");
+  if (prtf) CK(cudaMemsetAsync(p->mg_mag, 0, Np * NN * 4, p->stream), "merge clear");
+  CK(cudaStreamSynchronize(p->stream), "merge sync");
+  std::vector<int32_t> flips(n_l, 0);
+  for (int k = 0; k < n_l; ++k) {
+    cpra_plan_s* g = guesses[order[k]];
+    cudaStream_t gs = g->stream;
+    st = upload_rho_rows(g);
+    if (st != CPRA_OK) return fail(p, st, std::string("guess: ") + g->err);
+    MergeArgs ma{};
+    ma.ref = p->mg_ref;
+    ma.n0 = twin_ref;
+    cudaError_t e = timed(g, CPRA_KERNEL_ASSEMBLE, [&] {
+      cudaError_t r = launch_prime(plan_launch(g, 0, Np));
+      if (r != cudaSuccess) return r;
+      if (k == 0) return launch_merge_guess(g, p->asmb.moments, kSpecRef, ma, 1, gs);
+      ma.dist = p->mg_dist;
+      r = cudaMemsetAsync(p->mg_dist, 0, 2 * sizeof(double), gs);
+      return r == cudaSuccess ? launch_merge_guess(g, p->asmb.moments, kSpecDist, ma, 1, gs) : r;
+    });
+    CK(e, "merge spectra");
+    g->hp_valid = false;
+    if (k > 0) {  // R16: the version nearer to the best episode's reference PO
+      double d[2];
+      CK(cudaMemcpyAsync(d, p->mg_dist, sizeof(d), cudaMemcpyDeviceToHost, gs), "merge distances");
+      CK(cudaStreamSynchronize(gs), "merge sync");
+      flips[k] = d[1] < d[0] ? 1 : 0;
+    }
+    ma = MergeArgs{};
+    ma.acc = p->mg_acc;
+    ma.mag = prtf ? p->mg_mag : nullptr;
+    ma.inv = flips[k];
+    CK(timed(g, CPRA_KERNEL_ASSEMBLE, [&] {
+         return launch_merge_guess(g, p->asmb.moments, kSpecAcc, ma, Np, gs);
+       }), "merge accumulate");
+    CK(cudaStreamSynchronize(gs), "merge sync");
+  }
+  float* prtf_dev = nullptr;
+  const bool prtf_host = prtf && !is_device_ptr(prtf);
+  if (prtf) {
+    if (prtf_host && !p->mg_prtf) {
+      p->mg_prtf = (float*)dev_alloc(p, sizeof(float) * Np * (N / 2));
+      if (!p->mg_prtf) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "merge scratch");
+    }
+    prtf_dev = prtf_host ? p->mg_prtf : prtf;
+  }
+  CK(timed(p, CPRA_KERNEL_ASSEMBLE, [&] {
+       return launch_merge_finish(p, p->mg_acc, p->mg_mag, prtf_dev, n_l);
+     }), "merge finish");
+  p->asmb.ready = true;
+  p->merged = true;
+  if (prtf_host) {
+    st = copy_out(p, prtf, prtf_dev, sizeof(float) * Np * (N / 2));
+    if (st != CPRA_OK) return st;
+  }
+  CK(cudaStreamSynchronize(p->stream), "merge sync");
+  for (int k = 0; k < n_l; ++k) {
+    if (selected) selected[k] = order[k];
+    if (inverted) inverted[k] = flips[k];
+  }
   return CPRA_OK;
 }
 
@@ -926,6 +1050,10 @@ cpra_status cpra_result(cpra_plan_t p, int32_t what, void* dst, size_t bytes) {
       if (need == 0) return CPRA_OK;
       return copy_out(p, dst, p->err_hist, need);
     }
+    case CPRA_RESULT_MERGED_SPECTRA:
+      if (!p->merged) return fail(p, CPRA_ERR_NOT_READY, "no merge into this plan yet");
+      if (bytes < Np * NN * 8) return fail(p, CPRA_ERR_INVALID_ARG, "dst too small");
+      return copy_out(p, dst, p->mg_acc, Np * NN * 8);
     case CPRA_RESULT_VOLUME:
       if (!p->asmb.vol || !p->asmb.ready) return fail(p, CPRA_ERR_NOT_READY, "no volume yet");
       if (bytes < N * NN * 8) return fail(p, CPRA_ERR_INVALID_ARG, "dst too small");
@@ -1103,7 +1231,7 @@ JobStep next_step(cpra_plan_s* p) {
   }
   s.g = p->g;
   s.err_slot = t;
-  s.algo = t < c.hio_iters ? kHIO : kER;
+  s.algo = t < c.hio_iters ? update_rule(c) : kER;
   s.forward = ((t + 1) % c.n_ei) != 0;
   s.active = 1;
   p->hp_valid = s.forward != 0;
@@ -1131,7 +1259,7 @@ JobStep next_window(cpra_plan_s* p, int64_t max_iters) {
   }
   s.g = p->g;
   s.err_slot = t;
-  s.algo = t < c.hio_iters ? kHIO : kER;
+  s.algo = t < c.hio_iters ? update_rule(c) : kER;
   s.active = 1;
   s.n_iters = (int)(tb - t);
   s.hio_left = (int)std::max<int64_t>(0, std::min<int64_t>(tb - t, (int64_t)c.hio_iters - t));

@@ -74,6 +74,13 @@ struct cpra_plan_s {
   int sw_ntaps = 0;
   float* po_tmp = nullptr;
   cpra::Assembly asmb;
+  // Step C merge scratch (cpra_merge with this plan as destination)
+  float2* mg_acc = nullptr;    // [Np][N][N] merged spectra (sums, then the mean)
+  float* mg_mag = nullptr;     // [Np][N][N] sums of |E| for the PRTF
+  float2* mg_ref = nullptr;    // [N][N] E of the reference PO of the best guess
+  double* mg_dist = nullptr;   // [2] twin distances
+  float* mg_prtf = nullptr;    // [Np][N/2] PRTF staging for host outputs
+  bool merged = false;         // mg_acc holds the mean of the last merge
   // kernel tables of this plan as a one-job launch
   cpra::JobStatic* d_js = nullptr;
   int2* d_tiles = nullptr;     // (0, angle) of every iterating angle, ascending
@@ -103,7 +110,22 @@ namespace cpra {
 // kernels launched by this library in this process (cpra_launch_count)
 extern std::atomic<long long> g_launches;
 
-enum Algo { kHIO = 0, kER = 1 };
+enum Algo { kHIO = 0, kER = 1, kRAAR = 2 };
+
+// Real-space step of one pixel from the old iterate g, g' = Re IFFT2(P_M G)
+// and its support bit.
+//   HIO  (Fienup):  g' on V = {in S, g' >= 0}, g - beta g' elsewhere
+//   ER:             g' on V, 0 elsewhere
+//   RAAR (Luke 2005, T = beta/2 (R_S R_M + I) + (1 - beta) P_M with the
+//        reflections R = 2P - I): R_M g = 2g' - g, so g' where 2g' - g lies
+//        in the support-positivity set, beta g + (1 - 2 beta) g' elsewhere;
+//        c2 = 1 - 2 beta.
+__device__ __forceinline__ float update_pixel(float g, float gp, bool in_s, int algo, float beta,
+                                              float c2) {
+  if (algo == kRAAR) return (in_s && fmaf(2.0f, gp, -g) >= 0.0f) ? gp : fmaf(beta, g, c2 * gp);
+  if (in_s && gp >= 0.0f) return gp;
+  return algo == kHIO ? fmaf(-beta, gp, g) : 0.0f;
+}
 
 // prepare / state kernels (k_prepare.cu)
 cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count);
@@ -154,7 +176,8 @@ struct JobStep {
   float* g;            // the iterate the row pass updates in place
   long long err_slot;  // error-history row, -1 = none
   int prime;           // run the prime kernel (coupling and/or row R2C)
-  int algo;            // kHIO / kER
+  int algo;            // kHIO / kRAAR / kER; fused engine: the rule of its
+                       // first hio_left iterations (ER after them)
   int forward;         // row pass also computes the next row spectra
   int active;          // 0: the column and row passes skip this job
   CoupleArgs ca;
@@ -182,6 +205,25 @@ cudaError_t launch_shrinkwrap(cpra_plan_s* p);
 
 // assembly (k_assemble.cu)
 cudaError_t launch_assemble(cpra_plan_s* p);
+
+// Step C merge (k_assemble.cu): modes of the spectra kernel
+enum SpecMode { kSpecF = 0, kSpecRef = 1, kSpecDist = 2, kSpecAcc = 3 };
+struct MergeArgs {
+  int n0;         // first angle of the launch
+  int inv;        // ACC: add conj(E), the spectrum of the centrally inverted PO
+  float2* ref;    // REF: E of one PO, [kz][ku] (written); DIST: read
+  float2* acc;    // ACC: [Np][kz][ku] += E or conj(E)
+  float* mag;     // ACC: [Np][kz][ku] += |E| (NULL = skip)
+  double* dist;   // DIST: [0] += sum |ref - E|^2, [1] += sum |ref - conj E|^2
+};
+// moments of guess g into `moments`, then the spectra kernel in `mode` over
+// angles ma.n0 .. ma.n0 + count - 1 (the R2C rows of rho are in g's Hp)
+cudaError_t launch_merge_guess(cpra_plan_s* g, double* moments, int mode, const MergeArgs& ma,
+                               int count, cudaStream_t st);
+// PRTF (prtf != NULL, needs mag), acc <- acc / n_l, its IDFT_z into dst's F,
+// gridding and the plane IFFTs into dst's volume, on dst's stream
+cudaError_t launch_merge_finish(cpra_plan_s* dst, float2* acc, const float* mag, float* prtf,
+                                int n_l);
 
 bool n_supported(int N);
 

@@ -4,7 +4,7 @@
 // every line transform is the two-level register FFT of fftw.cuh: one
 // warp-local transpose per transform instead of one block-wide shared-memory
 // round trip per radix pass, and no block barriers inside a transform.
-//   k_rowpass_w  Hp rows -> C2R -> HIO/ER update of g -> R2C -> Hp rows
+//   k_rowpass_w  Hp rows -> C2R -> HIO/RAAR/ER update of g -> R2C -> Hp rows
 //   k_prime_w    Eq. 4 coupling of g (optional) -> R2C -> Hp rows
 //   k_colpass_w  Hp column block -> FFT_y -> modulus projection onto A_sym
 //                with the FP64 Fourier error -> IFFT_y -> Hp column block
@@ -156,6 +156,7 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const float2* __restrict__ xtw = J->xtw;
   const int Np = J->Np, W = J->W;
   const float beta = J->beta;
+  const float c2 = 1.0f - 2.0f * beta;
   const int algo = Z->algo, forward = Z->forward;
   float2* xs = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -228,10 +229,10 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       const int x = FL::a_x(t, m);
       const float2 z = a[i][m];
       const float gp0 = z.x * inv, gp1 = z.y * inv;
-      const bool v0 = ((__ldg(s0 + (x >> 5)) >> (x & 31)) & 1u) && gp0 >= 0.0f;
-      const bool v1 = ((__ldg(s1 + (x >> 5)) >> (x & 31)) & 1u) && gp1 >= 0.0f;
-      const float n0 = v0 ? gp0 : (algo == kHIO ? fmaf(-beta, gp0, o0s[x]) : 0.0f);
-      const float n1 = v1 ? gp1 : (algo == kHIO ? fmaf(-beta, gp1, o1s[x]) : 0.0f);
+      const bool in0 = (__ldg(s0 + (x >> 5)) >> (x & 31)) & 1u;
+      const bool in1 = (__ldg(s1 + (x >> 5)) >> (x & 31)) & 1u;
+      const float n0 = update_pixel(o0s[x], gp0, in0, algo, beta, c2);
+      const float n1 = update_pixel(o1s[x], gp1, in1, algo, beta, c2);
       g0[x] = n0;
       g1[x] = n1;
       a[i][m] = make_float2(n0, n1);

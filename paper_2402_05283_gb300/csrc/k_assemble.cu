@@ -10,6 +10,12 @@
 //            their sum, FP64) are built on the host.  The sign makes the
 //            inverse transform land centred in x and y.
 //   c2c      inverse FFT along kx (rows) then ky (columns) of every z plane.
+// Step C merge of several guesses (cpra_merge) reuses the spectra kernel in
+// three more modes: REF stores the best guess's E of one PO, DIST sums the
+// squared distances of another guess's E to it as is and conjugated (the
+// spectrum of the centrally inverted PO), ACC adds E or conj(E) and |E| into
+// full-plane accumulators; k_merged_f then takes IDFT_z of the mean and
+// k_prtf the ring averages of |sum E'| / sum |E'|.
 // The inverse 3D DFT is applied as IDFT_z on each slice before gridding
 // (gridding acts on kx, ky only and its weights do not depend on kz), then
 // IDFT_xy on each z plane after gridding.
@@ -63,19 +69,20 @@ struct SpecTile {
   static constexpr int NT = clampi(B * N / 32, 64, 1024);
 };
 
-template <int N>
+template <int N, int MODE>
 __global__ void __launch_bounds__(SpecTile<N>::NT)
 k_spectra(const float2* __restrict__ Hp, const double* __restrict__ moments, float2* F,
-          const float2* __restrict__ tw, int com_align) {
+          const float2* __restrict__ tw, int com_align, MergeArgs ma) {
   using T = SpecTile<N>;
   constexpr int B = T::B, PI = T::PI, NT = T::NT, H = N / 2;
+  double d_plain = 0.0, d_twin = 0.0;  // DIST partial sums
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
   float2* G = tw_s + N;        // [ky][b], pitch B
   float2* E = G + N * B;       // [kz][b], pitch PI
   float2* rz = E + N * PI;     // exp(2 pi i kz c_z / N)
   float2* ru = rz + N;         // [2B]: +ku then -ku ramps
-  const int n = blockIdx.y;
+  const int n = ma.n0 + blockIdx.y;
   const int c0 = blockIdx.x * B;
   for (int i = threadIdx.x; i < N; i += NT) tw_s[i] = tw[i];
   const double m0 = moments[3 * n];
@@ -119,8 +126,27 @@ k_spectra(const float2* __restrict__ Hp, const double* __restrict__ moments, flo
         v = pass == 0 ? G[kz * B + b] : cconj(G[km * B + b]);  // G(kz, c) or G(kz, -c)
       }
       v = cmul(cmul(v, rz[kz]), ru[pass * B + b]);
-      E[kz * PI + b] = v;
+      if constexpr (MODE == kSpecF) {
+        E[kz * PI + b] = v;
+      } else {
+        const int ku = pass == 0 ? c : (c == 0 ? H : N - c);
+        if constexpr (MODE == kSpecRef) {
+          ma.ref[(size_t)kz * N + ku] = v;
+        } else if constexpr (MODE == kSpecDist) {
+          const float2 r = ma.ref[(size_t)kz * N + ku];
+          const double ax = (double)r.x - v.x, ay = (double)r.y - v.y;  // |ref - E|^2
+          const double bx = (double)r.x - v.x, by = (double)r.y + v.y;  // |ref - conj E|^2
+          d_plain += ax * ax + ay * ay;
+          d_twin += bx * bx + by * by;
+        } else {
+          const size_t o = ((size_t)n * N + kz) * N + ku;
+          const float2 a = ma.acc[o];
+          ma.acc[o] = make_float2(a.x + v.x, a.y + (ma.inv ? -v.y : v.y));
+          if (ma.mag) ma.mag[o] += sqrtf(fmaf(v.x, v.x, v.y * v.y));
+        }
+      }
     }
+    if constexpr (MODE != kSpecF) continue;
     __syncthreads();
     fft_lines<N, +1, B, PI, NT>(E, tw_s);
     for (int idx = threadIdx.x; idx < N * B; idx += NT) {
@@ -131,6 +157,80 @@ k_spectra(const float2* __restrict__ Hp, const double* __restrict__ moments, flo
     }
     __syncthreads();
   }
+  if constexpr (MODE == kSpecDist) {
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+      d_plain += __shfl_down_sync(0xffffffffu, d_plain, o);
+      d_twin += __shfl_down_sync(0xffffffffu, d_twin, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red[0][wid] = d_plain; red[1][wid] = d_twin; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, c = 0.0;
+      for (int i = 0; i < NT / 32; ++i) { a += red[0][i]; c += red[1][i]; }
+      atomicAdd(ma.dist + 0, a);
+      atomicAdd(ma.dist + 1, c);
+    }
+  }
+}
+
+// acc <- scale * acc (the mean of the merged spectra, in place) and
+// F[n][ku][z] = (1/N) IDFT_z of it (z stored fftshifted), B adjacent ku
+// columns a block: the merged spectra of Step C in the layout of the gather.
+template <int N>
+__global__ void __launch_bounds__(SpecTile<N>::NT)
+k_merged_f(float2* acc, float2* F, const float2* __restrict__ tw, float scale) {
+  using T = SpecTile<N>;
+  constexpr int B = T::B, PI = T::PI, NT = T::NT, H = N / 2;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* E = tw_s + N;  // [kz][b], pitch PI
+  const int n = blockIdx.y;
+  const int c0 = blockIdx.x * B;
+  for (int i = threadIdx.x; i < N; i += NT) tw_s[i] = tw[i];
+  float2* An = acc + (size_t)n * N * N;
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int kz = idx / B, b = idx - kz * B;
+    const float2 v = cscale(An[(size_t)kz * N + c0 + b], scale);
+    An[(size_t)kz * N + c0 + b] = v;  // the merged spectra, kept for the result
+    E[kz * PI + b] = v;
+  }
+  __syncthreads();
+  fft_lines<N, +1, B, PI, NT>(E, tw_s);
+  const float inv = 1.0f / N;
+  float2* Fn = F + (size_t)n * N * N;
+  for (int idx = threadIdx.x; idx < N * B; idx += NT) {
+    const int b = idx / N, z = idx - b * N;
+    Fn[(size_t)(c0 + b) * N + ((z + H) % N)] = cscale(E[z * PI + b], inv);
+  }
+}
+
+// PRTF of one PO a block: ring s = round(|k|) (signed k), s < N/2, mean of
+// |acc| / mag (0 where mag = 0); FP64 ring sums in shared memory.
+__global__ void k_prtf(const float2* __restrict__ acc, const float* __restrict__ mag, float* prtf,
+                       int N) {
+  extern __shared__ double rs[];  // [N/2] sums, then [N/2] counts
+  const int H = N / 2, n = blockIdx.x;
+  double* sum = rs;
+  double* cnt = rs + H;
+  for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) rs[i] = 0.0;
+  __syncthreads();
+  const size_t base = (size_t)n * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int kz = idx / N, ku = idx - kz * N;
+    const int sz = kz < H ? kz : kz - N, su = ku < H ? ku : ku - N;
+    const int ring = (int)rint(sqrt((double)(sz * sz + su * su)));
+    if (ring >= H) continue;
+    const float2 a = acc[base + idx];
+    const float m = mag[base + idx];
+    const double r = m > 0.0f ? (double)sqrtf(fmaf(a.x, a.x, a.y * a.y)) / (double)m : 0.0;
+    atomicAdd(sum + ring, r);
+    atomicAdd(cnt + ring, 1.0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < H; i += blockDim.x)
+    prtf[(size_t)n * H + i] = cnt[i] > 0.0 ? (float)(sum[i] / cnt[i]) : 0.0f;
 }
 
 // V[z][cell] for a chunk of 8 planes; one thread per cell.
@@ -212,29 +312,46 @@ __global__ void __launch_bounds__(ColTile<N>::NT) k_c2c_cols(float2* V, const fl
 }
 
 template <int N>
-static cudaError_t assemble_n(cpra_plan_s* p) {
-  cudaStream_t st = p->stream;
-  Assembly& a = p->asmb;
-  const int Np = p->Np;
-  cudaError_t e;
-  // moments of rho; the caller has put the R2C rows of rho into Hp
-  e = cudaMemsetAsync(a.moments, 0, sizeof(double) * 3 * Np, st);
+static size_t spectra_smem() {
+  using T = SpecTile<N>;
+  return sizeof(float2) * (N + N * T::B + N * T::PI + N + 2 * T::B);
+}
+
+template <int N, int MODE>
+static cudaError_t spectra_n(const float2* Hp, const double* moments, float2* F, const float2* tw,
+                             int com_align, const MergeArgs& ma, int count, cudaStream_t st) {
+  using T = SpecTile<N>;
+  const size_t smem = spectra_smem<N>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_spectra<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  g_launches += 1;
+  k_spectra<N, MODE><<<dim3((N / 2) / T::B, count), T::NT, smem, st>>>(Hp, moments, F, tw, com_align, ma);
+  return cudaGetLastError();
+}
+
+// moments of rho = P_{S+} g of every angle of p into `moments`
+static cudaError_t moments_of(cpra_plan_s* p, double* moments, cudaStream_t st) {
+  const int N = p->N, Np = p->Np;
+  cudaError_t e = cudaMemsetAsync(moments, 0, sizeof(double) * 3 * Np, st);
   if (e != cudaSuccess) return e;
   const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
-  g_launches += 5;  // moments, spectra, gather, rows, columns
-  k_moments<<<dim3(N, Np), threads, 0, st>>>(p->g, p->S, a.moments, N, p->W);
-  {
-    using T = SpecTile<N>;
-    const size_t smem = sizeof(float2) * (N + N * T::B + N * T::PI + N + 2 * T::B);
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(k_spectra<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_spectra<N><<<dim3((N / 2) / T::B, Np), T::NT, smem, st>>>(p->Hp, a.moments, a.F, p->tw,
-                                                               p->cfg.com_align);
-  }
+  g_launches += 1;
+  k_moments<<<dim3(N, Np), threads, 0, st>>>(p->g, p->S, moments, N, p->W);
+  return cudaGetLastError();
+}
+
+// gather into the grid, then the inverse FFT of every z plane
+template <int N>
+static cudaError_t grid_n(cpra_plan_s* p) {
+  cudaStream_t st = p->stream;
+  Assembly& a = p->asmb;
+  cudaError_t e;
+  g_launches += 3;  // gather, rows, columns
   k_gather<<<dim3((N * N + 255) / 256, N / 8), 256, 0, st>>>(a.F, a.cell_ptr, a.ent_idx, a.ent_w,
                                                             a.vol, N);
   {
@@ -262,10 +379,78 @@ static cudaError_t assemble_n(cpra_plan_s* p) {
   return cudaGetLastError();
 }
 
+template <int N>
+static cudaError_t assemble_n(cpra_plan_s* p) {
+  // the caller has put the R2C rows of rho into Hp
+  cudaError_t e = moments_of(p, p->asmb.moments, p->stream);
+  if (e == cudaSuccess)
+    e = spectra_n<N, kSpecF>(p->Hp, p->asmb.moments, p->asmb.F, p->tw, p->cfg.com_align, MergeArgs{},
+                             p->Np, p->stream);
+  return e == cudaSuccess ? grid_n<N>(p) : e;
+}
+
 cudaError_t launch_assemble(cpra_plan_s* p) {
 #define CPRA_CASE(NN) \
   case NN: return assemble_n<NN>(p);
   switch (p->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+#undef CPRA_CASE
+}
+
+// ------------------------------------------------------------ Step C merge
+template <int N>
+static cudaError_t merge_guess_n(cpra_plan_s* g, double* moments, int mode, const MergeArgs& ma,
+                                 int count, cudaStream_t st) {
+  cudaError_t e = moments_of(g, moments, st);
+  if (e != cudaSuccess) return e;
+  switch (mode) {
+    case kSpecRef: return spectra_n<N, kSpecRef>(g->Hp, moments, nullptr, g->tw, g->cfg.com_align, ma, count, st);
+    case kSpecDist: return spectra_n<N, kSpecDist>(g->Hp, moments, nullptr, g->tw, g->cfg.com_align, ma, count, st);
+    case kSpecAcc: return spectra_n<N, kSpecAcc>(g->Hp, moments, nullptr, g->tw, g->cfg.com_align, ma, count, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_merge_guess(cpra_plan_s* g, double* moments, int mode, const MergeArgs& ma,
+                               int count, cudaStream_t st) {
+#define CPRA_CASE(NN) \
+  case NN: return merge_guess_n<NN>(g, moments, mode, ma, count, st);
+  switch (g->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
+#undef CPRA_CASE
+}
+
+// PRTF from the sums (before they become the mean), the mean spectra and
+// their IDFT_z, then gridding and the inverse FFT of the planes
+template <int N>
+static cudaError_t merge_finish_n(cpra_plan_s* d, float2* acc, const float* mag, float* prtf,
+                                  int n_l) {
+  using T = SpecTile<N>;
+  cudaStream_t st = d->stream;
+  cudaError_t e;
+  if (prtf) {
+    g_launches += 1;
+    k_prtf<<<d->Np, 256, sizeof(double) * N, st>>>(acc, mag, prtf, N);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const size_t smem = sizeof(float2) * (N + N * T::PI);
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_merged_f<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  g_launches += 1;
+  k_merged_f<N><<<dim3(N / T::B, d->Np), T::NT, smem, st>>>(acc, d->asmb.F, d->tw, 1.0f / (float)n_l);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return grid_n<N>(d);
+}
+
+cudaError_t launch_merge_finish(cpra_plan_s* dst, float2* acc, const float* mag, float* prtf,
+                                int n_l) {
+#define CPRA_CASE(NN) \
+  case NN: return merge_finish_n<NN>(dst, acc, mag, prtf, n_l);
+  switch (dst->N) { CPRA_FOR_EACH_N(CPRA_CASE) default: return cudaErrorInvalidValue; }
 #undef CPRA_CASE
 }
 

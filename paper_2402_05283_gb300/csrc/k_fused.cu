@@ -4,7 +4,7 @@
 // prime (Eq. 4 coupling, or a plain read of g, then the row R2C) and
 // n_iters iterations of
 //   column FFT -> modulus projection onto A_sym (FP64 Fourier error) ->
-//   column IFFT -> row C2R -> HIO / ER update -> row R2C,
+//   column IFFT -> row C2R -> HIO / RAAR / ER update -> row R2C,
 // with the packed half spectrum (N x N/2 complex, column 0 holding
 // (Re H(y,0), Re H(y,N/2)) as in the two-pass engine) never leaving the
 // cluster's distributed shared memory.  CTA r keeps packed columns
@@ -16,8 +16,8 @@
 //                 again and scattered back to the same slab places.
 // Two cluster barriers per iteration separate the phases; loads that do not
 // depend on other CTAs (A_sym, the old iterate) are issued between the
-// arrive and the wait.  Global memory per angle-iteration: g read (HIO
-// needs the old iterate) and written, A_sym read; within one launch these
+// arrive and the wait.  Global memory per angle-iteration: g read (HIO and
+// RAAR need the old iterate) and written, A_sym read; within one launch these
 // stay in L2, and the support bits are read once per launch into registers.
 // Up to N = 256 the line transforms are the warp-resident FFTs of fftw.cuh
 // with the same task-to-lane maps as the two-pass warp engine (bit-identical
@@ -219,6 +219,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const uint32_t sb = smem_u32(slab);
   const int Np = J->Np, W = J->W;
   const float beta = J->beta;
+  const float c2 = 1.0f - 2.0f * beta;
   const float* __restrict__ A_T = J->A_main;
   float* g = Z->g;
   const CoupleArgs& ca = Z->ca;
@@ -263,7 +264,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       });
     });
   };
-  // the old iterate of row task q (A layout): HIO's g - beta g' outside V
+  // the old iterate of row task q (A layout), read by the HIO and RAAR rules
   auto load_old = [&](int q, float2 (&old)[FL::TA][FL::E1]) {
     const int pair0 = rank * F::CW + (warp + q * F::NW) * FL::L;
     static_for<0, FL::TA>([&](auto II) {
@@ -346,9 +347,9 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       });
     });
   };
-  // HIO / ER update of row task q from g' = a / N; a <- the new iterate
+  // HIO / RAAR / ER update of row task q from g' = a / N; a <- the new iterate
   auto update = [&](int q, float2 (&a)[FL::TA][FL::E1], const float2 (&old)[FL::TA][FL::E1],
-                    bool hio) {
+                    int rule) {
     const int pair0 = rank * F::CW + (warp + q * F::NW) * FL::L;
     uint32_t mq[F::MASKW];
     static_for<0, F::MASKW>([&](auto WW) {
@@ -365,10 +366,10 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
         const int x = FL::a_x(t, m);
         const float2 z = a[i][m];
         const float gp0 = z.x * inv, gp1 = z.y * inv;
-        const bool v0 = ((mq[bit >> 5] >> (bit & 31)) & 1u) && gp0 >= 0.0f;
-        const bool v1 = ((mq[bit >> 5] >> ((bit + 1) & 31)) & 1u) && gp1 >= 0.0f;
-        const float n0 = v0 ? gp0 : (hio ? fmaf(-beta, gp0, old[i][m].x) : 0.0f);
-        const float n1 = v1 ? gp1 : (hio ? fmaf(-beta, gp1, old[i][m].y) : 0.0f);
+        const bool s0 = (mq[bit >> 5] >> (bit & 31)) & 1u;
+        const bool s1 = (mq[bit >> 5] >> ((bit + 1) & 31)) & 1u;
+        const float n0 = update_pixel(old[i][m].x, gp0, s0, rule, beta, c2);
+        const float n1 = update_pixel(old[i][m].y, gp1, s1, rule, beta, c2);
         g0[x] = n0;
         g0[N + x] = n1;
         a[i][m] = make_float2(n0, n1);
@@ -380,7 +381,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   float2 old[FL::TA][FL::E1];
   load_av(0, av);
   for (int it = 0; it < n_iters; ++it) {
-    const bool hio = it < hio_left;
+    const int rule = it < hio_left ? Z->algo : kER;  // HIO or RAAR, then ER
     const bool fwd = it + 1 < n_iters;
     double errd = 0.0;
 #pragma unroll 1
@@ -393,17 +394,17 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     for (int o = 16; o > 0; o >>= 1) errd += __shfl_down_sync(0xffffffffu, errd, o);
     if (lane == 0) red[warp] = errd;
     cluster_arrive();
-    if (hio) load_old(0, old);  // in flight across the barrier
+    if (rule != kER) load_old(0, old);  // in flight across the barrier
     cluster_wait();
 #pragma unroll 1
     for (int q = 0; q < 2; ++q) {
       const int pq = rank * F::CW + (warp + q * F::NW) * FL::L;
-      if (hio && q) load_old(q, old);
+      if (rule != kER && q) load_old(q, old);
       float2 b[FL::TB][FL::E2];
       float2 a[FL::TA][FL::E1];
       gather_pairs<N, FL>(b, sb, pq, lane);
       FL::inv(b, a, T, xs, lane);
-      update(q, a, old, hio);
+      update(q, a, old, rule);
       if (fwd) {
         FL::fwd(a, b, T, xs, lane);
         scatter_pairs<N, FL>(b, T, sb, pq, lane);

@@ -3,7 +3,7 @@
 // One conventional 2D iteration (Step B inner loop) of every angle:
 //   column pass  Hp -> FFT_y -> modulus projection onto A_sym + Fourier error
 //                -> IFFT_y -> Hp                                   (k_colpass)
-//   row pass     Hp -> C2R rows -> HIO/ER support+positivity update of g
+//   row pass     Hp -> C2R rows -> HIO/RAAR/ER support+positivity update of g
 //                -> R2C rows of the new g -> Hp                    (k_rowpass)
 // Two real rows travel as one complex line (z = row0 + i row1); the half
 // spectrum is packed so every array has N x N/2 complex entries (column 0
@@ -209,6 +209,7 @@ k_rowpass(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const float2* __restrict__ tw = J->tw;
   const int Np = J->Np, W = J->W;
   const float beta = J->beta;
+  const float c2 = 1.0f - 2.0f * beta;
   const int algo = Z->algo, forward = Z->forward;
   float2* tw_s = smem;
   float2* buf = smem + N;
@@ -248,9 +249,8 @@ k_rowpass(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       const int y = y0 + 2 * p + s;
       const size_t gi = ((size_t)n * N + y) * N + x;
       const float gp = (s ? z.y : z.x) * inv;
-      const bool valid = sbit(S, ((size_t)n * N + y) * W, x) && gp >= 0.0f;
-      const float gold = g[gi];
-      const float gn = valid ? gp : (algo == kHIO ? fmaf(-beta, gp, gold) : 0.0f);
+      const bool ins = sbit(S, ((size_t)n * N + y) * W, x);
+      const float gn = update_pixel(g[gi], gp, ins, algo, beta, c2);
       g[gi] = gn;
       out[s] = gn;
     }

@@ -46,6 +46,17 @@ def test_default_config_values(cp):
     assert list(cfg.alpha[:3]) == [0.2, 0.6, 0.2]
     assert abs(cfg.beta - 0.9) < 1e-7 and abs(cfg.sw_tau - 0.1) < 1e-7
     assert cfg.hio_iters == 200 and cfg.er_iters == 20 and cfg.com_align == 1
+    assert cfg.update == cp.UPDATE_HIO and cfg.seed == 0
+
+
+def test_config_layout_matches_c(cp):
+    """The ctypes mirror of cpra_config has the C layout: a field past the
+    padding before seed round-trips through the library's validation."""
+    cfg = cp.make_config(64, 8, update=cp.UPDATE_RAAR, seed=(1 << 63) + 5)
+    cp.cpra_plan_bytes(cfg)  # RAAR is valid
+    cfg.update = 5
+    with pytest.raises(cp.CpraError, match="update"):
+        cp.cpra_plan_bytes(cfg)
 
 
 def test_plan_bytes_scales(cp):
@@ -63,6 +74,7 @@ def test_plan_bytes_scales(cp):
     (dict(alpha=(1.0 / 17,) * 17), 1),
     (dict(wrap_mode=7), 1), (dict(blend_target=3), 1), (dict(hio_iters=-1), 1),
     (dict(shrinkwrap_every=5, sw_sigma=0.0), 1), (dict(precision=9), 1),
+    (dict(update=2), 1), (dict(update=-1), 1),
 ])
 def test_config_validation(cp, kw, status):
     N = kw.pop("N", 64)

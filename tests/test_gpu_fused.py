@@ -50,13 +50,14 @@ def _rel(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
 
 
-@pytest.mark.parametrize("N", [64, 128, 256])
-def test_fused_equals_warp_engine(cp, N):
-    """HIO with coupling every 4, the HIO -> ER switch inside a window, and a
-    mid-episode split of the iterate calls (the fused engine re-primes)."""
+@pytest.mark.parametrize("N,update", [(64, 0), (128, 0), (256, 0), (64, 1), (256, 1)])
+def test_fused_equals_warp_engine(cp, N, update):
+    """HIO (update 0) or RAAR (update 1) with coupling every 4, the switch to
+    ER inside a window, and a mid-episode split of the iterate calls (the
+    fused engine re-primes)."""
     Np = 3
     d = synth.make_case("tiny", N=N, Np=Np)
-    kw = dict(n_ei=4, seed=11, hio_iters=6, er_iters=5)
+    kw = dict(n_ei=4, seed=11, hio_iters=6, er_iters=5, update=update)
     gw, ew, _ = _run(cp, cp.make_config(N, Np, engine=cp.ENGINE_WARP, **kw), d, d["support"], [11])
     for chunks in ([11], [3, 5, 3]):
         gf, ef, _ = _run(cp, cp.make_config(N, Np, engine=cp.ENGINE_FUSED, **kw), d, d["support"], chunks)
