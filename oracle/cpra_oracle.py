@@ -19,7 +19,10 @@ diffraction imaging"):
               Delta r_n = -int O'_n r dv, twin (central inversion) choice by
               Euclidean distance to the best episode, average -> E_n; the
               PRTF of the merged guesses (results section, its ref. 23).
-  * Step D    interpolation of the spectra E_n into the 3D E(q); inverse 3D FT.
+  * Step D    interpolation of the spectra E_n into the 3D E(q); inverse 3D FT;
+              the tomographic 3D iteration on E(q) with a 3D support from the
+              back-projected 2D supports, shrunk every few iterations (results
+              section: 50 iterations, shrink every 5, GENFIRE its ref. 33).
   * HIO (Fienup, the paper's ref. 22) and ER updates; shrink-wrap (ref. 36)
     with the paper's 0.1 relative threshold.
   * RAAR (Luke, the paper's ref. 39), the update the paper runs with
@@ -76,6 +79,18 @@ design notes):
       kept episodes (equivalently the mean of their spectra).
   R18 PRTF per PO: |sum_g E'_g| / sum_g |E'_g| over the kept, corrected
       episodes, averaged on rings s = round(|k|), s < N/2.
+  R19 Step D's data: the gridded spectrum V of R11 on the cells the scatter
+      reaches (summed weight >= 1e-12, every kz); elsewhere the iteration
+      leaves the spectrum free.
+  R20 3D support from the 2D supports ("projected back to 3D"): a voxel is
+      inside iff its projection lands inside the 2D support at every angle
+      (nearest pixel in u, exact z).
+  R21 The refinement (GENFIRE-like, the paper gives only "like conventional
+      3D CXDI but using E(q)", 50 iterations, shrink every 5): alternating
+      projections, P_{S3+} in real space and the replacement of the measured
+      cells by V in Fourier space; it starts from the real part of the Step D
+      volume (the phases of E(q) make one start enough); shrink-wrap as R9 in
+      3D; the result is P_{S3+} of the last iterate.
 """
 from __future__ import annotations
 
@@ -97,7 +112,8 @@ __all__ = [
     "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d",
     "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
     "r_factor", "raar_update", "episode_error", "select_best", "centrally_inverted", "prtf",
-    "merge_episodes", "assemble_spectra",
+    "merge_episodes", "assemble_spectra", "measured_cells", "backprojected_support", "blur3",
+    "refine_3d",
 ]
 
 
@@ -482,6 +498,82 @@ def merge_episodes(gs, Ss, final_errors, n_l, twin_ref=0, com_align=True):
 def assemble_spectra(E, thetas):
     """Step D from given spectra E[Np][N][N] (e.g. the merged episode)."""
     return volume(grid_3d(E, thetas))
+
+
+# --------------------------------------------------------------------------
+# Step D refinement: the tomographic 3D iteration (R19-R21)
+# --------------------------------------------------------------------------
+def measured_cells(N: int, thetas, wmin: float = 1e-12) -> np.ndarray:
+    """R19: the (ky, kx) cells the bilinear scatter of R11 reaches with summed
+    weight >= wmin; the same for every kz (the slices span all of kz)."""
+    k = signed_freq(N)
+    wsum = np.zeros((N, N))
+    for th in thetas:
+        px = k * math.cos(th)
+        py = k * math.sin(th)
+        i0 = np.floor(px)
+        j0 = np.floor(py)
+        fx = px - i0
+        fy = py - j0
+        for di in (0, 1):
+            for dj in (0, 1):
+                w = (fx if di else 1 - fx) * (fy if dj else 1 - fy)
+                np.add.at(wsum, ((j0.astype(np.int64) + dj) % N, (i0.astype(np.int64) + di) % N), w)
+    return wsum >= wmin
+
+
+def backprojected_support(S2: np.ndarray, thetas) -> np.ndarray:
+    """R20: voxel (z, y, x) is in the 3D support iff at every angle its
+    projection coordinate u = rint((x - c) cos theta + (y - c) sin theta + c),
+    c = N/2 (the geometry of R16), lies in [0, N) with S2[n][z][u] set."""
+    Np, N, _ = S2.shape
+    c = N // 2
+    y, x = np.meshgrid(np.arange(N) - c, np.arange(N) - c, indexing="ij")
+    out = np.ones((N, N, N), dtype=bool)
+    for n in range(Np):
+        u = np.rint(x * math.cos(thetas[n]) + y * math.sin(thetas[n]) + c).astype(np.int64)
+        inside = (u >= 0) & (u < N)
+        uc = np.clip(u, 0, N - 1)
+        hit = S2[n].astype(bool)[:, uc] & inside[None, :, :]  # [z][y][x]
+        out &= hit
+    return out
+
+
+def blur3(rho: np.ndarray, sigma: float) -> np.ndarray:
+    """Circular convolution with the wrapped Gaussian of R9 along every axis."""
+    N = rho.shape[-1]
+    w = wrapped_gaussian(N, sigma)
+    W = w[(np.arange(N)[:, None] - np.arange(N)[None, :]) % N]
+    for ax in range(3):
+        rho = _along(W, rho, ax)
+    return rho
+
+
+def refine_3d(V, M, S3, rho0, n_iters, shrink_every=0, sigma=2.0, tau=0.1):
+    """Step D's tomographic iteration on the assembled spectrum (R21).
+
+    V: the gridded spectrum [kz][ky][kx] (R11, FFT order); M: measured cells
+    [ky][kx] (R19); S3: 3D support (R20); rho0: the start (real, FFT-order
+    volume).  Each iteration: rho_S = P_{S3+} rho; X = DFT3(rho_S); error
+    sqrt(sum_M |X - V|^2 / sum_M |V|^2); X <- V on the measured cells;
+    rho = Re IDFT3(X); every shrink_every iterations the 3D support shrinks
+    to {blur(P_{S3+} rho) >= tau max} (R9 in 3D).
+    Returns (P_{S3+} rho, S3, errors)."""
+    M3 = np.broadcast_to(np.asarray(M, bool)[None], V.shape)
+    S3 = np.asarray(S3, bool)
+    den = (np.abs(V[M3]) ** 2).sum()
+    rho = np.asarray(rho0, dtype=np.float64)
+    errs = []
+    for t in range(n_iters):
+        X = dft3(np.where(S3 & (rho >= 0), rho, 0.0))
+        errs.append(math.sqrt((np.abs(X - V)[M3] ** 2).sum() / den) if den > 0 else 0.0)
+        rho = idft3(np.where(M3, V, X)).real
+        if shrink_every > 0 and (t + 1) % shrink_every == 0:
+            b = blur3(np.where(S3 & (rho >= 0), rho, 0.0), sigma)
+            mx = b.max()
+            if mx > 0:
+                S3 = b >= tau * mx
+    return np.where(S3 & (rho >= 0), rho, 0.0), S3, errs
 
 
 # --------------------------------------------------------------------------

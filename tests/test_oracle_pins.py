@@ -530,6 +530,125 @@ def test_prtf_hand_cases():
     assert np.allclose(pr[0], [0.0, 0.125])
 
 
+# ---------------------------------------------------------------- Step D refinement (R19-R21)
+def _box3(N, lo, hi):
+    S = np.zeros((N, N, N), bool)
+    S[lo:hi, lo:hi, lo:hi] = True
+    return S
+
+
+def test_refine_full_data_reaches_the_object_in_one_step():
+    """With every cell measured the Fourier replacement is the whole
+    spectrum: one iteration returns Re IDFT3(V), here the object itself, and
+    the next error is 0 (V from numpy's FFT, a library routine)."""
+    N = 12
+    S3 = _box3(N, 3, 9)
+    obj = np.where(S3, rng.random((N, N, N)), 0.0)
+    V = np.fft.fftn(obj)
+    M = np.ones((N, N), bool)
+    out, _, errs = O.refine_3d(V, M, S3, rng.standard_normal((N, N, N)), 2)
+    assert np.allclose(out, obj, atol=1e-12)
+    assert errs[0] > 0.1 and errs[1] < 1e-12
+
+
+def test_refine_without_data_is_the_support_projection():
+    N = 10
+    S3 = _box3(N, 2, 7)
+    rho0 = rng.standard_normal((N, N, N))
+    out, _, _ = O.refine_3d(np.zeros((N, N, N), complex), np.zeros((N, N), bool), S3, rho0, 3)
+    assert np.allclose(out, np.where(S3 & (rho0 >= 0), rho0, 0.0), atol=1e-12)
+
+
+def test_refine_error_never_increases():
+    """Alternating projections between the support-positivity cone and the
+    affine set of spectra equal to V on the measured cells: the gap between
+    P_S rho_t and its Fourier replacement cannot grow (each projection is the
+    nearest point of its set), whatever the data."""
+    N = 12
+    th = np.arange(5) * math.pi / 5
+    M = O.measured_cells(N, th)
+    assert 0 < M.sum() < N * N
+    S3 = _box3(N, 2, 10)
+    V = np.fft.fftn(np.abs(rng.standard_normal((N, N, N)))) * (1 + 0.3 * rng.standard_normal((N, N, N)))
+    _, _, errs = O.refine_3d(V, M, S3, rng.random((N, N, N)), 15)
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < errs[0]
+
+
+def test_refine_dc_column_closed_form():
+    """Only the (ky, kx) = (0, 0) cells measured: replacing them fixes the sum
+    of every z plane, i.e. adds (target plane sum - current plane sum) / N^2
+    to each voxel of the plane.  One iteration from rho0 must give
+    P_{S3+}(P_{S3+} rho0 + that shift), and its error is the relative L2 gap
+    of the plane sums (Parseval along z).  Checks the positivity inside the
+    iteration, the real part and the error definition by plain sums."""
+    N = 8
+    S3 = _box3(N, 2, 6)
+    obj = np.where(S3, rng.random((N, N, N)), 0.0)
+    V = np.fft.fftn(obj)
+    M = np.zeros((N, N), bool)
+    M[0, 0] = True
+    rho0 = rng.standard_normal((N, N, N))
+    p0 = np.where(S3 & (rho0 >= 0), rho0, 0.0)
+    t = obj.sum(axis=(1, 2))
+    c = p0.sum(axis=(1, 2))
+    rho1 = p0 + ((t - c) / N ** 2)[:, None, None]
+    out, _, errs = O.refine_3d(V, M, S3, rho0, 1)
+    assert np.allclose(out, np.where(S3 & (rho1 >= 0), rho1, 0.0), atol=1e-12)
+    assert errs[0] == pytest.approx(np.linalg.norm(c - t) / np.linalg.norm(t), rel=1e-10)
+
+
+def test_refine_shrinkwrap_point_source_ball():
+    """No data, one bright voxel: the 3D shrink-wrap keeps the ball where
+    exp(-r^2 / 2 sigma^2) >= tau (the 3D form of the 2D closed form)."""
+    N, sg, tau = 24, 1.5, 0.1
+    rho0 = np.zeros((N, N, N)); rho0[12, 12, 12] = 1.0
+    _, S3, _ = O.refine_3d(np.zeros((N, N, N), complex), np.zeros((N, N), bool),
+                           np.ones((N, N, N), bool), rho0, 1, shrink_every=1, sigma=sg, tau=tau)
+    z, y, x = np.meshgrid(*(np.arange(N) - 12,) * 3, indexing="ij")
+    assert np.array_equal(S3, x * x + y * y + z * z <= 2 * sg * sg * math.log(1 / tau))
+
+
+def test_measured_cells_axis_aligned():
+    N = 8
+    M0 = O.measured_cells(N, [0.0])
+    assert M0[0].all() and not M0[1:].any()          # theta = 0: the ky = 0 row
+    M1 = O.measured_cells(N, [math.pi / 2])
+    assert M1[:, 0].all() and not M1[:, 1:].any()    # theta = 90 deg: the kx = 0 column
+
+
+def test_backprojected_support_axis_aligned():
+    N = 8
+    S2 = rng.random((2, N, N)) > 0.4
+    only0 = O.backprojected_support(S2[:1], [0.0])
+    assert np.array_equal(only0, np.broadcast_to(S2[0][:, None, :], (N, N, N)))
+    both = O.backprojected_support(S2, [0.0, math.pi / 2])
+    assert np.array_equal(both, S2[0][:, None, :] & S2[1][:, :, None])
+
+
+def test_backprojected_support_contains_the_object():
+    """The supports of the object's projections, projected back, contain the
+    object's own support (every voxel of it projects inside at every angle)."""
+    import synth
+    N, Np = 32, 12
+    vol = synth.pad_volume(synth.ellipsoid_phantom(16, 3, 33), N)
+    th = synth.angles(Np)
+    P = synth.project(vol, th, r_max=8).numpy()
+    S3 = O.backprojected_support(P > 1e-9, th)
+    inside = vol > 0
+    assert np.all(S3[inside])
+    assert S3.sum() < 0.2 * N ** 3  # and it is tight
+
+
+def test_blur3_constant_and_separable():
+    N = 8
+    c = np.full((N, N, N), 2.5)
+    assert np.allclose(O.blur3(c, 1.5), 2.5)
+    d = np.zeros((N, N, N)); d[0, 0, 0] = 1.0
+    w = O.wrapped_gaussian(N, 1.5)
+    assert np.allclose(O.blur3(d, 1.5), w[:, None, None] * w[None, :, None] * w[None, None, :])
+
+
 # ---------------------------------------------------------------- schedule
 def test_schedule_coupling_and_switch():
     """The run applies Eq. 4 at episode starts and switches HIO -> ER at hio_iters."""
