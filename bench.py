@@ -115,6 +115,14 @@ def make_inputs(device, n_angles=NP):
     return synth.make_case("metric", device=device, Np=n_angles)
 
 
+# DRAM bytes (read + write) per angle of one launch, from the ncu capture in
+# profiles/k_rowpass_w_k_colpass_w_n512_np180.md (180 angles a launch; every
+# angle moves the same bytes, so a launch's traffic scales with its angles).
+# Valid only while the kernel is the one captured there.
+NCU_TRAFFIC_PER_ANGLE = {("k_rowpass", 512): (383.465472e6 + 316.068352e6) / 180,
+                         ("k_colpass", 512): (283.662848e6 + 135.292672e6) / 180}
+
+
 def roofline_figures(plan, cp, peaks, Np_total, angle_iters):
     """Dominant kernel's algorithmic bytes / its mean CUDA-event duration."""
     stats = {k: plan.kernel_stats(k) for k in range(cp.KERNEL_KINDS)}
@@ -142,7 +150,11 @@ def roofline_figures(plan, cp, peaks, Np_total, angle_iters):
     peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "kernel": names[kind], "achieved": round(achieved, 1),
             "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": None, "bytes_per_launch": int(bytes_launch),
+            "traffic": (round(NCU_TRAFFIC_PER_ANGLE[(names[kind], N)] * units)
+                        if (names[kind], N) in NCU_TRAFFIC_PER_ANGLE and kind != cp.KERNEL_FUSED else None),
+            "traffic_source": "ncu capture at Np=180 scaled to the launch's angles "
+                              "(profiles/k_rowpass_w_k_colpass_w_n512_np180.md)",
+            "bytes_per_launch": int(bytes_launch),
             "mean_launch_ms": round(ms / launches, 4),
             "share_of_kernel_time": round(ms / total, 3),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}, stats
@@ -247,6 +259,86 @@ def form_batch(cp, torch, seed=3):
             "batched_graph": {"value": round(work / t_batch, 1), "seconds": round(t_batch, 3)},
             "speedup": round(t_alone / t_batch, 3), "tuned_engines": tuned,
             "bit_identical": bool(same), "compared": len(pairs)}
+
+
+def form_multi_guess(cp, torch, N_=256, Np_=144, n_r=32, n_l=8, iters=220, seed=6):
+    """Step C: n_r reconstructions of one pattern set from n_r random starts
+    (RAAR beta 0.9 then ER, the paper's rule for its cell data), iterated as
+    one batch, then merged (the n_l of lowest error kept, mass centres moved,
+    twins chosen, averaged) and assembled; the PRTF of the kept guesses.
+    N = 256 with Np = 144 is one of the paper's performance sizes."""
+    import synth
+    d = synth.make_case("cfg1", device="cuda", N=N_, Np=Np_, request=seed)
+    I, th = d["I"].contiguous(), d["thetas"]
+    hio = iters - 20
+    plans = []
+    for i in range(n_r):
+        p = cp.Plan(cp.make_config(N_, Np_, seed=100 + i, hio_iters=hio, er_iters=20,
+                                   update=cp.UPDATE_RAAR))
+        p.load_intensities(I, 0, th)
+        plans.append(p)
+    dst = cp.Plan(cp.make_config(N_, Np_))
+    dst.load_intensities(I, 0, th)
+    b = cp.Batch(plans, use_graph=True)
+    b.iterate(10)  # capture
+    prtf = torch.zeros((Np_, N_ // 2), device="cuda")
+    cp.cpra_merge(plans[:2], 1, 0, dst, prtf)  # first use: scratch and gridding lists
+    for p in plans:
+        p.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters // 10):
+        b.iterate(10)
+    torch.cuda.synchronize()
+    t_iter = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sel, inv = cp.cpra_merge(plans, n_l, 0, dst, prtf)
+    torch.cuda.synchronize()
+    t_merge = time.perf_counter() - t0
+    ring = prtf.mean(0).cpu().numpy()
+    below = np.nonzero(ring < 0.5)[0]
+    errs = [float(p.result(cp.RESULT_ERRORS)[-1].mean()) for p in plans]
+    b.close()
+    for p in plans + [dst]:
+        p.close()
+    work = n_r * Np_ * iters
+    return {"workload": f"N={N_}, Np={Np_}: {n_r} random starts x ({hio} RAAR + 20 ER), "
+                        f"batched with a CUDA graph; merge of the best {n_l}",
+            "angle_iterations": work, "value": round(work / t_iter, 1), "unit": "angle-iterations/s",
+            "iterate_s": round(t_iter, 3), "merge_and_assemble_ms": round(t_merge * 1e3, 2),
+            "selected": sel, "inverted": [int(v) for v in inv],
+            "final_fourier_error_best_worst": [round(min(errs), 5), round(max(errs), 5)],
+            "prtf_mean_ring_0_to_8": [round(float(v), 4) for v in ring[:8]],
+            "prtf_first_ring_below_0.5": int(below[0]) if below.size else None}
+
+
+def form_refine(cp, torch, plan, iters=50, shrink_every=5):
+    """Step D refinement on the bench plan's assembled N = 512 volume: the
+    paper's 50 tomographic iterations with the 3D support shrunk every 5.
+    Bytes of the five-pass design per iteration: x rows read rho and write
+    the spectrum, y and z lines read and write it twice, the z pass reads
+    the data on the measured cells, x rows read it and write rho:
+    (4 + 1/8 + 8 + 16 + 16 + 8 f + 16 + 12) N^3, f = measured fraction."""
+    Nn = plan.N
+    plan.assemble_3d()
+    plan.refine_3d(2)  # allocation and set-up outside the timed region
+    plan.assemble_3d()
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    t0 = time.perf_counter()
+    errs = plan.refine_3d(iters, shrink_every=shrink_every, sigma=2.0, tau=0.1)
+    wall = time.perf_counter() - t0
+    ms, launches = plan.kernel_stats(cp.KERNEL_REFINE)
+    plan.set_profiling(False)
+    n3 = float(Nn) ** 3
+    per_iter = (4 + 1 / 8 + 8 + 16 + 16 + 16 + 12) * n3
+    return {"workload": f"N={Nn}^3 refinement of the bench reconstruction, {iters} iterations, "
+                        f"3D shrink-wrap every {shrink_every} (sigma 2, tau 0.1)",
+            "device_ms": round(ms, 2), "ms_per_iteration": round(ms / iters, 3),
+            "wall_s": round(wall, 3), "launches": launches,
+            "design_bytes_per_iteration_excl_data": int(per_iter),
+            "achieved_gbs_excl_data": round(per_iter * iters / (ms * 1e-3) / 1e9, 1),
+            "error_first_last": [round(float(errs[0]), 5), round(float(errs[-1]), 5)]}
 
 
 def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0, early_start=False):
@@ -568,10 +660,12 @@ def run_gpu(args):
 
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
-        forms = {"p0_cufft_pointwise": form_p0(torch, I_dev, S_box),
+        forms = {"refine_3d": form_refine(cp, torch, plan),
+                 "p0_cufft_pointwise": form_p0(torch, I_dev, S_box),
                  "precision": form_precision(cp, torch, I_dev, thetas, S_box),
                  "precision_large": form_precision_large(cp, torch),
                  "batching": form_batch(cp, torch),
+                 "multi_guess_merge": form_multi_guess(cp, torch),
                  "serving_continuous": form_serving(cp, torch, max_active=0),
                  "serving_one_at_a_time": form_serving(cp, torch, max_active=1),
                  "serving_early_start": form_serving(cp, torch, max_active=0, early_start=True)}

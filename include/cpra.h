@@ -248,6 +248,35 @@ cpra_status cpra_assemble_3d(cpra_plan_t plan, void* out_volume);
 cpra_status cpra_merge(const cpra_plan_t* guesses, int32_t n_r, int32_t n_l, int32_t twin_ref,
                        cpra_plan_t dst, int32_t* selected, int32_t* inverted, float* prtf);
 
+/* Step D refinement: the paper's tomographic 3D reconstruction "like
+ * conventional 3D CXDI but using E(q)" (about 50 iterations, the 3D support
+ * from the 2D supports projected back, shrunk every 5 iterations in its cell
+ * example).  Alternating projections on the plan's Step D result:
+ *   V = the gridded spectrum E(q) (the FFT of the last volume of
+ *       cpra_assemble_3d or cpra_merge), M = the (kx, ky) cells the slices
+ *       reach (every kz);
+ *   S3 = voxels whose projection lands inside the plan's current 2D support
+ *       at every angle (nearest pixel in u, exact z), each 2D support first
+ *       moved by the whole-pixel part of its PO's mass-centre move (the
+ *       plan's own state; no move with com_align 0);
+ *   the iteration runs on the centred volume (the frame of the supports);
+ *   start: rho = the real part of that volume;
+ *   each iteration: X = FFT3(P_{S3+} rho); X <- V on M; rho = Re IFFT3(X);
+ *   after iteration t with (t+1) % shrink_every == 0 (0 = never):
+ *   S3 <- {blur(P_{S3+} rho) >= tau * max}, blur = periodic Gaussian of
+ *   sigma voxels along x, y, z.
+ * The refined volume P_{S3+} rho replaces the plan's volume (centred,
+ * complex64 with imaginary part 0; CPRA_RESULT_VOLUME).  Successive calls
+ * continue the refinement (and its shrink-wrap count); the next assemble or
+ * merge restarts it.  err_out (NULL, or n_iters doubles, host or device):
+ * sqrt(sum_M |X - V|^2 / sum_M |V|^2) of every iteration (FP64 sums).
+ * Allocates about 25 N^3 bytes on first use.  NOT_READY without a Step D
+ * volume, INVALID_ARG for negative counts or bad shrink-wrap parameters.
+ * Runs on the plan's stream; returns after queuing (after the copy when
+ * err_out is given). */
+cpra_status cpra_refine_3d(cpra_plan_t plan, int32_t n_iters, int32_t shrink_every, float sigma,
+                           float tau, double* err_out);
+
 /* Copy one result (CPRA_RESULT_*) into dst, which holds `bytes` bytes (host
  * or device).  INVALID_ARG if bytes is smaller than the result, NOT_READY for
  * a volume before cpra_assemble_3d. */
@@ -267,7 +296,8 @@ enum {
   CPRA_KERNEL_ASSEMBLE = 4,
   CPRA_KERNEL_FUSED = 5,     /* fused engine: prime + a run of whole iterations    */
   CPRA_KERNEL_PREPARE = 6,
-  CPRA_KERNEL_KINDS = 7
+  CPRA_KERNEL_REFINE = 7,    /* Step D refinement (3D line passes, support)       */
+  CPRA_KERNEL_KINDS = 8
 };
 
 /* Device-time profiling: with on = 1 the plan records CUDA events around each

@@ -24,7 +24,7 @@ UPDATE_HIO, UPDATE_RAAR = 0, 1
 ENGINE_AUTO, ENGINE_TWO_PASS, ENGINE_FUSED, ENGINE_WARP, ENGINE_TUNED = 0, 1, 2, 3, 4
 RESULT_PO, RESULT_STATE, RESULT_SUPPORT, RESULT_ERRORS, RESULT_VOLUME, RESULT_MERGED_SPECTRA = range(6)
 (KERNEL_COLPASS, KERNEL_ROWPASS, KERNEL_PRIME, KERNEL_SHRINKWRAP, KERNEL_ASSEMBLE, KERNEL_FUSED,
- KERNEL_PREPARE, KERNEL_KINDS) = range(8)
+ KERNEL_PREPARE, KERNEL_REFINE, KERNEL_KINDS) = range(9)
 MAX_TAPS = 15
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -104,6 +104,7 @@ def lib() -> C.CDLL:
             "cpra_launch_count": (C.c_int64, []),
             "cpra_shrinkwrap_static": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_float,
                                                  C.c_float, P]),
+            "cpra_refine_3d": (C.c_int, [P, C.c_int32, C.c_int32, C.c_float, C.c_float, P]),
             "cpra_merge": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, P,
                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), P]),
             "cpra_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]),
@@ -229,6 +230,13 @@ def cpra_merge(guesses, n_l: int, twin_ref: int, dst, prtf=None):
     p, keep = _ptr(prtf)
     _check(lib().cpra_merge(arr, n_r, n_l, twin_ref, dst, sel, inv, p), dst)
     return list(sel)[:n_l], [bool(v) for v in inv][:n_l]
+
+
+def cpra_refine_3d(plan, n_iters: int, shrink_every: int = 0, sigma: float = 2.0, tau: float = 0.1,
+                   err_out=None):
+    p, keep = _ptr(err_out)
+    _check(lib().cpra_refine_3d(plan, n_iters, shrink_every, sigma, tau, p), plan)
+    return keep
 
 
 def cpra_iteration(plan) -> int:
@@ -391,6 +399,12 @@ class Plan:
 
     def assemble_3d(self, out=None):
         cpra_assemble_3d(self.h, out)
+        return out
+
+    def refine_3d(self, n: int, shrink_every: int = 0, sigma: float = 2.0, tau: float = 0.1):
+        """Step D refinement; returns the n per-iteration errors."""
+        out = np.empty(n, np.float64) if n > 0 else None
+        cpra_refine_3d(self.h, n, shrink_every, sigma, tau, out)
         return out
 
     def result(self, what: int):

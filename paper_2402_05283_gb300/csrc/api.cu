@@ -229,7 +229,7 @@ struct Range {
   explicit Range(int kind) {
     static const char* names[CPRA_KERNEL_KINDS] = {"cpra colpass", "cpra rowpass", "cpra prime",
                                                    "cpra shrinkwrap", "cpra assemble",
-                                                   "cpra fused", "cpra prepare"};
+                                                   "cpra fused", "cpra prepare", "cpra refine"};
     nvtxRangePushA(names[kind]);
   }
   ~Range() { nvtxRangePop(); }
@@ -909,6 +909,7 @@ cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
   p->asmb.ready = true;
   p->hp_valid = false;
   p->merged = false;
+  p->vol_state = 1;
   if (out) return copy_out(p, out, p->asmb.vol, N * NN * 8);
   return CPRA_OK;
 }
@@ -1008,6 +1009,7 @@ cpra_status cpra_merge(const cpra_plan_t* guesses, int32_t n_r, int32_t n_l, int
      }), "merge finish");
   p->asmb.ready = true;
   p->merged = true;
+  p->vol_state = 1;
   if (prtf_host) {
     st = copy_out(p, prtf, prtf_dev, sizeof(float) * Np * (N / 2));
     if (st != CPRA_OK) return st;
@@ -1016,6 +1018,101 @@ cpra_status cpra_merge(const cpra_plan_t* guesses, int32_t n_r, int32_t n_l, int
   for (int k = 0; k < n_l; ++k) {
     if (selected) selected[k] = order[k];
     if (inverted) inverted[k] = flips[k];
+  }
+  return CPRA_OK;
+}
+
+cpra_status cpra_refine_3d(cpra_plan_t p, int32_t n_iters, int32_t shrink_every, float sigma,
+                           float tau, double* err_out) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (n_iters < 0 || shrink_every < 0) return fail(p, CPRA_ERR_INVALID_ARG, "negative count");
+  if (shrink_every > 0 && (!(sigma > 0.0f) || !(tau >= 0.0f) || !(tau <= 1.0f)))
+    return fail(p, CPRA_ERR_INVALID_ARG, "shrink-wrap needs sigma > 0 and 0 <= tau <= 1");
+  if (p->vol_state == 0)
+    return fail(p, CPRA_ERR_NOT_READY, "no Step D volume: cpra_assemble_3d or cpra_merge first");
+  const int N = p->N, Np = p->Np, W3 = (N + 31) / 32;
+  const size_t NN = (size_t)N * N, N3 = NN * N;
+  if (!p->rf_X) {
+    p->rf_X = (float2*)dev_alloc(p, N3 * 8);
+    p->rf_V = (float2*)dev_alloc(p, N3 * 8);
+    p->rf_R = (float*)dev_alloc(p, N3 * 4);
+    p->rf_B = (float*)dev_alloc(p, N3 * 4);
+    p->rf_S3 = (uint32_t*)dev_alloc(p, NN * W3 * 4);
+    p->rf_M = (uint8_t*)dev_alloc(p, NN);
+    p->rf_cs = (double2*)dev_alloc(p, sizeof(double2) * Np);
+    p->rf_taps = (float*)dev_alloc(p, sizeof(float) * N);
+    p->rf_max = (unsigned*)dev_alloc(p, sizeof(unsigned));
+    p->rf_shift = (int2*)dev_alloc(p, sizeof(int2) * Np);
+    if (!p->rf_X || !p->rf_V || !p->rf_R || !p->rf_B || !p->rf_S3 || !p->rf_M || !p->rf_cs ||
+        !p->rf_taps || !p->rf_max || !p->rf_shift)
+      return fail(p, CPRA_ERR_OUT_OF_MEMORY, "refinement allocation failed");
+  }
+  if (n_iters > p->rf_err_cap) {
+    dev_free(p, p->rf_err);
+    p->rf_err = (double*)dev_alloc(p, sizeof(double) * 2 * n_iters);
+    if (!p->rf_err) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "refinement allocation failed");
+    p->rf_err_cap = n_iters;
+  }
+  RefineArgs a{N, W3, p->rf_X, p->rf_V, p->rf_R, p->rf_B, p->rf_S3, p->rf_M, p->tw};
+  cudaStream_t st = p->stream;
+  if (p->vol_state == 1) {  // start from the Step D volume of the last assemble / merge
+    // each 2D support moves with its PO: the whole-pixel part of its
+    // mass-centre move, from this plan's own state
+    std::vector<double> mom(3 * (size_t)Np, 0.0);
+    std::vector<int2> shift(Np, make_int2(0, 0));
+    if (p->cfg.com_align && p->state_ready) {
+      CK(launch_moments(p, p->asmb.moments, st), "refine moments");
+      CK(cudaMemcpyAsync(mom.data(), p->asmb.moments, sizeof(double) * 3 * Np, cudaMemcpyDeviceToHost, st),
+         "refine moments");
+      CK(cudaStreamSynchronize(st), "refine sync");
+      for (int n = 0; n < Np; ++n)
+        if (mom[3 * n] > 0.0)
+          shift[n] = make_int2((int)std::nearbyint(mom[3 * n + 1] / mom[3 * n] - N / 2),
+                               (int)std::nearbyint(mom[3 * n + 2] / mom[3 * n] - N / 2));
+    }
+    std::vector<double2> cs(Np);
+    for (int n = 0; n < Np; ++n) cs[n] = make_double2(std::cos(p->theta[n]), std::sin(p->theta[n]));
+    CK(cudaMemcpyAsync(p->rf_cs, cs.data(), sizeof(double2) * Np, cudaMemcpyHostToDevice, st),
+       "refine upload");
+    CK(cudaMemcpyAsync(p->rf_shift, shift.data(), sizeof(int2) * Np, cudaMemcpyHostToDevice, st),
+       "refine upload");
+    CK(timed(p, CPRA_KERNEL_REFINE, [&] {
+         cudaError_t e = launch_refine_setup(a, p->asmb.vol, st);
+         return e == cudaSuccess
+                    ? launch_refine_support(a, p->S, p->rf_cs, p->rf_shift, Np, p->asmb.cell_ptr, st)
+                    : e;
+       }), "refine setup");
+    CK(cudaStreamSynchronize(st), "refine sync");  // cs and shift live on this stack
+    p->rf_t = 0;
+  }
+  int ntaps = 0;
+  if (shrink_every > 0) {
+    std::vector<float> taps = gaussian_taps(N, sigma, ntaps);
+    CK(cudaMemcpyAsync(p->rf_taps, taps.data(), sizeof(float) * ntaps, cudaMemcpyHostToDevice, st),
+       "refine taps");
+    CK(cudaStreamSynchronize(st), "refine sync");
+  }
+  if (n_iters > 0) CK(cudaMemsetAsync(p->rf_err, 0, sizeof(double) * 2 * n_iters, st), "refine clear");
+  for (int i = 0; i < n_iters; ++i) {
+    CK(timed(p, CPRA_KERNEL_REFINE, [&] { return launch_refine_iter(a, p->rf_err + 2 * i, st); }),
+       "refine iteration");
+    if (shrink_every > 0 && (p->rf_t + 1) % shrink_every == 0)
+      CK(timed(p, CPRA_KERNEL_REFINE, [&] {
+           return launch_refine_shrink(a, p->rf_taps, ntaps, tau, p->rf_max, st);
+         }), "refine shrink-wrap");
+    p->rf_t++;
+  }
+  CK(timed(p, CPRA_KERNEL_REFINE, [&] { return launch_refine_output(a, p->asmb.vol, st); }),
+     "refine output");
+  p->vol_state = 2;
+  if (err_out && n_iters > 0) {
+    std::vector<double> sums(2 * (size_t)n_iters), errs(n_iters);
+    CK(cudaMemcpyAsync(sums.data(), p->rf_err, sizeof(double) * 2 * n_iters, cudaMemcpyDeviceToHost, st),
+       "refine errors");
+    CK(cudaStreamSynchronize(st), "refine sync");
+    for (int i = 0; i < n_iters; ++i)
+      errs[i] = sums[2 * i + 1] > 0.0 ? std::sqrt(sums[2 * i] / sums[2 * i + 1]) : 0.0;
+    CK(cudaMemcpy(err_out, errs.data(), sizeof(double) * n_iters, cudaMemcpyDefault), "refine errors");
   }
   return CPRA_OK;
 }

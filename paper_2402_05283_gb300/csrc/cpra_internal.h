@@ -81,6 +81,21 @@ struct cpra_plan_s {
   double* mg_dist = nullptr;   // [2] twin distances
   float* mg_prtf = nullptr;    // [Np][N/2] PRTF staging for host outputs
   bool merged = false;         // mg_acc holds the mean of the last merge
+  // Step D refinement (cpra_refine_3d)
+  int vol_state = 0;           // 0 none, 1 Step D volume (assemble or merge), 2 refined
+  float2* rf_X = nullptr;
+  float2* rf_V = nullptr;
+  float* rf_R = nullptr;
+  float* rf_B = nullptr;
+  uint32_t* rf_S3 = nullptr;
+  uint8_t* rf_M = nullptr;
+  double* rf_err = nullptr;    // [2 * rf_err_cap] error sums per iteration
+  int64_t rf_err_cap = 0;
+  double2* rf_cs = nullptr;    // [Np] (cos, sin) of the angles
+  int2* rf_shift = nullptr;    // [Np] whole-pixel mass-centre shifts (dz, du)
+  float* rf_taps = nullptr;    // [N] periodic Gaussian taps of the last shrink
+  unsigned* rf_max = nullptr;
+  int64_t rf_t = 0;            // refinement iterations run
   // kernel tables of this plan as a one-job launch
   cpra::JobStatic* d_js = nullptr;
   int2* d_tiles = nullptr;     // (0, angle) of every iterating angle, ascending
@@ -220,6 +235,33 @@ struct MergeArgs {
 // angles ma.n0 .. ma.n0 + count - 1 (the R2C rows of rho are in g's Hp)
 cudaError_t launch_merge_guess(cpra_plan_s* g, double* moments, int mode, const MergeArgs& ma,
                                int count, cudaStream_t st);
+// Step D refinement (k_refine.cu): buffers of one plan's refinement
+struct RefineArgs {
+  int N, W;            // W = ceil(N/32) words per x row of S3
+  float2* X;           // [N^3] working spectrum / volume
+  float2* V;           // [N^3] gridded spectrum, FFT order
+  float* R;            // [N^3] real iterate rho
+  float* Bv;           // [N^3] shrink-wrap blur scratch
+  uint32_t* S3;        // [N][N][W] 3D support bits
+  uint8_t* M;          // [N][N] measured (ky, kx) cells
+  const float2* tw;    // twiddles exp(-2 pi i k/N)
+};
+// X = vol (centred), R = Re vol, V = FFT3(X)
+cudaError_t launch_refine_setup(const RefineArgs& a, const float2* vol, cudaStream_t st);
+// S3 from the 2D supports S2 [Np][N][W] moved by shift[n] = (dz, du), with
+// (cos, sin) of every angle; M from the gridding lists
+cudaError_t launch_refine_support(const RefineArgs& a, const uint32_t* S2, const double2* cs,
+                                  const int2* shift, int Np, const int32_t* cell_ptr, cudaStream_t st);
+// FP64 moments (sum rho, sum rho z, sum rho u) of rho = P_{S+} g of every angle
+cudaError_t launch_moments(cpra_plan_s* p, double* moments, cudaStream_t st);
+// one iteration; err2[0..1] += sum_M |X - V|^2, sum_M |V|^2
+cudaError_t launch_refine_iter(const RefineArgs& a, double* err2, cudaStream_t st);
+// S3 <- {blur(P_{S3+} R) >= tau max} (mx: one unsigned of scratch)
+cudaError_t launch_refine_shrink(const RefineArgs& a, const float* taps, int ntaps, float tau,
+                                 unsigned* mx, cudaStream_t st);
+// vol = P_{S3+} R
+cudaError_t launch_refine_output(const RefineArgs& a, float2* vol, cudaStream_t st);
+
 // PRTF (prtf != NULL, needs mag), acc <- acc / n_l, its IDFT_z into dst's F,
 // gridding and the plane IFFTs into dst's volume, on dst's stream
 cudaError_t launch_merge_finish(cpra_plan_s* dst, float2* acc, const float* mag, float* prtf,

@@ -345,6 +345,10 @@ static cudaError_t moments_of(cpra_plan_s* p, double* moments, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+cudaError_t launch_moments(cpra_plan_s* p, double* moments, cudaStream_t st) {
+  return moments_of(p, moments, st);
+}
+
 // gather into the grid, then the inverse FFT of every z plane
 template <int N>
 static cudaError_t grid_n(cpra_plan_s* p) {
