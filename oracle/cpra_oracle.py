@@ -84,13 +84,24 @@ design notes):
       leaves the spectrum free.
   R20 3D support from the 2D supports ("projected back to 3D"): a voxel is
       inside iff its projection lands inside the 2D support at every angle
-      (nearest pixel in u, exact z).
+      (nearest pixel in u, exact z).  Each 2D support first moves with its
+      PO: the mass-centre move of R10, rounded to whole pixels, so that it
+      frames the moved PO in the centred volume.
   R21 The refinement (GENFIRE-like, the paper gives only "like conventional
       3D CXDI but using E(q)", 50 iterations, shrink every 5): alternating
       projections, P_{S3+} in real space and the replacement of the measured
-      cells by V in Fourier space; it starts from the real part of the Step D
-      volume (the phases of E(q) make one start enough); shrink-wrap as R9 in
-      3D; the result is P_{S3+} of the last iterate.
+      cells by the data in Fourier space.  It runs in the centred frame of
+      the Step D volume (the frame of the 2D supports): the data are the
+      spectrum of the centred volume, DFT3(fftshift3(IDFT3(V))), and the
+      start is the real part of that volume (the phases of E(q) make one
+      start enough); shrink-wrap as R9 in 3D; the result is P_{S3+} of the
+      last iterate, centred.
+  R22 Gauss-Seidel sweep (Step B's "consecutively, from n = 1 to n = N_p"):
+      within an episode the angles are reconstructed in turn; angle n starts
+      from Eq. 4 with the current episode's images of the angles before it
+      and the previous episode's images of the others, then runs its N_ei
+      iterations; an episode is the unit of a call.  Jacobi (R1) stays the
+      default, the equation's literal form.
 """
 from __future__ import annotations
 
@@ -108,12 +119,12 @@ __all__ = [
     "dft_matrix", "dft2", "idft2", "dft3", "idft3", "fftshift2", "ifftshift2",
     "fftshift3", "amplitudes", "a_sym", "splitmix64", "initial_guess",
     "modulus_projection", "fourier_error_terms", "support_update",
-    "iterate_2d", "positivity_margin", "couple", "wrapped_gaussian", "blur", "shrinkwrap",
+    "iterate_2d", "positivity_margin", "couple", "couple_sweep_one", "wrapped_gaussian", "blur", "shrinkwrap",
     "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d",
     "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
     "r_factor", "raar_update", "episode_error", "select_best", "centrally_inverted", "prtf",
     "merge_episodes", "assemble_spectra", "measured_cells", "backprojected_support", "blur3",
-    "refine_3d",
+    "refine_3d", "support_shifts",
 ]
 
 
@@ -325,6 +336,26 @@ def couple(g, alpha, wrap=WRAP_LITERAL, blend=BLEND_STATE, S=None, present=None)
     return out
 
 
+def couple_sweep_one(g_old, g_new, n, alpha, wrap=WRAP_LITERAL, blend=BLEND_STATE, S=None):
+    """R22 (Gauss-Seidel sweep): the start of angle n in an episode whose
+    angles are reconstructed one after another from n = 0: Eq. 4 with the
+    episode-m image for the angles already done in this sweep (index < n,
+    g_new) and the episode m-1 image for the others (g_old)."""
+    Np = g_old.shape[0]
+    alpha = np.asarray(alpha, dtype=np.float64)
+    r = len(alpha) // 2
+    out = np.zeros(g_old.shape[1:], dtype=np.float64)
+    for k in range(-r, r + 1):
+        j = n + k
+        jm = j % Np
+        src = g_new if jm < n else g_old
+        img = src[jm] if blend == BLEND_STATE else object_estimate(src[jm], S[jm])
+        if wrap == WRAP_MIRROR and (j // Np) % 2 != 0:
+            img = _mirror_u(img)
+        out += alpha[k + r] * img
+    return out
+
+
 # --------------------------------------------------------------------------
 # Shrink-wrap (R9)
 # --------------------------------------------------------------------------
@@ -522,21 +553,35 @@ def measured_cells(N: int, thetas, wmin: float = 1e-12) -> np.ndarray:
     return wsum >= wmin
 
 
-def backprojected_support(S2: np.ndarray, thetas) -> np.ndarray:
+def backprojected_support(S2: np.ndarray, thetas, shifts=None) -> np.ndarray:
     """R20: voxel (z, y, x) is in the 3D support iff at every angle its
     projection coordinate u = rint((x - c) cos theta + (y - c) sin theta + c),
-    c = N/2 (the geometry of R16), lies in [0, N) with S2[n][z][u] set."""
+    c = N/2 (the geometry of R16), lies in [0, N) and the 2D support, moved
+    by that angle's whole-pixel shift (dz, du) (periodic), holds (z, u):
+    S2[n][(z + dz) mod N][(u + du) mod N]."""
     Np, N, _ = S2.shape
     c = N // 2
     y, x = np.meshgrid(np.arange(N) - c, np.arange(N) - c, indexing="ij")
     out = np.ones((N, N, N), dtype=bool)
     for n in range(Np):
+        dz, du = (0, 0) if shifts is None else (int(shifts[n][0]), int(shifts[n][1]))
+        moved = np.roll(S2[n].astype(bool), (-dz, -du), axis=(0, 1))
         u = np.rint(x * math.cos(thetas[n]) + y * math.sin(thetas[n]) + c).astype(np.int64)
         inside = (u >= 0) & (u < N)
         uc = np.clip(u, 0, N - 1)
-        hit = S2[n].astype(bool)[:, uc] & inside[None, :, :]  # [z][y][x]
+        hit = moved[:, uc] & inside[None, :, :]  # [z][y][x]
         out &= hit
     return out
+
+
+def support_shifts(g, S, com_align=True):
+    """R20: the whole-pixel part of each PO's mass-centre move (R10) in the
+    centred frame, (rint(c_z - N/2), rint(c_u - N/2)); zeros without it."""
+    N = g.shape[-1]
+    if not com_align:
+        return np.zeros((g.shape[0], 2), dtype=np.int64)
+    c = centre_of_mass(object_estimate(g, S))
+    return np.rint(c - N / 2).astype(np.int64)
 
 
 def blur3(rho: np.ndarray, sigma: float) -> np.ndarray:
@@ -552,9 +597,9 @@ def blur3(rho: np.ndarray, sigma: float) -> np.ndarray:
 def refine_3d(V, M, S3, rho0, n_iters, shrink_every=0, sigma=2.0, tau=0.1):
     """Step D's tomographic iteration on the assembled spectrum (R21).
 
-    V: the gridded spectrum [kz][ky][kx] (R11, FFT order); M: measured cells
-    [ky][kx] (R19); S3: 3D support (R20); rho0: the start (real, FFT-order
-    volume).  Each iteration: rho_S = P_{S3+} rho; X = DFT3(rho_S); error
+    V: the spectrum [kz][ky][kx] (FFT order) of the frame the iteration runs
+    in; M: measured cells [ky][kx] (R19); S3: 3D support (R20); rho0: the
+    start (real).  Each iteration: rho_S = P_{S3+} rho; X = DFT3(rho_S); error
     sqrt(sum_M |X - V|^2 / sum_M |V|^2); X <- V on the measured cells;
     rho = Re IDFT3(X); every shrink_every iterations the 3D support shrinks
     to {blur(P_{S3+} rho) >= tau max} (R9 in 3D).
@@ -597,6 +642,7 @@ class OracleConfig:
     com_align: bool = True
     seed: int = 0
     update: int = HIO  # the rule before hio_iters: HIO or RAAR (R14)
+    sweep: bool = False  # Gauss-Seidel episodes (R22) instead of Jacobi (R1)
 
 
 @dataclass
@@ -646,7 +692,33 @@ class OracleRun:
         self.t += 1
         return self
 
+    def sweep_episode(self):
+        """One Gauss-Seidel episode (R22): angles n = 0 .. Np-1 in turn, each
+        started from couple_sweep_one and run n_ei iterations alone."""
+        c = self.cfg
+        if self.t % c.n_ei != 0:
+            raise ValueError("a sweep starts at an episode boundary")
+        new = self.g.copy()
+        errs = np.zeros((c.n_ei, c.Np))
+        for n in range(c.Np):
+            x = couple_sweep_one(self.g, new, n, c.alpha, c.wrap, c.blend, self.S)[None]
+            for it in range(c.n_ei):
+                algo = c.update if self.t + it < c.hio_iters else ER
+                x, num, den = iterate_2d(x, self.A[n:n + 1], self.S[n:n + 1], c.beta, algo)
+                errs[it, n] = math.sqrt(num[0] / den[0]) if den[0] > 0 else 0.0
+            new[n] = x[0]
+        self.g = new
+        self.errors.extend(list(errs))
+        self.t += c.n_ei
+        return self
+
     def run(self, n):
+        if self.cfg.sweep:
+            if n % self.cfg.n_ei != 0:
+                raise ValueError("sweeps run whole episodes")
+            for _ in range(n // self.cfg.n_ei):
+                self.sweep_episode()
+            return self
         for _ in range(n):
             self.step()
         return self

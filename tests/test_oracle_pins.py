@@ -285,6 +285,55 @@ def test_iterate_fft_mode_equals_dft_mode():
             assert np.allclose(x, y, rtol=1e-11, atol=1e-12)
 
 
+def test_sweep_coupling_hand_case_np3():
+    """Gauss-Seidel starts on Np = 3 with the paper's alpha (0.2, 0.6, 0.2),
+    old images 1, 2, 3 and this sweep's images 10, 20, 30 (hand arithmetic):
+    angle 0 sees old 3, 1, 2 -> 1.6; angle 1 sees new 10, old 2, 3 -> 3.8;
+    angle 2 sees new 20, old 3 and (wrapping to angle 0, already done) new
+    10 -> 7.8."""
+    old = np.array([1.0, 2.0, 3.0])[:, None, None] * np.ones((3, 2, 2))
+    new = np.array([10.0, 20.0, 30.0])[:, None, None] * np.ones((3, 2, 2))
+    got = [O.couple_sweep_one(old, new, n, (0.2, 0.6, 0.2))[0, 0] for n in range(3)]
+    assert np.allclose(got, [1.6, 3.8, 7.8], atol=1e-14)
+
+
+def test_sweep_spreads_one_episode_around_the_carousel():
+    """The point of the sweep: a signal at angle 0 reaches every angle within
+    one episode (each start uses the previous angle's new image), while the
+    Jacobi coupling moves it one neighbour per episode."""
+    Np = 6
+    old = np.zeros((Np, 1, 1)); old[0] = 1.0
+    new = np.zeros_like(old)
+    for n in range(Np):
+        new[n] = O.couple_sweep_one(old, new, n, (0.2, 0.6, 0.2))
+    assert np.all(new[:, 0, 0] > 0)
+    jac = O.couple(old, (0.2, 0.6, 0.2))
+    assert np.count_nonzero(jac[:, 0, 0]) == 3
+    # one tap: the sweep is the identity, like Jacobi
+    assert np.array_equal(O.couple_sweep_one(old, new, 2, (1.0,)), old[2])
+
+
+def test_sweep_schedule():
+    """OracleRun in sweep mode = per angle: the sweep start, then n_ei
+    iterations of that angle alone; HIO -> ER by the global index."""
+    P, A_true = _true_case(16, 9)
+    I = np.fft.fftshift(A_true ** 2, axes=(-2, -1))
+    cfg = O.OracleConfig(N=16, Np=2, n_ei=2, hio_iters=3, er_iters=1, seed=2, sweep=True)
+    run = O.OracleRun.start(cfg, I)
+    g = run.g.copy()
+    for ep in range(2):
+        new = g.copy()
+        for n in range(2):
+            x = O.couple_sweep_one(g, new, n, cfg.alpha)[None]
+            for it in range(2):
+                t = 2 * ep + it
+                x, _, _ = O.iterate_2d(x, run.A[n:n + 1], run.S[n:n + 1], 0.9, O.HIO if t < 3 else O.ER)
+            new[n] = x[0]
+        g = new
+    run.run(4)
+    assert np.array_equal(run.g, g) and run.t == 4 and len(run.errors) == 4
+
+
 def test_coupling_present_mask_hand_case():
     """R13 on Np = 3 with angle 2 absent and alpha = (0.2, 0.6, 0.2), constant
     images 1, 10, 100: angle 0 keeps taps 0 (0.6) and 1 (0.2), renormalised by
@@ -624,6 +673,12 @@ def test_backprojected_support_axis_aligned():
     assert np.array_equal(only0, np.broadcast_to(S2[0][:, None, :], (N, N, N)))
     both = O.backprojected_support(S2, [0.0, math.pi / 2])
     assert np.array_equal(both, S2[0][:, None, :] & S2[1][:, :, None])
+    # a 2D support moved by (dz, du) = (1, -2) moves the 3D support by (-1, 2) in (z, x)
+    moved = O.backprojected_support(S2[:1], [0.0], shifts=[(1, -2)])
+    assert np.array_equal(moved, np.roll(only0, (-1, 2), axis=(0, 2)))
+    # the shift of a PO whose mass centre sits at (N/2 + 1.2, N/2 - 2.8) is (1, -3)
+    g = np.zeros((1, N, N)); g[0, N // 2 + 1, N // 2 - 3] = 0.8; g[0, N // 2 + 2, N // 2 - 2] = 0.2
+    assert O.support_shifts(g, np.ones_like(g, bool)).tolist() == [[1, -3]]
 
 
 def test_backprojected_support_contains_the_object():
