@@ -119,6 +119,17 @@ enum {
  *                  beta/2 (R_S R_M + I) g + (1 - beta) P_M g with the
  *                  reflections R = 2P - I of the support-positivity and
  *                  modulus projections.
+ *   sweep          0 (default): Jacobi episodes, every angle starts an
+ *                  episode from Eq. 4 over the previous episode (the
+ *                  equation's literal form; all angles run in parallel).
+ *                  1: Gauss-Seidel sweep (Step B's "consecutively, from n = 1
+ *                  to N_p"): angle n starts from Eq. 4 with this episode's
+ *                  images of the angles before it and the previous
+ *                  episode's of the others, and runs its n_ei iterations
+ *                  before angle n + 1 starts, so one episode carries a
+ *                  pre-reconstructed PO around the whole carousel.  Calls
+ *                  run whole episodes (t and n_iters multiples of n_ei);
+ *                  no shrink-wrap, present mask or batch (UNSUPPORTED).
  *   seed           seeds the random initial guess (SplitMix64 per pixel).
  *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
  */
@@ -138,6 +149,7 @@ typedef struct {
   int32_t com_align;
   int32_t engine;
   int32_t update;
+  int32_t sweep;
   uint64_t seed;
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);
@@ -147,7 +159,7 @@ typedef struct {
 /* Fill *cfg with defaults for an N x N, Np-angle problem: n_ei 10, alpha
  * (0.2, 0.6, 0.2) and beta 0.9 (the paper's Eq. 4 example and HIO value),
  * 200 HIO + 20 ER, shrink-wrap off, sigma 2, tau 0.1, LITERAL, STATE, FP32,
- * com_align 1, engine AUTO, update HIO, seed 0, cudaMalloc.  Returns INVALID_ARG for a NULL cfg. */
+ * com_align 1, engine AUTO, update HIO, sweep 0, seed 0, cudaMalloc.  Returns INVALID_ARG for a NULL cfg. */
 cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* cfg);
 
 /* Device bytes a plan for *cfg holds while iterating (iter_bytes) and the
@@ -447,8 +459,9 @@ typedef struct {
 cpra_status cpra_server_default_config(cpra_server_config* cfg);
 /* Start the serving thread on the current device. */
 cpra_status cpra_server_start(const cpra_server_config* cfg, cpra_server_t* out);
-/* Queue a request (cfg is copied; shrink-wrap unsupported; the serving
- * thread allocates with cudaMalloc, cfg->alloc is ignored). */
+/* Queue a request (cfg is copied; shrink-wrap and the Gauss-Seidel sweep
+ * unsupported; the serving thread allocates with cudaMalloc, cfg->alloc is
+ * ignored). */
 cpra_status cpra_server_submit(cpra_server_t s, const cpra_config* cfg, int64_t* request_id);
 /* Stream count patterns [count][N][N] (host or device float32, centred) for
  * angles first..first+count-1, with optional angles theta (host).  The data

@@ -38,7 +38,7 @@ class cpra_config(C.Structure):
         ("blend_target", C.c_int32), ("hio_iters", C.c_int32), ("er_iters", C.c_int32),
         ("shrinkwrap_every", C.c_int32), ("sw_sigma", C.c_float), ("sw_tau", C.c_float),
         ("n_pre", C.c_int32), ("precision", C.c_int32), ("com_align", C.c_int32),
-        ("engine", C.c_int32), ("update", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+        ("engine", C.c_int32), ("update", C.c_int32), ("sweep", C.c_int32), ("seed", C.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
         ("alloc_ctx", C.c_void_p),
     ]
 

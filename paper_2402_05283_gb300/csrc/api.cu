@@ -121,6 +121,10 @@ cpra_status validate(const cpra_config* c, std::string& why) {
     why = "bad update rule";
     return CPRA_ERR_INVALID_ARG;
   }
+  if (c->sweep != 0 && c->sweep != 1) {
+    why = "sweep must be 0 (Jacobi) or 1 (Gauss-Seidel)";
+    return CPRA_ERR_INVALID_ARG;
+  }
   if (c->wrap_mode != CPRA_WRAP_LITERAL && c->wrap_mode != CPRA_WRAP_MIRROR) {
     why = "bad wrap_mode";
     return CPRA_ERR_INVALID_ARG;
@@ -132,6 +136,10 @@ cpra_status validate(const cpra_config* c, std::string& why) {
   if (c->hio_iters < 0 || c->er_iters < 0 || c->n_pre < 0 || c->shrinkwrap_every < 0) {
     why = "negative iteration count";
     return CPRA_ERR_INVALID_ARG;
+  }
+  if (c->sweep && c->shrinkwrap_every > 0) {
+    why = "the Gauss-Seidel sweep runs without shrink-wrap";
+    return CPRA_ERR_UNSUPPORTED;
   }
   if (c->shrinkwrap_every > 0 && (!(c->sw_sigma > 0.0f) || !(c->sw_tau >= 0.0f) || !(c->sw_tau <= 1.0f))) {
     why = "shrink-wrap needs sigma > 0 and 0 <= tau <= 1";
@@ -315,6 +323,7 @@ CoupleArgs coupling_args(const cpra_config& c) {
   ca.mirror = c.wrap_mode == CPRA_WRAP_MIRROR;
   ca.object = c.blend_target == CPRA_BLEND_OBJECT;
   ca.store_g = 1;
+  ca.sweep = c.sweep;
   return ca;
 }
 
@@ -336,7 +345,7 @@ cpra_status upload_steps(cpra_plan_s* p, const std::vector<JobStep>& steps) {
   return CPRA_OK;
 }
 
-Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles) {
+Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles, int first_tile = 0) {
   Launch L;
   L.N = p->N;
   L.engine = p->engine;
@@ -344,7 +353,7 @@ Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles) {
   L.stream = p->stream;
   L.js = p->d_js;
   L.st = p->d_steps + step;
-  L.tiles = p->d_tiles;
+  L.tiles = p->d_tiles + first_tile;
   L.ntiles = ntiles;
   return L;
 }
@@ -525,6 +534,7 @@ cpra_status cpra_default_config(int32_t N, int32_t Np, cpra_config* c) {
   c->com_align = 1;
   c->engine = CPRA_ENGINE_AUTO;
   c->update = CPRA_UPDATE_HIO;
+  c->sweep = 0;
   c->seed = 0;
   return CPRA_OK;
 }
@@ -771,12 +781,86 @@ cpra_status cpra_load_state(cpra_plan_t p, const float* g, int64_t t) {
   return CPRA_OK;
 }
 
+static cpra_status iterate_core(cpra_plan_s* p, int32_t n_iters, double* err_out);
+
+// Gauss-Seidel episodes (cfg.sweep): angle n starts from Eq. 4 over this
+// episode's images of the angles before it (g_alt, written as the sweep
+// goes) and the previous episode's of the others (g), then runs the
+// episode's n_ei iterations alone; one launch per angle with the fused
+// engine, prime + n_ei (column + row) launches per angle with the others.
+static cpra_status iterate_sweep(cpra_plan_s* p, int32_t n_iters, double* err_out) {
+  const cpra_config& c = p->cfg;
+  const int E = c.n_ei, Np = p->Np;
+  if (p->partial) return fail(p, CPRA_ERR_UNSUPPORTED, "the Gauss-Seidel sweep needs every angle present");
+  if (p->t % E != 0 || n_iters % E != 0)
+    return fail(p, CPRA_ERR_INVALID_ARG, "Gauss-Seidel sweeps run whole episodes (t and n_iters multiples of n_ei)");
+  if (!p->state_ready) {  // seeded start and Step A
+    cpra_status st = iterate_core(p, 0, nullptr);
+    if (st != CPRA_OK) return st;
+  }
+  cpra_status st = ensure_err_cap(p, p->t + n_iters);
+  if (st != CPRA_OK) return st;
+  const bool fused = p->engine == CPRA_ENGINE_FUSED;
+  const int64_t t0 = p->t;
+  for (int ep = 0; ep < n_iters / E; ++ep) {
+    const int64_t t = p->t;
+    std::vector<JobStep> steps;
+    steps.reserve((size_t)Np * (fused ? 1 : E));
+    for (int n = 0; n < Np; ++n) {
+      for (int it = 0; it < (fused ? 1 : E); ++it) {
+        JobStep s{};
+        s.prime = it == 0;
+        s.ca = it == 0 ? coupling_args(c) : plain_args();
+        s.g_src = p->g;
+        s.g_dst = p->g_alt;
+        s.g = p->g_alt;
+        s.err_slot = t + it;
+        s.algo = t + it < c.hio_iters ? update_rule(c) : kER;
+        s.forward = it + 1 < E;
+        s.active = 1;
+        s.n_iters = E;
+        s.hio_left = (int)std::max<int64_t>(0, std::min<int64_t>(E, (int64_t)c.hio_iters - t));
+        steps.push_back(s);
+      }
+    }
+    st = upload_steps(p, steps);
+    if (st != CPRA_OK) return st;
+    int64_t k = 0;
+    for (int n = 0; n < Np; ++n) {
+      if (fused) {
+        CK(timed(p, CPRA_KERNEL_FUSED, [&] { return launch_fused(plan_launch(p, k++, 1, n)); }), "fused");
+        continue;
+      }
+      for (int it = 0; it < E; ++it, ++k) {
+        if (it == 0)
+          CK(timed(p, CPRA_KERNEL_PRIME, [&] { return launch_prime(plan_launch(p, k, 1, n)); }), "prime");
+        CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(plan_launch(p, k, 1, n)); }), "colpass");
+        CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(plan_launch(p, k, 1, n)); }), "rowpass");
+      }
+    }
+    std::swap(p->g, p->g_alt);
+    p->t += E;
+    p->hp_valid = false;
+  }
+  if (err_out && n_iters > 0) {
+    st = copy_out(p, err_out, p->err_hist + t0 * p->Np, sizeof(double) * n_iters * p->Np);
+    if (st != CPRA_OK) return st;
+  }
+  CK(cudaGetLastError(), "iterate");
+  return CPRA_OK;
+}
+
 cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
   if (n_iters < 0) return fail(p, CPRA_ERR_INVALID_ARG, "n_iters < 0");
   if (!present_loaded(p)) return fail(p, CPRA_ERR_NOT_READY, "an iterating angle has no intensities");
   if (!p->state_ready && p->cfg.n_pre > 0 && !p->present_h[0])
     return fail(p, CPRA_ERR_NOT_READY, "Step A needs angle 0");
+  if (p->cfg.sweep) return iterate_sweep(p, n_iters, err_out);
+  return iterate_core(p, n_iters, err_out);
+}
+
+static cpra_status iterate_core(cpra_plan_s* p, int32_t n_iters, double* err_out) {
   const cpra_config& c = p->cfg;
   cpra_status st = ensure_err_cap(p, p->t + n_iters);
   if (st != CPRA_OK) return st;
@@ -1174,6 +1258,8 @@ cpra_status cpra_set_present(cpra_plan_t p, const uint8_t* mask) {
   const bool all = (int)tiles.size() == p->Np;
   if (!all && p->cfg.shrinkwrap_every > 0)
     return fail(p, CPRA_ERR_UNSUPPORTED, "a present mask runs without shrink-wrap");
+  if (!all && p->cfg.sweep)
+    return fail(p, CPRA_ERR_UNSUPPORTED, "the Gauss-Seidel sweep needs every angle present");
   if (m == p->present_h) return CPRA_OK;
   if (!p->present) {
     p->present = (uint8_t*)dev_alloc(p, (size_t)p->Np);
@@ -1390,6 +1476,8 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
     if (!plans[i]) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "NULL plan in batch");
     if (plans[i]->cfg.shrinkwrap_every > 0)
       return bfail(nullptr, CPRA_ERR_UNSUPPORTED, "batches run plans without shrink-wrap");
+    if (plans[i]->cfg.sweep)
+      return bfail(nullptr, CPRA_ERR_UNSUPPORTED, "batches run Jacobi episodes (sweep 0)");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "plan listed twice");
   }

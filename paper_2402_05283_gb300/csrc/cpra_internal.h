@@ -161,6 +161,7 @@ struct CoupleArgs {
   int mirror;
   int object;        // blend P_{S+} g instead of g
   int store_g;       // write the coupled rows to g_dst
+  int sweep;         // Gauss-Seidel: taps on angles before n read g_dst
 };
 
 // Per-reconstruction pointers and constants, read by the kernels from a

@@ -329,7 +329,7 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const int pair0 = (blockIdx.x * RW::WARPS + warp) * FL::L;
   __shared__ TapTab tt;
   load_xtw<N>(xs, xtw, RW::WARPS * 32);
-  fill_taps<N>(tt, ca, g_src, S, n, Np, W, J->present);
+  fill_taps<N>(tt, ca, g_src, Z->g_dst, S, n, Np, W, J->present);
   __syncthreads();
   float2 a[FL::TA][FL::E1];
   blend_rows<N, FL>(a, tt, ca, W, pair0, lane);

@@ -227,7 +227,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const long long err_slot = Z->err_slot;
 
   load_xtw<N>(xs, J->xtw, F::NT);
-  fill_taps<N>(tt, ca, Z->g_src, J->S, n, Np, W, J->present);
+  fill_taps<N>(tt, ca, Z->g_src, Z->g_dst, J->S, n, Np, W, J->present);
   // the support is fixed during a launch: each lane keeps its pixels' bits
   uint32_t mask[2][F::MASKW];
   static_for<0, 2>([&](auto QQ) {

@@ -72,7 +72,7 @@ k_prime(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const int y0 = blockIdx.x * 2 * P;
   __shared__ TapTab tt;
   load_twiddles<N>(tw_s, tw);
-  fill_taps<N>(tt, ca, g_src, S, n, Np, W, J->present);
+  fill_taps<N>(tt, ca, g_src, Z->g_dst, S, n, Np, W, J->present);
   __syncthreads();
   for (int idx = threadIdx.x; idx < P * N; idx += NT) {
     const int p = idx / N, x = idx - p * N;

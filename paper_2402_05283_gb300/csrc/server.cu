@@ -363,6 +363,7 @@ cpra_status cpra_server_submit(cpra_server_t s, const cpra_config* cfg, int64_t*
   cpra_status st = cpra_plan_bytes(cfg, &a, &b);
   if (st != CPRA_OK) return st;
   if (cfg->shrinkwrap_every > 0) return sfail(s, CPRA_ERR_UNSUPPORTED, "served requests run without shrink-wrap");
+  if (cfg->sweep) return sfail(s, CPRA_ERR_UNSUPPORTED, "served requests run Jacobi episodes (sweep 0)");
   Request* r = new (std::nothrow) Request();
   if (!r) return sfail(s, CPRA_ERR_OUT_OF_MEMORY, "host allocation failed");
   r->cfg = *cfg;

@@ -23,10 +23,12 @@ struct TapTab {
 };
 
 // filled by thread 0; the caller synchronises the block before use
+// With ca.sweep (Gauss-Seidel), a tap on an angle before n in the sweep
+// reads this episode's image from g_new; every other tap reads g_src.
 template <int N>
 __device__ __forceinline__ void fill_taps(TapTab& tt, const CoupleArgs& ca, const float* g_src,
-                                          const uint32_t* S, int n, int Np, int W,
-                                          const uint8_t* present) {
+                                          const float* g_new, const uint32_t* S, int n, int Np,
+                                          int W, const uint8_t* present) {
   if (threadIdx.x != 0) return;
   const int nt = ca.n_taps;
   double sum = 0.0;
@@ -35,7 +37,7 @@ __device__ __forceinline__ void fill_taps(TapTab& tt, const CoupleArgs& ca, cons
     const int j = n + k - nt / 2;
     const int jm = ((j % Np) + Np) % Np;
     const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
-    tt.src[k] = g_src + (size_t)jm * N * N;
+    tt.src[k] = (ca.sweep && jm < n ? g_new : g_src) + (size_t)jm * N * N;
     tt.s[k] = S + (size_t)jm * N * W;
     tt.mir[k] = ca.mirror && (wraps & 1);
     const bool on = present == nullptr || present[jm] != 0;

@@ -1,0 +1,99 @@
+"""Gauss-Seidel sweep of Step B (cpra_config.sweep = 1) on the GPU against the
+oracle's sweep_episode (reading R22).
+
+ER iterations (continuous in the sign test) on the true-projection supports
+over two episodes, every engine: each angle's iterate within 1e-4 relative
+L2 and every error within 1e-4; Step A (3 HIO iterations on angle 0) before
+the sweeps; one RAAR episode of 3 iterations.  The sweep must differ from
+the Jacobi episodes it replaces, and calls must cover whole episodes.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+ENGINES = {"two_pass": 1, "warp": 3, "fused": 2}
+
+
+@pytest.fixture(scope="module")
+def cp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_05283_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def case():
+    d = synth.make_case("cfg1", N=64, Np=8)
+    d["S_true"] = (d["proj"].numpy() > 1e-9).astype(np.uint8)
+    return d
+
+
+def _rel(a, b):
+    a = a.reshape(a.shape[0], -1).astype(np.float64)
+    b = b.reshape(b.shape[0], -1).astype(np.float64)
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def _both(cp, d, iters, **kw):
+    cfg = cp.make_config(64, 8, **kw)
+    plan = cp.Plan(cfg)
+    plan.load_intensities(d["I"], 0, d["thetas"])
+    plan.load_support(d["S_true"])
+    e_gpu = plan.iterate(iters, errors=True)
+    g_gpu = plan.result(cp.RESULT_STATE)
+    plan.close()
+    oc = O.OracleConfig(N=64, Np=8, n_ei=cfg.n_ei, hio_iters=cfg.hio_iters, er_iters=cfg.er_iters,
+                        seed=cfg.seed, n_pre=cfg.n_pre, sweep=bool(cfg.sweep),
+                        update=O.RAAR if cfg.update == 1 else O.HIO,
+                        beta=float(np.float32(cfg.beta)))
+    run = O.OracleRun.start(oc, d["I"], d["S_true"]).run(iters)
+    return g_gpu, e_gpu, run.g, np.array(run.errors)
+
+
+@pytest.mark.parametrize("engine", ["two_pass", "warp", "fused"])
+def test_sweep_er_two_episodes(cp, case, engine):
+    g, e, g_ref, e_ref = _both(cp, case, 10, seed=3, hio_iters=0, er_iters=10, n_ei=5,
+                               engine=ENGINES[engine], sweep=1)
+    r = _rel(g, g_ref).max()
+    er = (np.abs(e - e_ref) / e_ref).max()
+    print(f"{engine}: sweep ER 2 x 5: iterate {r:.2e}, errors {er:.2e}")
+    assert r < TOL and er < TOL
+
+
+def test_sweep_after_step_a_and_raar(cp, case):
+    g, e, g_ref, e_ref = _both(cp, case, 10, seed=4, hio_iters=0, er_iters=10, n_ei=5, n_pre=3,
+                               sweep=1)
+    assert _rel(g, g_ref).max() < TOL and (np.abs(e - e_ref) / e_ref).max() < TOL
+    g, e, g_ref, e_ref = _both(cp, case, 3, seed=5, hio_iters=3, er_iters=0, n_ei=3,
+                               update=cp.UPDATE_RAAR, sweep=1)
+    r = _rel(g, g_ref).max()
+    print(f"sweep RAAR 1 x 3: iterate {r:.2e}")
+    assert r < TOL and (np.abs(e - e_ref) / e_ref).max() < TOL
+
+
+def test_sweep_differs_from_jacobi_and_runs_whole_episodes(cp, case):
+    kw = dict(seed=3, hio_iters=0, er_iters=10, n_ei=5)
+    g_s, _, _, _ = _both(cp, case, 5, sweep=1, **kw)
+    g_j, _, _, _ = _both(cp, case, 5, sweep=0, **kw)
+    assert _rel(g_s, g_j).max() > 1e-3
+    plan = cp.Plan(cp.make_config(64, 8, sweep=1, **kw))
+    plan.load_intensities(case["I"], 0, case["thetas"])
+    with pytest.raises(cp.CpraError) as ei:
+        plan.iterate(3)
+    assert ei.value.status == cp.ERR_INVALID_ARG
+    with pytest.raises(cp.CpraError) as ei:
+        cp.Batch([plan])
+    assert ei.value.status == cp.ERR_UNSUPPORTED
+    with pytest.raises(cp.CpraError) as ei:
+        plan.set_present(np.arange(8) < 4)
+    assert ei.value.status == cp.ERR_UNSUPPORTED
+    plan.close()
