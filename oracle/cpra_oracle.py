@@ -102,6 +102,12 @@ design notes):
       and the previous episode's images of the others, then runs its N_ei
       iterations; an episode is the unit of a call.  Jacobi (R1) stays the
       default, the equation's literal form.
+  R23 Missing data (the beamstop of the paper's cell patterns): a mask marks
+      the measured pixels; the pair {k, -k} is constrained iff both are
+      measured (a real PO has |G(-k)| = |G(k)|, and a centred beamstop is
+      symmetric, so this loses nothing there); the modulus projection keeps
+      G on the unconstrained pixels and the Fourier error sums over the
+      constrained ones only.
 """
 from __future__ import annotations
 
@@ -118,7 +124,7 @@ __all__ = [
     "HIO", "ER", "RAAR", "WRAP_LITERAL", "WRAP_MIRROR", "BLEND_STATE", "BLEND_OBJECT",
     "dft_matrix", "dft2", "idft2", "dft3", "idft3", "fftshift2", "ifftshift2",
     "fftshift3", "amplitudes", "a_sym", "splitmix64", "initial_guess",
-    "modulus_projection", "fourier_error_terms", "support_update",
+    "modulus_projection", "fourier_error_terms", "support_update", "constrained_pairs",
     "iterate_2d", "positivity_margin", "couple", "couple_sweep_one", "wrapped_gaussian", "blur", "shrinkwrap",
     "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d",
     "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
@@ -242,17 +248,32 @@ def initial_guess(seed: int, Np: int, N: int, S: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 # One conventional 2D iteration (Step B inner loop; R6-R8)
 # --------------------------------------------------------------------------
-def modulus_projection(G: np.ndarray, A: np.ndarray) -> np.ndarray:
-    """Replace |G| by A and keep the phase; phase 1 where G = 0."""
+def constrained_pairs(mask_centred: np.ndarray) -> np.ndarray:
+    """R23: the FFT-order pixels the modulus constraint applies to: k is
+    constrained iff k and -k are both measured (mask nonzero, centred like
+    the intensities)."""
+    m = ifftshift2(np.asarray(mask_centred).astype(bool))
+    neg = _neg_index(m.shape[-1])
+    return m & m[..., neg[:, None], neg[None, :]]
+
+
+def modulus_projection(G: np.ndarray, A: np.ndarray, C=None) -> np.ndarray:
+    """Replace |G| by A and keep the phase; phase 1 where G = 0.  With a
+    constrained set C (R23), pixels outside it keep G."""
     mag = np.abs(G)
     phase = np.where(mag > 0, G / np.where(mag > 0, mag, 1.0), 1.0)
-    return A * phase
+    return A * phase if C is None else np.where(C, A * phase, G)
 
 
-def fourier_error_terms(G: np.ndarray, A: np.ndarray):
-    """(sum (|G| - A)^2, sum A^2) per pattern over the full plane."""
+def fourier_error_terms(G: np.ndarray, A: np.ndarray, C=None):
+    """(sum (|G| - A)^2, sum A^2) per pattern over the full plane, or over the
+    constrained pixels C (R23)."""
     d = np.abs(G) - A
-    return (d * d).sum(axis=(-2, -1)), (A * A).sum(axis=(-2, -1))
+    a = A
+    if C is not None:
+        d = np.where(C, d, 0.0)
+        a = np.where(C, A, 0.0)
+    return (d * d).sum(axis=(-2, -1)), (a * a).sum(axis=(-2, -1))
 
 
 def raar_update(g, gp, S, beta):
@@ -273,17 +294,18 @@ def support_update(g, gp, S, beta, algo):
     return np.where(valid, gp, 0.0)
 
 
-def iterate_2d(g, A, S, beta, algo, return_gp=False, fft=False):
+def iterate_2d(g, A, S, beta, algo, return_gp=False, fft=False, C=None):
     """One iteration for a stack of POs; returns (g_new, err_num, err_den[, g']).
     fft=True takes the transforms from numpy.fft (FP64, the same unnormalised
     forward / 1/N^2 inverse) instead of the dense DFT matrices: for sizes
-    where the matrices are too slow."""
+    where the matrices are too slow.  C: constrained pixels (R23), None =
+    every pixel."""
     if fft:
         G = np.fft.fft2(g)
     else:
         G = dft2(g)
-    num, den = fourier_error_terms(G, A)
-    P = modulus_projection(G, A)
+    num, den = fourier_error_terms(G, A, C)
+    P = modulus_projection(G, A, C)
     gp = (np.fft.ifft2(P) if fft else idft2(P)).real
     out = support_update(g, gp, S, beta, algo)
     return (out, num, den, gp) if return_gp else (out, num, den)
@@ -656,9 +678,10 @@ class OracleRun:
     errors: list = field(default_factory=list)
     margins: list = field(default_factory=list)
     present: np.ndarray = None  # R13: angles that iterate (None = all)
+    C: np.ndarray = None  # R23: constrained pixels [Np][N][N] (None = all)
 
     @classmethod
-    def start(cls, cfg: OracleConfig, I_centred, S0=None, g0=None):
+    def start(cls, cfg: OracleConfig, I_centred, S0=None, g0=None, mask=None):
         A = amplitudes(I_centred)
         if S0 is None:
             S0 = np.zeros((cfg.N, cfg.N), dtype=bool)
@@ -666,11 +689,15 @@ class OracleRun:
             S0[o:o + cfg.N // 2, o:o + cfg.N // 2] = True
         S = np.broadcast_to(np.asarray(S0).astype(bool), A.shape).copy()
         g = initial_guess(cfg.seed, cfg.Np, cfg.N, S) if g0 is None else np.array(g0, dtype=np.float64)
-        run = cls(cfg=cfg, A=A, S=S, g=g)
+        C = None if mask is None else np.broadcast_to(constrained_pairs(mask), A.shape).copy()
+        run = cls(cfg=cfg, A=A, S=S, g=g, C=C)
         for _ in range(cfg.n_pre):  # Step A: angle 0 alone, the update rule
-            g1, _, _ = iterate_2d(run.g[0:1], A[0:1], S[0:1], cfg.beta, cfg.update)
+            g1, _, _ = iterate_2d(run.g[0:1], A[0:1], S[0:1], cfg.beta, cfg.update, C=run._c(0, 1))
             run.g[0] = g1[0]
         return run
+
+    def _c(self, a, b):
+        return None if self.C is None else self.C[a:b]
 
     def step(self):
         """One global iteration t (coupling first at episode starts)."""
@@ -678,7 +705,7 @@ class OracleRun:
         if self.t % c.n_ei == 0:
             self.g = couple(self.g, c.alpha, c.wrap, c.blend, self.S, self.present)
         algo = c.update if self.t < c.hio_iters else ER
-        g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True)
+        g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True, C=self.C)
         err = np.sqrt(num / den)
         if self.present is not None:  # absent angles keep their state (R13)
             on = np.asarray(self.present).astype(bool)
@@ -704,7 +731,8 @@ class OracleRun:
             x = couple_sweep_one(self.g, new, n, c.alpha, c.wrap, c.blend, self.S)[None]
             for it in range(c.n_ei):
                 algo = c.update if self.t + it < c.hio_iters else ER
-                x, num, den = iterate_2d(x, self.A[n:n + 1], self.S[n:n + 1], c.beta, algo)
+                x, num, den = iterate_2d(x, self.A[n:n + 1], self.S[n:n + 1], c.beta, algo,
+                                         C=self._c(n, n + 1))
                 errs[it, n] = math.sqrt(num[0] / den[0]) if den[0] > 0 else 0.0
             new[n] = x[0]
         self.g = new
