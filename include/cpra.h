@@ -129,7 +129,9 @@ enum {
  *                  before angle n + 1 starts, so one episode carries a
  *                  pre-reconstructed PO around the whole carousel.  Calls
  *                  run whole episodes (t and n_iters multiples of n_ei);
- *                  no shrink-wrap, present mask or batch (UNSUPPORTED).
+ *                  shrink-wrap runs at episode ends (shrinkwrap_every a
+ *                  multiple of n_ei); no present mask or batch
+ *                  (UNSUPPORTED).
  *   seed           seeds the random initial guess (SplitMix64 per pixel).
  *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
  */
@@ -183,6 +185,18 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out);
  * INVALID_ARG and leave the angles unloaded. */
 cpra_status cpra_load_intensities(cpra_plan_t plan, const float* I, int32_t first_angle,
                                   int32_t count, const double* theta_rad);
+
+/* Missing data (the beamstop of measured patterns): mask marks the measured
+ * pixels (uint8, nonzero = measured), centred like the intensities;
+ * per_angle = 1: mask is [Np][N][N], 0: one [N][N] mask for every angle;
+ * NULL: every pixel measured (the default).  It applies to the intensities
+ * loaded after the call.  A frequency pair {k, -k} is constrained only when
+ * both pixels are measured (a real PO has |G(-k)| = |G(k)|, and a centred
+ * beamstop is symmetric): the modulus projection leaves the others' G as it
+ * is and the Fourier error sums over the constrained pixels only.  Paper:
+ * its cell patterns were cropped with a beamstop in the centre (results
+ * section).  Host or device memory, read during the call. */
+cpra_status cpra_load_mask(cpra_plan_t plan, const uint8_t* mask, int32_t per_angle);
 
 /* Set the support from S (uint8, nonzero = inside).  per_angle = 1: S is
  * [Np][N][N]; per_angle = 0: one [N][N] mask for every angle.  S = NULL sets

@@ -101,7 +101,10 @@ design notes):
       from Eq. 4 with the current episode's images of the angles before it
       and the previous episode's images of the others, then runs its N_ei
       iterations; an episode is the unit of a call.  Jacobi (R1) stays the
-      default, the equation's literal form.
+      default, the equation's literal form.  Shrink-wrap (R9) then runs at
+      episode ends, for every angle, when its period is a whole number of
+      episodes (the paper's cell run: one CSWA step at the end of each
+      episode).
   R23 Missing data (the beamstop of the paper's cell patterns): a mask marks
       the measured pixels; the pair {k, -k} is constrained iff both are
       measured (a real PO has |G(-k)| = |G(k)|, and a centred beamstop is
@@ -738,6 +741,8 @@ class OracleRun:
         self.g = new
         self.errors.extend(list(errs))
         self.t += c.n_ei
+        if c.shrinkwrap_every > 0 and self.t % c.shrinkwrap_every == 0:  # at episode ends
+            self.S = shrinkwrap(self.g, self.S, c.sw_sigma, c.sw_tau)
         return self
 
     def run(self, n):

@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
             "cpra_plan": (C.c_int, [C.POINTER(cpra_config), P, C.POINTER(P)]),
             "cpra_load_intensities": (C.c_int, [P, P, C.c_int32, C.c_int32, P]),
             "cpra_load_support": (C.c_int, [P, P, C.c_int32]),
+            "cpra_load_mask": (C.c_int, [P, P, C.c_int32]),
             "cpra_load_state": (C.c_int, [P, P, C.c_int64]),
             "cpra_iterate": (C.c_int, [P, C.c_int32, P]),
             "cpra_assemble_3d": (C.c_int, [P, P]),
@@ -189,6 +190,12 @@ def cpra_load_intensities(plan, I, first: int, count: int, thetas=None):
 def cpra_load_support(plan, S, per_angle: int):
     p, keep = _ptr(S)
     _check(lib().cpra_load_support(plan, p, per_angle), plan)
+    return keep
+
+
+def cpra_load_mask(plan, mask, per_angle: int):
+    p, keep = _ptr(mask)
+    _check(lib().cpra_load_mask(plan, p, per_angle), plan)
     return keep
 
 
@@ -386,6 +393,13 @@ class Plan:
         if isinstance(S, np.ndarray):
             S = S.astype(np.uint8)
         cpra_load_support(self.h, S, per)
+
+    def load_mask(self, mask=None):
+        """Measured-pixel mask (centred; None = every pixel measured)."""
+        per = 1 if (mask is not None and mask.ndim == 3) else 0
+        if isinstance(mask, np.ndarray):
+            mask = np.ascontiguousarray(mask.astype(np.uint8))
+        cpra_load_mask(self.h, mask, per)
 
     def load_state(self, g, t: int):
         if isinstance(g, np.ndarray):

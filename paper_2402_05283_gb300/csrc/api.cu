@@ -99,11 +99,14 @@ Sizes plan_sizes(const cpra_config& c) {
 
 cpra_status validate(const cpra_config* c, std::string& why) {
   if (!c) { why = "config is NULL"; return CPRA_ERR_INVALID_ARG; }
-  if (c->N < 16 || c->N > 1024 || c->N % 16 != 0) {
-    why = "N must be a multiple of 16 in [16, 1024]";
+  if (c->N < 16 || c->N > 1024 || c->N % 2 != 0) {
+    why = "N must be even and in [16, 1024]";
     return c->N > 0 ? CPRA_ERR_UNSUPPORTED : CPRA_ERR_INVALID_ARG;
   }
-  if (!n_supported(c->N)) { why = "N must be 2^a 3^b"; return CPRA_ERR_UNSUPPORTED; }
+  if (!n_supported(c->N)) {
+    why = "N must be 2^a 3^b and a multiple of 16, or one of 160, 320, 640, 700";
+    return CPRA_ERR_UNSUPPORTED;
+  }
   if (c->Np < 1 || c->Np > 65535) { why = "Np must be in [1, 65535]"; return CPRA_ERR_INVALID_ARG; }
   if (c->n_ei < 1) { why = "n_ei must be >= 1"; return CPRA_ERR_INVALID_ARG; }
   if (c->n_taps < 1 || c->n_taps > CPRA_MAX_TAPS || c->n_taps % 2 == 0) {
@@ -137,8 +140,8 @@ cpra_status validate(const cpra_config* c, std::string& why) {
     why = "negative iteration count";
     return CPRA_ERR_INVALID_ARG;
   }
-  if (c->sweep && c->shrinkwrap_every > 0) {
-    why = "the Gauss-Seidel sweep runs without shrink-wrap";
+  if (c->sweep && c->shrinkwrap_every % c->n_ei != 0) {
+    why = "the Gauss-Seidel sweep shrink-wraps at episode ends: shrinkwrap_every must be a multiple of n_ei";
     return CPRA_ERR_UNSUPPORTED;
   }
   if (c->shrinkwrap_every > 0 && (!(c->sw_sigma > 0.0f) || !(c->sw_tau >= 0.0f) || !(c->sw_tau <= 1.0f))) {
@@ -746,6 +749,31 @@ cpra_status cpra_load_intensities(cpra_plan_t p, const float* I, int32_t first, 
   return CPRA_OK;
 }
 
+cpra_status cpra_load_mask(cpra_plan_t p, const uint8_t* mask, int32_t per_angle) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!mask) {
+    p->mask_per_angle = false;
+    if (p->mask) dev_free(p, p->mask);
+    p->mask = nullptr;
+    return CPRA_OK;
+  }
+  const size_t bytes = (size_t)p->N * p->N * (per_angle ? p->Np : 1);
+  if (p->mask && p->mask_per_angle != (per_angle != 0)) {
+    dev_free(p, p->mask);
+    p->mask = nullptr;
+  }
+  if (!p->mask) {
+    p->mask = (uint8_t*)dev_alloc(p, bytes);
+    if (!p->mask) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "mask allocation failed");
+  }
+  p->mask_per_angle = per_angle != 0;
+  CK(cudaMemcpyAsync(p->mask, mask, bytes, is_device_ptr(mask) ? cudaMemcpyDeviceToDevice
+                                                              : cudaMemcpyHostToDevice, p->stream),
+     "mask upload");
+  CK(cudaStreamSynchronize(p->stream), "mask sync");
+  return CPRA_OK;
+}
+
 cpra_status cpra_load_support(cpra_plan_t p, const uint8_t* S, int32_t per_angle) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
   if (!S) {
@@ -841,6 +869,8 @@ static cpra_status iterate_sweep(cpra_plan_s* p, int32_t n_iters, double* err_ou
     std::swap(p->g, p->g_alt);
     p->t += E;
     p->hp_valid = false;
+    if (c.shrinkwrap_every > 0 && p->t % c.shrinkwrap_every == 0)  // at episode ends
+      CK(timed(p, CPRA_KERNEL_SHRINKWRAP, [&] { return launch_shrinkwrap(p); }), "shrinkwrap");
   }
   if (err_out && n_iters > 0) {
     st = copy_out(p, err_out, p->err_hist + t0 * p->Np, sizeof(double) * n_iters * p->Np);

@@ -73,6 +73,8 @@ struct cpra_plan_s {
   float* sw_taps = nullptr;    // periodic Gaussian taps
   int sw_ntaps = 0;
   float* po_tmp = nullptr;
+  uint8_t* mask = nullptr;     // measured-pixel mask (cpra_load_mask), centred; NULL = all
+  bool mask_per_angle = false;
   cpra::Assembly asmb;
   // Step C merge scratch (cpra_merge with this plan as destination)
   float2* mg_acc = nullptr;    // [Np][N][N] merged spectra (sums, then the mean)

@@ -358,10 +358,12 @@ template <int N, int PREC> struct ColW {
 template <int N, int PREC>
 constexpr size_t col_smem() { return ColW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(ColW<N, PREC>::WARPS); }
 
-// G' = a G / |G| (a where G = 0); err += w (|G| - a)^2.  The per-thread
+// G' = a G / |G| (a where G = 0); err += w (|G| - a)^2; a < 0 marks a pixel
+// left free by a missing-data mask.  The per-thread
 // partial sum stays in FP32 (at most a few hundred terms); the reduction
 // across threads, blocks and columns is FP64.
 __device__ __forceinline__ float2 project_w(float2 G, float a, float& err, float w) {
+  if (a < 0.0f) return G;  // an unmeasured pair (mask): free, no error term
   const float r2 = fmaf(G.x, G.x, G.y * G.y);
   if (r2 > 0.0f) {
     const float inv = rsqrtf(r2);

@@ -11,6 +11,7 @@
 // Twiddles come from a table tw[k] = exp(-2 pi i k / N), k = 0..N-1, computed
 // in FP64 on the host and rounded once to FP32.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -29,6 +30,55 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 template <int DIR>
 __device__ __forceinline__ float2 mul_i(float2 a) {
   return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// cos and sin at compile time (Taylor series in FP64, exact at multiples of
+// pi/2), for the twiddles of the register DFTs
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+
+constexpr double cx_series_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int n = 1; n < 30; ++n) {
+    t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    s += t;
+  }
+  return s;
+}
+constexpr double cx_series_sin(double x) {
+  double t = x, s = x;
+  for (int n = 1; n < 30; ++n) {
+    t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    s += t;
+  }
+  return s;
+}
+// cos(2 pi q / M), sin(2 pi q / M)
+constexpr double cx_cos2pi(int q, int M) {
+  q = ((q % M) + M) % M;
+  if (q == 0) return 1.0;
+  if (2 * q == M) return -1.0;
+  if (4 * q == M || 4 * q == 3 * M) return 0.0;
+  double x = 2.0 * kPiD * q / M;
+  if (x > kPiD) x -= 2.0 * kPiD;
+  return cx_series_cos(x);
+}
+constexpr double cx_sin2pi(int q, int M) {
+  q = ((q % M) + M) % M;
+  if (q == 0 || 2 * q == M) return 0.0;
+  if (4 * q == M) return 1.0;
+  if (4 * q == 3 * M) return -1.0;
+  double x = 2.0 * kPiD * q / M;
+  if (x > kPiD) x -= 2.0 * kPiD;
+  return cx_series_sin(x);
+}
+
+// compile-time loop: f(std::integral_constant<int, i>) for i = I .. End-1
+template <int I, int End, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < End) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, End>(f);
+  }
 }
 
 // R-point DFT in registers, y_k = sum_r x_r exp(DIR * 2 pi i r k / R).
@@ -92,13 +142,56 @@ template <int DIR> struct Dft<3, DIR> {
   }
 };
 
+// Odd prime R (5, 7): pair the inputs r and R - r,
+//   y_k = x_0 + sum_{r=1}^{(R-1)/2} [ (x_r + x_{R-r}) cos(2 pi r k / R)
+//                                    + DIR i (x_r - x_{R-r}) sin(2 pi r k / R) ],
+// and y_{R-k} the same with the sine term negated.
+template <int R, int DIR> struct DftOdd {
+  static __device__ __forceinline__ void run(float2* v) {
+    constexpr int Hh = (R - 1) / 2;
+    float2 s[Hh + 1], d[Hh + 1];
+#pragma unroll
+    for (int r = 1; r <= Hh; ++r) {
+      s[r] = cadd(v[r], v[R - r]);
+      d[r] = csub(v[r], v[R - r]);
+    }
+    float2 y[R];
+    float2 y0 = v[0];
+#pragma unroll
+    for (int r = 1; r <= Hh; ++r) y0 = cadd(y0, s[r]);
+    y[0] = y0;
+    static_for<1, Hh + 1>([&](auto KK) {
+      constexpr int k = decltype(KK)::value;
+      float2 a = v[0];   // the cosine part
+      float2 b = make_float2(0.0f, 0.0f);  // sum sin * d, to be multiplied by DIR i
+      static_for<1, Hh + 1>([&](auto RR) {
+        constexpr int r = decltype(RR)::value;
+        constexpr float c = (float)cx_cos2pi(r * k, R);
+        constexpr float sn = (float)cx_sin2pi(r * k, R);
+        a = make_float2(fmaf(c, s[r].x, a.x), fmaf(c, s[r].y, a.y));
+        b = make_float2(fmaf(sn, d[r].x, b.x), fmaf(sn, d[r].y, b.y));
+      });
+      const float2 ib = mul_i<DIR>(b);  // DIR i b
+      y[k] = cadd(a, ib);
+      y[R - k] = csub(a, ib);
+    });
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = y[k];
+  }
+};
+template <int DIR> struct Dft<5, DIR> : DftOdd<5, DIR> {};
+template <int DIR> struct Dft<7, DIR> : DftOdd<7, DIR> {};
+
 __host__ __device__ constexpr int pick_radix(int rem) {
-  return (rem % 8 == 0) ? 8 : (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : 3;
+  return (rem % 8 == 0) ? 8 : (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : (rem % 3 == 0) ? 3
+                                                                     : (rem % 5 == 0) ? 5 : 7;
 }
 
 __host__ __device__ constexpr bool fft_size_ok(int n) {
   while (n % 2 == 0 && n > 1) n /= 2;
   while (n % 3 == 0 && n > 1) n /= 3;
+  while (n % 5 == 0 && n > 1) n /= 5;
+  while (n % 7 == 0 && n > 1) n /= 7;
   return n == 1;
 }
 

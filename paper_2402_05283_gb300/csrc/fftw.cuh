@@ -25,57 +25,11 @@
 
 namespace cpra {
 
-constexpr double kPiD = 3.14159265358979323846264338327950288;
-
-constexpr double cx_series_cos(double x) {
-  double t = 1.0, s = 1.0;
-  for (int n = 1; n < 30; ++n) {
-    t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
-    s += t;
-  }
-  return s;
-}
-constexpr double cx_series_sin(double x) {
-  double t = x, s = x;
-  for (int n = 1; n < 30; ++n) {
-    t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
-    s += t;
-  }
-  return s;
-}
-// cos(2 pi q / M), sin(2 pi q / M)
-constexpr double cx_cos2pi(int q, int M) {
-  q = ((q % M) + M) % M;
-  if (q == 0) return 1.0;
-  if (2 * q == M) return -1.0;
-  if (4 * q == M || 4 * q == 3 * M) return 0.0;
-  double x = 2.0 * kPiD * q / M;
-  if (x > kPiD) x -= 2.0 * kPiD;
-  return cx_series_cos(x);
-}
-constexpr double cx_sin2pi(int q, int M) {
-  q = ((q % M) + M) % M;
-  if (q == 0 || 2 * q == M) return 0.0;
-  if (4 * q == M) return 1.0;
-  if (4 * q == 3 * M) return -1.0;
-  double x = 2.0 * kPiD * q / M;
-  if (x > kPiD) x -= 2.0 * kPiD;
-  return cx_series_sin(x);
-}
-
 // exp(DIR * 2 pi i Q / M) as compile-time constants
 template <int M, int Q, int DIR> struct TwC {
   static constexpr float re = (float)cx_cos2pi(Q, M);
   static constexpr float im = (float)(DIR * cx_sin2pi(Q, M));
 };
-
-template <int I, int End, class F>
-__device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < End) {
-    f(std::integral_constant<int, I>{});
-    static_for<I + 1, End>(f);
-  }
-}
 
 // In-register E-point DFT, y_k = sum_j v_j exp(DIR 2 pi i jk / E), as
 // self-sorting Stockham passes over compile-time indices.

@@ -66,7 +66,7 @@ template <int N>
 struct SpecTile {
   static constexpr int B = cmin(N >= 1024 ? 8 : 16, pow2_div(N / 2));
   static constexpr int PI = B + 1;
-  static constexpr int NT = clampi(B * N / 32, 64, 1024);
+  static constexpr int NT = warps32(clampi(B * N / 32, 64, 1024));
 };
 
 template <int N, int MODE>
@@ -233,7 +233,9 @@ __global__ void k_prtf(const float2* __restrict__ acc, const float* __restrict__
     prtf[(size_t)n * H + i] = cnt[i] > 0.0 ? (float)(sum[i] / cnt[i]) : 0.0f;
 }
 
-// V[z][cell] for a chunk of 8 planes; one thread per cell.
+// V[z][cell] for a chunk of 8 planes; one thread per cell.  N is even, so
+// a chunk starts on a 16-byte boundary of F's rows; the last chunk of an N
+// that is not a multiple of 8 reads and writes its nz < 8 planes one by one.
 __global__ void k_gather(const float2* __restrict__ F, const int32_t* __restrict__ cell_ptr,
                          const int32_t* __restrict__ ent_idx, const double* __restrict__ ent_w,
                          float2* V, int N) {
@@ -241,27 +243,42 @@ __global__ void k_gather(const float2* __restrict__ F, const int32_t* __restrict
   const int NN = N * N;
   if (cell >= NN) return;
   const int z0 = blockIdx.y * 8;
+  const int nz = min(8, N - z0);
   float acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
   const int e0 = cell_ptr[cell], e1 = cell_ptr[cell + 1];
-  for (int e = e0; e < e1; ++e) {
-    const float w = (float)ent_w[e];
-    const float4* src = reinterpret_cast<const float4*>(F + (size_t)ent_idx[e] * N + z0);
+  if (nz == 8) {
+    for (int e = e0; e < e1; ++e) {
+      const float w = (float)ent_w[e];
+      const float4* src = reinterpret_cast<const float4*>(F + (size_t)ent_idx[e] * N + z0);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 f = __ldg(src + q);
-      acc[4 * q + 0] = fmaf(w, f.x, acc[4 * q + 0]);
-      acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
-      acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
-      acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = __ldg(src + q);
+        acc[4 * q + 0] = fmaf(w, f.x, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
+      }
+    }
+  } else {
+    for (int e = e0; e < e1; ++e) {
+      const float w = (float)ent_w[e];
+      const float2* src = F + (size_t)ent_idx[e] * N + z0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < nz) {
+          const float2 f = __ldg(src + i);
+          acc[2 * i] = fmaf(w, f.x, acc[2 * i]);
+          acc[2 * i + 1] = fmaf(w, f.y, acc[2 * i + 1]);
+        }
     }
   }
   const int ky = cell / N, kx = cell - ky * N;
   const float sg = ((kx + ky) & 1) ? -1.0f : 1.0f;
 #pragma unroll
   for (int i = 0; i < 8; ++i)
-    V[(size_t)(z0 + i) * NN + cell] = make_float2(sg * acc[2 * i], sg * acc[2 * i + 1]);
+    if (i < nz) V[(size_t)(z0 + i) * NN + cell] = make_float2(sg * acc[2 * i], sg * acc[2 * i + 1]);
 }
 
 // inverse FFT along x of P lines (rows of the N^2 x N array), in place
@@ -356,8 +373,8 @@ static cudaError_t grid_n(cpra_plan_s* p) {
   Assembly& a = p->asmb;
   cudaError_t e;
   g_launches += 3;  // gather, rows, columns
-  k_gather<<<dim3((N * N + 255) / 256, N / 8), 256, 0, st>>>(a.F, a.cell_ptr, a.ent_idx, a.ent_w,
-                                                            a.vol, N);
+  k_gather<<<dim3((N * N + 255) / 256, (N + 7) / 8), 256, 0, st>>>(a.F, a.cell_ptr, a.ent_idx,
+                                                                  a.ent_w, a.vol, N);
   {
     using T = RowTile<N>;
     const size_t smem = sizeof(float2) * (N + T::SMEM_LINES);

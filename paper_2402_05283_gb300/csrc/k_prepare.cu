@@ -9,14 +9,20 @@ std::atomic<long long> g_launches{0};
 // One block per (FFT-order row ky, angle).  A(k) = sqrt(I) at the centred
 // index of k; A_sym(k) = (A(k) + A(-k)) / 2 on the half plane kx <= N/2;
 // the full-plane sums of ((A(k) - A(-k))/2)^2 and A(k)^2 go to Cn and sumA2.
+// With a measured-pixel mask (centred, nonzero = measured; per angle when
+// mask_stride is N*N, one for all when 0) only the pairs {k, -k} with both
+// pixels measured are constrained: the others get A_sym = -1 (the modulus
+// projection leaves them free) and stay out of Cn and sumA2.
 __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* A_rows,
-                          float* A_nyq, double* Cn, double* sumA2, int* flag) {
+                          float* A_nyq, double* Cn, double* sumA2, int* flag,
+                          const uint8_t* __restrict__ mask, size_t mask_stride) {
   const int ky = blockIdx.x;
   const int n = first + blockIdx.y;
   const int h = N / 2;
   const float* In = I + (size_t)blockIdx.y * N * N;
   const int ry = (ky + h) % N;           // centred row of +ky
   const int my = (N - ky + h) % N;       // centred row of -ky
+  const uint8_t* Mn = mask ? mask + (size_t)n * mask_stride : nullptr;
   double c_part = 0.0, a_part = 0.0;
   int bad = 0;
   for (int kx = threadIdx.x; kx < N; kx += blockDim.x) {
@@ -25,12 +31,15 @@ __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* 
     float ip = In[(size_t)ry * N + rx];
     float im = In[(size_t)my * N + mx];
     if (!(ip >= 0.0f) || !isfinite(ip)) bad = 1;
+    const bool on = !Mn || (Mn[(size_t)ry * N + rx] && Mn[(size_t)my * N + mx]);
     float ap = sqrtf(fmaxf(ip, 0.0f));
     float am = sqrtf(fmaxf(im, 0.0f));
     double d = 0.5 * ((double)ap - (double)am);
-    c_part += d * d;
-    a_part += (double)ap * (double)ap;
-    float as = 0.5f * (ap + am);
+    if (on) {
+      c_part += d * d;
+      a_part += (double)ap * (double)ap;
+    }
+    float as = on ? 0.5f * (ap + am) : -1.0f;
     if (kx < h) A_rows[((size_t)blockIdx.y * N + ky) * h + kx] = as;
     if (kx == h) A_nyq[(size_t)n * N + ky] = as;
   }
@@ -89,7 +98,8 @@ cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count)
   float* rows = p->g_alt;
   g_launches += 2;
   k_prepare<<<grid, threads, 0, p->stream>>>(I, p->N, first, rows, p->A_nyq, p->Cn, p->sumA2,
-                                             p->flag);
+                                             p->flag, p->mask,
+                                             p->mask_per_angle ? (size_t)p->N * p->N : 0);
   const int h = p->N / 2;
   dim3 tg((h + 31) / 32, (p->N + 31) / 32, count);
   k_transpose_amp<<<tg, dim3(32, 8), 0, p->stream>>>(rows, p->A_main, p->N, first);

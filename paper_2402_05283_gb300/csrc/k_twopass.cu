@@ -103,6 +103,7 @@ k_prime(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 
 // ---------------------------------------------------------------- column pass
 __device__ __forceinline__ float2 project(float2 G, float a, double& err, double w) {
+  if (a < 0.0f) return G;  // an unmeasured pair (mask): free, no error term
   const float m = sqrtf(G.x * G.x + G.y * G.y);
   const double d = (double)m - (double)a;
   err += w * d * d;

@@ -75,7 +75,7 @@ def test_plan_bytes_scales(cp):
     (dict(wrap_mode=7), 1), (dict(blend_target=3), 1), (dict(hio_iters=-1), 1),
     (dict(shrinkwrap_every=5, sw_sigma=0.0), 1), (dict(precision=9), 1),
     (dict(update=2), 1), (dict(update=-1), 1), (dict(sweep=2), 1),
-    (dict(sweep=1, shrinkwrap_every=10), 6),
+    (dict(sweep=1, shrinkwrap_every=15), 6),
 ])
 def test_config_validation(cp, kw, status):
     N = kw.pop("N", 64)

@@ -239,6 +239,7 @@ def test_cfg1_final_reconstruction_quality(cp, cfg1):
 @pytest.mark.parametrize("N,Np,engine", [
     (16, 3, 1), (32, 5, 1), (48, 4, 1), (64, 3, 1), (96, 3, 1), (128, 2, 1), (192, 2, 1),
     (256, 2, 1), (384, 2, 1), (512, 2, 1), (768, 1, 1), (1024, 1, 1),
+    (160, 3, 1), (320, 2, 1),
     (64, 3, 3), (128, 2, 3), (256, 2, 3), (512, 2, 3), (1024, 1, 3)])
 def test_sizes_and_radices(cp, N, Np, engine):
     """Every supported radix chain and tile shape of both engines (1 = block-wide
@@ -252,6 +253,30 @@ def test_sizes_and_radices(cp, N, Np, engine):
     # ER steps 1..5 from the seeded start (continuous, so compare the trajectory)
     cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=0, er_iters=6, engine=engine)
     _check_traj(cp, d, cfg, 6, S)
+
+
+@pytest.mark.parametrize("N", [640, 700])
+def test_radix_5_and_7_sizes(cp, N):
+    """The paper's N = 640 (2^7 5) and N = 700 (2^2 5^2 7, its cell patterns)
+    on the block-wide engine: patterns of a random object in the central box
+    (2D, no phantom volume at this size), one HIO step with coupling, then
+    the first 6 ER iterates."""
+    Np = 2
+    rng = np.random.default_rng(N)
+    obj = np.zeros((Np, N, N))
+    q = N // 4
+    obj[:, q:N - q, q:N - q] = rng.random((Np, N - 2 * q, N - 2 * q))
+    I = np.fft.fftshift(np.abs(np.fft.fft2(obj)) ** 2, axes=(-2, -1)).astype(np.float32)
+    S = np.zeros((N, N), np.uint8)
+    S[q:N - q, q:N - q] = 1
+    d = {"I": I, "thetas": np.arange(Np) * np.pi / Np}
+    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=1, er_iters=5)
+    g0 = O.initial_guess(7, Np, N, np.broadcast_to(S.astype(bool), (Np, N, N)))
+    rel, erel, _ = _one_step(cp, d, cfg, S, g0, 0)
+    assert erel.max() < TOL, erel
+    cfg = cp.make_config(N, Np, n_ei=3, seed=2, hio_iters=0, er_iters=6)
+    worst, _ = _check_traj(cp, d, cfg, 6, S)
+    print(f"N={N}: one HIO step {rel.max():.2e}, 6 ER iterates {worst:.2e}")
 
 
 def test_single_angle_and_wide_taps(cp):
@@ -318,7 +343,7 @@ def test_assembly_matches_oracle(cp):
         plan.close()
 
 
-@pytest.mark.parametrize("N,Np", [(48, 5), (96, 3)])
+@pytest.mark.parametrize("N,Np", [(48, 5), (96, 3), (160, 3)])
 def test_assembly_sizes(cp, N, Np):
     d = synth.make_case("tiny", N=N, Np=Np)
     rng = np.random.default_rng(N)

@@ -80,6 +80,28 @@ def test_sweep_after_step_a_and_raar(cp, case):
     assert r < TOL and (np.abs(e - e_ref) / e_ref).max() < TOL
 
 
+def test_sweep_with_shrinkwrap_at_episode_ends(cp, case):
+    """Shrink-wrap every episode (sigma 2, tau 0.1) after ER sweeps: iterates
+    and supports equal to the oracle's."""
+    kw = dict(seed=6, hio_iters=0, er_iters=10, n_ei=5, shrinkwrap_every=5, sweep=1)
+    cfg = cp.make_config(64, 8, **kw)
+    plan = cp.Plan(cfg)
+    plan.load_intensities(case["I"], 0, case["thetas"])
+    plan.load_support(case["S_true"])
+    plan.iterate(10)
+    g = plan.result(cp.RESULT_STATE)
+    S = plan.result(cp.RESULT_SUPPORT).astype(bool)
+    plan.close()
+    oc = O.OracleConfig(N=64, Np=8, n_ei=5, hio_iters=0, er_iters=10, seed=6, sweep=True,
+                        shrinkwrap_every=5, sw_sigma=float(np.float32(cfg.sw_sigma)),
+                        sw_tau=float(np.float32(cfg.sw_tau)))
+    run = O.OracleRun.start(oc, case["I"], case["S_true"]).run(10)
+    assert np.array_equal(S, run.S)
+    r = _rel(g, run.g).max()
+    print(f"sweep + shrink-wrap: iterate {r:.2e}")
+    assert r < TOL
+
+
 def test_sweep_differs_from_jacobi_and_runs_whole_episodes(cp, case):
     kw = dict(seed=3, hio_iters=0, er_iters=10, n_ei=5)
     g_s, _, _, _ = _both(cp, case, 5, sweep=1, **kw)

@@ -402,6 +402,13 @@ def test_sweep_schedule():
         g = new
     run.run(4)
     assert np.array_equal(run.g, g) and run.t == 4 and len(run.errors) == 4
+    # shrink-wrap every episode: after each sweep, for every angle
+    cfg2 = O.OracleConfig(N=16, Np=2, n_ei=2, hio_iters=3, er_iters=1, seed=2, sweep=True,
+                          shrinkwrap_every=2, sw_sigma=1.0)
+    r2 = O.OracleRun.start(cfg2, I).run(2)
+    r1 = O.OracleRun.start(cfg, I).run(2)
+    assert np.array_equal(r2.g, r1.g)
+    assert np.array_equal(r2.S, O.shrinkwrap(r1.g, r1.S, 1.0, 0.1))
 
 
 def test_coupling_present_mask_hand_case():
