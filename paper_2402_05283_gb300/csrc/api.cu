@@ -353,6 +353,7 @@ Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles, int first_til
   L.N = p->N;
   L.engine = p->engine;
   L.prec = p->cfg.precision;
+  L.masked = p->masked;
   L.stream = p->stream;
   L.js = p->d_js;
   L.st = p->d_steps + step;
@@ -741,6 +742,7 @@ cpra_status cpra_load_intensities(cpra_plan_t p, const float* I, int32_t first, 
     }
     p->asmb.ready = false;
   }
+  if (p->mask) p->masked = true;
   for (int i = 0; i < count; ++i)
     if (!p->loaded[first + i]) {
       p->loaded[first + i] = 1;
@@ -1589,9 +1591,13 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
       b->graph_sig.clear();
     }
   }
-  // step tables (and the launch pattern) of every group for this call
+  // step tables (and the launch pattern) of every group for this call; the
+  // last G entries of the pattern: whether a group runs the masked kernels
   const size_t G = b->groups.size();
-  std::vector<char> sig((size_t)n_iters * G, 0);
+  std::vector<char> sig((size_t)n_iters * G + G, 0);
+  for (size_t gi = 0; gi < G; ++gi)
+    for (int j : b->groups[gi].members)
+      if (b->plans[j]->masked) sig[(size_t)n_iters * G + gi] = 1;
   std::vector<std::vector<JobStep>> steps(G);
   for (size_t gi = 0; gi < G; ++gi) {
     auto& g = b->groups[gi];
@@ -1675,6 +1681,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
         L.N = g.N;
         L.engine = g.engine;
         L.prec = g.prec;
+        L.masked = sig[(size_t)n_iters * G + gi];
         L.stream = on;
         L.js = g.d_js;
         L.st = g.d_steps + (size_t)i * g.members.size();

@@ -75,6 +75,7 @@ struct cpra_plan_s {
   float* po_tmp = nullptr;
   uint8_t* mask = nullptr;     // measured-pixel mask (cpra_load_mask), centred; NULL = all
   bool mask_per_angle = false;
+  bool masked = false;         // intensities were loaded under a mask (kernels check A_sym < 0)
   cpra::Assembly asmb;
   // Step C merge scratch (cpra_merge with this plan as destination)
   float2* mg_acc = nullptr;    // [Np][N][N] merged spectra (sums, then the mean)
@@ -137,11 +138,18 @@ enum Algo { kHIO = 0, kER = 1, kRAAR = 2 };
 //        reflections R = 2P - I): R_M g = 2g' - g, so g' where 2g' - g lies
 //        in the support-positivity set, beta g + (1 - 2 beta) g' elsewhere;
 //        c2 = 1 - 2 beta.
+template <int ALGO>
+__device__ __forceinline__ float update_pixel_t(float g, float gp, bool in_s, float beta, float c2) {
+  if constexpr (ALGO == kRAAR) return (in_s && fmaf(2.0f, gp, -g) >= 0.0f) ? gp : fmaf(beta, g, c2 * gp);
+  const bool v = in_s && gp >= 0.0f;
+  if constexpr (ALGO == kHIO) return v ? gp : fmaf(-beta, gp, g);
+  return v ? gp : 0.0f;
+}
 __device__ __forceinline__ float update_pixel(float g, float gp, bool in_s, int algo, float beta,
                                               float c2) {
-  if (algo == kRAAR) return (in_s && fmaf(2.0f, gp, -g) >= 0.0f) ? gp : fmaf(beta, g, c2 * gp);
-  if (in_s && gp >= 0.0f) return gp;
-  return algo == kHIO ? fmaf(-beta, gp, g) : 0.0f;
+  if (algo == kRAAR) return update_pixel_t<kRAAR>(g, gp, in_s, beta, c2);
+  if (algo == kHIO) return update_pixel_t<kHIO>(g, gp, in_s, beta, c2);
+  return update_pixel_t<kER>(g, gp, in_s, beta, c2);
 }
 
 // prepare / state kernels (k_prepare.cu)
@@ -208,6 +216,7 @@ struct Launch {
   int N;
   int engine;
   int prec;  // CPRA_FP32 / CPRA_BF16_TC / CPRA_FP16_TC
+  int masked;  // some amplitude carries the missing-data sentinel (A_sym < 0)
   cudaStream_t stream;
   const JobStatic* js;
   const JobStep* st;

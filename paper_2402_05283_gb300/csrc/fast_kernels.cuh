@@ -42,6 +42,27 @@ __device__ __forceinline__ void lines_inv(float2 (&b)[FL::TB][FL::E2], float2 (&
   else warp_fft_inv<N, PREC>(b, a, T, xs, lane, tc);
 }
 
+// v = row `lane` of a 32 x 32 bit matrix (bit c = column c); returns column
+// `lane`: five butterfly rounds that swap the off-diagonal blocks of size
+// 16, 8, 4, 2, 1 between lane pairs.
+__device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t v, int lane) {
+  static_for<0, 5>([&](auto KK) {
+    constexpr int j = 16 >> decltype(KK)::value;
+    constexpr uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                         : j == 2 ? 0x33333333u : 0x55555555u;
+    const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+    v = (lane & j) ? ((v & ~m) | ((o >> j) & m)) : ((v & m) | ((o & m) << j));
+  });
+  return v;
+}
+
+// The one-line 512-point plan holds pixels x = lane + 32 m (m < 16) of two
+// rows, so its support bits are the 32 words of those rows (16 each) read
+// one a lane and transposed: bit 16 r + m of the result is the bit of pixel
+// lane + 32 m in row r.
+template <int N, class FL>
+constexpr bool kRowMaskInRegs = kSlimLines<FL> && FL::L == 1 && N == 512;
+
 // per-warp shared memory of the row kernels: transpose tile + the warp's g
 // rows; 4 warps a block with the L-line plans, 8 with the one-line plan
 template <int N, class FL_> struct RowCfg {
@@ -184,6 +205,9 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     }
     err_acc[n] = 0.0;
   }
+  uint32_t smask = 0;  // the one-line plan's support bits (kRowMaskInRegs)
+  if constexpr (kRowMaskInRegs<N, FL>)
+    smask = __ldg(S + ((size_t)n * N + 2 * pair0 + (lane >> 4)) * W + (lane & 15));
   load_xtw<N>(xs, xtw, RW::WARPS * 32);
   cp_async_wait_group<1>();  // this lane's spectrum copies have landed
   __syncthreads();           // xs, and every lane's copies
@@ -210,34 +234,48 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   __syncwarp();  // the tile is the transforms' scratch from here on
   float2 a[FL::TA][FL::E1];
   lines_inv<N, PREC, FL>(b, a, T, xs, lane, &tc);
+  if constexpr (kRowMaskInRegs<N, FL>) smask = warp_bit_transpose(smask, lane);
   cp_async_wait_all();
   __syncwarp();
   const float inv = 1.0f / N;
-  static_for<0, FL::TA>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const int line = FL::a_line(t);
-    const int y0 = 2 * (pair0 + line);
-    float* g0 = g + ((size_t)n * N + y0) * N;
-    float* g1 = g0 + N;
-    const float* o0s = Gs + (2 * line) * N;
-    const float* o1s = o0s + N;
-    const uint32_t* s0 = S + ((size_t)n * N + y0) * W;
-    const uint32_t* s1 = s0 + W;
-    static_for<0, FL::E1>([&](auto MM) {
-      constexpr int m = decltype(MM)::value;
-      const int x = FL::a_x(t, m);
-      const float2 z = a[i][m];
-      const float gp0 = z.x * inv, gp1 = z.y * inv;
-      const bool in0 = (__ldg(s0 + (x >> 5)) >> (x & 31)) & 1u;
-      const bool in1 = (__ldg(s1 + (x >> 5)) >> (x & 31)) & 1u;
-      const float n0 = update_pixel(o0s[x], gp0, in0, algo, beta, c2);
-      const float n1 = update_pixel(o1s[x], gp1, in1, algo, beta, c2);
-      g0[x] = n0;
-      g1[x] = n1;
-      a[i][m] = make_float2(n0, n1);
+  // the real-space rule is uniform over the launch: one specialised loop each
+  auto update_rows = [&](auto AA) {
+    constexpr int ALGO = decltype(AA)::value;
+    static_for<0, FL::TA>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      const int t = lane + 32 * i;
+      const int line = FL::a_line(t);
+      const int y0 = 2 * (pair0 + line);
+      float* g0 = g + ((size_t)n * N + y0) * N;
+      float* g1 = g0 + N;
+      const float* o0s = Gs + (2 * line) * N;
+      const float* o1s = o0s + N;
+      const uint32_t* s0 = S + ((size_t)n * N + y0) * W;
+      const uint32_t* s1 = s0 + W;
+      static_for<0, FL::E1>([&](auto MM) {
+        constexpr int m = decltype(MM)::value;
+        const int x = FL::a_x(t, m);
+        const float2 z = a[i][m];
+        const float gp0 = z.x * inv, gp1 = z.y * inv;
+        bool in0, in1;
+        if constexpr (kRowMaskInRegs<N, FL>) {
+          in0 = (smask >> m) & 1u;
+          in1 = (smask >> (16 + m)) & 1u;
+        } else {
+          in0 = (__ldg(s0 + (x >> 5)) >> (x & 31)) & 1u;
+          in1 = (__ldg(s1 + (x >> 5)) >> (x & 31)) & 1u;
+        }
+        const float n0 = update_pixel_t<ALGO>(o0s[x], gp0, in0, beta, c2);
+        const float n1 = update_pixel_t<ALGO>(o1s[x], gp1, in1, beta, c2);
+        g0[x] = n0;
+        g1[x] = n1;
+        a[i][m] = make_float2(n0, n1);
+      });
     });
-  });
+  };
+  if (algo == kHIO) update_rows(std::integral_constant<int, kHIO>{});
+  else if (algo == kER) update_rows(std::integral_constant<int, kER>{});
+  else update_rows(std::integral_constant<int, kRAAR>{});
   if (!forward) return;
   lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
   store_pairs_w<N, FL>(b, T, Hn, pair0, lane);
@@ -358,12 +396,14 @@ template <int N, int PREC> struct ColW {
 template <int N, int PREC>
 constexpr size_t col_smem() { return ColW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(ColW<N, PREC>::WARPS); }
 
-// G' = a G / |G| (a where G = 0); err += w (|G| - a)^2; a < 0 marks a pixel
-// left free by a missing-data mask.  The per-thread
+// G' = a G / |G| (a where G = 0); err += w (|G| - a)^2; in plans with a
+// missing-data mask (MASKED), a < 0 marks a pixel left free.  The per-thread
 // partial sum stays in FP32 (at most a few hundred terms); the reduction
 // across threads, blocks and columns is FP64.
+template <bool MASKED>
 __device__ __forceinline__ float2 project_w(float2 G, float a, float& err, float w) {
-  if (a < 0.0f) return G;  // an unmeasured pair (mask): free, no error term
+  if constexpr (MASKED)
+    if (a < 0.0f) return G;  // an unmeasured pair (mask): free, no error term
   const float r2 = fmaf(G.x, G.x, G.y * G.y);
   if (r2 > 0.0f) {
     const float inv = rsqrtf(r2);
@@ -376,7 +416,7 @@ __device__ __forceinline__ float2 project_w(float2 G, float a, float& err, float
   return make_float2(a, 0.0f);
 }
 
-template <int N, int PREC>
+template <int N, int PREC, bool MASKED>
 __global__ void __launch_bounds__(ColW<N, PREC>::NT, ColW<N, PREC>::MINB)
 k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
             const int2* __restrict__ tiles) {
@@ -435,7 +475,7 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       const float* Ac = As + col * N;
       static_for<0, FL::E2>([&](auto KK) {
         constexpr int j = decltype(KK)::value;
-        b[i][j] = project_w(b[i][j], Ac[FL::b_k(t, j)], err, 2.0f);
+        b[i][j] = project_w<MASKED>(b[i][j], Ac[FL::b_k(t, j)], err, 2.0f);
       });
     }
   });
@@ -464,8 +504,8 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
           const float2 z = T[ky], zm = T[(N - ky) % N];
           const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
           const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-          const float2 p0 = project_w(g0, A0[ky], err, 1.0f);
-          const float2 pn = project_w(gn, __ldg(An + ky), err, 1.0f);
+          const float2 p0 = project_w<MASKED>(g0, A0[ky], err, 1.0f);
+          const float2 pn = project_w<MASKED>(gn, __ldg(An + ky), err, 1.0f);
           b[i][j] = make_float2(p0.x - pn.y, p0.y + pn.x);
         });
       }
@@ -512,7 +552,8 @@ static cudaError_t prepare_w() {
   if (done) return cudaSuccess;
   cudaError_t e = smem_attr(k_rowpass_w<N, PREC>, row_smem<N, PREC>());
   if (e == cudaSuccess) e = smem_attr(k_prime_w<N, PREC>, prime_smem<N, PREC>());
-  if (e == cudaSuccess) e = smem_attr(k_colpass_w<N, PREC>, col_smem<N, PREC>());
+  if (e == cudaSuccess) e = smem_attr(k_colpass_w<N, PREC, false>, col_smem<N, PREC>());
+  if (e == cudaSuccess) e = smem_attr(k_colpass_w<N, PREC, true>, col_smem<N, PREC>());
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -549,7 +590,8 @@ static cudaError_t colpass_w(const Launch& L) {
   if (e != cudaSuccess) return e;
   dim3 grid((N / 2) / C::CB, L.ntiles);
   g_launches += 1;
-  k_colpass_w<N, PREC><<<grid, C::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
+  if (L.masked) k_colpass_w<N, PREC, true><<<grid, C::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
+  else k_colpass_w<N, PREC, false><<<grid, C::NT, smem, L.stream>>>(L.js, L.st, L.tiles);
   return cudaGetLastError();
 }
 

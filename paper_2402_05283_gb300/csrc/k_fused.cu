@@ -196,7 +196,7 @@ __device__ __forceinline__ void support_mask(uint32_t (&mk)[FusedCfg<N>::MASKW],
   });
 }
 
-template <int N>
+template <int N, bool MASKED>
 __global__ void __launch_bounds__(FusedCfg<N>::NT, FusedCfg<N>::MINB)
 k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
         const int2* __restrict__ tiles) {
@@ -300,7 +300,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       if (cg0 + FL::b_line(t) != 0) {
         static_for<0, FL::E2>([&](auto KK) {
           constexpr int j = decltype(KK)::value;
-          b[i][j] = project_w(b[i][j], av[i][j], err, 2.0f);
+          b[i][j] = project_w<MASKED>(b[i][j], av[i][j], err, 2.0f);
         });
       }
     });
@@ -328,8 +328,8 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
             const float2 z = T[ky], zm = T[(N - ky) % N];
             const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
             const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-            const float2 p0 = project_w(g0, av[i][j], err, 1.0f);
-            const float2 pn = project_w(gn, __ldg(An + ky), err, 1.0f);
+            const float2 p0 = project_w<MASKED>(g0, av[i][j], err, 1.0f);
+            const float2 pn = project_w<MASKED>(gn, __ldg(An + ky), err, 1.0f);
             b[i][j] = make_float2(p0.x - pn.y, p0.y + pn.x);
           });
         }
@@ -436,9 +436,13 @@ static cudaError_t fused_prepare() {
   static cudaError_t err = cudaSuccess;
   if (done) return err;
   using F = FusedCfg<N>;
-  err = cudaFuncSetAttribute(k_fused<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
+  err = cudaFuncSetAttribute(k_fused<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fused<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
   if (err == cudaSuccess && F::C > 8)
-    err = cudaFuncSetAttribute(k_fused<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    err = cudaFuncSetAttribute(k_fused<N, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (err == cudaSuccess && F::C > 8)
+    err = cudaFuncSetAttribute(k_fused<N, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (err == cudaSuccess) {
     // a cluster of C CTAs with this much shared memory must fit on the device
     cudaLaunchConfig_t cfg = {};
@@ -453,7 +457,7 @@ static cudaError_t fused_prepare() {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int clusters = 0;
-    err = cudaOccupancyMaxActiveClusters(&clusters, k_fused<N>, &cfg);
+    err = cudaOccupancyMaxActiveClusters(&clusters, k_fused<N, false>, &cfg);
     if (err == cudaSuccess && clusters < 1) err = cudaErrorNotSupported;
   }
   done = true;
@@ -478,7 +482,8 @@ static cudaError_t fused_launch(const Launch& L) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   g_launches += 1;
-  return cudaLaunchKernelEx(&cfg, k_fused<N>, L.js, L.st, L.tiles);
+  if (L.masked) return cudaLaunchKernelEx(&cfg, k_fused<N, true>, L.js, L.st, L.tiles);
+  return cudaLaunchKernelEx(&cfg, k_fused<N, false>, L.js, L.st, L.tiles);
 }
 
 #define CPRA_FOR_EACH_FUSED_N(X) X(64) X(128) X(256) X(512)
