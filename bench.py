@@ -119,8 +119,8 @@ def make_inputs(device, n_angles=NP):
 # profiles/k_rowpass_w_k_colpass_w_n512_np180.md (180 angles a launch; every
 # angle moves the same bytes, so a launch's traffic scales with its angles).
 # Valid only while the kernel is the one captured there.
-NCU_TRAFFIC_PER_ANGLE = {("k_rowpass", 512): (383.465472e6 + 316.068352e6) / 180,
-                         ("k_colpass", 512): (283.662848e6 + 135.292672e6) / 180}
+NCU_TRAFFIC_PER_ANGLE = {("k_rowpass", 512): (383.463168e6 + 316.570368e6) / 180,
+                         ("k_colpass", 512): (283.570176e6 + 135.188480e6) / 180}
 
 
 def roofline_figures(plan, cp, peaks, Np_total, angle_iters):
@@ -342,7 +342,7 @@ def form_refine(cp, torch, plan, iters=50, shrink_every=5):
 
 
 def form_cell_pipeline(cp, torch, N_=700, Np_=27, n_r=100, n_l=10, n_pre=500, n_e=2, n_ei=10,
-                       refine_iters=50, n_streams=8, seed=7):
+                       refine_iters=50, seed=7):
     """The whole method at the sizes of the paper's cell data (its results
     section: N = 700 with 27 patterns; RAAR beta 0.9; Step A 500 iterations
     on the first pattern; two episodes of 10; a CSWA step at each episode
@@ -350,30 +350,31 @@ def form_cell_pipeline(cp, torch, N_=700, Np_=27, n_r=100, n_l=10, n_pre=500, n_
     iterations with the support shrunk every 5).  Patterns: a seeded
     6-ellipsoid phantom of 350^3 voxels, 1e6 photons (the data are not
     available).  Step B runs as the Gauss-Seidel sweep the text describes;
-    the guesses run on n_streams CUDA streams."""
+    the guesses run as one batch (Step A as rows over every guess's first
+    pattern, then one launch per angle of the sweep over all guesses)."""
     import synth
     t_gen = time.perf_counter()
     d = synth.make_case("cfg1", device="cuda", N=N_, Np=Np_, request=seed)
     I, th = d["I"].contiguous(), d["thetas"]
     t_gen = time.perf_counter() - t_gen
-    streams = [torch.cuda.Stream() for _ in range(n_streams)]
     T = n_e * n_ei
     er = n_ei // 2  # ER in the second half of the last episode: ranks object estimates
     plans = []
     for i in range(n_r):
         cfg = cp.make_config(N_, Np_, seed=1000 + i, hio_iters=T - er, er_iters=er, n_ei=n_ei,
                              n_pre=n_pre, update=cp.UPDATE_RAAR, sweep=1, shrinkwrap_every=n_ei)
-        p = cp.Plan(cfg, stream=streams[i % n_streams].cuda_stream)
+        p = cp.Plan(cfg)
         p.load_intensities(I, 0, th)
         plans.append(p)
     dst = cp.Plan(cp.make_config(N_, Np_, shrinkwrap_every=n_ei, n_ei=n_ei))
     dst.load_intensities(I, 0, th)
+    batch = cp.Batch(plans, use_graph=False)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for p in plans:  # Steps A and B of every guess, queued on its stream
-        p.iterate(T)
+    batch.iterate(T)  # Steps A and B of every guess
     torch.cuda.synchronize()
     t_ab = time.perf_counter() - t0
+    batch.close()
     t1 = time.perf_counter()
     prtf = torch.zeros((Np_, N_ // 2), device="cuda")
     sel, inv = cp.cpra_merge(plans, n_l, 0, dst, prtf)  # Step C (and the Step D volume)

@@ -130,8 +130,8 @@ enum {
  *                  pre-reconstructed PO around the whole carousel.  Calls
  *                  run whole episodes (t and n_iters multiples of n_ei);
  *                  shrink-wrap runs at episode ends (shrinkwrap_every a
- *                  multiple of n_ei); no present mask or batch
- *                  (UNSUPPORTED).
+ *                  multiple of n_ei); no present mask (UNSUPPORTED);
+ *                  batches run many sweep plans together.
  *   seed           seeds the random initial guess (SplitMix64 per pixel).
  *   alloc, free, alloc_ctx  device allocator; NULL alloc = cudaMalloc.
  */
@@ -386,8 +386,14 @@ cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_in, uint8_t*
 typedef struct cpra_batch_s* cpra_batch_t;
 
 /* plans: n plans (n >= 1) on the same device, all using plans[0]'s stream.
- * Plans must not use shrink-wrap (UNSUPPORTED) and must stay alive until
- * cpra_batch_destroy.  The batch holds device tables only (a few KB). */
+ * Jacobi plans must not use shrink-wrap (UNSUPPORTED).  Gauss-Seidel plans
+ * (sweep 1) of the same N, engine and n_ei form a group whose sweeps run
+ * together: their Step A as rows over every member's angle 0, then one
+ * launch per angle of the sweep (fused engine; prime + n_ei column and row
+ * launches otherwise) over every member that has that angle, shrink-wrap at
+ * episode ends; calls must run whole episodes (INVALID_ARG otherwise) and
+ * are not captured in a graph.  Plans must stay alive until
+ * cpra_batch_destroy.  The batch holds device tables only. */
 cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_graph,
                               cpra_batch_t* out);
 

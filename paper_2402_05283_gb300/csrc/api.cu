@@ -1169,7 +1169,7 @@ cpra_status cpra_refine_3d(cpra_plan_t p, int32_t n_iters, int32_t shrink_every,
     if (!p->rf_err) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "refinement allocation failed");
     p->rf_err_cap = n_iters;
   }
-  RefineArgs a{N, W3, p->rf_X, p->rf_V, p->rf_R, p->rf_B, p->rf_S3, p->rf_M, p->tw};
+  RefineArgs a{N, W3, p->rf_X, p->rf_V, p->rf_R, p->rf_B, p->rf_S3, p->rf_M, p->tw, p->xtw};
   cudaStream_t st = p->stream;
   if (p->vol_state == 1) {  // start from the Step D volume of the last assemble / merge
     // each 2D support moves with its PO: the whole-pixel part of its
@@ -1377,6 +1377,10 @@ struct cpra_batch_s {
     JobStatic* d_js = nullptr;
     int2* d_tiles = nullptr;   // room for every angle of every member
     int ntiles = 0;
+    // Gauss-Seidel groups: one launch per angle of the sweep over all members
+    int sweep = 0, n_ei = 0, np_max = 0;
+    int2* d_sweep_tiles = nullptr;  // [np_max][members]: (j, n) of the members with Np_j > n
+    std::vector<int> sweep_count;   // tiles of angle n
     std::vector<int64_t> versions;  // members' present-mask versions the tiles follow
     JobStep* d_steps = nullptr;
     int64_t steps_cap = 0;
@@ -1401,6 +1405,12 @@ cpra_status bfail(cpra_batch_s* b, cpra_status st, const std::string& msg) {
   g_last_error = msg;
   return st;
 }
+
+#define CK_B(expr, where)                                                               \
+  do {                                                                                  \
+    cudaError_t _e = (expr);                                                            \
+    if (_e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
 
 // (member, angle) tiles of a group: every iterating angle of every member
 cudaError_t group_tiles(cpra_batch_s* b, cpra_batch_s::Group& g) {
@@ -1506,10 +1516,10 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
   if (!plans || n < 1) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "need at least one plan");
   for (int i = 0; i < n; ++i) {
     if (!plans[i]) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "NULL plan in batch");
-    if (plans[i]->cfg.shrinkwrap_every > 0)
-      return bfail(nullptr, CPRA_ERR_UNSUPPORTED, "batches run plans without shrink-wrap");
-    if (plans[i]->cfg.sweep)
-      return bfail(nullptr, CPRA_ERR_UNSUPPORTED, "batches run Jacobi episodes (sweep 0)");
+    if (plans[i]->cfg.shrinkwrap_every > 0 && !plans[i]->cfg.sweep)
+      return bfail(nullptr, CPRA_ERR_UNSUPPORTED, "batches run Jacobi plans without shrink-wrap");
+    if (plans[i]->cfg.sweep && plans[i]->stream != plans[0]->stream)
+      return bfail(nullptr, CPRA_ERR_UNSUPPORTED, "Gauss-Seidel members share the batch's stream");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "plan listed twice");
   }
@@ -1528,13 +1538,16 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
     size_t gi = 0;
     for (; gi < b->groups.size(); ++gi)
       if (b->groups[gi].N == p->N && b->groups[gi].engine == p->engine &&
-          b->groups[gi].prec == p->cfg.precision)
+          b->groups[gi].prec == p->cfg.precision && b->groups[gi].sweep == p->cfg.sweep &&
+          (!p->cfg.sweep || b->groups[gi].n_ei == p->cfg.n_ei))
         break;
     if (gi == b->groups.size()) {
       cpra_batch_s::Group g;
       g.N = p->N;
       g.engine = p->engine;
       g.prec = p->cfg.precision;
+      g.sweep = p->cfg.sweep;
+      g.n_ei = p->cfg.n_ei;
       b->groups.push_back(g);
     }
     b->groups[gi].members.push_back(i);
@@ -1549,6 +1562,22 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
       return bfail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "batch tables");
     }
     cudaError_t e = group_tiles(b, g);
+    if (e == cudaSuccess && g.sweep) {
+      const int m = (int)g.members.size();
+      for (int mi : g.members) g.np_max = std::max(g.np_max, b->plans[mi]->Np);
+      std::vector<int2> st((size_t)g.np_max * m, make_int2(0, 0));
+      g.sweep_count.assign(g.np_max, 0);
+      for (int n = 0; n < g.np_max; ++n)
+        for (int j = 0; j < m; ++j)
+          if (b->plans[g.members[j]]->Np > n) st[(size_t)n * m + g.sweep_count[n]++] = make_int2(j, n);
+      g.d_sweep_tiles = (int2*)balloc(b, sizeof(int2) * st.size());
+      if (!g.d_sweep_tiles) {
+        cpra_batch_destroy(b);
+        return bfail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "batch tables");
+      }
+      e = cudaMemcpyAsync(g.d_sweep_tiles, st.data(), sizeof(int2) * st.size(), cudaMemcpyHostToDevice,
+                          b->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess) e = prepare_kernels(g.N, g.engine, g.prec);
     if (e != cudaSuccess) {
@@ -1560,20 +1589,185 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
   return CPRA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// upload steps to a group's table (grown as needed; the group's graph, if
+// any, is never used for Gauss-Seidel groups)
+cudaError_t group_steps(cpra_batch_s* b, cpra_batch_s::Group& g, const std::vector<JobStep>& steps) {
+  const int64_t need = (int64_t)steps.size();
+  cudaError_t e = cudaSuccess;
+  if (need > g.steps_cap) {
+    e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return e;
+    if (g.d_steps) {
+      for (size_t k = 0; k < b->owned.size(); ++k)
+        if (b->owned[k] == g.d_steps) {
+          b->owned.erase(b->owned.begin() + k);
+          break;
+        }
+      cudaFree(g.d_steps);
+      g.d_steps = nullptr;
+    }
+    g.d_steps = (JobStep*)balloc(b, sizeof(JobStep) * need);
+    if (!g.d_steps) return cudaErrorMemoryAllocation;
+    g.steps_cap = need;
+  }
+  return need ? cudaMemcpyAsync(g.d_steps, steps.data(), sizeof(JobStep) * need, cudaMemcpyHostToDevice,
+                                b->stream)
+              : cudaSuccess;
+}
+
+// Steps A and B of a Gauss-Seidel group: Step A of every member that has not
+// started, as rows over the members' angle 0, then whole sweeps, one launch
+// (or prime + n_ei column and row launches) per angle over every member that
+// has that angle.  Every member computes what cpra_iterate computes.
+cpra_status batch_sweep_group(cpra_batch_s* b, cpra_batch_s::Group& g, int32_t n_iters) {
+  const size_t m = g.members.size();
+  const int E = g.n_ei;
+  const bool fused = g.engine == CPRA_ENGINE_FUSED;
+  cudaStream_t st = b->stream;
+  for (int mi : g.members) {
+    const cpra_plan_s* p = b->plans[mi];
+    if ((p->state_ready && p->t % E != 0) || n_iters % E != 0)
+      return bfail(b, CPRA_ERR_INVALID_ARG, "Gauss-Seidel sweeps run whole episodes (t and n_iters multiples of n_ei)");
+  }
+  std::vector<JobStatic> js;
+  bool masked = false;
+  for (int mi : g.members) {
+    js.push_back(job_static(b->plans[mi]));
+    masked = masked || b->plans[mi]->masked;
+  }
+  cudaError_t e = cudaMemcpyAsync(g.d_js, js.data(), sizeof(JobStatic) * m, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+  auto launch = [&](int64_t row, int n, bool prime, bool iterate) -> cudaError_t {
+    Launch L;
+    L.N = g.N;
+    L.engine = g.engine;
+    L.prec = g.prec;
+    L.masked = masked;
+    L.stream = st;
+    L.js = g.d_js;
+    L.st = g.d_steps + row * (int64_t)m;
+    L.tiles = g.d_sweep_tiles + (size_t)n * m;
+    L.ntiles = g.sweep_count[n];
+    if (fused) return launch_fused(L);
+    cudaError_t r = prime ? launch_prime(L) : cudaSuccess;
+    if (r == cudaSuccess && iterate) r = launch_colpass(L);
+    if (r == cudaSuccess && iterate) r = launch_rowpass(L);
+    return r;
+  };
+  // Step A (n_pre iterations of the update rule on angle 0) of the members that start now
+  int pre = 0;
+  std::vector<int> pre_j(m, 0);
+  for (size_t j = 0; j < m; ++j) {
+    cpra_plan_s* p = b->plans[g.members[j]];
+    if (p->state_ready) continue;
+    CK_B(launch_init_guess(p), "initial guess");
+    pre_j[j] = p->cfg.n_pre;
+    pre = std::max(pre, pre_j[j]);
+  }
+  if (pre > 0) {
+    const int rows = fused ? 1 : pre;
+    std::vector<JobStep> steps((size_t)rows * m);
+    for (int it = 0; it < rows; ++it)
+      for (size_t j = 0; j < m; ++j) {
+        if (it >= pre_j[j]) continue;  // inactive: no prime, no iteration
+        cpra_plan_s* p = b->plans[g.members[j]];
+        JobStep& s = steps[(size_t)it * m + j];
+        s.prime = it == 0;
+        s.ca = plain_args();
+        s.g_src = p->g;
+        s.g = p->g;
+        s.err_slot = -1;
+        s.algo = update_rule(p->cfg);
+        s.forward = it + 1 < pre_j[j];
+        s.active = 1;
+        s.n_iters = pre_j[j];
+        s.hio_left = pre_j[j];
+      }
+    e = group_steps(b, g, steps);
+    for (int it = 0; e == cudaSuccess && it < rows; ++it) e = launch(it, 0, it == 0, true);
+    if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch Step A: ") + cudaGetErrorString(e));
+  }
+  for (int mi : g.members) {
+    cpra_plan_s* p = b->plans[mi];
+    p->state_ready = true;
+    p->hp_valid = false;
+  }
+  const int per_n = fused ? 1 : E;
+  for (int ep = 0; ep < n_iters / E; ++ep) {
+    std::vector<JobStep> steps((size_t)g.np_max * per_n * m);
+    for (int n = 0; n < g.np_max; ++n)
+      for (int it = 0; it < per_n; ++it)
+        for (size_t j = 0; j < m; ++j) {
+          cpra_plan_s* p = b->plans[g.members[j]];
+          if (n >= p->Np) continue;
+          const cpra_config& c = p->cfg;
+          const int64_t t = p->t;
+          JobStep& s = steps[((size_t)n * per_n + it) * m + j];
+          s.prime = it == 0;
+          s.ca = it == 0 ? coupling_args(c) : plain_args();
+          s.g_src = p->g;
+          s.g_dst = p->g_alt;
+          s.g = p->g_alt;
+          s.err_slot = t + it;
+          s.algo = t + it < c.hio_iters ? update_rule(c) : kER;
+          s.forward = it + 1 < E;
+          s.active = 1;
+          s.n_iters = E;
+          s.hio_left = (int)std::max<int64_t>(0, std::min<int64_t>(E, (int64_t)c.hio_iters - t));
+        }
+    e = group_steps(b, g, steps);
+    for (int n = 0; e == cudaSuccess && n < g.np_max; ++n)
+      for (int it = 0; e == cudaSuccess && it < per_n; ++it)
+        e = launch((int64_t)n * per_n + it, n, it == 0, true);
+    if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
+    for (int mi : g.members) {
+      cpra_plan_s* p = b->plans[mi];
+      std::swap(p->g, p->g_alt);
+      p->t += E;
+      p->hp_valid = false;
+      if (p->cfg.shrinkwrap_every > 0 && p->t % p->cfg.shrinkwrap_every == 0) {
+        e = launch_shrinkwrap(p);  // the members share the batch's stream
+        if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch shrink-wrap: ") + cudaGetErrorString(e));
+      }
+    }
+    // the next episode's table overwrites this one: wait for its launches
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
+  }
+  return CPRA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
   if (!b) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "batch is NULL");
   if (n_iters < 0) return bfail(b, CPRA_ERR_INVALID_ARG, "n_iters < 0");
   for (cpra_plan_s* p : b->plans)
     if (!present_loaded(p)) return bfail(b, CPRA_ERR_NOT_READY, "a plan lacks intensities");
   for (cpra_plan_s* p : b->plans) {
-    if (!p->state_ready) {  // seeded start and Step A through the plan itself
+    if (!p->state_ready && !p->cfg.sweep) {  // seeded start and Step A through the plan itself
       cpra_status st = cpra_iterate(p, 0, nullptr);
       if (st != CPRA_OK) return bfail(b, st, p->err);
     }
     cpra_status st = ensure_err_cap(p, p->t + n_iters);
     if (st != CPRA_OK) return bfail(b, st, p->err);
   }
-  if (n_iters == 0) return CPRA_OK;
+  bool jacobi = false;
+  for (auto& g : b->groups) {
+    if (!g.sweep) {
+      jacobi = true;
+      continue;
+    }
+    cpra_status st = batch_sweep_group(b, g, n_iters);
+    if (st != CPRA_OK) return st;
+  }
+  if (n_iters == 0 || !jacobi) return CPRA_OK;
   cudaStream_t stream = b->stream;
   for (auto& g : b->groups) {  // present masks changed since the tiles were built
     bool stale = false;
@@ -1602,6 +1796,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
   for (size_t gi = 0; gi < G; ++gi) {
     auto& g = b->groups[gi];
     const size_t m = g.members.size();
+    if (g.sweep) continue;
     if (g.engine == CPRA_ENGINE_FUSED) {
       // rounds of windows: round r launches every member's r-th window
       // (members with none left sit the round out)
@@ -1630,7 +1825,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
   for (int i = 0; i < n_iters; ++i)
     for (size_t gi = 0; gi < G; ++gi) {
       auto& g = b->groups[gi];
-      if (g.engine == CPRA_ENGINE_FUSED) continue;
+      if (g.engine == CPRA_ENGINE_FUSED || g.sweep) continue;
       const size_t m = g.members.size();
       for (size_t j = 0; j < m; ++j) {
         JobStep s = next_step(b->plans[g.members[j]]);
@@ -1640,6 +1835,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
     }
   for (size_t gi = 0; gi < G; ++gi) {
     auto& g = b->groups[gi];
+    if (g.sweep) continue;
     std::vector<JobStatic> js;
     for (int mi : g.members) js.push_back(job_static(b->plans[mi]));
     cudaError_t e = cudaMemcpyAsync(g.d_js, js.data(), sizeof(JobStatic) * js.size(),
@@ -1677,6 +1873,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
     for (int i = 0; i < n_iters; ++i)
       for (size_t gi = 0; gi < G; ++gi) {
         auto& g = b->groups[gi];
+        if (g.sweep) continue;
         Launch L;
         L.N = g.N;
         L.engine = g.engine;
@@ -1746,6 +1943,11 @@ int64_t cpra_batch_launches(cpra_batch_t b, int32_t n_iters) {
   if (!b) return -1;
   int64_t k = 0;
   for (auto& g : b->groups) {
+    if (g.sweep) {  // per episode and angle: one fused launch, or prime + n_ei (column, row)
+      k += (int64_t)(n_iters / g.n_ei) * g.np_max *
+           (g.engine == CPRA_ENGINE_FUSED ? 1 : 1 + 2 * (int64_t)g.n_ei);
+      continue;
+    }
     if (g.engine == CPRA_ENGINE_FUSED) {  // one launch per round of windows
       int64_t rounds = 0;
       for (int mi : g.members) {
@@ -1759,7 +1961,7 @@ int64_t cpra_batch_launches(cpra_batch_t b, int32_t n_iters) {
   }
   // coupling launches: one per group at every iteration where a member primes
   for (auto& g : b->groups) {
-    if (g.engine == CPRA_ENGINE_FUSED) continue;
+    if (g.engine == CPRA_ENGINE_FUSED || g.sweep) continue;
     for (int i = 0; i < n_iters; ++i) {
       bool any = false;
       for (int mi : g.members) {

@@ -257,6 +257,7 @@ struct RefineArgs {
   uint32_t* S3;        // [N][N][W] 3D support bits
   uint8_t* M;          // [N][N] measured (ky, kx) cells
   const float2* tw;    // twiddles exp(-2 pi i k/N)
+  const float2* xtw;   // warp-FFT cross twiddles (N = 64 ... 1024, powers of two)
 };
 // X = vol (centred), R = Re vol, V = FFT3(X)
 cudaError_t launch_refine_setup(const RefineArgs& a, const float2* vol, cudaStream_t st);
@@ -268,6 +269,9 @@ cudaError_t launch_refine_support(const RefineArgs& a, const uint32_t* S2, const
 cudaError_t launch_moments(cpra_plan_s* p, double* moments, cudaStream_t st);
 // one iteration; err2[0..1] += sum_M |X - V|^2, sum_M |V|^2
 cudaError_t launch_refine_iter(const RefineArgs& a, double* err2, cudaStream_t st);
+// the same passes with warp-resident FFTs (k_refine_w.cu; fast_supported(N))
+cudaError_t launch_refine_fft3_w(const RefineArgs& a, cudaStream_t st);
+cudaError_t launch_refine_iter_w(const RefineArgs& a, double* err2, cudaStream_t st);
 // S3 <- {blur(P_{S3+} R) >= tau max} (mx: one unsigned of scratch)
 cudaError_t launch_refine_shrink(const RefineArgs& a, const float* taps, int ntaps, float tau,
                                  unsigned* mx, cudaStream_t st);

@@ -6,7 +6,8 @@
 // slices reach (the measured mask M, the same for every kz).  Volumes are
 // [z][y][x], N^3, in the centred frame of the Step D volume (the frame of
 // the 2D supports); V is the spectrum of that volume.  One iteration is five
-// line passes:
+// line passes (block-wide Stockham FFTs here; warp-resident FFTs in
+// k_refine_w.cu for N = 64 ... 1024, powers of two):
 //   x rows    rho -> P_{S3+} rho -> forward FFT_x           (k_xlines, PROJ_FWD)
 //   y lines   forward FFT_y                                  (k_vlines, DIR -1)
 //   z lines   forward FFT_z -> error, X <- V where M -> IFFT_z (k_zconstrain)
@@ -215,23 +216,29 @@ __global__ void k_backproject(const uint32_t* __restrict__ S2, const double2* __
   S3[i] = bits;
 }
 
+// The periodic blur out[i] = sum_t taps[t] v[(i - lo - t) mod N] reads, for
+// output i, the staged values h[i + ntaps - 1 - t] of a line copied once with
+// a halo: h[k] = v[(k - lo - ntaps + 1) mod N], k < N + ntaps - 1.
+
 // blur along x of P_{S3+} rho into B (one row a CTA)
 __global__ void k_blur3_x(const float* __restrict__ R, const uint32_t* __restrict__ S3, float* Bv,
                           const float* __restrict__ taps, int ntaps, int lo, int N, int W) {
-  extern __shared__ float line[];
+  extern __shared__ float sm[];
+  float* tp = sm;           // [ntaps]
+  float* h = sm + ntaps;    // [N + ntaps - 1]
   const size_t row = blockIdx.x;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+  const int base = -lo - ntaps + 1;
+  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
+  for (int k = threadIdx.x; k < N + ntaps - 1; k += blockDim.x) {
+    const int x = ((k + base) % N + N) % N;
     const float v = R[row * N + x];
-    line[x] = (sbit(S3, row * W, x) && v >= 0.0f) ? v : 0.0f;
+    h[k] = (sbit(S3, row * W, x) && v >= 0.0f) ? v : 0.0f;
   }
   __syncthreads();
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     float acc = 0.0f;
-    for (int t = 0; t < ntaps; ++t) {
-      int xs = x - (lo + t);
-      xs = ((xs % N) + N) % N;
-      acc = fmaf(taps[t], line[xs], acc);
-    }
+    const float* hx = h + x + ntaps - 1;
+    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], hx[-t], acc);
     Bv[row * N + x] = acc;
   }
 }
@@ -241,32 +248,37 @@ __device__ __forceinline__ float warp_max3(float v) {
   return v;
 }
 
-// blur along y or z in place: 32 adjacent x columns of one line set a CTA
-// (blockIdx.x = x block, blockIdx.y = the other index), the lines staged in
-// shared memory; with mx the maximum of the result (float bits, values >= 0)
+// blur along y or z in place: cw adjacent x columns of one line set a CTA
+// (blockIdx.x = x block, blockIdx.y = the other index), the lines staged
+// with their halo in shared memory (pitch cw + 1); with mx the maximum of the
+// result (float bits, values >= 0)
 __global__ void k_blur3_v(float* Bv, const float* __restrict__ taps, int ntaps, int lo, int N,
-                          size_t outer, size_t estride, unsigned* mx) {
-  extern __shared__ float cols[];  // [N][33]
+                          size_t outer, size_t estride, unsigned* mx, int cw) {
+  extern __shared__ float sm[];
   __shared__ float red[32];
-  const int x0 = blockIdx.x * 32;
-  float* base = Bv + blockIdx.y * outer + x0;
-  const int nx = min(32, N - x0);
-  for (int idx = threadIdx.x; idx < N * 32; idx += blockDim.x) {
-    const int j = idx >> 5, b = idx & 31;
-    if (b < nx) cols[j * 33 + b] = base[j * estride + b];
+  float* tp = sm;             // [ntaps]
+  float* cols = sm + ntaps;   // [N + ntaps - 1][cw + 1]
+  const int pitch = cw + 1;
+  const int x0 = blockIdx.x * cw;
+  float* bp = Bv + blockIdx.y * outer + x0;
+  const int nx = min(cw, N - x0);
+  const int base = -lo - ntaps + 1;
+  const int ext = N + ntaps - 1;
+  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
+  for (int idx = threadIdx.x; idx < ext * cw; idx += blockDim.x) {
+    const int k = idx / cw, b = idx - k * cw;
+    const int j = ((k + base) % N + N) % N;
+    if (b < nx) cols[k * pitch + b] = bp[j * estride + b];
   }
   __syncthreads();
   float m = 0.0f;
-  for (int idx = threadIdx.x; idx < N * 32; idx += blockDim.x) {
-    const int j = idx >> 5, b = idx & 31;
+  for (int idx = threadIdx.x; idx < N * cw; idx += blockDim.x) {
+    const int j = idx / cw, b = idx - j * cw;
     if (b >= nx) continue;
     float acc = 0.0f;
-    for (int t = 0; t < ntaps; ++t) {
-      int js = j - (lo + t);
-      js = ((js % N) + N) % N;
-      acc = fmaf(taps[t], cols[js * 33 + b], acc);
-    }
-    base[j * estride + b] = acc;
+    const float* cj = cols + (j + ntaps - 1) * pitch + b;
+    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], cj[-t * pitch], acc);
+    bp[j * estride + b] = acc;
     m = fmaxf(m, acc);
   }
   if (mx) {
@@ -318,7 +330,7 @@ static cudaError_t refine_prepare_n() {
   if (e == cudaSuccess) e = smem_attr3(k_vlines<N, -1>, vs);
   if (e == cudaSuccess) e = smem_attr3(k_vlines<N, +1>, vs);
   if (e == cudaSuccess) e = smem_attr3(k_zconstrain<N>, vs);
-  if (e == cudaSuccess) e = smem_attr3(k_blur3_v, sizeof(float) * 33 * 1024);
+
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -348,9 +360,14 @@ static cudaError_t refine_setup_n(const RefineArgs& a, const float2* vol, cudaSt
   const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
   g_launches += 1;
   k_refine_in<<<blocks, 256, 0, st>>>(vol, a.X, a.R, total);
-  xlines<N, kXFwd>(a, st);
-  vlines<N, -1>(a, false, st);
-  vlines<N, -1>(a, true, st);
+  if (fast_supported(N)) {
+    e = launch_refine_fft3_w(a, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    xlines<N, kXFwd>(a, st);
+    vlines<N, -1>(a, false, st);
+    vlines<N, -1>(a, true, st);
+  }
   e = cudaMemcpyAsync(a.V, a.X, sizeof(float2) * total, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -358,6 +375,7 @@ static cudaError_t refine_setup_n(const RefineArgs& a, const float2* vol, cudaSt
 
 template <int N>
 static cudaError_t refine_iter_n(const RefineArgs& a, double* err2, cudaStream_t st) {
+  if (fast_supported(N)) return launch_refine_iter_w(a, err2, st);
   cudaError_t e = refine_prepare_n<N>();
   if (e != cudaSuccess) return e;
   using C = ColTile<N>;
@@ -401,13 +419,26 @@ cudaError_t launch_refine_shrink(const RefineArgs& a, const float* taps, int nta
   const size_t NN = (size_t)N * N;
   const int lo = -(ntaps / 2) + ((ntaps % 2) ? 0 : 1);
   const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t ea = smem_attr3(k_blur3_v, 200 * 1024);
+    if (ea != cudaSuccess) return ea;
+    attr = true;
+  }
   cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  const size_t vsm = sizeof(float) * 33 * N;
+  // columns a CTA for the y and z blurs: 32, or fewer while the haloed
+  // lines would not fit in 200 KB of shared memory (ntaps <= N)
+  int cw = 32;
+  while (cw > 4 && sizeof(float) * ((size_t)(N + ntaps - 1) * (cw + 1) + ntaps) > 200 * 1024) cw /= 2;
+  const size_t vsm = sizeof(float) * ((size_t)(N + ntaps - 1) * (cw + 1) + ntaps);
+  const size_t xsm = sizeof(float) * (N + 2 * ntaps);
   g_launches += 4;
-  k_blur3_x<<<(unsigned)NN, threads, sizeof(float) * N, st>>>(a.R, a.S3, a.Bv, taps, ntaps, lo, N, a.W);
-  k_blur3_v<<<dim3((N + 31) / 32, N), 256, vsm, st>>>(a.Bv, taps, ntaps, lo, N, NN, (size_t)N, nullptr);
-  k_blur3_v<<<dim3((N + 31) / 32, N), 256, vsm, st>>>(a.Bv, taps, ntaps, lo, N, (size_t)N, NN, mx);
+  k_blur3_x<<<(unsigned)NN, threads, xsm, st>>>(a.R, a.S3, a.Bv, taps, ntaps, lo, N, a.W);
+  k_blur3_v<<<dim3((N + cw - 1) / cw, N), 256, vsm, st>>>(a.Bv, taps, ntaps, lo, N, NN, (size_t)N,
+                                                        nullptr, cw);
+  k_blur3_v<<<dim3((N + cw - 1) / cw, N), 256, vsm, st>>>(a.Bv, taps, ntaps, lo, N, (size_t)N, NN,
+                                                        mx, cw);
   const size_t words = NN * a.W;
   k_thresh3<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(a.Bv, mx, a.S3, tau, N, a.W);
   return cudaGetLastError();

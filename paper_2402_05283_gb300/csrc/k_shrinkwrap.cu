@@ -13,24 +13,29 @@
 
 namespace cpra {
 
+// Row blur: out[x] = sum_t taps[t] rho[(x - lo - t) mod N], reading the row
+// staged once with a halo, h[k] = rho[(k - lo - ntaps + 1) mod N] (the same
+// terms in the same order as the definition).
 __global__ void k_sw_rows(const float* __restrict__ g, const uint32_t* __restrict__ S, float* tmp,
                           const float* __restrict__ taps, int ntaps, int lo, int N, int W) {
-  extern __shared__ float row[];
+  extern __shared__ float sm[];
+  float* tp = sm;          // [ntaps]
+  float* h = sm + ntaps;   // [N + ntaps - 1]
   const int y = blockIdx.x, n = blockIdx.y;
   const size_t base = ((size_t)n * N + y) * N;
   const size_t srow = ((size_t)n * N + y) * W;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+  const int hb = -lo - ntaps + 1;
+  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
+  for (int k = threadIdx.x; k < N + ntaps - 1; k += blockDim.x) {
+    const int x = ((k + hb) % N + N) % N;
     const float v = g[base + x];
-    row[x] = (sbit(S, srow, x) && v >= 0.0f) ? v : 0.0f;
+    h[k] = (sbit(S, srow, x) && v >= 0.0f) ? v : 0.0f;
   }
   __syncthreads();
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     float acc = 0.0f;
-    for (int t = 0; t < ntaps; ++t) {
-      int xs = x - (lo + t);
-      xs = ((xs % N) + N) % N;
-      acc = fmaf(taps[t], row[xs], acc);
-    }
+    const float* hx = h + x + ntaps - 1;
+    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], hx[-t], acc);
     tmp[base + x] = acc;
   }
 }
@@ -42,17 +47,21 @@ __device__ __forceinline__ float warp_max(float v) {
 
 __global__ void k_sw_cols(const float* __restrict__ tmp, float* b, unsigned* mx,
                           const float* __restrict__ taps, int ntaps, int lo, int N) {
+  extern __shared__ float sm[];
   __shared__ float red[32];
+  float* tp = sm;                                   // [ntaps]
+  int* rows = reinterpret_cast<int*>(sm + ntaps);   // [ntaps]: (y - lo - t) mod N
   const int y = blockIdx.x, n = blockIdx.y;
   const float* tn = tmp + (size_t)n * N * N;
+  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) {
+    tp[t] = taps[t];
+    rows[t] = ((y - (lo + t)) % N + N) % N;
+  }
+  __syncthreads();
   float m = 0.0f;
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
     float acc = 0.0f;
-    for (int t = 0; t < ntaps; ++t) {
-      int ys = y - (lo + t);
-      ys = ((ys % N) + N) % N;
-      acc = fmaf(taps[t], tn[(size_t)ys * N + x], acc);
-    }
+    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], tn[(size_t)rows[t] * N + x], acc);
     b[((size_t)n * N + y) * N + x] = acc;
     m = fmaxf(m, acc);
   }
@@ -90,10 +99,10 @@ cudaError_t launch_shrinkwrap(cpra_plan_s* p) {
   cudaError_t e = cudaMemsetAsync(p->sw_max, 0, sizeof(unsigned) * Np, p->stream);
   if (e != cudaSuccess) return e;
   g_launches += 3;
-  k_sw_rows<<<dim3(N, Np), threads, N * sizeof(float), p->stream>>>(p->g, p->S, p->sw_tmp,
+  k_sw_rows<<<dim3(N, Np), threads, (N + 2 * p->sw_ntaps) * sizeof(float), p->stream>>>(p->g, p->S, p->sw_tmp,
                                                                     p->sw_taps, p->sw_ntaps, lo,
                                                                     N, p->W);
-  k_sw_cols<<<dim3(N, Np), threads, 0, p->stream>>>(p->sw_tmp, p->g_alt, p->sw_max, p->sw_taps,
+  k_sw_cols<<<dim3(N, Np), threads, 2 * p->sw_ntaps * sizeof(float), p->stream>>>(p->sw_tmp, p->g_alt, p->sw_max, p->sw_taps,
                                                     p->sw_ntaps, lo, N);
   k_sw_thresh<<<dim3(N, Np), 32, 0, p->stream>>>(p->g_alt, p->sw_max, p->S, p->cfg.sw_tau, N,
                                                  p->W);
@@ -213,9 +222,9 @@ extern "C" cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_i
   if (e == cudaSuccess) e = launch_bits_from_u8(sc.bits, S_in, N, count, st);
   if (e == cudaSuccess) {
     g_launches += 3;
-    k_sw_rows<<<dim3(N, count), threads, N * sizeof(float), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps,
+    k_sw_rows<<<dim3(N, count), threads, (N + 2 * ntaps) * sizeof(float), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps,
                                                                    lo, N, W);
-    k_sw_cols<<<dim3(N, count), threads, 0, st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
+    k_sw_cols<<<dim3(N, count), threads, 2 * ntaps * sizeof(float), st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
     k_sw_thresh<<<dim3(N, count), 32, 0, st>>>(sc.b, sc.mx, sc.bits, tau, N, W);
     e = cudaGetLastError();
   }

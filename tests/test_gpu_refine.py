@@ -32,9 +32,8 @@ def cp():
     return pkg
 
 
-@pytest.fixture(scope="module")
-def case():
-    d = synth.make_case("cfg1", N=N, Np=NP)
+def _case(N_, Np_):
+    d = synth.make_case("cfg1", N=N_, Np=Np_)
     P = d["proj"].numpy().astype(np.float64)
     r = np.random.default_rng(5)
     S = P > 1e-9
@@ -43,7 +42,13 @@ def case():
     return d
 
 
+@pytest.fixture(scope="module")
+def case():
+    return _case(N, NP)
+
+
 def _plan(cp, d):
+    N, NP = d["N"], d["Np"]
     p = cp.Plan(cp.make_config(N, NP))
     p.load_intensities(d["I"], 0, d["thetas"])
     p.load_support(d["S2"].astype(np.uint8))
@@ -56,6 +61,7 @@ def _oracle(d, iters, shrink_every=0, sigma=1.5, tau=0.1):
     """Step D volume of the loaded state, then the refinement in its centred
     frame (R19-R21)."""
     th = d["thetas"]
+    N = d["N"]
     g = d["g"].astype(np.float64)
     vol_c = O.volume(O.grid_3d(O.spectra(g, d["S2"]), th))
     M = O.measured_cells(N, th)
@@ -78,6 +84,21 @@ def test_refine_matches_oracle(cp, case):
     assert r < TOL and er.max() < TOL
     assert all(b <= a * (1 + 1e-4) for a, b in zip(e_gpu, e_gpu[1:]))  # the gap never grows
     p.close()
+
+
+def test_refine_warp_fft_path_matches_oracle(cp):
+    """N = 64 runs the line passes on the warp-resident FFTs (N = 32 above
+    runs the block-wide ones): 12 iterations with shrink-wrap every 4."""
+    d = _case(64, 12)
+    p = _plan(cp, d)
+    e_gpu = p.refine_3d(12, shrink_every=4, sigma=1.5, tau=0.1)
+    vol = p.result(cp.RESULT_VOLUME)
+    p.close()
+    ref, e_ref, _, _ = _oracle(d, 12, shrink_every=4, sigma=1.5, tau=0.1)
+    r = np.linalg.norm(vol - ref) / np.linalg.norm(ref)
+    er = np.abs(e_gpu - e_ref) / np.array(e_ref)
+    print(f"refine N=64 (warp FFTs) 12: volume rel-L2 {r:.2e}, errors {er.max():.2e}")
+    assert r < TOL and er.max() < TOL
 
 
 def test_refine_with_shrinkwrap_and_split_calls(cp, case):
@@ -104,7 +125,7 @@ def test_refine_with_shrinkwrap_and_split_calls(cp, case):
 
 
 def test_refine_needs_a_volume_and_valid_arguments(cp, case):
-    p = cp.Plan(cp.make_config(N, NP))
+    p = cp.Plan(cp.make_config(case["N"], case["Np"]))
     p.load_intensities(case["I"], 0, case["thetas"])
     with pytest.raises(cp.CpraError) as ei:
         p.refine_3d(3)

@@ -5,7 +5,9 @@ ER iterations (continuous in the sign test) on the true-projection supports
 over two episodes, every engine: each angle's iterate within 1e-4 relative
 L2 and every error within 1e-4; Step A (3 HIO iterations on angle 0) before
 the sweeps; one RAAR episode of 3 iterations.  The sweep must differ from
-the Jacobi episodes it replaces, and calls must cover whole episodes.
+the Jacobi episodes it replaces, and calls must cover whole episodes.  A
+batch runs the sweeps of many guesses together (one launch per angle over
+all of them) and must give every member's standalone result bit for bit.
 """
 import numpy as np
 import pytest
@@ -113,9 +115,46 @@ def test_sweep_differs_from_jacobi_and_runs_whole_episodes(cp, case):
         plan.iterate(3)
     assert ei.value.status == cp.ERR_INVALID_ARG
     with pytest.raises(cp.CpraError) as ei:
-        cp.Batch([plan])
-    assert ei.value.status == cp.ERR_UNSUPPORTED
-    with pytest.raises(cp.CpraError) as ei:
         plan.set_present(np.arange(8) < 4)
     assert ei.value.status == cp.ERR_UNSUPPORTED
     plan.close()
+
+
+@pytest.mark.parametrize("engine", ["two_pass", "fused"])
+def test_batched_sweeps_equal_standalone(cp, case, engine):
+    """Four guesses (different seeds, Step A on two of them, one with 6
+    angles instead of 8, shrink-wrap every episode on one) as one batch:
+    each ends bit for bit where it ends alone."""
+    import torch
+    d = case
+
+    def plans():
+        out = []
+        for i in range(4):
+            Np = 6 if i == 3 else 8
+            kw = dict(seed=20 + i, hio_iters=6, er_iters=4, n_ei=5, sweep=1,
+                      engine=ENGINES[engine], update=cp.UPDATE_RAAR if i % 2 else cp.UPDATE_HIO,
+                      n_pre=3 if i < 2 else 0, shrinkwrap_every=5 if i == 2 else 0)
+            p = cp.Plan(cp.make_config(64, Np, **kw), stream=torch.cuda.current_stream().cuda_stream)
+            p.load_intensities(d["I"][:Np], 0, d["thetas"][:Np])
+            p.load_support(d["S_true"][:Np])
+            out.append(p)
+        return out
+
+    alone = plans()
+    for p in alone:
+        p.iterate(10)
+    together = plans()
+    b = cp.Batch(together, use_graph=True)
+    b.iterate(5)
+    b.iterate(5)
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.result(cp.RESULT_STATE), t.result(cp.RESULT_STATE))
+        assert np.array_equal(a.result(cp.RESULT_SUPPORT), t.result(cp.RESULT_SUPPORT))
+        np.testing.assert_allclose(t.result(cp.RESULT_ERRORS), a.result(cp.RESULT_ERRORS), rtol=1e-12)
+    with pytest.raises(cp.CpraError) as ei:
+        b.iterate(3)
+    assert ei.value.status == cp.ERR_INVALID_ARG
+    b.close()
+    for p in alone + together:
+        p.close()
