@@ -25,31 +25,44 @@
 
 namespace cpra {
 
+// One warp a row, 8 rows a CTA: each lane sums its pixels of the row in
+// FP32 (at most N/32 terms), the sums go to FP64 across lanes, rows and CTAs
+// (FP64 stays out of the per-pixel work: its pipe is narrow).
 __global__ void k_moments(const float* __restrict__ g, const uint32_t* __restrict__ S,
                           double* moments, int N, int W) {
-  __shared__ double red[3][32];
-  const int y = blockIdx.x, n = blockIdx.y;
-  const size_t base = ((size_t)n * N + y) * N;
-  const size_t srow = ((size_t)n * N + y) * W;
+  __shared__ double red[3][8];
+  const int n = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = blockIdx.x * 8 + warp;
   double m0 = 0.0, mu = 0.0;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    const float v = g[base + x];
-    const double r = (sbit(S, srow, x) && v >= 0.0f) ? (double)v : 0.0;
-    m0 += r;
-    mu += r * x;
+  if (y < N) {
+    const size_t base = ((size_t)n * N + y) * N;
+    const size_t srow = ((size_t)n * N + y) * W;
+    float s0 = 0.0f, su = 0.0f;
+    for (int x = lane; x < N; x += 32) {
+      const float v = g[base + x];
+      const float r = (sbit(S, srow, x) && v >= 0.0f) ? v : 0.0f;
+      s0 += r;
+      su = fmaf(r, (float)x, su);
+    }
+    m0 = s0;
+    mu = su;
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 += __shfl_down_sync(0xffffffffu, m0, o);
+      mu += __shfl_down_sync(0xffffffffu, mu, o);
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    m0 += __shfl_down_sync(0xffffffffu, m0, o);
-    mu += __shfl_down_sync(0xffffffffu, mu, o);
+  if (lane == 0) {
+    red[0][warp] = m0;
+    red[1][warp] = m0 * (double)y;
+    red[2][warp] = mu;
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { red[0][wid] = m0; red[1][wid] = mu; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, c = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += red[0][i]; c += red[1][i]; }
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < 8; ++i) { a += red[0][i]; b += red[1][i]; c += red[2][i]; }
     atomicAdd(moments + 3 * n + 0, a);
-    atomicAdd(moments + 3 * n + 1, a * y);
+    atomicAdd(moments + 3 * n + 1, b);
     atomicAdd(moments + 3 * n + 2, c);
   }
 }
@@ -356,9 +369,8 @@ static cudaError_t moments_of(cpra_plan_s* p, double* moments, cudaStream_t st) 
   const int N = p->N, Np = p->Np;
   cudaError_t e = cudaMemsetAsync(moments, 0, sizeof(double) * 3 * Np, st);
   if (e != cudaSuccess) return e;
-  const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
   g_launches += 1;
-  k_moments<<<dim3(N, Np), threads, 0, st>>>(p->g, p->S, moments, N, p->W);
+  k_moments<<<dim3((N + 7) / 8, Np), 256, 0, st>>>(p->g, p->S, moments, N, p->W);
   return cudaGetLastError();
 }
 

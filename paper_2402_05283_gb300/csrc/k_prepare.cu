@@ -6,65 +6,65 @@ namespace cpra {
 
 std::atomic<long long> g_launches{0};
 
-// One block per (FFT-order row ky, angle).  A(k) = sqrt(I) at the centred
+// Rows ky (FFT order) of every loaded angle.  A(k) = sqrt(I) at the centred
 // index of k; A_sym(k) = (A(k) + A(-k)) / 2 on the half plane kx <= N/2;
 // the full-plane sums of ((A(k) - A(-k))/2)^2 and A(k)^2 go to Cn and sumA2.
 // With a measured-pixel mask (centred, nonzero = measured; per angle when
 // mask_stride is N*N, one for all when 0) only the pairs {k, -k} with both
 // pixels measured are constrained: the others get A_sym = -1 (the modulus
 // projection leaves them free) and stay out of Cn and sumA2.
+//
+// One warp a row ky, 8 rows a CTA: each lane sums its pixels' terms in FP32
+// (at most N/32 of them), the sums go to FP64 across lanes, rows and CTAs.
 __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* A_rows,
                           float* A_nyq, double* Cn, double* sumA2, int* flag,
                           const uint8_t* __restrict__ mask, size_t mask_stride) {
-  const int ky = blockIdx.x;
+  __shared__ double sc[8], sa[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ky = blockIdx.x * 8 + warp;
   const int n = first + blockIdx.y;
   const int h = N / 2;
-  const float* In = I + (size_t)blockIdx.y * N * N;
-  const int ry = (ky + h) % N;           // centred row of +ky
-  const int my = (N - ky + h) % N;       // centred row of -ky
-  const uint8_t* Mn = mask ? mask + (size_t)n * mask_stride : nullptr;
   double c_part = 0.0, a_part = 0.0;
-  int bad = 0;
-  for (int kx = threadIdx.x; kx < N; kx += blockDim.x) {
-    const int rx = (kx + h) % N;
-    const int mx = (N - kx + h) % N;
-    float ip = In[(size_t)ry * N + rx];
-    float im = In[(size_t)my * N + mx];
-    if (!(ip >= 0.0f) || !isfinite(ip)) bad = 1;
-    const bool on = !Mn || (Mn[(size_t)ry * N + rx] && Mn[(size_t)my * N + mx]);
-    float ap = sqrtf(fmaxf(ip, 0.0f));
-    float am = sqrtf(fmaxf(im, 0.0f));
-    double d = 0.5 * ((double)ap - (double)am);
-    if (on) {
-      c_part += d * d;
-      a_part += (double)ap * (double)ap;
+  if (ky < N) {
+    const float* In = I + (size_t)blockIdx.y * N * N;
+    const int ry = (ky + h) % N;           // centred row of +ky
+    const int my = (N - ky + h) % N;       // centred row of -ky
+    const uint8_t* Mn = mask ? mask + (size_t)n * mask_stride : nullptr;
+    float cf = 0.0f, af = 0.0f;
+    int bad = 0;
+    for (int kx = lane; kx < N; kx += 32) {
+      const int rx = (kx + h) % N;
+      const int mx = (N - kx + h) % N;
+      float ip = In[(size_t)ry * N + rx];
+      float im = In[(size_t)my * N + mx];
+      if (!(ip >= 0.0f) || !isfinite(ip)) bad = 1;
+      const bool on = !Mn || (Mn[(size_t)ry * N + rx] && Mn[(size_t)my * N + mx]);
+      float ap = sqrtf(fmaxf(ip, 0.0f));
+      float am = sqrtf(fmaxf(im, 0.0f));
+      const float d = 0.5f * (ap - am);
+      if (on) {
+        cf = fmaf(d, d, cf);
+        af = fmaf(ap, ap, af);
+      }
+      float as = on ? 0.5f * (ap + am) : -1.0f;
+      if (kx < h) A_rows[((size_t)blockIdx.y * N + ky) * h + kx] = as;
+      if (kx == h) A_nyq[(size_t)n * N + ky] = as;
     }
-    float as = on ? 0.5f * (ap + am) : -1.0f;
-    if (kx < h) A_rows[((size_t)blockIdx.y * N + ky) * h + kx] = as;
-    if (kx == h) A_nyq[(size_t)n * N + ky] = as;
-  }
-  if (bad) atomicExch(flag, 1);
-  // block reduction in FP64
-  __shared__ double sc[32], sa[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    c_part += __shfl_down_sync(0xffffffffu, c_part, o);
-    a_part += __shfl_down_sync(0xffffffffu, a_part, o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { sc[wid] = c_part; sa[wid] = a_part; }
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    c_part = lane < nw ? sc[lane] : 0.0;
-    a_part = lane < nw ? sa[lane] : 0.0;
+    if (bad) atomicExch(flag, 1);
+    c_part = cf;
+    a_part = af;
     for (int o = 16; o > 0; o >>= 1) {
       c_part += __shfl_down_sync(0xffffffffu, c_part, o);
       a_part += __shfl_down_sync(0xffffffffu, a_part, o);
     }
-    if (lane == 0) {
-      atomicAdd(Cn + n, c_part);
-      atomicAdd(sumA2 + n, a_part);
-    }
+  }
+  if (lane == 0) { sc[warp] = c_part; sa[warp] = a_part; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = 0.0, a = 0.0;
+    for (int i = 0; i < 8; ++i) { c += sc[i]; a += sa[i]; }
+    atomicAdd(Cn + n, c);
+    atomicAdd(sumA2 + n, a);
   }
 }
 
@@ -92,12 +92,11 @@ cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count)
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(p->sumA2 + first, 0, sizeof(double) * count, p->stream);
   if (e != cudaSuccess) return e;
-  dim3 grid(p->N, count);
-  int threads = p->N >= 256 ? 256 : ((p->N + 31) / 32) * 32;
+  dim3 grid((p->N + 7) / 8, count);
   // g_alt is free outside cpra_iterate: it holds the row-major amplitudes
   float* rows = p->g_alt;
   g_launches += 2;
-  k_prepare<<<grid, threads, 0, p->stream>>>(I, p->N, first, rows, p->A_nyq, p->Cn, p->sumA2,
+  k_prepare<<<grid, 256, 0, p->stream>>>(I, p->N, first, rows, p->A_nyq, p->Cn, p->sumA2,
                                              p->flag, p->mask,
                                              p->mask_per_angle ? (size_t)p->N * p->N : 0);
   const int h = p->N / 2;

@@ -18,6 +18,7 @@
 // projection lands in the moved 2D support at every angle) and shrinks on
 // schedule: blur P_{S3+} rho with the periodic Gaussian along x, y, z, keep
 // the voxels at or above tau times the maximum.
+#include <algorithm>
 #include <cmath>
 
 #include "cpra_internal.h"
@@ -178,42 +179,92 @@ __global__ void k_measured(const int32_t* __restrict__ cell_ptr, uint8_t* M, int
   if (c < NN) M[c] = cell_ptr[c + 1] > cell_ptr[c] ? 1 : 0;
 }
 
-// One 32-voxel word of S3 a thread: voxel (z, y, x) is in when at every angle
-// u = rint((x - c) cos + (y - c) sin + c) lies in [0, N) with
-// S2[n][(z + dz) mod N][(u + du) mod N] set ((dz, du): the angle's shift)
-// (FP64, rounded step by step, so that the nearest pixel is the one an FP64
-// host evaluation in the same order picks).
+// One 32-voxel word of S3 a thread, the CTA on YB rows (y) of one plane z:
+// voxel (z, y, x) is in when at every angle u = rint((x - c) cos + (y - c)
+// sin + c) lies in [0, N) with S2[n][(z + dz) mod N][(u + du) mod N] set
+// ((dz, du): the angle's shift).  The rows of S2 this plane needs go
+// through shared memory, NC angles at a time, and only the voxels still in
+// are tested.  The nearest pixel is the one an FP64 evaluation in the host's
+// order picks: FP32 where that cannot differ, FP64 near a tie.
+// u = rint(((x - c) cos + (y - c) sin) + c) in FP64, each step rounded, no
+// contraction.  Not inlined: kept out of line, the rare call leaves the FP64
+// pipe idle instead of being predicated into every evaluation.
+__device__ __noinline__ int u_fp64(int x, int y, int N, double2 t) {
+  const double c = N / 2;
+  const double b = __dmul_rn((double)(y - N / 2), t.y);
+  return (int)rint(__dadd_rn(__dadd_rn(__dmul_rn((double)(x - N / 2), t.x), b), c));
+}
+
 __global__ void k_backproject(const uint32_t* __restrict__ S2, const double2* __restrict__ cs,
-                              const int2* __restrict__ shift, uint32_t* S3, int N, int W, int Np) {
-  const size_t words = (size_t)N * N * W;
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= words) return;
-  const int w = (int)(i % W);
-  const size_t row = i / W;
-  const int y = (int)(row % N), z = (int)(row / N);
+                              const int2* __restrict__ shift, uint32_t* S3, int N, int W, int Np,
+                              int YB, int NC) {
+  // per chunk of NC angles: S2 rows [NC][W]; (cos, sin) [NC] for the FP64
+  // path; du [NC]; cos in FP32 [NC]; (y - c) sin + c in FP32 [NC][YB]
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double2* tcs = reinterpret_cast<double2*>(sm_raw);
+  uint32_t* rows = reinterpret_cast<uint32_t*>(tcs + NC);
+  int* tdu = reinterpret_cast<int*>(rows + (size_t)NC * W);
+  float* cfs = reinterpret_cast<float*>(tdu + NC);
+  float* bfs = cfs + NC;
+  const int z = blockIdx.y;
+  const int y0 = blockIdx.x * YB;
+  const int yl = threadIdx.x / W, w = threadIdx.x - yl * W;
+  const int y = y0 + yl;
+  const bool mine = yl < YB && y < N;
   const double c = N / 2;
   uint32_t bits = 0;
-  for (int j = 0; j < 32; ++j)
-    if (w * 32 + j < N) bits |= 1u << j;
-  for (int n = 0; n < Np && bits; ++n) {
-    const double2 t = cs[n];
-    const int2 d = shift[n];  // the 2D support moves with its PO: (dz, du)
-    const double b = __dmul_rn((double)(y - N / 2), t.y);
-    const uint32_t* s2 = S2 + ((size_t)n * N + (z + d.x + N) % N) * W;
-    uint32_t keep = 0;
-    for (int j = 0; j < 32; ++j) {
-      if (!((bits >> j) & 1u)) continue;
-      const int x = w * 32 + j;
-      // ((x - c) cos + (y - c) sin) + c, each step rounded, no contraction
-      const double u = rint(__dadd_rn(__dadd_rn(__dmul_rn((double)(x - N / 2), t.x), b), c));
-      if (u >= 0.0 && u < (double)N) {
-        const int ui = ((int)u + d.y + N) % N;
-        if ((s2[ui >> 5] >> (ui & 31)) & 1u) keep |= 1u << j;
-      }
+  if (mine)
+    for (int j = 0; j < 32; ++j)
+      if (w * 32 + j < N) bits |= 1u << j;
+  for (int n0 = 0; n0 < Np; n0 += NC) {
+    const int nc = min(NC, Np - n0);
+    __syncthreads();  // the previous chunk is done
+    for (int q = threadIdx.x; q < nc * W; q += blockDim.x) {
+      const int k = q / W, ww = q - k * W;
+      int zr = z + shift[n0 + k].x;
+      zr = zr < 0 ? zr + N : (zr >= N ? zr - N : zr);
+      rows[k * W + ww] = S2[((size_t)(n0 + k) * N + zr) * W + ww];
     }
-    bits = keep;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      tcs[k] = cs[n0 + k];
+      tdu[k] = shift[n0 + k].y;
+      cfs[k] = (float)cs[n0 + k].x;
+    }
+    for (int q = threadIdx.x; q < nc * YB; q += blockDim.x) {
+      const int k = q / YB, r = q - k * YB;
+      bfs[q] = (float)__dmul_rn((double)(y0 + r - N / 2), cs[n0 + k].y) + (float)c;
+    }
+    __syncthreads();
+    // conversions and rounding by the 1.5 * 2^23 shift (exact integers and
+    // round-half-even additions for |u| < 2^22), so that the inner loop stays
+    // on the FP32 and integer pipes
+    const float xb = (float)(w * 32 - N / 2);
+    for (int k = 0; k < nc && bits; ++k) {
+      // FP32 estimate of u: within 2e-4 of the FP64 value for |x - c|,
+      // |y - c| <= 512, so its nearest integer is the FP64 one unless it sits
+      // within 1e-3 of a half; those few are redone in FP64
+      const float cf = cfs[k], bf = bfs[k * YB + yl];
+      const int du = tdu[k];
+      const uint32_t* r = rows + k * W;
+      uint32_t keep = 0;
+      for (uint32_t todo = bits; todo; todo &= todo - 1) {
+        const int j = __ffs(todo) - 1;
+        const float jf = __fsub_rn(__int_as_float(0x4B000000 | j), 8388608.0f);  // (float)j
+        const float uf = fmaf(__fadd_rn(xb, jf), cf, bf);
+        const float sh = __fadd_rn(uf, 12582912.0f);
+        int ui = __float_as_int(sh) - 0x4B400000;                  // rint(uf)
+        const float fr = __fsub_rn(uf, __fsub_rn(sh, 12582912.0f));  // uf - rint(uf)
+        if (fabsf(fabsf(fr) - 0.5f) < 1e-3f) ui = u_fp64(w * 32 + j, y, N, tcs[k]);
+        if (ui >= 0 && ui < N) {
+          ui += du;
+          ui = ui < 0 ? ui + N : (ui >= N ? ui - N : ui);
+          if ((r[ui >> 5] >> (ui & 31)) & 1u) keep |= 1u << j;
+        }
+      }
+      bits = keep;
+    }
   }
-  S3[i] = bits;
+  if (mine) S3[((size_t)z * N + y) * W + w] = bits;
 }
 
 // The periodic blur out[i] = sum_t taps[t] v[(i - lo - t) mod N] reads, for
@@ -235,11 +286,25 @@ __global__ void k_blur3_x(const float* __restrict__ R, const uint32_t* __restric
     h[k] = (sbit(S3, row * W, x) && v >= 0.0f) ? v : 0.0f;
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    float acc = 0.0f;
-    const float* hx = h + x + ntaps - 1;
-    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], hx[-t], acc);
-    Bv[row * N + x] = acc;
+  // four consecutive outputs a thread (N is a multiple of 4): a window of
+  // four staged values slides down one place a tap, one load a tap
+  for (int x0 = 4 * threadIdx.x; x0 < N; x0 += 4 * blockDim.x) {
+    const float* hx = h + x0 + ntaps - 1;
+    float w0 = hx[0], w1 = hx[1], w2 = hx[2], w3 = hx[3];
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    for (int t = 0; t < ntaps; ++t) {
+      const float c = tp[t];
+      a0 = fmaf(c, w0, a0);
+      a1 = fmaf(c, w1, a1);
+      a2 = fmaf(c, w2, a2);
+      a3 = fmaf(c, w3, a3);
+      w3 = w2;
+      w2 = w1;
+      w1 = w0;
+      if (t + 1 < ntaps) w0 = hx[-t - 1];
+    }
+    float4* dst = reinterpret_cast<float4*>(Bv + row * N + x0);
+    *dst = make_float4(a0, a1, a2, a3);
   }
 }
 
@@ -272,14 +337,31 @@ __global__ void k_blur3_v(float* Bv, const float* __restrict__ taps, int ntaps, 
   }
   __syncthreads();
   float m = 0.0f;
-  for (int idx = threadIdx.x; idx < N * cw; idx += blockDim.x) {
-    const int j = idx / cw, b = idx - j * cw;
+  // four consecutive outputs of one column a thread, with the sliding window
+  // of k_blur3_x
+  for (int idx = threadIdx.x; idx < (N / 4) * cw; idx += blockDim.x) {
+    const int jb = idx / cw, b = idx - jb * cw;
     if (b >= nx) continue;
-    float acc = 0.0f;
-    const float* cj = cols + (j + ntaps - 1) * pitch + b;
-    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], cj[-t * pitch], acc);
-    bp[j * estride + b] = acc;
-    m = fmaxf(m, acc);
+    const int j0 = 4 * jb;
+    const float* cj = cols + (j0 + ntaps - 1) * pitch + b;
+    float w0 = cj[0], w1 = cj[pitch], w2 = cj[2 * pitch], w3 = cj[3 * pitch];
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    for (int t = 0; t < ntaps; ++t) {
+      const float c = tp[t];
+      a0 = fmaf(c, w0, a0);
+      a1 = fmaf(c, w1, a1);
+      a2 = fmaf(c, w2, a2);
+      a3 = fmaf(c, w3, a3);
+      w3 = w2;
+      w2 = w1;
+      w1 = w0;
+      if (t + 1 < ntaps) w0 = cj[-(t + 1) * pitch];
+    }
+    bp[(size_t)j0 * estride + b] = a0;
+    bp[(size_t)(j0 + 1) * estride + b] = a1;
+    bp[(size_t)(j0 + 2) * estride + b] = a2;
+    bp[(size_t)(j0 + 3) * estride + b] = a3;
+    m = fmaxf(m, fmaxf(fmaxf(a0, a1), fmaxf(a2, a3)));
   }
   if (mx) {
     m = warp_max3(m);
@@ -405,10 +487,22 @@ cudaError_t launch_refine_iter(const RefineArgs& a, double* err2, cudaStream_t s
 
 cudaError_t launch_refine_support(const RefineArgs& a, const uint32_t* S2, const double2* cs,
                                   const int2* shift, int Np, const int32_t* cell_ptr, cudaStream_t st) {
-  const int N = a.N;
-  const size_t words = (size_t)N * N * a.W;
+  const int N = a.N, W = a.W;
+  const int YB = std::max(1, 256 / W);
+  // angles a chunk: their tables (see k_backproject) within 96 KB
+  const int per = (int)(sizeof(double2) + W * sizeof(uint32_t) + sizeof(int) + sizeof(float) +
+                        YB * sizeof(float));
+  const int NC = std::max(1, std::min(Np, (96 * 1024) / per));
+  const size_t smem = (size_t)NC * per;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         96 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   g_launches += 2;
-  k_backproject<<<(unsigned)((words + 127) / 128), 128, 0, st>>>(S2, cs, shift, a.S3, N, a.W, Np);
+  k_backproject<<<dim3((N + YB - 1) / YB, N), YB * W, smem, st>>>(S2, cs, shift, a.S3, N, W, Np, YB, NC);
   k_measured<<<(N * N + 255) / 256, 256, 0, st>>>(cell_ptr, a.M, N * N);
   return cudaGetLastError();
 }

@@ -7,7 +7,8 @@
 //            contiguous), FFT, stores from the B layout;
 //   y, z     CB adjacent x columns staged through shared memory (rows of
 //            CB * 8 bytes, estride apart), one column a warp, as in the
-//            column pass of the iteration.
+//            column pass of the iteration; the z pass stages the data
+//            columns beside them.
 // The z pass applies the data constraint between its forward and inverse
 // transforms; the error terms are summed per thread in FP32 (at most a few
 // dozen terms) and across threads and blocks in FP64.
@@ -25,6 +26,9 @@ template <int N>
 constexpr size_t xw_smem() { return sizeof(float2) * (N + XW<N>::WARPS * XW<N>::FL::TSIZE); }
 template <int N>
 constexpr size_t vw_smem() { return sizeof(float2) * (N + VW<N>::BUF); }
+// the constraint pass also stages the data columns (same rows, same pitch)
+template <int N>
+constexpr size_t vw_smem_c() { return vw_smem<N>() + sizeof(float2) * VW<N>::STAGE; }
 
 enum { kWFwd = 0, kWProjFwd = 1, kWInvReal = 2 };
 
@@ -108,7 +112,6 @@ k_vw(float2* X, const float2* __restrict__ V, const uint8_t* __restrict__ M,
      const float2* __restrict__ xtw, double* err2, size_t outer, size_t estride) {
   using C = VW<N>;
   using FL = typename C::FL;
-  constexpr size_t NN = (size_t)N * N;
   extern __shared__ float2 smem[];
   __shared__ double red[2][32];
   float2* xs = smem;
@@ -116,9 +119,12 @@ k_vw(float2* X, const float2* __restrict__ V, const uint8_t* __restrict__ M,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = blockIdx.x * C::CB;
   float2* base = X + blockIdx.y * outer + c0;
+  float2* vbuf = buf + C::BUF;  // kVConstrain: the data of the block's columns
   for (int idx = threadIdx.x; idx < N * C::CB; idx += C::NT) {
     const int y = idx / C::CB, c = idx - y * C::CB;
     cp_async8(buf + y * C::SP + c, base + y * estride + c);
+    if constexpr (MODE == kVConstrain)
+      cp_async8(vbuf + y * C::SP + c, V + blockIdx.y * outer + c0 + y * estride + c);
   }
   cp_async_commit();
   load_xtw<N>(xs, xtw, C::NT);
@@ -156,13 +162,11 @@ k_vw(float2* X, const float2* __restrict__ V, const uint8_t* __restrict__ M,
     static_for<0, FL::TB>([&](auto II) {
       constexpr int i = decltype(II)::value;
       const int t = lane + 32 * i;
-      const int kx = c0 + warp * FL::L + FL::b_line(t);
-      if (M[(size_t)ky * N + kx]) {
-        const int k0 = FL::b_k(t, 0);
-        const float2* Vc = V + (size_t)k0 * NN + (size_t)ky * N + kx;
+      const int col = warp * FL::L + FL::b_line(t);
+      if (M[(size_t)ky * N + c0 + col]) {
         static_for<0, FL::E2>([&](auto JJ) {
           constexpr int j = decltype(JJ)::value;
-          const float2 v = __ldg(Vc + (size_t)(FL::b_k(t, j) - k0) * NN);
+          const float2 v = vbuf[FL::b_k(t, j) * C::SP + col];
           const float dx = b[i][j].x - v.x, dy = b[i][j].y - v.y;
           ef = fmaf(dx, dx, fmaf(dy, dy, ef));
           df = fmaf(v.x, v.x, fmaf(v.y, v.y, df));
@@ -232,7 +236,7 @@ cudaError_t refine_w_prepare() {
   if (e == cudaSuccess) e = attr_w(k_xw<N, kWInvReal>, xw_smem<N>());
   if (e == cudaSuccess) e = attr_w(k_vw<N, kVFwd>, vw_smem<N>());
   if (e == cudaSuccess) e = attr_w(k_vw<N, kVInv>, vw_smem<N>());
-  if (e == cudaSuccess) e = attr_w(k_vw<N, kVConstrain>, vw_smem<N>());
+  if (e == cudaSuccess) e = attr_w(k_vw<N, kVConstrain>, vw_smem_c<N>());
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -250,7 +254,8 @@ template <int N, int MODE>
 void vw(const RefineArgs& a, bool along_z, double* err2, cudaStream_t st) {
   const size_t NN = (size_t)N * N;
   g_launches += 1;
-  k_vw<N, MODE><<<dim3(N / VW<N>::CB, N), VW<N>::NT, vw_smem<N>(), st>>>(
+  constexpr size_t smem = MODE == kVConstrain ? vw_smem_c<N>() : vw_smem<N>();
+  k_vw<N, MODE><<<dim3(N / VW<N>::CB, N), VW<N>::NT, smem, st>>>(
       a.X, a.V, a.M, a.xtw, err2, along_z ? (size_t)N : NN, along_z ? NN : (size_t)N);
 }
 
