@@ -117,17 +117,18 @@ k_zconstrain(float2* X, const float2* __restrict__ V, const uint8_t* __restrict_
   }
   __syncthreads();
   fft_lines<N, -1, B, B, NT>(buf, tw_s);
-  double e = 0.0, d = 0.0;
+  float ef = 0.0f, df = 0.0f;  // a thread's few dozen terms; FP64 across threads
   for (int idx = threadIdx.x; idx < N * B; idx += NT) {
     const int kz = idx / B, b = idx - kz * B;
     if (!M[off + b]) continue;
     const float2 v = V[kz * NN + off + b];
     const float2 x = buf[idx];
-    const double dx = (double)x.x - v.x, dy = (double)x.y - v.y;
-    e += dx * dx + dy * dy;
-    d += (double)v.x * v.x + (double)v.y * v.y;
+    const float dx = x.x - v.x, dy = x.y - v.y;
+    ef = fmaf(dx, dx, fmaf(dy, dy, ef));
+    df = fmaf(v.x, v.x, fmaf(v.y, v.y, df));
     buf[idx] = v;
   }
+  double e = ef, d = df;
   __syncthreads();
   fft_lines<N, +1, B, B, NT>(buf, tw_s);
   const float s = 1.0f / N;

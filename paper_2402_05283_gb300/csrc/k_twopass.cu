@@ -102,11 +102,13 @@ k_prime(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 }
 
 // ---------------------------------------------------------------- column pass
-__device__ __forceinline__ float2 project(float2 G, float a, double& err, double w) {
+// G' = a G / |G|; err += w (|G| - a)^2 in FP32 (a thread's few dozen
+// terms; FP64 across threads and blocks)
+__device__ __forceinline__ float2 project(float2 G, float a, float& err, float w) {
   if (a < 0.0f) return G;  // an unmeasured pair (mask): free, no error term
   const float m = sqrtf(G.x * G.x + G.y * G.y);
-  const double d = (double)m - (double)a;
-  err += w * d * d;
+  const float d = m - a;
+  err = fmaf(w * d, d, err);
   if (m > 0.0f) {
     const float s = a / m;
     return make_float2(G.x * s, G.y * s);
@@ -154,13 +156,13 @@ k_colpass(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   }
   __syncthreads();
   fft_lines<N, -1, B, B, NT>(buf, tw_s);
-  double err = 0.0;
+  float err = 0.0f;
   const float* An = A_main + (size_t)n * N * H;  // [kx][ky]
   for (int idx = threadIdx.x; idx < N * B; idx += NT) {
     const int ky = idx / B, b = idx - ky * B;
     const int c = c0 + b;
     if (c == 0) continue;
-    buf[idx] = project(buf[idx], An[(size_t)c * N + ky], err, 2.0);
+    buf[idx] = project(buf[idx], An[(size_t)c * N + ky], err, 2.0f);
   }
   if (c0 == 0) {
     // packed column: Z = G(.,0) + i G(.,N/2), both Hermitian along ky
@@ -169,7 +171,7 @@ k_colpass(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       const float2 z = buf[ky * B], zm = buf[km * B];
       const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
       const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-      const double w = (ky == 0 || ky == H) ? 1.0 : 2.0;
+      const float w = (ky == 0 || ky == H) ? 1.0f : 2.0f;
       const float2 p0 = project(g0, An[ky], err, w);
       const float2 pn = project(gn, A_nyq[(size_t)n * N + ky], err, w);
       buf[ky * B] = make_float2(p0.x - pn.y, p0.y + pn.x);
@@ -183,7 +185,7 @@ k_colpass(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     const int y = idx / B, b = idx - y * B;
     Hn[(size_t)y * H + c0 + b] = cscale(buf[idx], inv);
   }
-  const double s = block_sum<NT>(err, red);
+  const double s = block_sum<NT>((double)err, red);
   if (threadIdx.x == 0) atomicAdd(err_acc + n, s);
 }
 
