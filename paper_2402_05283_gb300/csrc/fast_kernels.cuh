@@ -396,24 +396,25 @@ template <int N, int PREC> struct ColW {
 template <int N, int PREC>
 constexpr size_t col_smem() { return ColW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(ColW<N, PREC>::WARPS); }
 
-// G' = a G / |G| (a where G = 0); err += w (|G| - a)^2; in plans with a
-// missing-data mask (MASKED), a < 0 marks a pixel left free.  The per-thread
-// partial sum stays in FP32 (at most a few hundred terms); the reduction
-// across threads, blocks and columns is FP64.
+// G' = a G / |G| (a where G = 0); e += (|G| - a)^2, unweighted (the caller
+// keeps one sum per weight).  In plans with a missing-data mask (MASKED),
+// a < 0 marks a pixel left free.  Branch-free: G = 0 takes rsqrt(1) and the
+// direction (1, 0), and |G| - a = 0 * 1 - a.  The per-thread partial sum
+// stays in FP32 (at most a few hundred terms); the reduction across
+// threads, blocks and columns is FP64.
 template <bool MASKED>
-__device__ __forceinline__ float2 project_w(float2 G, float a, float& err, float w) {
+__device__ __forceinline__ float2 project_w(float2 G, float a, float& e) {
   if constexpr (MASKED)
     if (a < 0.0f) return G;  // an unmeasured pair (mask): free, no error term
   const float r2 = fmaf(G.x, G.x, G.y * G.y);
-  if (r2 > 0.0f) {
-    const float inv = rsqrtf(r2);
-    const float d = fmaf(r2, inv, -a);
-    err = fmaf(w * d, d, err);
-    const float s = a * inv;
-    return make_float2(G.x * s, G.y * s);
-  }
-  err = fmaf(w * a, a, err);
-  return make_float2(a, 0.0f);
+  const bool zero = !(r2 > 0.0f);
+  const float inv = rsqrtf(zero ? 1.0f : r2);
+  const float d = fmaf(r2, inv, -a);
+  e = fmaf(d, d, e);
+  const float s = a * inv;
+  // __fmul_rn: a product the compiler may not contract into the caller's
+  // next add, so every instance of the kernels rounds the same way
+  return make_float2(__fmul_rn(zero ? 1.0f : G.x, s), zero ? 0.0f : __fmul_rn(G.y, s));
 }
 
 template <int N, int PREC, bool MASKED>
@@ -442,12 +443,20 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const int n = tl.y;
   const int c0 = blockIdx.x * C::CB;
   float2* Hn = Hp + (size_t)n * N * H;
-  for (int idx = threadIdx.x; idx < N * C::CB; idx += C::NT) {
-    const int y = idx / C::CB, c = idx - y * C::CB;
-    cp_async8(buf + y * C::SP + c, Hn + (size_t)y * H + c0 + c);
+  // thread (row y0 + k RS, column cc) of the block: constant strides, so
+  // the unrolled copies differ only in immediate offsets
+  constexpr int RS = C::NT / C::CB;
+  static_assert(C::NT % C::CB == 0 && N % RS == 0 && (C::CB * N / 4) % C::NT == 0, "column staging");
+  const int y0 = threadIdx.x / C::CB, cc = threadIdx.x % C::CB;
+  {
+    const float2* src = Hn + (size_t)y0 * H + c0 + cc;
+    float2* dst = buf + y0 * C::SP + cc;
+#pragma unroll
+    for (int k = 0; k < N / RS; ++k) cp_async8(dst + k * RS * C::SP, src + (size_t)k * RS * H);
+    const float* Ablk = A_T + ((size_t)n * H + c0) * N + 4 * threadIdx.x;  // CB contiguous columns
+#pragma unroll
+    for (int k = 0; k < C::CB * N / 4 / C::NT; ++k) cp_async16(As + 4 * (threadIdx.x + k * C::NT), Ablk + 4 * k * C::NT);
   }
-  const float* Ablk = A_T + ((size_t)n * H + c0) * N;  // CB contiguous columns
-  for (int q = threadIdx.x; q < C::CB * N / 4; q += C::NT) cp_async16(As + 4 * q, Ablk + 4 * q);
   cp_async_commit();
   load_xtw<N>(xs, xtw, C::NT);
   cp_async_wait_all();
@@ -465,7 +474,7 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   __syncthreads();
   float2 b[FL::TB][FL::E2];
   lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
-  float err = 0.0f;
+  float err2 = 0.0f, err1 = 0.0f;  // error terms of weight 2 and 1
   const bool warp_packed = (c0 == 0 && warp == 0);  // line 0 of warp 0 holds column 0
   static_for<0, FL::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
@@ -475,7 +484,7 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       const float* Ac = As + col * N;
       static_for<0, FL::E2>([&](auto KK) {
         constexpr int j = decltype(KK)::value;
-        b[i][j] = project_w<MASKED>(b[i][j], Ac[FL::b_k(t, j)], err, 2.0f);
+        b[i][j] = project_w<MASKED>(b[i][j], Ac[FL::b_k(t, j)], err2);
       });
     }
   });
@@ -504,8 +513,8 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
           const float2 z = T[ky], zm = T[(N - ky) % N];
           const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
           const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-          const float2 p0 = project_w<MASKED>(g0, A0[ky], err, 1.0f);
-          const float2 pn = project_w<MASKED>(gn, __ldg(An + ky), err, 1.0f);
+          const float2 p0 = project_w<MASKED>(g0, A0[ky], err1);
+          const float2 pn = project_w<MASKED>(gn, __ldg(An + ky), err1);
           b[i][j] = make_float2(p0.x - pn.y, p0.y + pn.x);
         });
       }
@@ -525,11 +534,13 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
     });
   });
   __syncthreads();
-  for (int idx = threadIdx.x; idx < N * C::CB; idx += C::NT) {
-    const int y = idx / C::CB, c = idx - y * C::CB;
-    Hn[(size_t)y * H + c0 + c] = buf[y * C::SP + c];
+  {
+    float2* dst = Hn + (size_t)y0 * H + c0 + cc;
+    const float2* src = buf + y0 * C::SP + cc;
+#pragma unroll
+    for (int k = 0; k < N / RS; ++k) dst[(size_t)k * RS * H] = src[k * RS * C::SP];
   }
-  double errd = (double)err;
+  double errd = 2.0 * (double)err2 + (double)err1;
   for (int o = 16; o > 0; o >>= 1) errd += __shfl_down_sync(0xffffffffu, errd, o);
   if (lane == 0) red[warp] = errd;
   __syncthreads();

@@ -278,8 +278,9 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       });
     });
   };
-  // column task q: FFT_y, projection onto A_sym (error into err), IFFT_y
-  auto col_task = [&](int q, const float (&av)[FL::TB][FL::E2], float& err) {
+  // column task q: FFT_y, projection onto A_sym (error terms of weight 2
+  // into err2, of weight 1 into err1), IFFT_y
+  auto col_task = [&](int q, const float (&av)[FL::TB][FL::E2], float& err2, float& err1) {
     const int cl0 = (warp + q * F::NW) * FL::L;  // first local column of the task
     const int cg0 = rank * F::CW + cl0;           // its packed column index
     float2 a[FL::TA][FL::E1];
@@ -300,7 +301,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       if (cg0 + FL::b_line(t) != 0) {
         static_for<0, FL::E2>([&](auto KK) {
           constexpr int j = decltype(KK)::value;
-          b[i][j] = project_w<MASKED>(b[i][j], av[i][j], err, 2.0f);
+          b[i][j] = project_w<MASKED>(b[i][j], av[i][j], err2);
         });
       }
     });
@@ -328,8 +329,8 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
             const float2 z = T[ky], zm = T[(N - ky) % N];
             const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
             const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-            const float2 p0 = project_w<MASKED>(g0, av[i][j], err, 1.0f);
-            const float2 pn = project_w<MASKED>(gn, __ldg(An + ky), err, 1.0f);
+            const float2 p0 = project_w<MASKED>(g0, av[i][j], err1);
+            const float2 pn = project_w<MASKED>(gn, __ldg(An + ky), err1);
             b[i][j] = make_float2(p0.x - pn.y, p0.y + pn.x);
           });
         }
@@ -387,9 +388,9 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 #pragma unroll 1
     for (int q = 0; q < 2; ++q) {
       if (q) load_av(q, av);
-      float err = 0.0f;
-      col_task(q, av, err);
-      errd += (double)err;
+      float err2 = 0.0f, err1 = 0.0f;
+      col_task(q, av, err2, err1);
+      errd += 2.0 * (double)err2 + (double)err1;
     }
     for (int o = 16; o > 0; o >>= 1) errd += __shfl_down_sync(0xffffffffu, errd, o);
     if (lane == 0) red[warp] = errd;
