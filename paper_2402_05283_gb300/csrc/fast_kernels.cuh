@@ -135,9 +135,12 @@ __device__ __forceinline__ void store_pairs_w(float2 (&b)[FL::TB][FL::E2], float
     const float2* Z = T + line * N;
     float2* r0 = Hn + (size_t)(2 * (pair0 + line)) * H;
     float2* r1 = r0 + H;
-    for (int k = lane; k < H; k += 32) {
+    static_assert(H % 32 == 0, "row pairs");
+#pragma unroll
+    for (int kk = 0; kk < H / 32; ++kk) {
+      const int k = lane + 32 * kk;
       float2 h0, h1;
-      if (k == 0) {
+      if (kk == 0 && lane == 0) {
         const float2 z0 = Z[0], zn = Z[H];
         h0 = make_float2(z0.x, zn.x);
         h1 = make_float2(z0.y, zn.y);
@@ -192,11 +195,14 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   // the warp's 2L packed spectrum rows (contiguous) into its tile, then the
   // old iterate, which is needed only after the inverse FFT
   {
-    const float2* hrow = Hn + (size_t)(2 * pair0) * H;
-    for (int q = lane; q < FL::L * N / 2; q += 32) cp_async16(T + 2 * q, hrow + 2 * q);
+    static_assert((FL::L * N / 2) % 32 == 0 && (RW::GFLOATS / 4) % 32 == 0, "row staging");
+    const float2* hrow = Hn + (size_t)(2 * pair0) * H + 2 * lane;
+#pragma unroll
+    for (int k = 0; k < FL::L * N / 64; ++k) cp_async16(T + 2 * (lane + 32 * k), hrow + 64 * k);
     cp_async_commit();
   }
-  for (int q = lane; q < RW::GFLOATS / 4; q += 32) cp_async16(Gs + 4 * q, grow + 4 * q);
+#pragma unroll
+  for (int k = 0; k < RW::GFLOATS / 128; ++k) cp_async16(Gs + 4 * (lane + 32 * k), grow + 4 * lane + 128 * k);
   cp_async_commit();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (err_slot >= 0) {
@@ -214,23 +220,41 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   // packed row spectra -> Z = H(row 2p) + i H(row 2p+1), B layout, without
   // branches: k < H reads column k, k > H column N - k (sign s = -1)
   float2 b[FL::TB][FL::E2];
-  static_for<0, FL::TB>([&](auto II) {
-    constexpr int i = decltype(II)::value;
-    const int t = lane + 32 * i;
-    const float2* r0 = T + FL::b_line(t) * N;
-    const float2* r1 = r0 + H;
+  if constexpr (std::is_same_v<FL, PairLines512>) {
+    // lane (kl, h) holds k = kl + 16 j + H h: column c = kl + 16 j (h = 0)
+    // or N - k = H - kl - 16 j (h = 1), one base and one stride a lane;
+    // only j = 0 of lanes 0 and 1 meets column 0 (k = 0 and k = H)
+    const int h = lane & 1, kl = lane >> 1;
+    const int bo = h ? H - kl : kl, sj = h ? -16 : 16;
+    const float s = h ? -1.0f : 1.0f;
     static_for<0, FL::E2>([&](auto KK) {
       constexpr int j = decltype(KK)::value;
-      const int k = FL::b_k(t, j);
-      const bool up = k > H;
-      const int c = up ? N - k : (k == H ? 0 : k);
-      const float s = up ? -1.0f : 1.0f;
-      const float2 h0 = r0[c], h1 = r1[c];
+      const int c = (bo + sj * j) & (H - 1);
+      const float2 h0 = T[c], h1 = T[H + c];
       float2 z = make_float2(fmaf(-s, h1.y, h0.x), fmaf(s, h0.y, h1.x));
-      if (c == 0) z = k == 0 ? make_float2(h0.x, h1.x) : make_float2(h0.y, h1.y);
-      b[i][j] = z;
+      if constexpr (j == 0)
+        if (c == 0) z = h ? make_float2(h0.y, h1.y) : make_float2(h0.x, h1.x);
+      b[0][j] = z;
     });
-  });
+  } else {
+    static_for<0, FL::TB>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      const int t = lane + 32 * i;
+      const float2* r0 = T + FL::b_line(t) * N;
+      const float2* r1 = r0 + H;
+      static_for<0, FL::E2>([&](auto KK) {
+        constexpr int j = decltype(KK)::value;
+        const int k = FL::b_k(t, j);
+        const bool up = k > H;
+        const int c = up ? N - k : (k == H ? 0 : k);
+        const float s = up ? -1.0f : 1.0f;
+        const float2 h0 = r0[c], h1 = r1[c];
+        float2 z = make_float2(fmaf(-s, h1.y, h0.x), fmaf(s, h0.y, h1.x));
+        if (c == 0) z = k == 0 ? make_float2(h0.x, h1.x) : make_float2(h0.y, h1.y);
+        b[i][j] = z;
+      });
+    });
+  }
   __syncwarp();  // the tile is the transforms' scratch from here on
   float2 a[FL::TA][FL::E1];
   lines_inv<N, PREC, FL>(b, a, T, xs, lane, &tc);
