@@ -119,8 +119,8 @@ def make_inputs(device, n_angles=NP):
 # profiles/k_rowpass_w_k_colpass_w_n512_np180.md (180 angles a launch; every
 # angle moves the same bytes, so a launch's traffic scales with its angles).
 # Valid only while the kernel is the one captured there.
-NCU_TRAFFIC_PER_ANGLE = {("k_rowpass", 512): (383.463168e6 + 316.570368e6) / 180,
-                         ("k_colpass", 512): (283.570176e6 + 135.188480e6) / 180}
+NCU_TRAFFIC_PER_ANGLE = {("k_rowpass", 512): (383.464704e6 + 317.140224e6) / 180,
+                         ("k_colpass", 512): (283.579904e6 + 134.985728e6) / 180}
 
 
 def roofline_figures(plan, cp, peaks, Np_total, angle_iters):
