@@ -129,7 +129,7 @@ def roofline_figures(plan, cp, peaks, Np_total, angle_iters):
     total = sum(v[0] for v in stats.values()) or 1.0
     kind = max(stats, key=lambda k: stats[k][0])
     ms, launches = stats[kind]
-    # algorithmic bytes per angle of one launch (kernel table)
+    # algorithmic bytes per angle of one launch: what each kernel must read and write
     NN = N * N
     per_angle = {
         cp.KERNEL_COLPASS: 4 * NN + 4 * NN + 2 * NN + 4 * N,        # Hp in/out, A_sym
