@@ -308,7 +308,39 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 // ---------------------------------------------------------------- Eq. 4 taps
 // a (A layout) of this warp's row pairs = sum_k alpha_k tap_k (Eq. 4), or
 // the image itself for a single tap.  Taps outermost: every load of one tap
-// is independent, so a warp keeps 2 * TA * E1 loads in flight per tap.
+// is independent, so a warp keeps 2 * TA * E1 loads in flight per tap.  The
+// mirror and object choices are uniform over a tap, so each (mirrored,
+// object) combination runs its own loop: pixel x reads column x, or N - x
+// mirrored (0 for x = 0, which only m = 0 can hold), at a per-lane base plus
+// a constant offset.
+template <int N, class FL, bool MIR, bool OBJ>
+__device__ __forceinline__ void blend_tap(float2 (&a)[FL::TA][FL::E1], const float* src,
+                                          const uint32_t* sk, float alpha, int W, int pair0,
+                                          int lane) {
+  static_for<0, FL::TA>([&](auto II) {
+    constexpr int i = decltype(II)::value;
+    const int t = lane + 32 * i;
+    const int y0 = 2 * (pair0 + FL::a_line(t));
+    const float* r0 = src + (size_t)y0 * N;
+    const uint32_t* m0 = sk + (size_t)y0 * W;
+    static_for<0, FL::E1>([&](auto MM) {
+      constexpr int m = decltype(MM)::value;
+      const int x = FL::a_x(t, m);
+      const int xs_ = MIR ? (m == 0 ? (N - x) & (N - 1) : N - x) : x;
+      float v0 = __ldg(r0 + xs_);
+      float v1 = __ldg(r0 + N + xs_);
+      if constexpr (OBJ) {
+        const bool in0 = (__ldg(m0 + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
+        const bool in1 = (__ldg(m0 + W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
+        v0 = (in0 && v0 >= 0.0f) ? v0 : 0.0f;
+        v1 = (in1 && v1 >= 0.0f) ? v1 : 0.0f;
+      }
+      a[i][m].x = fmaf(alpha, v0, a[i][m].x);
+      a[i][m].y = fmaf(alpha, v1, a[i][m].y);
+    });
+  });
+}
+
 template <int N, class FL = WarpLines<N>>
 __device__ __forceinline__ void blend_rows(float2 (&a)[FL::TA][FL::E1], const TapTab& tt,
                                            const CoupleArgs& ca, int W, int pair0, int lane) {
@@ -316,32 +348,19 @@ __device__ __forceinline__ void blend_rows(float2 (&a)[FL::TA][FL::E1], const Ta
   static_for<0, FL::TA>([&](auto II) {
     static_for<0, FL::E1>([&](auto MM) { a[decltype(II)::value][decltype(MM)::value] = make_float2(0.f, 0.f); });
   });
+  const bool obj = ca.object != 0;
   for (int k = 0; k < ntaps; ++k) {
     const float alpha = tt.w[k];
     if (alpha == 0.0f) continue;  // a tap on an absent angle
     const float* src = tt.src[k];
     const uint32_t* sk = tt.s[k];
-    const bool mir = tt.mir[k] != 0;
-    static_for<0, FL::TA>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      const int t = lane + 32 * i;
-      const int y0 = 2 * (pair0 + FL::a_line(t));
-      static_for<0, FL::E1>([&](auto MM) {
-        constexpr int m = decltype(MM)::value;
-        const int x = FL::a_x(t, m);
-        const int xs_ = mir ? ((N - x) & (N - 1)) : x;
-        float v0 = __ldg(src + (size_t)y0 * N + xs_);
-        float v1 = __ldg(src + (size_t)(y0 + 1) * N + xs_);
-        if (ca.object) {
-          const bool in0 = (__ldg(sk + (size_t)y0 * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
-          const bool in1 = (__ldg(sk + (size_t)(y0 + 1) * W + (xs_ >> 5)) >> (xs_ & 31)) & 1u;
-          v0 = (in0 && v0 >= 0.0f) ? v0 : 0.0f;
-          v1 = (in1 && v1 >= 0.0f) ? v1 : 0.0f;
-        }
-        a[i][m].x = fmaf(alpha, v0, a[i][m].x);
-        a[i][m].y = fmaf(alpha, v1, a[i][m].y);
-      });
-    });
+    if (tt.mir[k]) {
+      if (obj) blend_tap<N, FL, true, true>(a, src, sk, alpha, W, pair0, lane);
+      else blend_tap<N, FL, true, false>(a, src, sk, alpha, W, pair0, lane);
+    } else {
+      if (obj) blend_tap<N, FL, false, true>(a, src, sk, alpha, W, pair0, lane);
+      else blend_tap<N, FL, false, false>(a, src, sk, alpha, W, pair0, lane);
+    }
   }
 }
 

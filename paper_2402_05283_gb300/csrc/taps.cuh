@@ -22,32 +22,47 @@ struct TapTab {
   float w[CPRA_MAX_TAPS];
 };
 
-// filled by thread 0; the caller synchronises the block before use
+// angle of tap offset j = n + k - n_taps/2 (mod Np) and the number of times
+// it crossed the seam; the common case 0 <= j < Np needs no division
+__device__ __forceinline__ int tap_angle(int j, int Np, int& wraps) {
+  if (j >= 0 && j < Np) {
+    wraps = 0;
+    return j;
+  }
+  wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
+  return ((j % Np) + Np) % Np;
+}
+
+// thread k < n_taps fills tap k (every such thread sums the present taps'
+// alpha in tap order, so the weights are the same in all of them); the
+// caller synchronises the block before use.
 // With ca.sweep (Gauss-Seidel), a tap on an angle before n in the sweep
 // reads this episode's image from g_new; every other tap reads g_src.
 template <int N>
 __device__ __forceinline__ void fill_taps(TapTab& tt, const CoupleArgs& ca, const float* g_src,
                                           const float* g_new, const uint32_t* S, int n, int Np,
                                           int W, const uint8_t* present) {
-  if (threadIdx.x != 0) return;
   const int nt = ca.n_taps;
+  const int k = threadIdx.x;
+  if (k >= nt) return;
   double sum = 0.0;
   bool all = true;
-  for (int k = 0; k < nt; ++k) {
-    const int j = n + k - nt / 2;
-    const int jm = ((j % Np) + Np) % Np;
-    const int wraps = (j >= 0) ? j / Np : -((-j + Np - 1) / Np);
-    tt.src[k] = (ca.sweep && jm < n ? g_new : g_src) + (size_t)jm * N * N;
-    tt.s[k] = S + (size_t)jm * N * W;
-    tt.mir[k] = ca.mirror && (wraps & 1);
-    const bool on = present == nullptr || present[jm] != 0;
-    tt.w[k] = on ? (nt == 1 ? 1.0f : ca.alpha[k]) : 0.0f;
-    if (on) sum += (double)ca.alpha[k];
+  for (int q = 0; q < nt; ++q) {
+    int wq;
+    const int jq = tap_angle(n + q - nt / 2, Np, wq);
+    const bool on = present == nullptr || present[jq] != 0;
+    if (on) sum += (double)ca.alpha[q];
     all = all && on;
   }
-  if (!all && nt > 1)
-    for (int k = 0; k < nt; ++k)
-      if (tt.w[k] != 0.0f) tt.w[k] = (float)((double)ca.alpha[k] / sum);
+  int wraps;
+  const int jm = tap_angle(n + k - nt / 2, Np, wraps);
+  tt.src[k] = (ca.sweep && jm < n ? g_new : g_src) + (size_t)jm * N * N;
+  tt.s[k] = S + (size_t)jm * N * W;
+  tt.mir[k] = ca.mirror && (wraps & 1);
+  const bool on = present == nullptr || present[jm] != 0;
+  float w = on ? (nt == 1 ? 1.0f : ca.alpha[k]) : 0.0f;
+  if (!all && nt > 1 && w != 0.0f) w = (float)((double)ca.alpha[k] / sum);
+  tt.w[k] = w;
 }
 
 }  // namespace cpra
