@@ -431,6 +431,7 @@ cpra_status build_gridding(cpra_plan_s* p) {
   }
   CK(cudaStreamSynchronize(p->stream), "grid upload sync");
   a.ready = true;
+  a.grid_ok = true;
   return CPRA_OK;
 }
 
@@ -741,11 +742,17 @@ cpra_status cpra_load_intensities(cpra_plan_t p, const float* I, int32_t first, 
   CK(cudaStreamSynchronize(p->stream), "prepare sync");
   if (flag) return fail(p, CPRA_ERR_INVALID_ARG, "intensities must be finite and non-negative");
   if (theta) {
-    for (int i = 0; i < count; ++i) {
+    for (int i = 0; i < count; ++i)
       if (!std::isfinite(theta[i])) return fail(p, CPRA_ERR_INVALID_ARG, "theta not finite");
-      p->theta[first + i] = theta[i];
-    }
+    bool moved = false;
+    for (int i = 0; i < count; ++i)
+      if (p->theta[first + i] != theta[i]) {
+        p->theta[first + i] = theta[i];
+        moved = true;
+      }
     p->asmb.ready = false;
+    // the gridding lists depend on the angles only: rebuilt when one moved
+    if (moved) p->asmb.grid_ok = false;
   }
   if (p->mask) p->masked = true;
   for (int i = 0; i < count; ++i)
@@ -999,7 +1006,7 @@ static cpra_status ensure_assembly(cpra_plan_s* p) {
     if (!a.F || !a.vol || !a.cell_ptr || !a.moments)
       return fail(p, CPRA_ERR_OUT_OF_MEMORY, "assembly allocation failed");
   }
-  if (!a.ready) return build_gridding(p);
+  if (!a.grid_ok) return build_gridding(p);
   return CPRA_OK;
 }
 

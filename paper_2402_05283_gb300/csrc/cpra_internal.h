@@ -35,7 +35,8 @@ struct Assembly {
   double* ent_w = nullptr;      // normalised bilinear weight
   double* moments = nullptr;    // [Np][3] sum rho, sum rho*z, sum rho*u
   int64_t n_ent = 0;
-  bool ready = false;
+  bool ready = false;    // a volume of the current angles may be read
+  bool grid_ok = false;  // the gridding lists match the current angles
 };
 
 }  // namespace cpra
