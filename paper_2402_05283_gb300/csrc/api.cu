@@ -370,7 +370,6 @@ Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles, int first_til
 cpra_status build_gridding(cpra_plan_s* p) {
   const int N = p->N, Np = p->Np, NN = N * N;
   std::vector<double> wsum(NN, 0.0);
-  std::vector<int32_t> cnt(NN, 0);
   struct Ent { int32_t cell, idx; double w; };
   std::vector<Ent> ents;
   ents.reserve((size_t)4 * Np * N);
@@ -385,8 +384,10 @@ cpra_status build_gridding(cpra_plan_s* p) {
         for (int dj = 0; dj < 2; ++dj) {
           const double w = (di ? fx : 1.0 - fx) * (dj ? fy : 1.0 - fy);
           if (w == 0.0) continue;
-          const int ii = (int)(((long long)i0 + di) % N + N) % N;
-          const int jj = (int)(((long long)j0 + dj) % N + N) % N;
+          // |ku cos|, |ku sin| <= N/2, so one conditional wrap is exact
+          int ii = (int)i0 + di, jj = (int)j0 + dj;
+          ii = ii < 0 ? ii + N : (ii >= N ? ii - N : ii);
+          jj = jj < 0 ? jj + N : (jj >= N ? jj - N : jj);
           const int cell = jj * N + ii;
           ents.push_back({cell, n * N + k, w});
           wsum[cell] += w;
