@@ -63,3 +63,35 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
     monkeypatch.setattr(bench, "cpu_baseline", lambda *a, **k: called.append(1))
     bench.run_reference(A())
     assert not called and capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
+    """Rank 0 prints one JSON line with the keys the driver reads, its e2e
+    moving no bytes and its cpu_baseline describing the same run."""
+    import json
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class A:
+        gpus, steps, warmup = 1, 3, 1
+
+    rates = iter([1.0, 40.0, 60.0, 50.0])
+    monkeypatch.setattr(bench, "sample_inputs", lambda: (None, None))
+    monkeypatch.setattr(bench, "cpu_baseline", lambda *a, **k: {
+        "value": next(rates), "unit": "angle-iterations/s", "cores": 4, "kind": "oracle",
+        "sample": "stub"})
+    bench.run_reference(A())
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] == 50.0  # median of the timed steps
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
