@@ -707,12 +707,13 @@ def run_gpu(args):
 
     # end to end through the C ABI with pinned host buffers
     I_host = I_dev.cpu().pin_memory()
+    S_host = S_box.cpu().pin_memory()
     vol_host = torch.empty((N, N, N, 2), dtype=torch.float32).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
 
     def step_host():
         plan.load_intensities(I_host, 0, thetas)
-        plan.load_support(S_box)
+        plan.load_support(S_host)
         plan.reset()
         plan.iterate(IT)
         plan.assemble_3d(vol_host)
@@ -758,7 +759,7 @@ def run_gpu(args):
             "kernel_ms": {k: round(v[0] / args.steps, 3) for k, v in kstats.items() if v[1]},
             "cpu_baseline": cb,
             "e2e": {"value": round(e2e_value, 1), "unit": "angle-iterations/s",
-                    "h2d_bytes_per_step": int(I_host.numel() * 4),
+                    "h2d_bytes_per_step": int(I_host.numel() * 4 + S_host.numel() * S_host.element_size()),
                     "d2h_bytes_per_step": int(vol_host.numel() * 4)},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
