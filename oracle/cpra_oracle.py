@@ -27,6 +27,9 @@ diffraction imaging"):
     with the paper's 0.1 relative threshold.
   * RAAR (Luke, the paper's ref. 39), the update the paper runs with
     beta = 0.9 on its S. aureus data (results section).
+  * Result verification (results section): PRTF and the Fourier shell
+    correlation (FSC, its ref. 37) against the known object, each read at
+    the 0.5 cut-off.
 
 Readings where the paper is silent or garbled (the same list is kept with the
 design notes):
@@ -133,7 +136,7 @@ __all__ = [
     "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
     "r_factor", "raar_update", "episode_error", "select_best", "centrally_inverted", "prtf",
     "merge_episodes", "assemble_spectra", "measured_cells", "backprojected_support", "blur3",
-    "refine_3d", "support_shifts",
+    "refine_3d", "support_shifts", "align_to", "fsc", "fsc_resolution",
 ]
 
 
@@ -767,21 +770,29 @@ class OracleRun:
 # Evaluation metrics
 # --------------------------------------------------------------------------
 def r_factor(g, A):
-    """R = sum ||G| - A| / sum A per pattern."""
+    """R = sum ||G| - A| / sum A per pattern, G = DFT2(g): the crystallographic
+    R-factor of the modulus fit (reading 11 of the error metrics; the paper
+    names only a "reconstruction error").  Sums run over the two pixel axes
+    of each pattern; returns one value per pattern."""
     G = dft2(g)
     return np.abs(np.abs(G) - A).sum(axis=(-2, -1)) / A.sum(axis=(-2, -1))
 
 
-def real_space_error(rec: np.ndarray, true: np.ndarray) -> float:
-    """min over {x, -x} and integer shifts of ||c rec - true|| / ||true||, best scale c.
+def align_to(rec: np.ndarray, true: np.ndarray):
+    """The copy of rec that best matches true under the ambiguities phase
+    retrieval leaves for a positive density: central inversion, integer
+    (periodic) translation and a scale.  Returns (aligned, error) with
+    aligned = c * roll(cand, shift), error = ||aligned - true|| / ||true||,
+    minimised over cand in {rec, flip(rec)} with, for each, the shift that
+    maximises the circular cross-correlation (an FFT, library step) and the
+    least-squares scale c = <moved, true> / <moved, moved>.
 
-    The shift maximising the circular cross-correlation is found with an FFT
-    (library step); -x is the central inversion about index 0.
-    """
+    np.flip maps x -> -1 - x, the central inversion x -> -x followed by a
+    shift of -1 on every axis, which the shift search absorbs."""
     rec = np.asarray(rec, dtype=np.float64)
     true = np.asarray(true, dtype=np.float64)
     axes = tuple(range(rec.ndim))
-    best = np.inf
+    best, best_img = np.inf, None
     Ft = np.fft.fftn(true)
     for cand in (rec, np.flip(rec, axis=axes)):
         xc = np.fft.ifftn(Ft * np.conj(np.fft.fftn(cand))).real
@@ -790,5 +801,47 @@ def real_space_error(rec: np.ndarray, true: np.ndarray) -> float:
         den = (moved * moved).sum()
         c = (moved * true).sum() / den if den > 0 else 0.0
         err = np.linalg.norm(c * moved - true) / np.linalg.norm(true)
-        best = min(best, err)
-    return float(best)
+        if err < best:
+            best, best_img = err, c * moved
+    return best_img, float(best)
+
+
+def real_space_error(rec: np.ndarray, true: np.ndarray) -> float:
+    """min over {x, -x} and integer shifts of ||c rec - true|| / ||true||, best
+    scale c (reading 11 of the error metrics): the error of align_to."""
+    return align_to(rec, true)[1]
+
+
+def fsc(vol_a: np.ndarray, vol_b: np.ndarray) -> np.ndarray:
+    """Fourier shell correlation of two N^3 volumes, the paper's measure of
+    agreement between the original and the reconstructed object (results
+    section, its ref. 37; the resolution is read where it falls below 0.5):
+
+        FSC(s) = Re sum_{k in s} F_a(k) conj(F_b(k))
+                 / sqrt( sum_{k in s} |F_a(k)|^2  sum_{k in s} |F_b(k)|^2 ),
+
+    F = DFT3 of the volume, shell s = {k : round(|k|) = s} over signed
+    frequencies k in [-N/2, N/2)^3, s = 0..N/2-1 (the rings of the PRTF, in
+    three dimensions); 0 where a shell has no power.  Translation and
+    inversion are not removed here: align the volumes first (align_to)."""
+    Fa = dft3(np.asarray(vol_a))
+    Fb = dft3(np.asarray(vol_b))
+    N = Fa.shape[-1]
+    k = signed_freq(N)
+    shell = np.rint(np.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2
+                            + k[None, None, :] ** 2)).astype(np.int64)
+    out = np.zeros(N // 2)
+    for s in range(N // 2):
+        m = shell == s
+        num = np.real(np.sum(Fa[m] * np.conj(Fb[m])))
+        den = math.sqrt(np.sum(np.abs(Fa[m]) ** 2) * np.sum(np.abs(Fb[m]) ** 2))
+        out[s] = num / den if den > 0 else 0.0
+    return out
+
+
+def fsc_resolution(curve: np.ndarray, threshold: float = 0.5) -> int:
+    """The first shell whose correlation falls below the threshold (0.5, the
+    paper's cut-off for FSC and PRTF); len(curve) when none does.  The
+    resolution R^-1 is that shell's spatial frequency, shell / (N px)."""
+    below = np.nonzero(np.asarray(curve) < threshold)[0]
+    return int(below[0]) if below.size else int(len(curve))
