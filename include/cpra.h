@@ -43,8 +43,25 @@ typedef enum {
   CPRA_ERR_CUDA = 3,          /* a CUDA runtime call failed                */
   CPRA_ERR_NOT_READY = 4,     /* inputs missing (e.g. angles not loaded)   */
   CPRA_ERR_TIMEOUT = 5,       /* a bounded device wait gave up             */
-  CPRA_ERR_UNSUPPORTED = 6    /* valid request the library cannot run     */
+  CPRA_ERR_UNSUPPORTED = 6,   /* valid request the library cannot run     */
+  CPRA_ERR_NONFINITE = 7      /* a non-finite iterate (diverged, NaN state) */
 } cpra_status;
+
+/* Device-side failures.  Each plan has a status word in pinned host memory
+ * that its kernels write (cudaHostAlloc, mapped; besides the device buffers
+ * the allocator callbacks provide).  The kernel that publishes an angle's
+ * FP64 Fourier error flags it when the error sums are not finite: a
+ * non-finite iterate (a diverged run, a loaded state holding NaN or Inf) or
+ * an invalid pattern (a negative or non-finite intensity, which the
+ * preparation turns into a NaN error constant).  Calls read the word without
+ * waiting for the stream: cpra_iterate, cpra_assemble_3d, cpra_refine_3d,
+ * cpra_result and cpra_batch_iterate report a flag set by work that has
+ * completed by the time they are called, and every call that waits for the
+ * stream (cpra_sync, results copied to host memory, cpra_iterate with
+ * err_out) reports a flag set by any work queued before it.  The status is
+ * CPRA_ERR_INVALID_ARG (naming the angle) when a loaded pattern was invalid,
+ * CPRA_ERR_NONFINITE otherwise; it stays set until cpra_reset or
+ * cpra_load_state clears it. */
 
 enum { CPRA_WRAP_LITERAL = 0, CPRA_WRAP_MIRROR = 1 };
 enum { CPRA_BLEND_STATE = 0, CPRA_BLEND_OBJECT = 1 };
@@ -181,8 +198,12 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out);
  * first_angle .. first_angle+count-1 with their angles theta_rad[count]
  * (radians, host memory, may be NULL to keep theta_n = n*pi/Np).  Prepares
  * A = sqrt(I) in FFT order, its Hermitian-symmetrised half plane and the FP64
- * error constants (Eq. 1-3).  Non-finite or negative intensities give
- * INVALID_ARG and leave the angles unloaded. */
+ * error constants (Eq. 1-3).  The call queues the upload and the preparation
+ * on the plan's stream and returns without waiting for them: host buffers in
+ * pinned memory must stay unchanged until the stream has passed the copy
+ * (pageable buffers are copied before the call returns).  Non-finite or
+ * negative intensities are reported by the first iteration on them, through
+ * the plan's status word (see above: INVALID_ARG naming the angle). */
 cpra_status cpra_load_intensities(cpra_plan_t plan, const float* I, int32_t first_angle,
                                   int32_t count, const double* theta_rad);
 
@@ -195,17 +216,20 @@ cpra_status cpra_load_intensities(cpra_plan_t plan, const float* I, int32_t firs
  * beamstop is symmetric): the modulus projection leaves the others' G as it
  * is and the Fourier error sums over the constrained pixels only.  Paper:
  * its cell patterns were cropped with a beamstop in the centre (results
- * section).  Host or device memory, read during the call. */
+ * section).  Host or device memory; the copy is queued on the plan's stream
+ * (pinned host buffers must stay unchanged until the stream has passed it). */
 cpra_status cpra_load_mask(cpra_plan_t plan, const uint8_t* mask, int32_t per_angle);
 
 /* Set the support from S (uint8, nonzero = inside).  per_angle = 1: S is
  * [Np][N][N]; per_angle = 0: one [N][N] mask for every angle.  S = NULL sets
- * the padded bounding box (central N/2 x N/2 square) for every angle. */
+ * the padded bounding box (central N/2 x N/2 square) for every angle.  Like
+ * cpra_load_intensities, the call returns once the copy is queued. */
 cpra_status cpra_load_support(cpra_plan_t plan, const uint8_t* S, int32_t per_angle);
 
 /* Checkpoint restore: set the iterate g[Np][N][N] (float32) and the global
  * iteration counter t (>= 0).  Without this call the first cpra_iterate
- * starts from the seeded random guess on the current support (Step A). */
+ * starts from the seeded random guess on the current support (Step A).
+ * Waits for the plan's stream and clears its status word. */
 cpra_status cpra_load_state(cpra_plan_t plan, const float* g, int64_t t);
 
 /* Run n_iters global iterations (Step B): coupling (Eq. 4) before every
@@ -310,7 +334,10 @@ cpra_status cpra_result(cpra_plan_t plan, int32_t what, void* dst, size_t bytes)
 
 /* Restart the reconstruction: t = 0, the error history is cleared and the
  * next cpra_iterate starts again from the seeded guess (Step A).
- * Intensities, angles and the current support are kept. */
+ * Intensities, angles and the current support are kept.  A set status word
+ * (device-side failure) is cleared after waiting for the plan's stream; a
+ * failure that work queued before the reset flags after it is reported on
+ * the new run, so call cpra_sync first to see it on the old one. */
 cpra_status cpra_reset(cpra_plan_t plan);
 
 /* Kernel classes for cpra_kernel_stats. */
@@ -362,8 +389,11 @@ int64_t cpra_launch_count(void);
  * arrays, so calls that overlap on the GPU race: queue them on one stream or
  * order them.  count*N*N may be at most CPRA_SHRINKWRAP_STATIC_MAX_PIXELS
  * (2^20, e.g. 4 patterns of 512^2 or 256 of 64^2); larger requests return
- * INVALID_ARG.  Host pointers return INVALID_ARG.  The call returns after
- * queuing the work; errors are readable with cpra_last_error(NULL). */
+ * INVALID_ARG.  Host pointers, and device pointers of a device other than
+ * the current one, return INVALID_ARG.  The Gaussian taps are passed to the
+ * device as a kernel argument, so no host buffer outlives the call.  The
+ * call returns after queuing the work; errors are readable with
+ * cpra_last_error(NULL). */
 #define CPRA_SHRINKWRAP_STATIC_MAX_PIXELS (1 << 20)
 cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_in, uint8_t* S_out, int32_t N,
                                    int32_t count, float sigma, float tau, void* stream);
@@ -506,7 +536,8 @@ cpra_status cpra_server_stop(cpra_server_t s);
 /* Global iteration counter t of the plan (-1 for a NULL plan). */
 int64_t cpra_iteration(cpra_plan_t plan);
 
-/* Wait for the plan's stream; reports device-side failures (CUDA). */
+/* Wait for the plan's stream; reports device-side failures (CUDA, and the
+ * status word: INVALID_ARG for an invalid pattern, NONFINITE). */
 cpra_status cpra_sync(cpra_plan_t plan);
 
 /* Free every device buffer through cfg->free and the plan itself. */

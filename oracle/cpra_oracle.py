@@ -671,6 +671,7 @@ class OracleConfig:
     seed: int = 0
     update: int = HIO  # the rule before hio_iters: HIO or RAAR (R14)
     sweep: bool = False  # Gauss-Seidel episodes (R22) instead of Jacobi (R1)
+    fft: bool = False  # Jacobi steps take numpy.fft transforms (iterate_2d fft mode)
 
 
 @dataclass
@@ -711,7 +712,8 @@ class OracleRun:
         if self.t % c.n_ei == 0:
             self.g = couple(self.g, c.alpha, c.wrap, c.blend, self.S, self.present)
         algo = c.update if self.t < c.hio_iters else ER
-        g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True, C=self.C)
+        g, num, den, gp = iterate_2d(self.g, self.A, self.S, c.beta, algo, return_gp=True,
+                                     fft=c.fft, C=self.C)
         err = np.sqrt(num / den)
         if self.present is not None:  # absent angles keep their state (R13)
             on = np.asarray(self.present).astype(bool)

@@ -16,7 +16,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcpra.so")
 
-OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_READY, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_READY, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NONFINITE = range(8)
 WRAP_LITERAL, WRAP_MIRROR = 0, 1
 BLEND_STATE, BLEND_OBJECT = 0, 1
 FP32, BF16_TC, FP16_TC = 0, 1, 2
@@ -274,14 +274,39 @@ def cpra_launch_count() -> int:
     return int(lib().cpra_launch_count())
 
 
+def _static_arg(a, name: str, dtype_np, dtype_torch: str, need: int):
+    """Check one array of cpra_shrinkwrap_static without copying it: the call
+    exists for callers that cannot allocate, so nothing is made contiguous or
+    converted here.  Host arrays pass through to the C call, which rejects
+    them (INVALID_ARG)."""
+    if isinstance(a, np.ndarray):
+        ok_type = a.dtype == dtype_np
+        n, contig, ptr = a.size, a.flags.c_contiguous, a.ctypes.data
+    elif hasattr(a, "data_ptr"):
+        ok_type = str(a.dtype) == dtype_torch
+        n, contig, ptr = a.numel(), a.is_contiguous(), a.data_ptr()
+    else:
+        raise TypeError(f"{name}: unsupported array type {type(a)}")
+    if not ok_type:
+        raise TypeError(f"{name} must be {dtype_torch}, got {a.dtype}")
+    if n < need:
+        raise ValueError(f"{name} holds {n} elements, count*N*N = {need} needed")
+    if not contig:
+        raise ValueError(f"{name} must be contiguous (no copy is made)")
+    return ptr
+
+
 def cpra_shrinkwrap_static(g, S_in, S_out, N: int, count: int, sigma: float, tau: float,
                            stream=None):
-    """Shrink-wrap support update with no device allocation (device tensors only)."""
-    pg, kg = _ptr(g)
-    ps, ks = _ptr(S_in)
-    po, ko = _ptr(S_out)
+    """Shrink-wrap support update with no device allocation.
+
+    g: float32 [count][N][N], S_in / S_out: uint8 [count][N][N], all
+    contiguous device tensors on the current device; S_out may be S_in."""
+    need = int(count) * int(N) * int(N)
+    pg = _static_arg(g, "g", np.float32, "torch.float32", need)
+    ps = _static_arg(S_in, "S_in", np.uint8, "torch.uint8", need)
+    po = _static_arg(S_out, "S_out", np.uint8, "torch.uint8", need)
     _check(lib().cpra_shrinkwrap_static(pg, ps, po, N, count, sigma, tau, stream))
-    return kg, ks, ko
 
 
 def cpra_batch_create(plans, use_graph: bool = True):

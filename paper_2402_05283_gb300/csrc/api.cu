@@ -226,6 +226,37 @@ cpra_status ensure_err_cap(cpra_plan_s* p, int64_t need) {
   return upload_static(p);
 }
 
+// A failure that earlier work of this plan flagged in its status word (read
+// without waiting for the stream).  The status stays set until cpra_reset or
+// cpra_load_state: INVALID_ARG when a flagged angle's last loaded pattern
+// was invalid, NONFINITE for a non-finite iterate.
+cpra_status check_status(cpra_plan_s* p) {
+  if (!p->status_h) return CPRA_OK;
+  const volatile DevStatus* s = p->status_h;
+  if (s->flags == 0) return CPRA_OK;
+  const int n = s->angle;
+  // the error path only: which loads were invalid
+  std::vector<uint8_t> bad(p->Np, 0);
+  if (cudaStreamSynchronize(p->stream) == cudaSuccess &&
+      cudaMemcpy(bad.data(), p->bad, (size_t)p->Np, cudaMemcpyDeviceToHost) == cudaSuccess) {
+    for (int a = 0; a < p->Np; ++a)
+      if (bad[a])
+        return fail(p, CPRA_ERR_INVALID_ARG,
+                    "intensities of angle " + std::to_string(a) +
+                        " must be finite and non-negative (reload them, then cpra_reset)");
+  }
+  cudaGetLastError();
+  return fail(p, CPRA_ERR_NONFINITE,
+              "non-finite iterate (Fourier error of angle " + std::to_string(n) +
+                  "); cpra_reset or cpra_load_state clears it");
+}
+
+void clear_status(cpra_plan_s* p) {
+  if (!p->status_h) return;
+  p->status_h->flags = 0;
+  p->status_h->angle = -1;
+}
+
 cpra_status copy_out(cpra_plan_s* p, void* dst, const void* src, size_t bytes) {
   const bool dd = is_device_ptr(dst);
   // A device-to-host copy queued behind running kernels measured about 5x
@@ -235,7 +266,10 @@ cpra_status copy_out(cpra_plan_s* p, void* dst, const void* src, size_t bytes) {
   if (!dd) CK(cudaStreamSynchronize(p->stream), "result sync");
   CK(cudaMemcpyAsync(dst, src, bytes, dd ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      p->stream), "result copy");
-  if (!dd) CK(cudaStreamSynchronize(p->stream), "result sync");
+  if (!dd) {
+    CK(cudaStreamSynchronize(p->stream), "result sync");
+    return check_status(p);
+  }
   return CPRA_OK;
 }
 
@@ -302,6 +336,7 @@ JobStatic job_static(const cpra_plan_s* p) {
   j.xtw = p->xtw;
   j.tcw = p->tcw;
   j.present = p->partial ? p->present : nullptr;
+  j.status = p->status_d;
   j.Np = p->Np;
   j.W = p->W;
   j.beta = p->cfg.beta;
@@ -626,7 +661,7 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   p->tw = (float2*)A(N * 8);
   p->xtw = (float2*)A(N * 8);
   p->stage = (float*)A(Np * NN * 4);
-  p->flag = (int*)A(sizeof(int) * 4);
+  p->bad = (uint8_t*)A(Np);
   p->d_js = (JobStatic*)A(sizeof(JobStatic));
   p->d_tiles = (int2*)A(sizeof(int2) * Np);
   if (ok && cfg->shrinkwrap_every > 0) {
@@ -642,6 +677,19 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   if (!ok) {
     cpra_destroy(p);
     return fail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "device allocation failed");
+  }
+  {
+    // the status word: pinned host memory the kernels write through its
+    // device address, read by the host without a stream wait
+    cudaError_t he = cudaHostAlloc((void**)&p->status_h, sizeof(DevStatus), cudaHostAllocMapped);
+    if (he == cudaSuccess) he = cudaHostGetDevicePointer((void**)&p->status_d, p->status_h, 0);
+    if (he != cudaSuccess) {
+      cuda_fail(nullptr, he, "status word");
+      cpra_destroy(p);
+      return CPRA_ERR_CUDA;
+    }
+    p->status_h->flags = 0;
+    p->status_h->angle = -1;
   }
   std::vector<float2> tw(N);
   for (size_t k = 0; k < N; ++k) {
@@ -702,6 +750,7 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
       e = cudaMemcpyAsync(p->tcw, tcw.data(), tcw.size() * 2, cudaMemcpyHostToDevice, p->stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(p->err_acc, 0, Np * 8, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->bad, 0, Np, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->g, 0, Np * NN * 4, p->stream);
   std::vector<int2> tiles(Np);
   for (size_t n = 0; n < Np; ++n) tiles[n] = make_int2(0, (int)n);
@@ -736,15 +785,13 @@ cpra_status cpra_load_intensities(cpra_plan_t p, const float* I, int32_t first, 
        "intensity upload");
     src = p->stage;
   }
-  CK(cudaMemsetAsync(p->flag, 0, sizeof(int), p->stream), "flag reset");
-  CK(timed(p, CPRA_KERNEL_PREPARE, [&] { return launch_prepare(p, src, first, count); }), "prepare");
-  int flag = 0;
-  CK(cudaMemcpyAsync(&flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream), "flag read");
-  CK(cudaStreamSynchronize(p->stream), "prepare sync");
-  if (flag) return fail(p, CPRA_ERR_INVALID_ARG, "intensities must be finite and non-negative");
-  if (theta) {
+  if (theta)
     for (int i = 0; i < count; ++i)
       if (!std::isfinite(theta[i])) return fail(p, CPRA_ERR_INVALID_ARG, "theta not finite");
+  // no wait for the device: an invalid pattern is reported through the
+  // status word by the first iteration on it (k_prepare)
+  CK(timed(p, CPRA_KERNEL_PREPARE, [&] { return launch_prepare(p, src, first, count); }), "prepare");
+  if (theta) {
     bool moved = false;
     for (int i = 0; i < count; ++i)
       if (p->theta[first + i] != theta[i]) {
@@ -785,7 +832,6 @@ cpra_status cpra_load_mask(cpra_plan_t p, const uint8_t* mask, int32_t per_angle
   CK(cudaMemcpyAsync(p->mask, mask, bytes, is_device_ptr(mask) ? cudaMemcpyDeviceToDevice
                                                               : cudaMemcpyHostToDevice, p->stream),
      "mask upload");
-  CK(cudaStreamSynchronize(p->stream), "mask sync");
   return CPRA_OK;
 }
 
@@ -802,7 +848,6 @@ cpra_status cpra_load_support(cpra_plan_t p, const uint8_t* S, int32_t per_angle
     }
     CK(launch_support_u8(p, src, per_angle ? 1 : 0), "support");
   }
-  CK(cudaStreamSynchronize(p->stream), "support sync");
   return CPRA_OK;
 }
 
@@ -815,6 +860,7 @@ cpra_status cpra_load_state(cpra_plan_t p, const float* g, int64_t t) {
   // both Jacobi buffers, so that angles outside a present mask keep it
   CK(cudaMemcpyAsync(p->g_alt, p->g, bytes, cudaMemcpyDeviceToDevice, p->stream), "state copy");
   CK(cudaStreamSynchronize(p->stream), "state sync");
+  clear_status(p);
   cpra_status st = ensure_err_cap(p, t);
   if (st != CPRA_OK) return st;
   if (t > p->t) CK(cudaMemsetAsync(p->err_hist + p->t * p->Np, 0, sizeof(double) * (t - p->t) * p->Np, p->stream), "hist");
@@ -897,6 +943,7 @@ static cpra_status iterate_sweep(cpra_plan_s* p, int32_t n_iters, double* err_ou
 
 cpra_status cpra_iterate(cpra_plan_t p, int32_t n_iters, double* err_out) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (cpra_status st = check_status(p); st != CPRA_OK) return st;
   if (n_iters < 0) return fail(p, CPRA_ERR_INVALID_ARG, "n_iters < 0");
   if (!present_loaded(p)) return fail(p, CPRA_ERR_NOT_READY, "an iterating angle has no intensities");
   if (!p->state_ready && p->cfg.n_pre > 0 && !p->present_h[0])
@@ -1025,6 +1072,7 @@ static cpra_status upload_rho_rows(cpra_plan_s* p) {
 
 cpra_status cpra_assemble_3d(cpra_plan_t p, void* out) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (cpra_status st = check_status(p); st != CPRA_OK) return st;
   if (!p->state_ready) return fail(p, CPRA_ERR_NOT_READY, "no iterate to assemble");
   if (p->partial) return fail(p, CPRA_ERR_NOT_READY, "assembly needs every angle present");
   const size_t N = p->N, NN = N * N;
@@ -1154,6 +1202,7 @@ cpra_status cpra_merge(const cpra_plan_t* guesses, int32_t n_r, int32_t n_l, int
 cpra_status cpra_refine_3d(cpra_plan_t p, int32_t n_iters, int32_t shrink_every, float sigma,
                            float tau, double* err_out) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (cpra_status st = check_status(p); st != CPRA_OK) return st;
   if (n_iters < 0 || shrink_every < 0) return fail(p, CPRA_ERR_INVALID_ARG, "negative count");
   if (shrink_every > 0 && (!(sigma > 0.0f) || !(tau >= 0.0f) || !(tau <= 1.0f)))
     return fail(p, CPRA_ERR_INVALID_ARG, "shrink-wrap needs sigma > 0 and 0 <= tau <= 1");
@@ -1248,6 +1297,7 @@ cpra_status cpra_refine_3d(cpra_plan_t p, int32_t n_iters, int32_t shrink_every,
 
 cpra_status cpra_result(cpra_plan_t p, int32_t what, void* dst, size_t bytes) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (cpra_status st = check_status(p); st != CPRA_OK) return st;
   if (!dst) return fail(p, CPRA_ERR_INVALID_ARG, "dst is NULL");
   const size_t N = p->N, Np = p->Np, NN = N * N;
   const bool dd = is_device_ptr(dst);
@@ -1324,6 +1374,11 @@ cpra_status cpra_set_present(cpra_plan_t p, const uint8_t* mask) {
 
 cpra_status cpra_reset(cpra_plan_t p) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (p->status_h && p->status_h->flags) {
+    // a flagged run: wait for its queued work, then start clean
+    CK(cudaStreamSynchronize(p->stream), "reset sync");
+    clear_status(p);
+  }
   p->t = 0;
   p->state_ready = false;
   p->hp_valid = false;
@@ -1355,7 +1410,7 @@ int64_t cpra_launch_count(void) { return (int64_t)g_launches.load(); }
 cpra_status cpra_sync(cpra_plan_t p) {
   if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
   CK(cudaStreamSynchronize(p->stream), "sync");
-  return CPRA_OK;
+  return check_status(p);
 }
 
 cpra_status cpra_destroy(cpra_plan_t p) {
@@ -1364,6 +1419,7 @@ cpra_status cpra_destroy(cpra_plan_t p) {
   cudaGetLastError();
   for (auto& ev : p->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto& ev : p->spare) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+  if (p->status_h) cudaFreeHost(p->status_h);
   std::vector<void*> own = p->owned;
   for (void* q : own) {
     if (p->cfg.free) p->cfg.free(q, p->cfg.alloc_ctx);
@@ -1763,6 +1819,8 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
   if (n_iters < 0) return bfail(b, CPRA_ERR_INVALID_ARG, "n_iters < 0");
   for (cpra_plan_s* p : b->plans)
     if (!present_loaded(p)) return bfail(b, CPRA_ERR_NOT_READY, "a plan lacks intensities");
+  for (cpra_plan_s* p : b->plans)
+    if (cpra_status st = check_status(p); st != CPRA_OK) return bfail(b, st, p->err);
   for (cpra_plan_s* p : b->plans) {
     if (!p->state_ready && !p->cfg.sweep) {  // seeded start and Step A through the plan itself
       cpra_status st = cpra_iterate(p, 0, nullptr);

@@ -27,6 +27,15 @@ namespace cpra {
 struct JobStatic;
 struct JobStep;
 
+// Device-side status of a plan.  It lives in mapped, pinned host memory, so
+// kernels set it with plain stores and the host reads it without waiting
+// for the plan's stream.
+struct DevStatus {
+  unsigned flags;  // kStatusNonFinite
+  int angle;       // an angle whose Fourier error was not finite
+};
+constexpr unsigned kStatusNonFinite = 1u;
+
 struct Assembly {
   float2* F = nullptr;        // [Np][N][N] z-transformed spectra, [n][ku][z]
   float2* vol = nullptr;      // [N][N][N] grid, then the centred volume
@@ -68,7 +77,9 @@ struct cpra_plan_s {
   float2* xtw = nullptr;       // warp-FFT cross twiddles, [k1][l] = exp(-2 pi i l k1/N)
   uint16_t* tcw = nullptr;     // tensor-core DFT matrices (BF16 / FP16 precision)
   float* stage = nullptr;      // staging for host inputs, Np*N*N floats
-  int* flag = nullptr;         // device status word
+  uint8_t* bad = nullptr;      // device, Np bytes: 1 where the last load of the angle was invalid
+  cpra::DevStatus* status_h = nullptr;  // mapped pinned host memory (cudaHostAlloc)
+  cpra::DevStatus* status_d = nullptr;  // its device address
   float* sw_tmp = nullptr;     // shrink-wrap scratch, Np*N*N floats
   unsigned* sw_max = nullptr;  // per-angle max (float bits)
   float* sw_taps = nullptr;    // periodic Gaussian taps
@@ -190,10 +201,27 @@ struct JobStatic {
   const float2* xtw;
   const uint16_t* tcw;  // 16-bit block DFT matrices (tensor-core precision)
   const uint8_t* present;  // angles that iterate (coupling renormalises), NULL = all
+  DevStatus* status;       // device address of the plan's status word
   int Np, W;
   float beta;
   int pad;
 };
+
+// The Fourier error E_F of angle n from its FP64 sums (error terms of the
+// column pass + the constant C_n, over sum A^2), as written to the error
+// history.  A non-finite sum means a non-finite iterate (a diverged run, a
+// NaN or Inf state) or an invalid pattern (the preparation poisons C_n):
+// it is flagged in the plan's status word, which the next call reports.
+__device__ __forceinline__ double publish_error(double acc, double cn, double den, DevStatus* st,
+                                                int n) {
+  const double num = acc + cn;
+  if (!isfinite(num) || !isfinite(den)) {
+    volatile DevStatus* v = st;
+    v->angle = n;
+    v->flags = kStatusNonFinite;
+  }
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}
 
 // What one reconstruction does in one iteration (device table, one entry
 // per job per iteration).

@@ -207,7 +207,7 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (err_slot >= 0) {
       const double den = sumA2[n];
-      err_hist[(size_t)err_slot * Np + n] = den > 0.0 ? sqrt((err_acc[n] + Cn[n]) / den) : 0.0;
+      err_hist[(size_t)err_slot * Np + n] = publish_error(err_acc[n], Cn[n], den, J->status, n);
     }
     err_acc[n] = 0.0;
   }

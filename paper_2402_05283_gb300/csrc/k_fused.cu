@@ -421,7 +421,7 @@ k_fused(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
       if (lane == 0) {
         const double den = J->sumA2[n];
-        J->err_hist[(size_t)(err_slot + it) * Np + n] = den > 0.0 ? sqrt((s + J->Cn[n]) / den) : 0.0;
+        J->err_hist[(size_t)(err_slot + it) * Np + n] = publish_error(s, J->Cn[n], den, J->status, n);
       }
     }
     cluster_arrive();

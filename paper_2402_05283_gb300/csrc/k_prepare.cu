@@ -16,8 +16,13 @@ std::atomic<long long> g_launches{0};
 //
 // One warp a row ky, 8 rows a CTA: each lane sums its pixels' terms in FP32
 // (at most N/32 of them), the sums go to FP64 across lanes, rows and CTAs.
+//
+// An invalid pattern (a negative or non-finite intensity) marks bad[n] and
+// makes C_n NaN, so the first iteration on it publishes a non-finite error
+// and flags the plan's status word: the load itself does not wait for the
+// device.
 __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* A_rows,
-                          float* A_nyq, double* Cn, double* sumA2, int* flag,
+                          float* A_nyq, double* Cn, double* sumA2, uint8_t* bad_angle,
                           const uint8_t* __restrict__ mask, size_t mask_stride) {
   __shared__ double sc[8], sa[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -25,13 +30,13 @@ __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* 
   const int n = first + blockIdx.y;
   const int h = N / 2;
   double c_part = 0.0, a_part = 0.0;
+  int bad = 0;
   if (ky < N) {
     const float* In = I + (size_t)blockIdx.y * N * N;
     const int ry = (ky + h) % N;           // centred row of +ky
     const int my = (N - ky + h) % N;       // centred row of -ky
     const uint8_t* Mn = mask ? mask + (size_t)n * mask_stride : nullptr;
     float cf = 0.0f, af = 0.0f;
-    int bad = 0;
     for (int kx = lane; kx < N; kx += 32) {
       const int rx = (kx + h) % N;
       const int mx = (N - kx + h) % N;
@@ -50,7 +55,6 @@ __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* 
       if (kx < h) A_rows[((size_t)blockIdx.y * N + ky) * h + kx] = as;
       if (kx == h) A_nyq[(size_t)n * N + ky] = as;
     }
-    if (bad) atomicExch(flag, 1);
     c_part = cf;
     a_part = af;
     for (int o = 16; o > 0; o >>= 1) {
@@ -59,10 +63,14 @@ __global__ void k_prepare(const float* __restrict__ I, int N, int first, float* 
     }
   }
   if (lane == 0) { sc[warp] = c_part; sa[warp] = a_part; }
-  __syncthreads();
+  const int block_bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     double c = 0.0, a = 0.0;
     for (int i = 0; i < 8; ++i) { c += sc[i]; a += sa[i]; }
+    if (block_bad) {
+      c = __longlong_as_double(0x7ff8000000000000ll);  // NaN
+      bad_angle[n] = 1;
+    }
     atomicAdd(Cn + n, c);
     atomicAdd(sumA2 + n, a);
   }
@@ -92,12 +100,14 @@ cudaError_t launch_prepare(cpra_plan_s* p, const float* I, int first, int count)
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(p->sumA2 + first, 0, sizeof(double) * count, p->stream);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(p->bad + first, 0, count, p->stream);
+  if (e != cudaSuccess) return e;
   dim3 grid((p->N + 7) / 8, count);
   // g_alt is free outside cpra_iterate: it holds the row-major amplitudes
   float* rows = p->g_alt;
   g_launches += 2;
   k_prepare<<<grid, 256, 0, p->stream>>>(I, p->N, first, rows, p->A_nyq, p->Cn, p->sumA2,
-                                             p->flag, p->mask,
+                                             p->bad, p->mask,
                                              p->mask_per_angle ? (size_t)p->N * p->N : 0);
   const int h = p->N / 2;
   dim3 tg((h + 31) / 32, (p->N + 31) / 32, count);

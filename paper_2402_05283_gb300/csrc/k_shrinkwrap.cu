@@ -157,13 +157,24 @@ cudaError_t static_scratch(StaticScratch& out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* ptr) {
+// device memory of the current device (the kernels run there, with that
+// device's scratch), or managed memory
+bool on_device(const void* ptr, int dev) {
   cudaPointerAttributes a;
   if (!ptr || cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
+// The taps travel as a kernel parameter, so no host buffer has to outlive
+// the call.
+struct SwTaps {
+  float v[1024];
+};
+__global__ void k_sw_static_taps(SwTaps t, float* dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = t.v[i];
 }
 
 }  // namespace
@@ -182,8 +193,14 @@ extern "C" cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_i
                         "(1048576) pixels");
   if (!(sigma > 0.0f) || !std::isfinite(sigma) || !(tau >= 0.0f) || !(tau <= 1.0f))
     return record_error(CPRA_ERR_INVALID_ARG, "need sigma > 0 and 0 <= tau <= 1");
-  if (!on_device(g) || !on_device(S_in) || !on_device(S_out))
-    return record_error(CPRA_ERR_INVALID_ARG, "g, S_in and S_out must be device memory");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return record_error(CPRA_ERR_CUDA, "no current device");
+  }
+  if (!on_device(g, dev) || !on_device(S_in, dev) || !on_device(S_out, dev))
+    return record_error(CPRA_ERR_INVALID_ARG,
+                        "g, S_in and S_out must be device memory of the current device");
   StaticScratch sc;
   cudaError_t e = static_scratch(sc);
   if (e != cudaSuccess)
@@ -211,13 +228,15 @@ extern "C" cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_i
     ntaps = 2 * R + 1;
     lo0 = -R;
   }
-  float taps[1024];
-  for (int t = 0; t < ntaps; ++t) taps[t] = (float)w[((lo0 + t) % N + N) % N];
+  SwTaps taps{};
+  for (int t = 0; t < ntaps; ++t) taps.v[t] = (float)w[((lo0 + t) % N + N) % N];
   cudaStream_t st = (cudaStream_t)stream;
   const int W = (N + 31) / 32;
   const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
   const int lo = -(ntaps / 2) + ((ntaps % 2) ? 0 : 1);
-  e = cudaMemcpyAsync(sc.taps, taps, sizeof(float) * ntaps, cudaMemcpyHostToDevice, st);
+  g_launches += 1;
+  k_sw_static_taps<<<1, 256, 0, st>>>(taps, sc.taps, ntaps);
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(sc.mx, 0, sizeof(unsigned) * count, st);
   if (e == cudaSuccess) e = launch_bits_from_u8(sc.bits, S_in, N, count, st);
   if (e == cudaSuccess) {

@@ -112,11 +112,16 @@ int64_t hold_at(const cpra_server_s* s, const Request* r) {
 // One round of the loop; returns true when it did GPU work.
 bool round(cpra_server_s* s) {
   std::vector<Request*> admit, resident, fresh_running;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    // admission in submission order, by free device memory
-    while (!s->queue.empty()) {
-      Request* r = s->reqs[s->queue.front()];
+  // admission in submission order, by free device memory.  Only this thread
+  // admits, so the decision taken under the lock still holds when the plan
+  // is made; cpra_plan itself (allocation, possibly a device-wide sync) runs
+  // outside the lock, so submit, push, poll and wait never wait for it.
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->queue.empty()) break;
+      r = s->reqs[s->queue.front()];
       int active = 0;
       for (auto& kv : s->reqs)
         if (kv.second->state == kResident || kv.second->state == kRunning) ++active;
@@ -129,18 +134,23 @@ bool round(cpra_server_s* s) {
         break;
       }
       if (fr < it + as + s->cfg.hbm_reserve_bytes) break;
-      cpra_plan_t p = nullptr;
-      cpra_status st = cpra_plan(&r->cfg, s->stream, &p);
       s->queue.pop_front();
-      if (st != CPRA_OK) {
-        fail_request(s, r, cpra_last_error(nullptr));
-        continue;
-      }
-      r->plan = p;
-      r->state = kResident;
-      r->t_admit = now_s(s->t0);
-      s->stats.admitted++;
     }
+    cpra_plan_t p = nullptr;
+    const cpra_status st = cpra_plan(&r->cfg, s->stream, &p);
+    const std::string msg = st == CPRA_OK ? std::string() : std::string(cpra_last_error(nullptr));
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (st != CPRA_OK) {
+      fail_request(s, r, msg.c_str());
+      continue;
+    }
+    r->plan = p;
+    r->state = kResident;
+    r->t_admit = now_s(s->t0);
+    s->stats.admitted++;
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
     // (a running request with early start still receives patterns)
     for (auto& kv : s->reqs)
       if ((kv.second->state == kResident || kv.second->state == kRunning) &&

@@ -5,6 +5,7 @@ work on other ranks."""
 import os
 import socket
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -79,7 +80,16 @@ def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
         gpus, steps, warmup = 1, 3, 1
 
     rates = iter([1.0, 40.0, 60.0, 50.0])
-    monkeypatch.setattr(bench, "sample_inputs", lambda: (None, None))
+    monkeypatch.setattr(bench, "sample_inputs", lambda *a: (np.zeros((8, 4, 4)), None))
+
+    class _Pool:
+        def close(self):
+            pass
+
+        def join(self):
+            pass
+
+    monkeypatch.setattr(bench, "oracle_pool", lambda n: _Pool())
     monkeypatch.setattr(bench, "cpu_baseline", lambda *a, **k: {
         "value": next(rates), "unit": "angle-iterations/s", "cores": 4, "kind": "oracle",
         "sample": "stub"})

@@ -353,6 +353,14 @@ def test_iterate_fft_mode_equals_dft_mode():
         b = O.iterate_2d(g, A, S, 0.9, algo, return_gp=True, fft=True)
         for x, y in zip(a, b):
             assert np.allclose(x, y, rtol=1e-11, atol=1e-12)
+    # a whole run in FFT mode (the CPU baseline's timing mode) follows the
+    # DFT-matrix run: ER with coupling, 6 iterations
+    I = np.fft.fftshift(A ** 2, axes=(-2, -1))
+    runs = [O.OracleRun.start(O.OracleConfig(N=N, Np=2, n_ei=3, alpha=(0.25, 0.5, 0.25), hio_iters=0,
+                                             er_iters=6, seed=4, fft=f), I, S[0]).run(6)
+            for f in (False, True)]
+    assert np.allclose(runs[0].g, runs[1].g, rtol=1e-10, atol=1e-12)
+    assert np.allclose(np.array(runs[0].errors), np.array(runs[1].errors), rtol=1e-10, atol=1e-14)
 
 
 def test_sweep_coupling_hand_case_np3():

@@ -69,3 +69,29 @@ def test_static_shrinkwrap_rejects_oversize_and_host_memory(cp):
     with pytest.raises(cp.CpraError) as e:
         cp.cpra_shrinkwrap_static(np.zeros((1, 64, 64), np.float32), S, S, 64, 1, 2.0, 0.1, None)
     assert e.value.status == cp.ERR_INVALID_ARG
+
+
+def test_static_shrinkwrap_rejects_wrong_types_sizes_and_layouts(cp):
+    """The binding checks what the C call cannot see from a pointer: element
+    types, sizes and contiguity, and it copies nothing (a contiguous copy of
+    S_out would receive the result while the caller's tensor stayed as it
+    was).  A device other than the current one is refused by the C call;
+    with one GPU visible that case is not exercised here."""
+    import torch
+    N = 64
+    g = torch.zeros((2, N, N), device="cuda")
+    S = torch.ones((2, N, N), dtype=torch.uint8, device="cuda")
+    with pytest.raises(TypeError):
+        cp.cpra_shrinkwrap_static(g.double(), S, S, N, 2, 2.0, 0.1, None)
+    with pytest.raises(TypeError):
+        cp.cpra_shrinkwrap_static(g, S.int(), S, N, 2, 2.0, 0.1, None)
+    with pytest.raises(TypeError):
+        cp.cpra_shrinkwrap_static(g, S, S.bool(), N, 2, 2.0, 0.1, None)
+    with pytest.raises(ValueError):  # too few elements for count = 3
+        cp.cpra_shrinkwrap_static(g, S, S, N, 3, 2.0, 0.1, None)
+    with pytest.raises(ValueError):
+        cp.cpra_shrinkwrap_static(g, S, S.transpose(1, 2), N, 2, 2.0, 0.1, None)
+    # a valid call still works after the refusals
+    out = torch.zeros_like(S)
+    cp.cpra_shrinkwrap_static(g, S, out, N, 2, 2.0, 0.1, None)
+    torch.cuda.synchronize()
