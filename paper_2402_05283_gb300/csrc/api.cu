@@ -153,7 +153,7 @@ cpra_status validate(const cpra_config* c, std::string& why) {
     return CPRA_ERR_INVALID_ARG;
   }
   if (c->precision != CPRA_FP32 &&
-      !(fast_supported(c->N) && (c->engine == CPRA_ENGINE_AUTO || c->engine == CPRA_ENGINE_WARP))) {
+      !(refine_fast_supported(c->N) && (c->engine == CPRA_ENGINE_AUTO || c->engine == CPRA_ENGINE_WARP))) {
     why = "tensor-core precision runs on the warp engine (N in {64, 128, 256, 512, 1024})";
     return CPRA_ERR_UNSUPPORTED;
   }
@@ -168,7 +168,7 @@ cpra_status validate(const cpra_config* c, std::string& why) {
     return CPRA_ERR_UNSUPPORTED;
   }
   if (c->engine == CPRA_ENGINE_WARP && !fast_supported(c->N)) {
-    why = "warp engine needs N in {64, 128, 256, 512, 1024}";
+    why = "warp engine needs N in {64, 128, 192, 256, 384, 512, 1024}";
     return CPRA_ERR_UNSUPPORTED;
   }
   if ((c->alloc == nullptr) != (c->free == nullptr)) {

@@ -315,7 +315,8 @@ cudaError_t launch_merge_finish(cpra_plan_s* dst, float2* acc, const float* mag,
 bool n_supported(int N);
 
 // two-pass engine with warp-resident FFTs (k_fast.cu)
-bool fast_supported(int N);
+bool fast_supported(int N);          // iteration kernels (WARP engine)
+bool refine_fast_supported(int N);   // 3D refinement passes and tensor-core forms
 bool fast_dims(int N, int* E1, int* E2);
 cudaError_t prepare_kernels_fast(int N);
 cudaError_t prepare_kernels_fast_tc(int N, int prec);

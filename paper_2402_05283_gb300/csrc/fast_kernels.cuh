@@ -157,15 +157,16 @@ __device__ __forceinline__ void store_pairs_w(float2 (&b)[FL::TB][FL::E2], float
 }
 
 // ---------------------------------------------------------------- row pass
+// One CTA of the row pass: row pairs [bx * WARPS * L, (bx + 1) * WARPS * L)
+// of tile tl = (job, angle).
 template <int N, int PREC>
-__global__ void __launch_bounds__(RowW<N, PREC>::WARPS * 32, 3)
-k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
-            const int2* __restrict__ tiles) {
+__device__ __forceinline__ void rowpass_tile(const JobStatic* __restrict__ js,
+                                             const JobStep* __restrict__ st, const int2 tl,
+                                             const int bx) {
   using RW = RowW<N, PREC>;
   using FL = typename RW::FL;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
-  const int2 tl = tiles[blockIdx.y];
   const JobStatic* J = js + tl.x;
   const JobStep* Z = st + tl.x;
   if (!Z->active) return;
@@ -189,7 +190,7 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(smem + N + RW::WARPS * RW::WARP_F2),
                                      J->tcw, warp);
   const int n = tl.y;
-  const int pair0 = (blockIdx.x * RW::WARPS + warp) * FL::L;
+  const int pair0 = (bx * RW::WARPS + warp) * FL::L;
   float* grow = g + ((size_t)n * N + 2 * pair0) * N;  // 2L contiguous rows
   float2* Hn = Hp + (size_t)n * N * H;
   // the warp's 2L packed spectrum rows (contiguous) into its tile, then the
@@ -204,7 +205,7 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 #pragma unroll
   for (int k = 0; k < RW::GFLOATS / 128; ++k) cp_async16(Gs + 4 * (lane + 32 * k), grow + 4 * lane + 128 * k);
   cp_async_commit();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bx == 0 && threadIdx.x == 0) {
     if (err_slot >= 0) {
       const double den = sumA2[n];
       err_hist[(size_t)err_slot * Np + n] = publish_error(err_acc[n], Cn[n], den, J->status, n);
@@ -303,6 +304,13 @@ k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   if (!forward) return;
   lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
   store_pairs_w<N, FL>(b, T, Hn, pair0, lane);
+}
+
+template <int N, int PREC>
+__global__ void __launch_bounds__(RowW<N, PREC>::WARPS * 32, 3)
+k_rowpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+            const int2* __restrict__ tiles) {
+  rowpass_tile<N, PREC>(js, st, tiles[blockIdx.y], blockIdx.x);
 }
 
 // ---------------------------------------------------------------- Eq. 4 taps
@@ -460,15 +468,16 @@ __device__ __forceinline__ float2 project_w(float2 G, float a, float& e) {
   return make_float2(__fmul_rn(zero ? 1.0f : G.x, s), zero ? 0.0f : __fmul_rn(G.y, s));
 }
 
+// One CTA of the column pass: packed columns [bx * CB, (bx + 1) * CB) of
+// tile tl = (job, angle).
 template <int N, int PREC, bool MASKED>
-__global__ void __launch_bounds__(ColW<N, PREC>::NT, ColW<N, PREC>::MINB)
-k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
-            const int2* __restrict__ tiles) {
+__device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
+                                             const JobStep* __restrict__ st, const int2 tl,
+                                             const int bx) {
   using C = ColW<N, PREC>;
   using FL = typename C::FL;
   constexpr int H = N / 2;
   extern __shared__ float2 smem[];
-  const int2 tl = tiles[blockIdx.y];
   const JobStatic* J = js + tl.x;
   if (!st[tl.x].active) return;
   float2* Hp = J->Hp;
@@ -484,7 +493,7 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(As + C::CB * N), J->tcw, threadIdx.x >> 5);
   float2* T = buf + warp * FL::TSIZE;
   const int n = tl.y;
-  const int c0 = blockIdx.x * C::CB;
+  const int c0 = bx * C::CB;
   float2* Hn = Hp + (size_t)n * N * H;
   // thread (row y0 + k RS, column cc) of the block: constant strides, so
   // the unrolled copies differ only in immediate offsets
@@ -594,6 +603,13 @@ k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   }
 }
 
+template <int N, int PREC, bool MASKED>
+__global__ void __launch_bounds__(ColW<N, PREC>::NT, ColW<N, PREC>::MINB)
+k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
+            const int2* __restrict__ tiles) {
+  colpass_tile<N, PREC, MASKED>(js, st, tiles[blockIdx.y], blockIdx.x);
+}
+
 // ---------------------------------------------------------------- launchers
 template <class K>
 static cudaError_t smem_attr(K kernel, size_t bytes) {
@@ -649,7 +665,9 @@ static cudaError_t colpass_w(const Launch& L) {
   return cudaGetLastError();
 }
 
-
+// sizes of the 3D refinement's warp passes and of the tensor-core forms
 #define CPRA_FOR_EACH_FAST_N(X) X(64) X(128) X(256) X(512) X(1024)
+// sizes of the warp engine's iteration kernels
+#define CPRA_FOR_EACH_WARP_N(X) X(64) X(128) X(192) X(256) X(384) X(512) X(1024)
 
 }  // namespace cpra

@@ -79,6 +79,9 @@ template <> struct WarpPlan<64> { static constexpr int E1 = 8, E2 = 8, L = 4; };
 template <> struct WarpPlan<128> { static constexpr int E1 = 8, E2 = 16, L = 4; };
 template <> struct WarpPlan<256> { static constexpr int E1 = 16, E2 = 16, L = 2; };
 template <> struct WarpPlan<512> { static constexpr int E1 = 16, E2 = 32, L = 2; };
+// N = 2^a 3: a radix-3 stage inside the E1-point register DFT
+template <> struct WarpPlan<192> { static constexpr int E1 = 24, E2 = 8, L = 4; };
+template <> struct WarpPlan<384> { static constexpr int E1 = 24, E2 = 16, L = 4; };
 template <> struct WarpPlan<1024> { static constexpr int E1 = 32, E2 = 32, L = 1; };
 
 template <int N> struct WP {
@@ -92,7 +95,8 @@ template <int N> struct WP {
   static_assert(E1 * E2 == N && TA * 32 == L * E2 && TB * 32 == L * E1, "warp plan");
 };
 
-template <int N> constexpr bool kHasWarpPlan = (N == 64 || N == 128 || N == 256 || N == 512 || N == 1024);
+template <int N> constexpr bool kHasWarpPlan = (N == 64 || N == 128 || N == 192 || N == 256 || N == 384 ||
+                                                N == 512 || N == 1024);
 
 // Tensor-core scratch of one warp and the block DFT matrices (16-bit).
 struct TcCtx {

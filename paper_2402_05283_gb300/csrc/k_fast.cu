@@ -5,10 +5,21 @@
 namespace cpra {
 
 
-bool fast_supported(int N) {
+bool refine_fast_supported(int N) {
   switch (N) {
 #define CPRA_CASE(NN) case NN:
     CPRA_FOR_EACH_FAST_N(CPRA_CASE)
+#undef CPRA_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+bool fast_supported(int N) {
+  switch (N) {
+#define CPRA_CASE(NN) case NN:
+    CPRA_FOR_EACH_WARP_N(CPRA_CASE)
 #undef CPRA_CASE
     return true;
     default:
@@ -23,7 +34,7 @@ bool fast_dims(int N, int* E1, int* E2) {
     *E1 = WP<NN>::E1; \
     *E2 = WP<NN>::E2; \
     return true;
-    CPRA_FOR_EACH_FAST_N(CPRA_CASE)
+    CPRA_FOR_EACH_WARP_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
       return false;
@@ -34,7 +45,7 @@ cudaError_t prepare_kernels_fast(int N) {
   switch (N) {
 #define CPRA_CASE(NN) \
   case NN: return prepare_w<NN, kPrecFP32>();
-    CPRA_FOR_EACH_FAST_N(CPRA_CASE)
+    CPRA_FOR_EACH_WARP_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
       return cudaErrorInvalidValue;
@@ -46,7 +57,7 @@ cudaError_t launch_rowpass_fast(const Launch& L) {
   switch (L.N) {
 #define CPRA_CASE(NN) \
   case NN: return rowpass_w<NN, kPrecFP32>(L);
-    CPRA_FOR_EACH_FAST_N(CPRA_CASE)
+    CPRA_FOR_EACH_WARP_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
       return cudaErrorInvalidValue;
@@ -58,7 +69,7 @@ cudaError_t launch_prime_fast(const Launch& L) {
   switch (L.N) {
 #define CPRA_CASE(NN) \
   case NN: return prime_w<NN, kPrecFP32>(L);
-    CPRA_FOR_EACH_FAST_N(CPRA_CASE)
+    CPRA_FOR_EACH_WARP_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
       return cudaErrorInvalidValue;
@@ -70,7 +81,7 @@ cudaError_t launch_colpass_fast(const Launch& L) {
   switch (L.N) {
 #define CPRA_CASE(NN) \
   case NN: return colpass_w<NN, kPrecFP32>(L);
-    CPRA_FOR_EACH_FAST_N(CPRA_CASE)
+    CPRA_FOR_EACH_WARP_N(CPRA_CASE)
 #undef CPRA_CASE
     default:
       return cudaErrorInvalidValue;

@@ -443,7 +443,7 @@ static cudaError_t refine_setup_n(const RefineArgs& a, const float2* vol, cudaSt
   const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
   g_launches += 1;
   k_refine_in<<<blocks, 256, 0, st>>>(vol, a.X, a.R, total);
-  if (fast_supported(N)) {
+  if (refine_fast_supported(N)) {
     e = launch_refine_fft3_w(a, st);
     if (e != cudaSuccess) return e;
   } else {
@@ -458,7 +458,7 @@ static cudaError_t refine_setup_n(const RefineArgs& a, const float2* vol, cudaSt
 
 template <int N>
 static cudaError_t refine_iter_n(const RefineArgs& a, double* err2, cudaStream_t st) {
-  if (fast_supported(N)) return launch_refine_iter_w(a, err2, st);
+  if (refine_fast_supported(N)) return launch_refine_iter_w(a, err2, st);
   cudaError_t e = refine_prepare_n<N>();
   if (e != cudaSuccess) return e;
   using C = ColTile<N>;

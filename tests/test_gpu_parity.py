@@ -240,7 +240,7 @@ def test_cfg1_final_reconstruction_quality(cp, cfg1):
     (16, 3, 1), (32, 5, 1), (48, 4, 1), (64, 3, 1), (96, 3, 1), (128, 2, 1), (192, 2, 1),
     (256, 2, 1), (384, 2, 1), (512, 2, 1), (768, 1, 1), (1024, 1, 1),
     (160, 3, 1), (320, 2, 1),
-    (64, 3, 3), (128, 2, 3), (256, 2, 3), (512, 2, 3), (1024, 1, 3)])
+    (64, 3, 3), (128, 2, 3), (192, 3, 3), (256, 2, 3), (384, 3, 3), (512, 2, 3), (1024, 1, 3)])
 def test_sizes_and_radices(cp, N, Np, engine):
     """Every supported radix chain and tile shape of both engines (1 = block-wide
     Stockham passes, 3 = warp-resident FFTs): HIO step with coupling, then ER."""
