@@ -269,10 +269,12 @@ def cpu_baseline(I, S, seconds: float = 10.0, pool=None):
 _SERVE_POOL = {}
 
 def form_batch(cp, torch, seed=3):
-    """cfg 3: 16 reconstructions of uneven N and Np, 300 iterations each, run
-    one at a time (plain plans, no graph) and as one batch (one launch per
-    kernel and size group, CUDA graph, autotuned engines).  Results must be
-    bit-identical between the two."""
+    """cfg 3: 16 reconstructions of uneven N and Np, 300 iterations each.
+    Three ways: one at a time (plain plans, AUTO engines, no graph); one
+    batch with one launch per kernel and size group (autotuned engines, CUDA
+    graph); one batch in persistent work-queue mode (warp engine, one
+    persistent launch per size group between coupling steps, CUDA graph).
+    Batched results must equal the same engine run alone bit for bit."""
     import synth
     rng = np.random.default_rng(seed)
     Ns = rng.choice([128, 192, 256, 384], size=16)
@@ -295,43 +297,69 @@ def form_batch(cp, torch, seed=3):
             out.append(p)
         return out
 
+    def one_at_a_time(ps):
+        for p in ps:
+            p.iterate(1)
+            p.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in ps:
+            p.iterate(iters)
+            p.sync()
+        return time.perf_counter() - t0
+
+    def batched(ps, persistent):
+        b = cp.Batch(ps, use_graph=True)
+        if persistent:
+            b.set_persistent(1)
+        b.iterate(30)  # capture the 30-iteration graph
+        for p in ps:
+            p.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(iters // 30):
+            b.iterate(30)
+        torch.cuda.synchronize()
+        return b, time.perf_counter() - t0
+
     work = int(sum(int(n) for n in Nps)) * iters
     alone = plans(cp.ENGINE_AUTO)
-    for p in alone:
-        p.iterate(1)
-        p.reset()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for p in alone:
-        p.iterate(iters)
-        p.sync()
-    t_alone = time.perf_counter() - t0
+    t_alone = one_at_a_time(alone)
     tuned = {int(n): cp.cpra_autotune(int(n))[0] for n in set(Ns.tolist())}
     mixed = plans(cp.ENGINE_TUNED)
-    b = cp.Batch(mixed, use_graph=True)
-    b.iterate(30)  # capture the 30-iteration graph
-    for p in mixed:
-        p.reset()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(iters // 30):
-        b.iterate(30)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+    b, t_batch = batched(mixed, False)
     # plans whose tuned engine is the one AUTO picks must agree bit for bit
-    auto = {n: (cp.ENGINE_FUSED if n in (64, 128, 256) else
-                cp.ENGINE_WARP if n in (512, 1024) else cp.ENGINE_TWO_PASS) for n in tuned}
+    auto = {n: (cp.ENGINE_FUSED if n in (64, 128, 256) else cp.ENGINE_WARP) for n in tuned}
     pairs = [(a, m) for a, m in zip(alone, mixed) if tuned[a.N] == auto[a.N]]
     same = all(np.array_equal(a.result(cp.RESULT_STATE), m.result(cp.RESULT_STATE)) for a, m in pairs)
     b.close()
     for p in alone + mixed:
         p.close()
+    warp_alone = plans(cp.ENGINE_WARP)
+    t_warp_alone = one_at_a_time(warp_alone)
+    pers = plans(cp.ENGINE_WARP)
+    bp, t_pers = batched(pers, True)
+    same_p = all(np.array_equal(a.result(cp.RESULT_STATE), m.result(cp.RESULT_STATE))
+                 for a, m in zip(warp_alone, pers))
+    launches_p = bp.launches(30)
+    bp.close()
+    for p in warp_alone + pers:
+        p.close()
     return {"workload": "16 reconstructions, N in {128,192,256,384}, Np in {90,180,360}, "
                         "280 HIO + 20 ER", "angle_iterations": work,
-            "one_at_a_time": {"value": round(work / t_alone, 1), "seconds": round(t_alone, 3)},
-            "batched_graph": {"value": round(work / t_batch, 1), "seconds": round(t_batch, 3)},
-            "speedup": round(t_alone / t_batch, 3), "tuned_engines": tuned,
-            "bit_identical": bool(same), "compared": len(pairs)}
+            "one_at_a_time": {"value": round(work / t_alone, 1), "seconds": round(t_alone, 3),
+                              "engines": "AUTO (fused at 128/256, warp at 192/384)"},
+            "batched_graph": {"value": round(work / t_batch, 1), "seconds": round(t_batch, 3),
+                              "speedup_vs_one_at_a_time": round(t_alone / t_batch, 3),
+                              "tuned_engines": tuned, "bit_identical": bool(same),
+                              "compared": len(pairs)},
+            "persistent_graph": {"value": round(work / t_pers, 1), "seconds": round(t_pers, 3),
+                                 "speedup_vs_one_at_a_time": round(t_alone / t_pers, 3),
+                                 "speedup_vs_warp_one_at_a_time": round(t_warp_alone / t_pers, 3),
+                                 "launches_per_30_iterations": int(launches_p),
+                                 "bit_identical_to_warp_alone": bool(same_p)},
+            "warp_one_at_a_time": {"value": round(work / t_warp_alone, 1),
+                                   "seconds": round(t_warp_alone, 3)}}
 
 
 def form_multi_guess(cp, torch, N_=256, Np_=144, n_r=32, n_l=8, iters=220, seed=6):
@@ -414,72 +442,49 @@ def form_refine(cp, torch, plan, iters=50, shrink_every=5):
             "error_first_last": [round(float(errs[0]), 5), round(float(errs[-1]), 5)]}
 
 
-def form_cell_pipeline(cp, torch, N_=700, Np_=27, n_r=100, n_l=10, n_pre=500, n_e=2, n_ei=10,
-                       refine_iters=50, seed=7):
-    """The whole method at the sizes of the paper's cell data (its results
-    section: N = 700 with 27 patterns; RAAR beta 0.9; Step A 500 iterations
-    on the first pattern; two episodes of 10; a CSWA step at each episode
-    end; 100 random starts, the best 10 merged; 3D refinement of 50
-    iterations with the support shrunk every 5).  Patterns: a seeded
-    6-ellipsoid phantom of 350^3 voxels, 1e6 photons (the data are not
-    available).  Step B runs as the Gauss-Seidel sweep the text describes;
-    the guesses run as one batch (Step A as rows over every guess's first
-    pattern, then one launch per angle of the sweep over all guesses)."""
+def form_config2(cp, torch, iters=500, every=20):
+    """cfg 2 as written: N = 256, Np = 180, a 128^3 object of 40 ellipsoids
+    with Gaussian-correlated texture (sigma 2 voxels) at 1e7 photons, 500 HIO
+    iterations with shrink-wrap every 20 (sigma 2 px, tau 0.1), then the
+    256^3 assembly and inverse 3D FFT.  The same run without shrink-wrap
+    gives the shrink-wrap overhead."""
     import synth
     t_gen = time.perf_counter()
-    d = synth.make_case("cfg1", device="cuda", N=N_, Np=Np_, request=seed)
-    I, th = d["I"].contiguous(), d["thetas"]
+    d = synth.make_case("cfg2", device="cuda")
     t_gen = time.perf_counter() - t_gen
-    T = n_e * n_ei
-    er = n_ei // 2  # ER in the second half of the last episode: ranks object estimates
-    plans = []
-    for i in range(n_r):
-        cfg = cp.make_config(N_, Np_, seed=1000 + i, hio_iters=T - er, er_iters=er, n_ei=n_ei,
-                             n_pre=n_pre, update=cp.UPDATE_RAAR, sweep=1, shrinkwrap_every=n_ei)
-        p = cp.Plan(cfg)
-        p.load_intensities(I, 0, th)
-        plans.append(p)
-    dst = cp.Plan(cp.make_config(N_, Np_, shrinkwrap_every=n_ei, n_ei=n_ei))
-    dst.load_intensities(I, 0, th)
-    batch = cp.Batch(plans, use_graph=False)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    batch.iterate(T)  # Steps A and B of every guess
-    torch.cuda.synchronize()
-    t_ab = time.perf_counter() - t0
-    batch.close()
-    t1 = time.perf_counter()
-    prtf = torch.zeros((Np_, N_ // 2), device="cuda")
-    sel, inv = cp.cpra_merge(plans, n_l, 0, dst, prtf)  # Step C (and the Step D volume)
-    torch.cuda.synchronize()
-    t_c = time.perf_counter() - t1
-    # the best guess's shrink-wrapped supports frame the 3D support
-    dst.load_support(plans[sel[0]].result(cp.RESULT_SUPPORT))
-    dst.load_state(plans[sel[0]].result(cp.RESULT_STATE), T)
-    t2 = time.perf_counter()
-    errs = dst.refine_3d(refine_iters, shrink_every=5, sigma=2.0, tau=0.1)
-    torch.cuda.synchronize()
-    t_d = time.perf_counter() - t2
-    ring = prtf.mean(0).cpu().numpy()
-    below = np.nonzero(ring < 1 / math.e)[0]
-    final = [float(p.result(cp.RESULT_ERRORS)[-1].mean()) for p in plans]
-    for p in plans + [dst]:
-        p.close()
-    return {"workload": f"N={N_}, Np={Np_}: {n_r} starts x (Step A {n_pre} RAAR on pattern 0 + "
-                        f"{n_e} Gauss-Seidel episodes of {n_ei} (RAAR, the last {er} ER), "
-                        f"shrink-wrap per episode), best {n_l} merged, {refine_iters} refinement "
-                        f"iterations (shrink every 5)",
-            "patterns": "synthetic 6-ellipsoid phantom, 1e6 photons (generated in "
-                        f"{t_gen:.1f} s, outside the timed stages)",
-            "seconds": {"steps_a_b": round(t_ab, 3), "step_c_merge_and_assembly": round(t_c, 3),
-                        "step_d_refinement": round(t_d, 3), "total": round(t_ab + t_c + t_d, 3)},
-            "two_d_iterations": n_r * (n_pre + Np_ * T),
-            "selected": sel, "inverted": [int(v) for v in inv],
-            "final_fourier_error_best_median": [round(min(final), 5), round(float(np.median(final)), 5)],
-            "prtf_first_ring_below_1_over_e": int(below[0]) if below.size else None,
-            "refinement_error_first_last": [round(float(errs[0]), 5), round(float(errs[-1]), 5)],
-            "paper_context": "the paper reports under 20 s on an RTX 3080 Ti for its 700 x 27 "
-                             "cell data with 100 guesses (different data and hardware)"}
+    N_, Np_ = d["N"], d["Np"]
+    I, th = d["I"].contiguous(), d["thetas"]
+    out = {"workload": f"N={N_}, Np={Np_}: 40-ellipsoid textured 128^3 object, 1e7 photons, "
+                       f"{iters} HIO, shrink-wrap every {every}; {N_}^3 assembly",
+           "input_seconds": round(t_gen, 2)}
+    for name, sw in (("shrinkwrap", every), ("no_shrinkwrap", 0)):
+        plan = cp.Plan(cp.make_config(N_, Np_, hio_iters=iters, er_iters=0, shrinkwrap_every=sw))
+        plan.load_intensities(I, 0, th)
+        plan.iterate(2)
+        plan.assemble_3d()  # first use allocates the assembly buffers and lists
+        plan.reset()
+        plan.load_support(None)
+        torch.cuda.synchronize()
+        plan.set_profiling(True)
+        t0 = time.perf_counter()
+        plan.iterate(iters)
+        plan.assemble_3d()
+        plan.sync()
+        dt = time.perf_counter() - t0
+        sw_ms, sw_n = plan.kernel_stats(cp.KERNEL_SHRINKWRAP)
+        asm_ms, _ = plan.kernel_stats(cp.KERNEL_ASSEMBLE)
+        plan.set_profiling(False)
+        err = plan.result(cp.RESULT_ERRORS)
+        sup = plan.result(cp.RESULT_SUPPORT)
+        out[name] = {"value": round(Np_ * iters / dt, 1), "unit": "angle-iterations/s",
+                     "seconds_with_assembly": round(dt, 4), "shrinkwrap_ms": round(sw_ms, 3),
+                     "shrinkwrap_launch_groups": sw_n, "assembly_ms": round(asm_ms, 3),
+                     "final_fourier_error_mean": round(float(err[-1].mean()), 5),
+                     "support_fraction_mean": round(float(sup.mean()), 4)}
+        plan.close()
+    a_, b_ = out["shrinkwrap"], out["no_shrinkwrap"]
+    out["shrinkwrap_overhead"] = round(a_["seconds_with_assembly"] / b_["seconds_with_assembly"] - 1.0, 4)
+    return out
 
 
 def form_serving(cp, torch, n_req=16, compress=10.0, seed=4, max_active=0, early_start=False):
@@ -830,7 +835,8 @@ def run_gpu(args):
                  "precision_large": form_precision_large(cp, torch),
                  "batching": form_batch(cp, torch),
                  "multi_guess_merge": form_multi_guess(cp, torch),
-                 "cell_pipeline": form_cell_pipeline(cp, torch),
+                 "config2": form_config2(cp, torch),
+                 "serving_config4": form_serving(cp, torch, compress=1.0, early_start=True),
                  "serving_continuous": form_serving(cp, torch, max_active=0),
                  "serving_one_at_a_time": form_serving(cp, torch, max_active=1),
                  "serving_early_start": form_serving(cp, torch, max_active=0, early_start=True)}

@@ -435,6 +435,28 @@ cpra_status cpra_batch_iterate(cpra_batch_t batch, int32_t n_iters);
  * graph holds); -1 for a NULL batch. */
 int64_t cpra_batch_launches(cpra_batch_t batch, int32_t n_iters);
 
+/* Persistent work-queue mode (mode 1; 0 returns to one launch per kernel
+ * and size group).  Each call then splits at the iterations where a member
+ * couples (Eq. 4 at its episode starts); for every such segment the size
+ * groups' coupling launches run first, then ONE persistent launch per size
+ * group runs all of the segment's column and row passes of every (member,
+ * angle) tile: its CTAs take tasks from a device queue ordered (iteration,
+ * pass, tile, block) and wait on per-tile completion counts instead of
+ * launch boundaries, so an angle's row pass starts as soon as its own
+ * column pass is done.  The groups' launches are forked onto a stream each
+ * (in the CUDA graph when the batch uses one), so one size group's tail
+ * overlaps the next group's start.  Every tile computes what the warp
+ * engine computes for it alone (states bit for bit; FP64 error sums to
+ * rounding).  Needs every Jacobi group on the FP32 warp engine with
+ * N in {64, 128, 192, 256, 384, 512} (UNSUPPORTED otherwise).
+ * wait_budget_s bounds every device-side wait (0 = 2 s): a wait that runs
+ * out sets TIMEOUT in the members' status words (reported by their next
+ * calls, see cpra_sync) and ends its CTA.  Mode 2 exists to test that path:
+ * the first task of every launch waits on a count that no task increments.
+ * The paper has no batching; the benchmark spec's batching form.  Waits for the
+ * batch's stream. */
+cpra_status cpra_batch_set_persistent(cpra_batch_t batch, int32_t mode, double wait_budget_s);
+
 cpra_status cpra_batch_destroy(cpra_batch_t batch);
 
 /* Autotuner: time each engine available for N (TWO_PASS, WARP, FUSED) on a sample

@@ -237,7 +237,7 @@ cpra_status check_status(cpra_plan_s* p) {
   const int n = s->angle;
   // the error path only: which loads were invalid
   std::vector<uint8_t> bad(p->Np, 0);
-  if (cudaStreamSynchronize(p->stream) == cudaSuccess &&
+  if ((s->flags & kStatusNonFinite) && cudaStreamSynchronize(p->stream) == cudaSuccess &&
       cudaMemcpy(bad.data(), p->bad, (size_t)p->Np, cudaMemcpyDeviceToHost) == cudaSuccess) {
     for (int a = 0; a < p->Np; ++a)
       if (bad[a])
@@ -246,6 +246,10 @@ cpra_status check_status(cpra_plan_s* p) {
                         " must be finite and non-negative (reload them, then cpra_reset)");
   }
   cudaGetLastError();
+  if (s->flags & kStatusTimeout)
+    return fail(p, CPRA_ERR_TIMEOUT,
+                "a device-side wait of a persistent batch launch gave up; cpra_reset or "
+                "cpra_load_state clears it");
   return fail(p, CPRA_ERR_NONFINITE,
               "non-finite iterate (Fourier error of angle " + std::to_string(n) +
                   "); cpra_reset or cpra_load_state clears it");
@@ -1453,6 +1457,9 @@ struct cpra_batch_s {
     std::vector<int64_t> versions;  // members' present-mask versions the tiles follow
     JobStep* d_steps = nullptr;
     int64_t steps_cap = 0;
+    // persistent mode: the queue's ticket pair and per-tile done counts
+    unsigned* d_queue = nullptr;
+    int blocks_per_sm = 0;
   };
   std::vector<cpra_plan_s*> plans;
   cudaStream_t stream = nullptr;
@@ -1465,6 +1472,13 @@ struct cpra_batch_s {
   int64_t graph_kernels = 0;
   std::vector<void*> owned;
   std::string err;
+  // persistent work-queue mode (cpra_batch_set_persistent)
+  int persistent = 0;              // 0 off, 1 on, 2 testing: every device wait runs out
+  long long budget = 0;            // clock64 cycles a device wait may take
+  int sms = 0;
+  std::vector<cudaStream_t> side;  // one per group: the groups' kernels overlap
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
 };
 
 namespace {
@@ -1939,7 +1953,72 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
                           cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
   }
+  // Persistent mode: the call splits at the rows where a member primes;
+  // each segment is the groups' prime launches, then one persistent
+  // work-queue launch per group over the segment's iterations, forked onto
+  // the groups' side streams so that one group's tail overlaps the next
+  // group's start, and joined before the next prime.
+  auto issue_persistent = [&](cudaStream_t on) -> cudaError_t {
+    int64_t kernels = 0;
+    for (int a = 0; a < n_iters;) {
+      int e = a + 1;
+      for (; e < n_iters; ++e) {
+        bool prime = false;
+        for (size_t gi = 0; gi < G; ++gi)
+          if (!b->groups[gi].sweep && sig[(size_t)e * G + gi] == 1) prime = true;
+        if (prime) break;
+      }
+      for (size_t gi = 0; gi < G; ++gi) {
+        auto& g = b->groups[gi];
+        if (g.sweep || sig[(size_t)a * G + gi] != 1) continue;
+        Launch L;
+        L.N = g.N;
+        L.engine = g.engine;
+        L.prec = g.prec;
+        L.masked = sig[(size_t)n_iters * G + gi];
+        L.stream = on;
+        L.js = g.d_js;
+        L.st = g.d_steps + (size_t)a * g.members.size();
+        L.tiles = g.d_tiles;
+        L.ntiles = g.ntiles;
+        cudaError_t r = launch_prime(L);
+        if (r != cudaSuccess) return r;
+        ++kernels;
+      }
+      cudaError_t r = cudaEventRecord(b->fork, on);
+      for (size_t gi = 0; r == cudaSuccess && gi < G; ++gi) {
+        auto& g = b->groups[gi];
+        if (g.sweep) continue;
+        cudaStream_t sg = b->side[gi];
+        const size_t qbytes = sizeof(unsigned) * (2 + 2 * (size_t)g.ntiles);
+        r = cudaStreamWaitEvent(sg, b->fork, 0);
+        if (r == cudaSuccess) r = cudaMemsetAsync(g.d_queue, 0, qbytes, sg);
+        PersistArgs pa{};
+        pa.js = g.d_js;
+        pa.st = g.d_steps;
+        pa.tiles = g.d_tiles;
+        pa.ntiles = g.ntiles;
+        pa.m = (int)g.members.size();
+        pa.row0 = a;
+        pa.iters = e - a;
+        pa.ticket = g.d_queue;
+        pa.done = g.d_queue + 2;
+        pa.budget = b->budget;
+        pa.hold = b->persistent == 2;
+        if (r == cudaSuccess)
+          r = launch_persist(g.N, pa, sig[(size_t)n_iters * G + gi], g.blocks_per_sm * b->sms, sg);
+        ++kernels;
+        if (r == cudaSuccess) r = cudaEventRecord(b->join[gi], sg);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(on, b->join[gi], 0);
+      }
+      if (r != cudaSuccess) return r;
+      a = e;
+    }
+    b->graph_kernels = kernels;
+    return cudaSuccess;
+  };
   auto issue = [&](cudaStream_t on) -> cudaError_t {
+    if (b->persistent) return issue_persistent(on);
     int64_t kernels = 0;
     for (int i = 0; i < n_iters; ++i)
       for (size_t gi = 0; gi < G; ++gi) {
@@ -2013,6 +2092,33 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
 int64_t cpra_batch_launches(cpra_batch_t b, int32_t n_iters) {
   if (!b) return -1;
   int64_t k = 0;
+  if (b->persistent) {
+    // per segment (split where a member primes): the primes, then one
+    // persistent launch per Jacobi group
+    int jacobi = 0;
+    for (auto& g : b->groups) {
+      if (g.sweep) {
+        k += (int64_t)(n_iters / g.n_ei) * g.np_max *
+             (g.engine == CPRA_ENGINE_FUSED ? 1 : 1 + 2 * (int64_t)g.n_ei);
+        continue;
+      }
+      ++jacobi;
+    }
+    for (int i = 0; i < n_iters; ++i) {
+      int primes = 0;
+      for (auto& g : b->groups) {
+        if (g.sweep) continue;
+        bool any = false;
+        for (int mi : g.members) {
+          const cpra_plan_s* p = b->plans[mi];
+          if ((p->t + i) % p->cfg.n_ei == 0) any = true;
+        }
+        primes += any ? 1 : 0;
+      }
+      if (i == 0 || primes > 0) k += primes + jacobi;
+    }
+    return k;
+  }
   for (auto& g : b->groups) {
     if (g.sweep) {  // per episode and angle: one fused launch, or prime + n_ei (column, row)
       k += (int64_t)(n_iters / g.n_ei) * g.np_max *
@@ -2046,12 +2152,71 @@ int64_t cpra_batch_launches(cpra_batch_t b, int32_t n_iters) {
   return k;
 }
 
+cpra_status cpra_batch_set_persistent(cpra_batch_t b, int32_t mode, double wait_budget_s) {
+  if (!b) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "batch is NULL");
+  if (mode < 0 || mode > 2) return bfail(b, CPRA_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+  if (!(wait_budget_s >= 0.0) || !(wait_budget_s <= 600.0))
+    return bfail(b, CPRA_ERR_INVALID_ARG, "wait budget must be in [0, 600] seconds");
+  if (mode != 0)
+    for (auto& g : b->groups) {
+      if (g.sweep) continue;
+      if (g.engine != CPRA_ENGINE_WARP || g.prec != CPRA_FP32 || !persist_supported(g.N))
+        return bfail(b, CPRA_ERR_UNSUPPORTED,
+                     "persistent batches run Jacobi groups of the FP32 warp engine "
+                     "(N in {64, 128, 192, 256, 384, 512})");
+    }
+  CK_B(cudaStreamSynchronize(b->stream), "batch sync");
+  if (mode != 0) {
+    int dev = 0, khz = 0;
+    CK_B(cudaGetDevice(&dev), "device");
+    CK_B(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    CK_B(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev), "clock rate");
+    const double secs = wait_budget_s > 0.0 ? wait_budget_s : 2.0;
+    b->budget = (long long)(secs * (double)khz * 1e3);
+    if (b->side.empty()) {
+      b->side.assign(b->groups.size(), nullptr);
+      b->join.assign(b->groups.size(), nullptr);
+      CK_B(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch event");
+      for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        CK_B(cudaStreamCreateWithFlags(&b->side[gi], cudaStreamNonBlocking), "batch stream");
+        CK_B(cudaEventCreateWithFlags(&b->join[gi], cudaEventDisableTiming), "batch event");
+      }
+    }
+    for (auto& g : b->groups) {
+      if (g.sweep) continue;
+      if (!g.d_queue) {
+        size_t room = 0;
+        for (int mi : g.members) room += (size_t)b->plans[mi]->Np;
+        g.d_queue = (unsigned*)balloc(b, sizeof(unsigned) * (2 + 2 * room));
+        if (!g.d_queue) return bfail(b, CPRA_ERR_OUT_OF_MEMORY, "batch queue");
+      }
+      CK_B(prepare_persist(g.N, &g.blocks_per_sm), "persistent kernel set-up");
+    }
+  }
+  b->persistent = mode;
+  if (b->exec) {  // the next call captures the new launch pattern
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_sig.clear();
+  }
+  return CPRA_OK;
+}
+
 cpra_status cpra_batch_destroy(cpra_batch_t b) {
   if (!b) return CPRA_OK;
   cudaStreamSynchronize(b->stream);
+  for (cudaStream_t sg : b->side)
+    if (sg) cudaStreamSynchronize(sg);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaStream_t sg : b->side)
+    if (sg) cudaStreamDestroy(sg);
+  for (cudaEvent_t ev : b->join)
+    if (ev) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (void* q : b->owned) cudaFree(q);
   delete b;
   return CPRA_OK;

@@ -35,6 +35,7 @@ struct DevStatus {
   int angle;       // an angle whose Fourier error was not finite
 };
 constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;  // a bounded device wait gave up
 
 struct Assembly {
   float2* F = nullptr;        // [Np][N][N] z-transformed spectra, [n][ku][z]
@@ -240,6 +241,19 @@ struct JobStep {
   int hio_left;        // fused engine: how many of them are HIO (the rest ER)
 };
 
+// Arguments of the warp engine's persistent work-queue kernel (k_persist_w
+// in fast_kernels.cuh).
+struct PersistArgs {
+  const JobStatic* js;
+  const JobStep* st;  // step rows of the call: iteration i of this launch at st + (row0 + i) * m
+  const int2* tiles;  // (member, angle) tiles
+  int ntiles, m, row0, iters;
+  unsigned* ticket;   // [2]: next task; [1] is a count that no task increments
+  unsigned* done;     // [2 * ntiles]: column and row blocks done in this launch
+  long long budget;   // clock64 cycles a wait may take
+  int hold;           // testing: the first task waits on ticket[1] >= 1 (never)
+};
+
 // One launch over ntiles (job, angle) tiles.
 struct Launch {
   int N;
@@ -326,6 +340,10 @@ cudaError_t launch_colpass_fast_tc(const Launch& L);
 cudaError_t launch_rowpass_fast(const Launch& L);
 cudaError_t launch_prime_fast(const Launch& L);
 cudaError_t launch_colpass_fast(const Launch& L);
+// persistent work-queue form of the column and row passes (FP32)
+bool persist_supported(int N);
+cudaError_t prepare_persist(int N, int* blocks_per_sm);
+cudaError_t launch_persist(int N, const PersistArgs& a, int masked, int grid, cudaStream_t st);
 
 // cluster-resident fused engine (k_fused.cu): one launch = prime + n_iters
 // iterations of every tile, the angle's spectrum held in distributed shared

@@ -109,8 +109,8 @@ __device__ __forceinline__ TcCtx tc_setup(char* base, const uint16_t* gW, int wa
 }
 
 template <int N>
-__device__ __forceinline__ void load_xtw(float2* xs, const float2* xtw, int nthreads) {
-  for (int i = threadIdx.x; i < N; i += nthreads) xs[i] = xtw[i];
+__device__ __forceinline__ void load_xtw(float2* xs, const float2* xtw, int) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) xs[i] = xtw[i];
 }
 
 // Z (B layout) of the row pairs of this warp -> packed half spectra of both
@@ -208,7 +208,8 @@ __device__ __forceinline__ void rowpass_tile(const JobStatic* __restrict__ js,
   if (bx == 0 && threadIdx.x == 0) {
     if (err_slot >= 0) {
       const double den = sumA2[n];
-      err_hist[(size_t)err_slot * Np + n] = publish_error(err_acc[n], Cn[n], den, J->status, n);
+      // err_acc from L2: a persistent launch's column tasks on other SMs sum into it
+      err_hist[(size_t)err_slot * Np + n] = publish_error(__ldcg(err_acc + n), Cn[n], den, J->status, n);
     }
     err_acc[n] = 0.0;
   }
@@ -470,7 +471,11 @@ __device__ __forceinline__ float2 project_w(float2 G, float a, float& e) {
 
 // One CTA of the column pass: packed columns [bx * CB, (bx + 1) * CB) of
 // tile tl = (job, angle).
-template <int N, int PREC, bool MASKED>
+//
+// L2_ONLY: stage the spectrum with L2-only loads instead of the 8-byte
+// cp.async (which allocates in L1): inside a persistent kernel other SMs
+// rewrite the spectrum between two reads of the same lines by this SM.
+template <int N, int PREC, bool MASKED, bool L2_ONLY = false>
 __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
                                              const JobStep* __restrict__ st, const int2 tl,
                                              const int bx) {
@@ -503,8 +508,13 @@ __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
   {
     const float2* src = Hn + (size_t)y0 * H + c0 + cc;
     float2* dst = buf + y0 * C::SP + cc;
+    if constexpr (L2_ONLY) {
 #pragma unroll
-    for (int k = 0; k < N / RS; ++k) cp_async8(dst + k * RS * C::SP, src + (size_t)k * RS * H);
+      for (int k = 0; k < N / RS; ++k) dst[k * RS * C::SP] = ld_cg(src + (size_t)k * RS * H);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N / RS; ++k) cp_async8(dst + k * RS * C::SP, src + (size_t)k * RS * H);
+    }
     const float* Ablk = A_T + ((size_t)n * H + c0) * N + 4 * threadIdx.x;  // CB contiguous columns
 #pragma unroll
     for (int k = 0; k < C::CB * N / 4 / C::NT; ++k) cp_async16(As + 4 * (threadIdx.x + k * C::NT), Ablk + 4 * k * C::NT);
@@ -608,6 +618,114 @@ __global__ void __launch_bounds__(ColW<N, PREC>::NT, ColW<N, PREC>::MINB)
 k_colpass_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
             const int2* __restrict__ tiles) {
   colpass_tile<N, PREC, MASKED>(js, st, tiles[blockIdx.y], blockIdx.x);
+}
+
+// ---------------------------------------------------------------- persistent
+// One launch of the warp engine over `iters` iterations of a group of
+// reconstructions of one N.  Every CTA takes the next task of a queue
+// ordered (iteration, pass, tile, block): the column-pass blocks of every
+// (member, angle) tile, then their row-pass blocks.  Before it runs a task
+// the CTA waits until the blocks it reads from are done: a column block of
+// iteration i needs every row block of its tile at i - 1 (the launch starts
+// after the coupling prime), a row block every column block of its tile at
+// i.  Dependencies point to earlier tasks, which running CTAs hold, so the
+// queue drains whatever the grid size.  A wait longer than `budget` clock
+// cycles flags TIMEOUT in every member's status word and the CTA returns.
+// Each task computes exactly what the same block of the separate passes
+// computes.
+
+template <int N> struct PersistCfg {
+  using C = ColW<N, kPrecFP32>;
+  using R = RowW<N, kPrecFP32>;
+  static constexpr int NT = C::NT;
+  static constexpr int RPT = C::NT / (R::WARPS * 32);  // row-pass blocks a task (its warps)
+  static constexpr int CB = (N / 2) / C::CB;            // column tasks an angle
+  static constexpr int RB = (N / 2) / (R::WARPS * R::FL::L) / (RPT > 0 ? RPT : 1);  // row tasks an angle
+  static constexpr size_t RSMEM = sizeof(float2) * (N + (size_t)(RPT > 0 ? RPT : 1) * R::WARPS * R::WARP_F2);
+  static constexpr size_t SMEM = col_smem<N, kPrecFP32>() > RSMEM ? col_smem<N, kPrecFP32>() : RSMEM;
+  // resident CTAs an SM the register budget is set for: the column pass's,
+  // or, for the 4-warp sizes, three (the row pass's) unless shared memory
+  // holds fewer anyway (then the registers are not what limits residency)
+  static constexpr int SMEM_CTAS = (int)((228u * 1024u) / (SMEM + 1024u));
+  static constexpr int MINB = NT == 128 ? (SMEM_CTAS < 3 ? (SMEM_CTAS > 0 ? SMEM_CTAS : 1) : 3) : C::MINB;
+  static constexpr bool OK = (RPT == 1 || RPT == 2) && C::NT == RPT * R::WARPS * 32 &&
+                             ((N / 2) / (R::WARPS * R::FL::L)) % (RPT > 0 ? RPT : 1) == 0 &&
+                             SMEM <= 227 * 1024;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// add 1 after every write this CTA made before its last barrier
+__device__ __forceinline__ void add_release(unsigned* p) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(p) : "memory");
+}
+// wait until *c >= need (acquire); false after `budget` cycles
+__device__ __forceinline__ bool wait_count(const unsigned* c, unsigned need, long long budget) {
+  if (ld_acquire(c) >= need) return true;
+  const long long t0 = clock64();
+  unsigned ns = 32;
+  while (ld_acquire(c) < need) {
+    if (clock64() - t0 > budget) return false;
+    __nanosleep(ns);
+    if (ns < 2048) ns *= 2;
+  }
+  return true;
+}
+
+template <int N, bool MASKED>
+__global__ void __launch_bounds__(PersistCfg<N>::NT, PersistCfg<N>::MINB)
+k_persist_w(const PersistArgs a) {
+  using P = PersistCfg<N>;
+  __shared__ unsigned task_s;
+  __shared__ int ok_s;
+  const unsigned ncol = (unsigned)a.ntiles * P::CB;
+  const unsigned per_iter = ncol + (unsigned)a.ntiles * P::RB;
+  const unsigned total = per_iter * (unsigned)a.iters;
+  // thread 0 holds the CTA's next ticket, fetched while the current task
+  // runs (a held ticket runs as soon as the current task ends, so the queue
+  // still drains: the smallest unfinished task is always running)
+  unsigned next = 0;
+  if (threadIdx.x == 0) next = atomicAdd(a.ticket, 1u);
+  for (;;) {
+    __syncthreads();  // the previous task is done with task_s, ok_s and shared memory
+    if (threadIdx.x == 0) task_s = next;
+    __syncthreads();
+    const unsigned task = task_s;
+    if (task >= total) return;
+    const int it = (int)(task / per_iter);
+    const unsigned r = task % per_iter;
+    const bool col = r < ncol;
+    const unsigned rr = col ? r : r - ncol;
+    const int tile = (int)(col ? rr / P::CB : rr / P::RB);
+    const int bx = (int)(col ? rr % P::CB : rr % P::RB);
+    if (threadIdx.x == 0) {
+      const unsigned* c = col ? a.done + 2 * tile + 1 : a.done + 2 * tile;
+      unsigned need = col ? (unsigned)(P::RB * it) : (unsigned)(P::CB * (it + 1));
+      if (a.hold && task == 0) {
+        c = a.ticket + 1;
+        need = 1;
+      }
+      next = atomicAdd(a.ticket, 1u);
+      const bool ok = wait_count(c, need, a.budget);
+      if (!ok)
+        for (int j = 0; j < a.m; ++j) {
+          volatile DevStatus* ds = a.js[j].status;
+          ds->flags = ds->flags | kStatusTimeout;
+        }
+      ok_s = ok;
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    const int2 tl = a.tiles[tile];
+    const JobStep* st = a.st + (size_t)(a.row0 + it) * a.m;
+    if (col) colpass_tile<N, kPrecFP32, MASKED, true>(a.js, st, tl, bx);
+    else rowpass_tile<N, kPrecFP32>(a.js, st, tl, bx * P::RPT);
+    __syncthreads();
+    if (threadIdx.x == 0) add_release(a.done + 2 * tile + (col ? 0 : 1));
+  }
 }
 
 // ---------------------------------------------------------------- launchers

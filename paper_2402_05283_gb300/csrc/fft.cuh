@@ -251,6 +251,12 @@ __device__ __forceinline__ void fft_lines(float2* buf, const float2* tw) {
 }
 
 // Asynchronous global -> shared copies (LDGSTS); completion by wait_all.
+// 8 bytes through L2 only (no L1 allocation)
+__device__ __forceinline__ float2 ld_cg(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");

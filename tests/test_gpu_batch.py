@@ -91,6 +91,81 @@ def test_autotune_cache(cp, tmp_path):
     doc = json.load(open(path))
     assert len(doc["entries"]) == 1 and doc["entries"][0]["engine"] == eng
     assert cp.cpra_autotune(128, cp.FP32, path) == (eng, pytest.approx(ms))
-    eng2, _ = cp.cpra_autotune(192, cp.FP32, path)  # only TWO_PASS exists for 192
-    assert eng2 == cp.ENGINE_TWO_PASS
+    eng2, _ = cp.cpra_autotune(192, cp.FP32, path)  # TWO_PASS and WARP exist for 192
+    assert eng2 in (cp.ENGINE_TWO_PASS, cp.ENGINE_WARP)
     assert len(json.load(open(path))["entries"]) == 2
+
+
+# ---------------------------------------------------------------- persistent work queue
+# uneven sizes on the warp engine (the sizes of the batching workload, and
+# small angle counts so the oracle-free comparison stays quick)
+UNEVEN = [(128, 6, 11, {}), (192, 5, 12, {"hio_iters": 9}), (256, 4, 13, {"n_ei": 4}),
+          (384, 3, 14, {"alpha": (0.1, 0.2, 0.4, 0.2, 0.1)}), (128, 3, 15, {"update": 1})]
+
+
+def _warp_plans(cp, mix):
+    return _plans(cp, [(N, Np, seed, {**kw, "engine": cp.ENGINE_WARP}) for N, Np, seed, kw in mix])
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_persistent_batch_uneven_n_equals_alone(cp, use_graph):
+    """One persistent work-queue launch per size group and segment (split at
+    the coupling steps), the groups forked onto their own streams: every
+    member's iterates equal the plan run alone bit for bit, over calls that
+    cross episode boundaries and the HIO -> ER switch."""
+    alone = _warp_plans(cp, UNEVEN)
+    for p in alone:
+        p.iterate(23)
+    mixed = _warp_plans(cp, UNEVEN)
+    b = cp.Batch(mixed, use_graph=use_graph)
+    b.set_persistent(1)
+    b.iterate(11)  # the first call also runs each member's seeded start
+    expect = b.launches(12)
+    n0 = cp.cpra_launch_count()
+    b.iterate(12)
+    assert cp.cpra_launch_count() - n0 == expect
+    for pa, pm in zip(alone, mixed):
+        assert pm.iteration == 23
+        assert np.array_equal(pa.result(cp.RESULT_STATE), pm.result(cp.RESULT_STATE))
+        np.testing.assert_allclose(pa.result(cp.RESULT_ERRORS), pm.result(cp.RESULT_ERRORS),
+                                   rtol=1e-12)
+    b.close()
+
+
+def test_persistent_wait_runs_out_and_recovers(cp):
+    """The bounded device wait: in mode 2 the first task of every launch
+    waits on a count that no task increments, so its wait runs out after the
+    budget (1 ms), the launch ends and every member reports TIMEOUT; a reset
+    clears it and the normal mode then equals the plans alone."""
+    plans = _warp_plans(cp, UNEVEN[:2])
+    b = cp.Batch(plans, use_graph=False)
+    b.set_persistent(2, wait_budget_s=1e-3)
+    b.iterate(3)
+    for p in plans:
+        with pytest.raises(cp.CpraError) as e:
+            p.sync()
+        assert e.value.status == cp.ERR_TIMEOUT
+        assert "wait" in cp.cpra_last_error(p.h)
+        with pytest.raises(cp.CpraError):  # sticky until reset
+            p.iterate(1)
+    for p in plans:
+        p.reset()
+    b.set_persistent(1)
+    b.iterate(4)
+    ref = _warp_plans(cp, UNEVEN[:2])
+    for pr, pm in zip(ref, plans):
+        pr.iterate(4)
+        assert np.array_equal(pr.result(cp.RESULT_STATE), pm.result(cp.RESULT_STATE))
+    b.close()
+
+
+def test_persistent_needs_the_warp_engine(cp):
+    plans = _plans(cp, [(128, 3, 1, {"engine": cp.ENGINE_FUSED}), (192, 2, 2, {})])
+    b = cp.Batch(plans, use_graph=False)
+    with pytest.raises(cp.CpraError) as e:
+        b.set_persistent(1)
+    assert e.value.status == cp.ERR_UNSUPPORTED
+    with pytest.raises(cp.CpraError) as e:
+        b.set_persistent(3)
+    assert e.value.status == cp.ERR_INVALID_ARG
+    b.close()
