@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include "cpra_internal.h"
+#include "fftw_tc.cuh"
 #include "tiling.cuh"
 
 using namespace cpra;
@@ -715,13 +716,15 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   std::vector<uint16_t> tcw;
   if (cfg->precision != CPRA_FP32) {
     // block DFT matrices [[Re W, Im W], [-Im W, Re W]] of the E1- and
-    // E2-point DFTs, forward and inverse, stored [n][k] with pitch 2E + 8,
-    // FP64 then rounded once to BF16 / FP16
+    // E2-point DFTs, forward and inverse, stored [n][k] (n = output column,
+    // k = depth) in the tensor cores' K-major operand layout (core matrices
+    // of 8 rows x 8 values, umma_offset), FP64 then rounded once to BF16 /
+    // FP16
     for (int which = 0; which < 2; ++which)
       for (int dir = -1; dir <= 1; dir += 2) {
         const int E = which == 0 ? E1 : E2;
-        const int K = 2 * E, P = 2 * E + 8;
-        std::vector<uint16_t> m((size_t)K * P, 0);
+        const int K = 2 * E, KC = K / 8;
+        std::vector<uint16_t> m((size_t)K * K, 0);
         for (int j = 0; j < E; ++j)
           for (int k = 0; k < E; ++k) {
             const double a = dir * 2.0 * M_PI * (double)((j * k) % E) / (double)E;
@@ -740,7 +743,7 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
                   __half h = __float2half_rn(v);
                   std::memcpy(&bits, &h, 2);
                 }
-                m[(size_t)nn * P + kk] = bits;
+                m[(size_t)umma_offset(nn, kk, KC) / 2] = bits;
               }
           }
         tcw.insert(tcw.end(), m.begin(), m.end());

@@ -78,34 +78,36 @@ template <int N, int PREC> using RowW = RowCfg<N, typename WLines<N, PREC>::type
 // registers, where the extra warps of the one-line plan do not pay
 template <int N, int PREC> using PrimeW = RowCfg<N, WarpLines<N>>;
 
-// extra shared memory of the tensor-core path: one 16-bit A tile and 32
-// unscale factors per warp (the block DFT matrices are read through L1)
+// extra shared memory of the tensor-core path (TcLayout of fftw_tc.cuh): the
+// block DFT matrices, the CTA's A tile, the unscale factors, the mbarrier
 template <int N, int PREC> struct TcSmem {
   using P = WP<N>;
-  static constexpr int EM = P::E1 > P::E2 ? P::E1 : P::E2;
-  static constexpr int W1 = TcDims<P::E1>::W_HALVES, W2 = TcDims<P::E2>::W_HALVES;
-  static constexpr size_t WARP_BYTES = PREC == kPrecFP32 ? 0 : 2 * TcDims<EM>::A_HALVES + 4 * 32;
-  static constexpr size_t bytes(int warps) { return warps * WARP_BYTES; }
+  template <int W>
+  static constexpr size_t bytes() {
+    if constexpr (PREC == kPrecFP32) return 0;
+    else return TcLayout<P::E1, P::E2, W>::BYTES;
+  }
 };
 template <int N, int PREC>
-constexpr size_t row_smem() { return RowW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(RowW<N, PREC>::WARPS); }
+constexpr size_t row_smem() {
+  return RowW<N, PREC>::SMEM + TcSmem<N, PREC>::template bytes<RowW<N, PREC>::WARPS>();
+}
 template <int N, int PREC>
-constexpr size_t prime_smem() { return PrimeW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(PrimeW<N, PREC>::WARPS); }
+constexpr size_t prime_smem() {
+  return PrimeW<N, PREC>::SMEM + TcSmem<N, PREC>::template bytes<PrimeW<N, PREC>::WARPS>();
+}
 
-// Tensor-core scratch of this warp; W = the plan's matrices in global memory
-template <int N, int PREC>
-__device__ __forceinline__ TcCtx tc_setup(char* base, const uint16_t* gW, int warp) {
-  using T = TcSmem<N, PREC>;
-  TcCtx c{};
-  if constexpr (PREC != kPrecFP32) {
-    c.W1f = gW;
-    c.W1i = gW + T::W1;
-    c.W2f = gW + 2 * T::W1;
-    c.W2i = gW + 2 * T::W1 + T::W2;
-    c.A16 = reinterpret_cast<uint16_t*>(base + warp * T::WARP_BYTES);
-    c.R = reinterpret_cast<float*>(base + warp * T::WARP_BYTES + 2 * TcDims<T::EM>::A_HALVES);
-  }
-  return c;
+// The CTA's tensor-core state (every thread calls it; tc_end releases it):
+// base = the kernel's tensor-core region, gW = the plan's matrices.
+template <int N, int PREC, int W>
+__device__ __forceinline__ TcCtx tc_setup(char* base, const uint16_t* gW, DevStatus* status,
+                                          uint32_t* phase) {
+  if constexpr (PREC != kPrecFP32) return tc_begin<WP<N>::E1, WP<N>::E2, W>(base, gW, status, phase);
+  else return TcCtx{};
+}
+template <int PREC>
+__device__ __forceinline__ void tc_finish(const TcCtx& c) {
+  if constexpr (PREC != kPrecFP32) tc_end(c);
 }
 
 template <int N>
@@ -187,8 +189,9 @@ __device__ __forceinline__ void rowpass_tile(const JobStatic* __restrict__ js,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* T = smem + N + warp * RW::WARP_F2;
   float* Gs = reinterpret_cast<float*>(T + FL::TSIZE);  // this warp's 2L rows of g
-  const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(smem + N + RW::WARPS * RW::WARP_F2),
-                                     J->tcw, warp);
+  uint32_t tc_phase = 0;
+  const TcCtx tc = tc_setup<N, PREC, RW::WARPS>(reinterpret_cast<char*>(smem + N + RW::WARPS * RW::WARP_F2),
+                                                J->tcw, J->status, &tc_phase);
   const int n = tl.y;
   const int pair0 = (bx * RW::WARPS + warp) * FL::L;
   float* grow = g + ((size_t)n * N + 2 * pair0) * N;  // 2L contiguous rows
@@ -302,9 +305,11 @@ __device__ __forceinline__ void rowpass_tile(const JobStatic* __restrict__ js,
   if (algo == kHIO) update_rows(std::integral_constant<int, kHIO>{});
   else if (algo == kER) update_rows(std::integral_constant<int, kER>{});
   else update_rows(std::integral_constant<int, kRAAR>{});
-  if (!forward) return;
-  lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
-  store_pairs_w<N, FL>(b, T, Hn, pair0, lane);
+  if (forward) {
+    lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
+    store_pairs_w<N, FL>(b, T, Hn, pair0, lane);
+  }
+  tc_finish<PREC>(tc);
 }
 
 template <int N, int PREC>
@@ -413,8 +418,9 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   float2* xs = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* T = smem + N + warp * RW::WARP_F2;
-  const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(smem + N + RW::WARPS * RW::WARP_F2),
-                                     J->tcw, warp);
+  uint32_t tc_phase = 0;
+  const TcCtx tc = tc_setup<N, PREC, RW::WARPS>(reinterpret_cast<char*>(smem + N + RW::WARPS * RW::WARP_F2),
+                                                J->tcw, J->status, &tc_phase);
   const int n = tl.y;
   const int pair0 = (blockIdx.x * RW::WARPS + warp) * FL::L;
   __shared__ TapTab tt;
@@ -427,6 +433,7 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
   float2 b[FL::TB][FL::E2];
   lines_fwd<N, PREC, FL>(a, b, T, xs, lane, &tc);
   store_pairs_w<N, FL>(b, T, Hp + (size_t)n * N * H, pair0, lane);
+  tc_finish<PREC>(tc);
 }
 
 // ---------------------------------------------------------------- column pass
@@ -446,7 +453,9 @@ template <int N, int PREC> struct ColW {
   static constexpr size_t SMEM = sizeof(float2) * (N + BUF) + sizeof(float) * CB * N;
 };
 template <int N, int PREC>
-constexpr size_t col_smem() { return ColW<N, PREC>::SMEM + TcSmem<N, PREC>::bytes(ColW<N, PREC>::WARPS); }
+constexpr size_t col_smem() {
+  return ColW<N, PREC>::SMEM + TcSmem<N, PREC>::template bytes<ColW<N, PREC>::WARPS>();
+}
 
 // G' = a G / |G| (a where G = 0); e += (|G| - a)^2, unweighted (the caller
 // keeps one sum per weight).  In plans with a missing-data mask (MASKED),
@@ -495,7 +504,9 @@ __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
   __shared__ double red[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* As = reinterpret_cast<float*>(buf + C::BUF);  // A_sym of the block, [c][ky]
-  const TcCtx tc = tc_setup<N, PREC>(reinterpret_cast<char*>(As + C::CB * N), J->tcw, threadIdx.x >> 5);
+  uint32_t tc_phase = 0;
+  const TcCtx tc = tc_setup<N, PREC, C::WARPS>(reinterpret_cast<char*>(As + C::CB * N), J->tcw, J->status,
+                                               &tc_phase);
   float2* T = buf + warp * FL::TSIZE;
   const int n = tl.y;
   const int c0 = bx * C::CB;
@@ -611,6 +622,7 @@ __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
     for (int w = 0; w < C::WARPS; ++w) s += red[w];
     atomicAdd(err_acc + n, s);
   }
+  tc_finish<PREC>(tc);
 }
 
 template <int N, int PREC, bool MASKED>
@@ -742,6 +754,25 @@ static cudaError_t prepare_w() {
   if (e == cudaSuccess) e = smem_attr(k_prime_w<N, PREC>, prime_smem<N, PREC>());
   if (e == cudaSuccess) e = smem_attr(k_colpass_w<N, PREC, false>, col_smem<N, PREC>());
   if (e == cudaSuccess) e = smem_attr(k_colpass_w<N, PREC, true>, col_smem<N, PREC>());
+  if constexpr (PREC != kPrecFP32) {
+    // the tensor-memory columns of every CTA that can be resident on an SM
+    // must fit its 512 (an allocation beyond them would wait for a release)
+    using P = WP<N>;
+    auto fits = [&](auto kernel, int threads, size_t smem, uint32_t cols) -> cudaError_t {
+      int blocks = 0;
+      cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, smem);
+      if (r != cudaSuccess) return r;
+      return (uint32_t)blocks * cols <= 512u ? cudaSuccess : cudaErrorNotSupported;
+    };
+    constexpr uint32_t row_cols = TcLayout<P::E1, P::E2, RowW<N, PREC>::WARPS>::COLS;
+    constexpr uint32_t prime_cols = TcLayout<P::E1, P::E2, PrimeW<N, PREC>::WARPS>::COLS;
+    constexpr uint32_t col_cols = TcLayout<P::E1, P::E2, ColW<N, PREC>::WARPS>::COLS;
+    if (e == cudaSuccess) e = fits(k_rowpass_w<N, PREC>, RowW<N, PREC>::WARPS * 32, row_smem<N, PREC>(), row_cols);
+    if (e == cudaSuccess)
+      e = fits(k_prime_w<N, PREC>, PrimeW<N, PREC>::WARPS * 32, prime_smem<N, PREC>(), prime_cols);
+    if (e == cudaSuccess) e = fits(k_colpass_w<N, PREC, false>, ColW<N, PREC>::NT, col_smem<N, PREC>(), col_cols);
+    if (e == cudaSuccess) e = fits(k_colpass_w<N, PREC, true>, ColW<N, PREC>::NT, col_smem<N, PREC>(), col_cols);
+  }
   if (e == cudaSuccess) done = true;
   return e;
 }

@@ -98,16 +98,6 @@ template <int N> struct WP {
 template <int N> constexpr bool kHasWarpPlan = (N == 64 || N == 128 || N == 192 || N == 256 || N == 384 ||
                                                 N == 512 || N == 1024);
 
-// Tensor-core scratch of one warp and the block DFT matrices (16-bit).
-struct TcCtx {
-  uint16_t* A16;
-  float* R;
-  const uint16_t* W1f;  // E1-point forward / inverse
-  const uint16_t* W1i;
-  const uint16_t* W2f;  // E2-point forward / inverse
-  const uint16_t* W2i;
-};
-
 // step-A DFTs of every task of this warp through the tensor cores; a[][]
 // goes through the warp tile T with pitch E1 + 1
 template <int N, int PREC, int DIR>
@@ -121,7 +111,7 @@ __device__ __forceinline__ void tc_step_a(float2 (&a)[WP<N>::TA][WP<N>::E1], flo
   });
   __syncwarp();
   for (int c = 0; c < P::TA; ++c)
-    warp_tc_dft<P::E1, PREC>(T + c * 32 * P::AP, P::AP, tc.A16, tc.R, DIR < 0 ? tc.W1f : tc.W1i, lane);
+    cta_tc_dft<P::E1, PREC>(T + c * 32 * P::AP, P::AP, tc, DIR < 0 ? 0 : 1, lane);
   static_for<0, P::TA>([&](auto II) {
     constexpr int i = decltype(II)::value;
     const int t = lane + 32 * i;
@@ -161,7 +151,7 @@ __device__ __forceinline__ void warp_fft_fwd(float2 (&a)[WP<N>::TA][WP<N>::E1],
   if constexpr (PREC != kPrecFP32) {
     // rows of T are the step-B tasks (line * E1 + k1 = t)
     for (int c = 0; c < P::TB; ++c)
-      warp_tc_dft<P::E2, PREC>(T + c * 32 * P::TP, P::TP, tc->A16, tc->R, tc->W2f, lane);
+      cta_tc_dft<P::E2, PREC>(T + c * 32 * P::TP, P::TP, *tc, 2, lane);
   }
   static_for<0, P::TB>([&](auto II) {
     constexpr int i = decltype(II)::value;
@@ -196,7 +186,7 @@ __device__ __forceinline__ void warp_fft_inv(float2 (&b)[WP<N>::TB][WP<N>::E2],
   __syncwarp();
   if constexpr (PREC != kPrecFP32) {
     for (int c = 0; c < P::TB; ++c)
-      warp_tc_dft<P::E2, PREC>(T + c * 32 * P::TP, P::TP, tc->A16, tc->R, tc->W2i, lane);
+      cta_tc_dft<P::E2, PREC>(T + c * 32 * P::TP, P::TP, *tc, 3, lane);
   }
   static_for<0, P::E1>([&](auto KK) {
     constexpr int k1 = decltype(KK)::value;
