@@ -439,10 +439,11 @@ k_prime_w(const JobStatic* __restrict__ js, const JobStep* __restrict__ st,
 // ---------------------------------------------------------------- column pass
 // packed columns per CTA: 16 (128 B of each row) with the L-line plans; 8
 // with the one-line plan (8 warps, three CTAs an SM) and for the 16-bit path
-// at N = 1024, whose extra per-warp tiles would not fit beside 16 columns
+// at N >= 512, where the tensor-core region (block DFT matrices, A tile)
+// beside 16 columns would leave room for one CTA an SM
 template <int N, int PREC> struct ColW {
   using FL = typename WLines<N, PREC>::type;
-  static constexpr int CB = ((PREC != kPrecFP32 && N >= 1024) || kSlimLines<FL>) ? 8 : 16;
+  static constexpr int CB = ((PREC != kPrecFP32 && N >= 512) || kSlimLines<FL>) ? 8 : 16;
   static constexpr int WARPS = CB / FL::L;
   static constexpr int NT = WARPS * 32;
   static constexpr int MINB = kSlimLines<FL> ? 3 : (NT <= 256 ? 2 : 1);

@@ -13,30 +13,39 @@
 
 namespace cpra {
 
+// image rows a block of the blur kernels
+constexpr int kSwRows = 4;
+
 // Row blur: out[x] = sum_t taps[t] rho[(x - lo - t) mod N], reading the row
 // staged once with a halo, h[k] = rho[(k - lo - ntaps + 1) mod N] (the same
-// terms in the same order as the definition).
+// terms in the same order as the definition).  Rows y0 .. y0 + kSwRows - 1
+// of angle n a block, one after the other.
 __global__ void k_sw_rows(const float* __restrict__ g, const uint32_t* __restrict__ S, float* tmp,
                           const float* __restrict__ taps, int ntaps, int lo, int N, int W) {
   extern __shared__ float sm[];
   float* tp = sm;          // [ntaps]
   float* h = sm + ntaps;   // [N + ntaps - 1]
-  const int y = blockIdx.x, n = blockIdx.y;
-  const size_t base = ((size_t)n * N + y) * N;
-  const size_t srow = ((size_t)n * N + y) * W;
+  const int n = blockIdx.y;
   const int hb = -lo - ntaps + 1;
   for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
-  for (int k = threadIdx.x; k < N + ntaps - 1; k += blockDim.x) {
-    const int x = ((k + hb) % N + N) % N;
-    const float v = g[base + x];
-    h[k] = (sbit(S, srow, x) && v >= 0.0f) ? v : 0.0f;
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    float acc = 0.0f;
-    const float* hx = h + x + ntaps - 1;
-    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], hx[-t], acc);
-    tmp[base + x] = acc;
+  for (int yy = 0; yy < kSwRows; ++yy) {
+    const int y = blockIdx.x * kSwRows + yy;
+    if (y >= N) break;  // uniform over the block
+    const size_t base = ((size_t)n * N + y) * N;
+    const size_t srow = ((size_t)n * N + y) * W;
+    __syncthreads();  // the previous row is done with h
+    for (int k = threadIdx.x; k < N + ntaps - 1; k += blockDim.x) {
+      const int x = ((k + hb) % N + N) % N;
+      const float v = g[base + x];
+      h[k] = (sbit(S, srow, x) && v >= 0.0f) ? v : 0.0f;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+      float acc = 0.0f;
+      const float* hx = h + x + ntaps - 1;
+      for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], hx[-t], acc);
+      tmp[base + x] = acc;
+    }
   }
 }
 
@@ -45,25 +54,30 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Column blur of output rows y0 .. y0 + kSwRows - 1 of angle n (the terms
+// of each pixel in the order of the definition), and the rows' maximum.
 __global__ void k_sw_cols(const float* __restrict__ tmp, float* b, unsigned* mx,
                           const float* __restrict__ taps, int ntaps, int lo, int N) {
   extern __shared__ float sm[];
   __shared__ float red[32];
   float* tp = sm;                                   // [ntaps]
   int* rows = reinterpret_cast<int*>(sm + ntaps);   // [ntaps]: (y - lo - t) mod N
-  const int y = blockIdx.x, n = blockIdx.y;
+  const int n = blockIdx.y;
   const float* tn = tmp + (size_t)n * N * N;
-  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) {
-    tp[t] = taps[t];
-    rows[t] = ((y - (lo + t)) % N + N) % N;
-  }
-  __syncthreads();
+  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
   float m = 0.0f;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    float acc = 0.0f;
-    for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], tn[(size_t)rows[t] * N + x], acc);
-    b[((size_t)n * N + y) * N + x] = acc;
-    m = fmaxf(m, acc);
+  for (int yy = 0; yy < kSwRows; ++yy) {
+    const int y = blockIdx.x * kSwRows + yy;
+    if (y >= N) break;  // uniform over the block
+    __syncthreads();  // the previous row is done with rows[]
+    for (int t = threadIdx.x; t < ntaps; t += blockDim.x) rows[t] = ((y - (lo + t)) % N + N) % N;
+    __syncthreads();
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+      float acc = 0.0f;
+      for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], tn[(size_t)rows[t] * N + x], acc);
+      b[((size_t)n * N + y) * N + x] = acc;
+      m = fmaxf(m, acc);
+    }
   }
   m = warp_max(m);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -75,20 +89,21 @@ __global__ void k_sw_cols(const float* __restrict__ tmp, float* b, unsigned* mx,
   }
 }
 
+// S <- {b >= tau max b} (kept when max b is 0): a warp a row, lane l tests
+// pixel 32 w + l and the warp's ballot is word w
 __global__ void k_sw_thresh(const float* __restrict__ b, const unsigned* __restrict__ mx,
                             uint32_t* S, float tau, int N, int W) {
-  const int y = blockIdx.x, n = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int y = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), n = blockIdx.y;
+  if (y >= N) return;  // whole warps
   const float m = __uint_as_float(mx[n]);
   if (!(m > 0.0f)) return;
   const float thr = tau * m;
   const float* bn = b + ((size_t)n * N + y) * N;
-  for (int w = threadIdx.x; w < W; w += blockDim.x) {
-    uint32_t bits = 0;
-    for (int j = 0; j < 32; ++j) {
-      const int x = w * 32 + j;
-      if (x < N && bn[x] >= thr) bits |= 1u << j;
-    }
-    S[((size_t)n * N + y) * W + w] = bits;
+  for (int w = 0; w < W; ++w) {
+    const int x = w * 32 + lane;
+    const uint32_t bits = __ballot_sync(0xffffffffu, x < N && bn[x] >= thr);
+    if (lane == 0) S[((size_t)n * N + y) * W + w] = bits;
   }
 }
 
@@ -99,12 +114,13 @@ cudaError_t launch_shrinkwrap(cpra_plan_s* p) {
   cudaError_t e = cudaMemsetAsync(p->sw_max, 0, sizeof(unsigned) * Np, p->stream);
   if (e != cudaSuccess) return e;
   g_launches += 3;
-  k_sw_rows<<<dim3(N, Np), threads, (N + 2 * p->sw_ntaps) * sizeof(float), p->stream>>>(p->g, p->S, p->sw_tmp,
+  const int rb = (N + kSwRows - 1) / kSwRows;
+  k_sw_rows<<<dim3(rb, Np), threads, (N + 2 * p->sw_ntaps) * sizeof(float), p->stream>>>(p->g, p->S, p->sw_tmp,
                                                                     p->sw_taps, p->sw_ntaps, lo,
                                                                     N, p->W);
-  k_sw_cols<<<dim3(N, Np), threads, 2 * p->sw_ntaps * sizeof(float), p->stream>>>(p->sw_tmp, p->g_alt, p->sw_max, p->sw_taps,
+  k_sw_cols<<<dim3(rb, Np), threads, 2 * p->sw_ntaps * sizeof(float), p->stream>>>(p->sw_tmp, p->g_alt, p->sw_max, p->sw_taps,
                                                     p->sw_ntaps, lo, N);
-  k_sw_thresh<<<dim3(N, Np), 32, 0, p->stream>>>(p->g_alt, p->sw_max, p->S, p->cfg.sw_tau, N,
+  k_sw_thresh<<<dim3((N + 7) / 8, Np), 256, 0, p->stream>>>(p->g_alt, p->sw_max, p->S, p->cfg.sw_tau, N,
                                                  p->W);
   return cudaGetLastError();
 }
@@ -241,10 +257,11 @@ extern "C" cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_i
   if (e == cudaSuccess) e = launch_bits_from_u8(sc.bits, S_in, N, count, st);
   if (e == cudaSuccess) {
     g_launches += 3;
-    k_sw_rows<<<dim3(N, count), threads, (N + 2 * ntaps) * sizeof(float), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps,
+    const int rb = (N + kSwRows - 1) / kSwRows;
+    k_sw_rows<<<dim3(rb, count), threads, (N + 2 * ntaps) * sizeof(float), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps,
                                                                    lo, N, W);
-    k_sw_cols<<<dim3(N, count), threads, 2 * ntaps * sizeof(float), st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
-    k_sw_thresh<<<dim3(N, count), 32, 0, st>>>(sc.b, sc.mx, sc.bits, tau, N, W);
+    k_sw_cols<<<dim3(rb, count), threads, 2 * ntaps * sizeof(float), st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
+    k_sw_thresh<<<dim3((N + 7) / 8, count), 256, 0, st>>>(sc.b, sc.mx, sc.bits, tau, N, W);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = launch_bits_to_u8(sc.bits, S_out, N, count, st);
