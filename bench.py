@@ -127,7 +127,13 @@ def method_bytes_per_angle_iteration(n: int) -> int:
 # of the iteration kernels, bytes per angle-iteration, with the capture's
 # date and a fingerprint of the kernel sources it was taken on.  The bench
 # reports it only while the sources still have that fingerprint.
-NCU_ITERATION_TRAFFIC = {}  # {(engine kernel names, N): (bytes, date, fingerprint)}
+NCU_ITERATION_TRAFFIC = {
+    # k_colpass_w<512> 418.85 MB + k_rowpass_w<512> 699.75 MB for 180 angles
+    # (one launch each, --set full); the coupling prime (one launch in ten
+    # iterations, 5 % of the time) was not captured and is not included
+    (("k_colpass", "k_rowpass", "k_prime"), 512): ((418.850816e6 + 699.752448e6) / 180,
+                                                   "2026-12-04", "1d113a1f3f6644fe"),
+}  # {(kernel classes that ran, N): (bytes per angle-iteration, capture date, fingerprint)}
 KERNEL_SOURCES = ("fast_kernels.cuh", "fftw.cuh", "fftw_pair.cuh", "fft.cuh", "cpra_internal.h",
                   "k_fast.cu", "k_fused.cu", "taps.cuh")
 
@@ -194,6 +200,11 @@ def roofline_figures(plan, cp, peaks, Np_total, iters_timed):
             entry.update({"design_bytes_per_launch": design[k] * Np_total,
                           "effective_gbs": round(gbs, 1), "effective_frac": round(gbs / peak, 4)})
         per_kernel[names[k]] = entry
+    # the FP32 context: radix-2 flop count of the R2C + C2R pair plus the
+    # pixel work, against 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+    flops = 10.0 * NN * math.log2(N) + 20.0 * NN
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    alu_tf = Np_total * flops / (ms_per_iter * 1e-3) / 1e12
     return {"bound": "hbm", "kernel": "one all-angle iteration: " + " + ".join(ran),
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_note": traffic_note,
@@ -201,6 +212,10 @@ def roofline_figures(plan, cp, peaks, Np_total, iters_timed):
             "bytes_per_angle_iteration": method_bytes_per_angle_iteration(N),
             "ms_per_iteration": round(ms_per_iter, 5),
             "per_kernel": per_kernel,
+            "alu_context": {"flops_per_angle_iteration": int(flops), "achieved_tflops": round(alu_tf, 2),
+                            "fp32_peak_tflops": round(alu_peak, 1), "frac": round(alu_tf / alu_peak, 4),
+                            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (unit counts and "
+                                           "maximum SM clock)"},
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"
                            if not peaks.get("_fallback") else "fallback 6800 GB/s"}, stats
 
@@ -763,7 +778,9 @@ def run_gpu(args):
     hio = min(T_HIO, IT)
     engine = {"auto": cp.ENGINE_AUTO, "warp": cp.ENGINE_WARP, "fused": cp.ENGINE_FUSED,
               "two_pass": cp.ENGINE_TWO_PASS}[args.engine]
-    cfg = cp.make_config(N, NPa, hio_iters=hio, er_iters=IT - hio, seed=rank, engine=engine)
+    prec = {"fp32": cp.FP32, "bf16": cp.BF16_TC, "fp16": cp.FP16_TC}[args.precision]
+    cfg = cp.make_config(N, NPa, hio_iters=hio, er_iters=IT - hio, seed=rank, engine=engine,
+                         precision=prec)
     plan = cp.Plan(cfg, stream=stream.cuda_stream)
     vol = torch.empty((N, N, N, 2), dtype=torch.float32, device=f"cuda:{local}")
 
@@ -848,7 +865,8 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 1), "unit": "angle-iterations/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision], "data": "synthetic",
             "config": {"workload": f"CPRA N={N} Np={NP}: {T_HIO} HIO + {T_ER} ER iterations, "
                                    "coupling alpha=(0.2,0.6,0.2) every 10, 512^3 assembly",
                        "N": N, "Np": NP, "iterations": ITERS,
@@ -886,6 +904,9 @@ def main():
                     help="skip the e2e and CPU-baseline legs (profiler captures)")
     ap.add_argument("--engine", default="auto", choices=["auto", "warp", "fused", "two_pass"],
                     help="iteration engine of the plain path")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="arithmetic of the DFT stages (the bench number is the FP32 default; "
+                         "bf16/fp16 run them on the tensor cores)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batching / serving / precision measurements")
     args = ap.parse_args()
