@@ -1579,6 +1579,19 @@ JobStep next_window(cpra_plan_s* p, int64_t max_iters) {
   return s;
 }
 
+// one stream and join event per group, and a fork event (created once)
+cpra_status ensure_side_streams(cpra_batch_s* b) {
+  if (!b->side.empty()) return CPRA_OK;
+  b->side.assign(b->groups.size(), nullptr);
+  b->join.assign(b->groups.size(), nullptr);
+  CK_B(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch event");
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    CK_B(cudaStreamCreateWithFlags(&b->side[gi], cudaStreamNonBlocking), "batch stream");
+    CK_B(cudaEventCreateWithFlags(&b->join[gi], cudaEventDisableTiming), "batch event");
+  }
+  return CPRA_OK;
+}
+
 // windows the fused engine needs for n iterations from iteration t
 int64_t fused_windows(int64_t t, int64_t n, int n_ei) {
   int64_t w = 0;
@@ -2176,15 +2189,7 @@ cpra_status cpra_batch_set_persistent(cpra_batch_t b, int32_t mode, double wait_
     CK_B(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev), "clock rate");
     const double secs = wait_budget_s > 0.0 ? wait_budget_s : 2.0;
     b->budget = (long long)(secs * (double)khz * 1e3);
-    if (b->side.empty()) {
-      b->side.assign(b->groups.size(), nullptr);
-      b->join.assign(b->groups.size(), nullptr);
-      CK_B(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch event");
-      for (size_t gi = 0; gi < b->groups.size(); ++gi) {
-        CK_B(cudaStreamCreateWithFlags(&b->side[gi], cudaStreamNonBlocking), "batch stream");
-        CK_B(cudaEventCreateWithFlags(&b->join[gi], cudaEventDisableTiming), "batch event");
-      }
-    }
+    if (cpra_status st = ensure_side_streams(b); st != CPRA_OK) return st;
     for (auto& g : b->groups) {
       if (g.sweep) continue;
       if (!g.d_queue) {
