@@ -603,37 +603,46 @@ def form_p0(torch, I_dev, S_box, iters=20, beta=0.9, n_ei=10):
                     f"N={N_}, Np={Np_}, {iters} HIO iterations with coupling every {n_ei}"}
 
 
-def form_precision_large(cp, torch, N_=1024, Np_=720, n_proj=45, iters_acc=20, iters_speed=50,
-                         sample=(0, 361)):
-    """S3 at the sizes of the large configuration (N = 1024, Np = 720).
-    Patterns: the cfg 1 recipe scaled to a 512^3 object (6 ellipsoids; the
-    200-ellipsoid object takes minutes to rasterise on the host) projected at
-    n_proj angles, each pattern serving Np / n_proj consecutive angles.
-    Speed: iters_speed HIO iterations per form.  Accuracy: relative L2 of
-    sampled angles against the FP64 oracle (numpy.fft transforms) after
-    iters_acc ER iterations from one seeded state (no coupling)."""
-    import oracle as O
+def _er_fp64(torch, I_rows, S, x0, iters):
+    """FP64 reference of `iters` ER iterations on a stack of patterns, plain
+    torch on the GPU: modulus projection onto sqrt(I) (phase 1 where G = 0),
+    then the support-positivity projection.  It serves the error figures of
+    the 16-bit forms here; the tests check the library against the oracle."""
+    A = torch.fft.ifftshift(torch.sqrt(torch.clamp(I_rows.double(), min=0.0)), dim=(-2, -1))
+    Sb = torch.as_tensor(S, device=I_rows.device).bool()
+    g = x0.double()
+    for _ in range(iters):
+        G = torch.fft.fft2(g)
+        mag = G.abs()
+        ph = torch.where(mag > 0, G / torch.where(mag > 0, mag, torch.ones_like(mag)), torch.ones_like(G))
+        gp = torch.fft.ifft2(A * ph).real
+        g = torch.where(Sb & (gp >= 0), gp, torch.zeros_like(gp))
+    return g
+
+
+def form_config5(cp, torch, iters_acc=20, iters_speed=50, sample=(0, 361)):
+    """cfg 5 as written: N = 1024, Np = 720 noiseless patterns of a 512^3
+    object of 200 ellipsoids (rasterised and projected on the GPU), run in
+    FP32 and with the BF16 / FP16 tensor-core DFT stages: speed over
+    iters_speed HIO iterations, error of sampled angles against an FP64
+    reference after iters_acc ER iterations from one seeded state (no
+    coupling), and the 1024^3 assembly with its inverse 3D FFT."""
     import synth
+    N_, Np_ = 1024, 720
     t_gen = time.perf_counter()
-    d = synth.make_case("cfg1", device="cuda", N=N_, Np=n_proj, request=5)
-    rep = Np_ // n_proj
-    I_dev = d["I"].repeat_interleave(rep, dim=0).contiguous()
-    thetas = [n * math.pi / Np_ for n in range(Np_)]
+    d = synth.make_case("cfg5", device="cuda", raster_on_device=True)
+    I_dev = d["I"].contiguous()
+    thetas = d["thetas"]
+    del d
+    torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     rng = np.random.default_rng(12)
     S = np.zeros((N_, N_), bool)
     S[N_ // 4:3 * N_ // 4, N_ // 4:3 * N_ // 4] = True
     g0 = (rng.random((Np_, N_, N_), dtype=np.float32) * S).astype(np.float32)
-    I_host = I_dev[list(sample)].cpu().numpy()
-    ref = {}
-    for i, n in enumerate(sample):
-        x = g0[n][None].astype(np.float64)
-        A = O.amplitudes(I_host[i])[None]
-        for _ in range(iters_acc):
-            x, _, _ = O.iterate_2d(x, A, S[None], 0.9, O.ER, fft=True)
-        ref[n] = x[0]
-    out = {"workload": f"N={N_}, Np={Np_} ({n_proj} projected patterns, each for {rep} angles), "
-                       f"6-ellipsoid 512^3 object, noisy 1e6 photons",
+    ref = {n: _er_fp64(torch, I_dev[n:n + 1], S, torch.from_numpy(g0[n:n + 1]).cuda(), iters_acc)[0]
+           for n in sample}
+    out = {"workload": f"N={N_}, Np={Np_}: 200-ellipsoid 512^3 object, noiseless, {Np_} projections",
            "input_seconds": round(t_gen, 1)}
     for name, prec in (("fp32", cp.FP32), ("bf16", cp.BF16_TC), ("fp16", cp.FP16_TC)):
         cfg = cp.make_config(N_, Np_, precision=prec, hio_iters=0, er_iters=iters_acc, n_ei=1 << 20)
@@ -643,7 +652,8 @@ def form_precision_large(cp, torch, N_=1024, Np_=720, n_proj=45, iters_acc=20, i
         plan.load_state(g0, 1)  # t = 1: no coupling step inside the run
         plan.iterate(iters_acc)
         g = plan.result(cp.RESULT_STATE)
-        errs = [float(np.linalg.norm(g[n] - ref[n]) / np.linalg.norm(ref[n])) for n in sample]
+        errs = [float(np.linalg.norm(g[n] - ref[n].cpu().numpy()) / np.linalg.norm(ref[n].cpu().numpy()))
+                for n in sample]
         plan.close()
         plan = cp.Plan(cp.make_config(N_, Np_, precision=prec, hio_iters=iters_speed, er_iters=0))
         plan.load_intensities(I_dev, 0, thetas)
@@ -653,34 +663,35 @@ def form_precision_large(cp, torch, N_=1024, Np_=720, n_proj=45, iters_acc=20, i
         plan.iterate(iters_speed)
         plan.sync()
         dt = time.perf_counter() - t0
+        entry = {"value": round(Np_ * iters_speed / dt, 1), "unit": "angle-iterations/s",
+                 "rel_l2_vs_fp64_after_%d_er" % iters_acc: [float("%.3e" % e) for e in errs]}
+        if prec == cp.FP32:
+            plan.assemble_3d()  # first use: buffers and gridding lists
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.assemble_3d()
+            plan.sync()
+            entry["assembly_1024cubed_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
         plan.close()
-        out[name] = {"value": round(Np_ * iters_speed / dt, 1), "unit": "angle-iterations/s",
-                     "rel_l2_vs_fp64_after_%d_er" % iters_acc: [float("%.3e" % e) for e in errs]}
+        out[name] = entry
     return out
 
 
 def form_precision(cp, torch, I_dev, thetas, S_box, n_angles=NP, N_=N, sample=(0, 1), iters=5):
     """Throughput of the FP32 / BF16 / FP16 forms on the bench workload and
-    their iterate error against the FP64 oracle after `iters` ER iterations
-    from a seeded state, on sampled angles (neighbours coupled at t = 0)."""
-    import oracle as O
+    their iterate error against an FP64 reference (_er_fp64) after `iters`
+    ER iterations from a seeded state, on sampled angles (neighbours coupled
+    at t = 0)."""
     rng = np.random.default_rng(11)
     S = np.zeros((N_, N_), bool)
     S[N_ // 4:3 * N_ // 4, N_ // 4:3 * N_ // 4] = True
     g0 = (rng.random((n_angles, N_, N_), dtype=np.float32) * S).astype(np.float32)
     out = {}
     ref = {}
-    I_host = None
     for n in sample:
-        if I_host is None:
-            I_host = I_dev.cpu().numpy()
         idx = [(n - 1) % n_angles, n, (n + 1) % n_angles]
         x = 0.2 * g0[idx[0]].astype(np.float64) + 0.6 * g0[idx[1]] + 0.2 * g0[idx[2]]
-        A = O.amplitudes(I_host[n])[None]
-        x = x[None]
-        for _ in range(iters):
-            x, _, _ = O.iterate_2d(x, A, S[None], 0.9, O.ER)
-        ref[n] = x[0]
+        ref[n] = _er_fp64(torch, I_dev[n:n + 1], S, torch.from_numpy(x[None]).cuda(), iters)[0].cpu().numpy()
     for name, prec in (("fp32", cp.FP32), ("bf16", cp.BF16_TC), ("fp16", cp.FP16_TC)):
         plan = cp.Plan(cp.make_config(N_, n_angles, precision=prec, hio_iters=0, er_iters=iters))
         plan.load_intensities(I_dev, 0, thetas)
@@ -849,7 +860,7 @@ def run_gpu(args):
         forms = {"refine_3d": form_refine(cp, torch, plan),
                  "p0_cufft_pointwise": form_p0(torch, I_dev, S_box),
                  "precision": form_precision(cp, torch, I_dev, thetas, S_box),
-                 "precision_large": form_precision_large(cp, torch),
+                 "config5": form_config5(cp, torch),
                  "batching": form_batch(cp, torch),
                  "multi_guess_merge": form_multi_guess(cp, torch),
                  "config2": form_config2(cp, torch),

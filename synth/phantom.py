@@ -44,12 +44,18 @@ def _rotation(rng: np.random.Generator) -> np.ndarray:
 
 
 def ellipsoid_phantom(n_obj: int, n_ell: int, seed: int,
-                      texture_sigma: float | None = None) -> np.ndarray:
-    """n_obj^3 float64 density [z][y][x]; coordinates relative to index n_obj/2."""
+                      texture_sigma: float | None = None, device=None):
+    """n_obj^3 float64 density [z][y][x]; coordinates relative to index n_obj/2.
+
+    With a CUDA ``device`` the inside tests run there with torch (the same
+    seeded draws; for large objects the host loop takes minutes) and the
+    result is a float32 torch tensor on that device."""
     rng = np.random.Generator(np.random.PCG64(seed))
     R = n_obj / 2 - 2
-    vol = np.zeros((n_obj, n_obj, n_obj))
     h = n_obj // 2
+    if device is not None and str(device) != "cpu":
+        return _ellipsoids_torch(n_obj, n_ell, rng, R, h, device)
+    vol = np.zeros((n_obj, n_obj, n_obj))
     for _ in range(n_ell):
         a = rng.uniform(n_obj / 16, n_obj / 4, size=3)
         rot = _rotation(rng)
@@ -78,6 +84,31 @@ def ellipsoid_phantom(n_obj: int, n_ell: int, seed: int,
             noise = _conv1d_circ(noise, k, ax)
         noise /= noise.std()
         vol = np.where(vol > 0, np.clip(vol * (1 + 0.2 * noise), 0, None), 0.0)
+    return vol
+
+
+def _ellipsoids_torch(n_obj, n_ell, rng, R, h, device):
+    vol = torch.zeros((n_obj, n_obj, n_obj), dtype=torch.float32, device=device)
+    for _ in range(n_ell):
+        a = rng.uniform(n_obj / 16, n_obj / 4, size=3)
+        rot = _rotation(rng)
+        amax = min(a.max(), R * 0.95)
+        rc = (R - amax) * math.sqrt(rng.uniform())
+        phi = rng.uniform(0, 2 * math.pi)
+        cz = rng.uniform(-(R - amax), R - amax)
+        centre = np.array([rc * math.cos(phi), rc * math.sin(phi), cz])
+        dens = rng.uniform(0.5, 1.0)
+        lo = np.maximum(np.floor(centre - a.max()).astype(int) + h, 0)
+        hi = np.minimum(np.ceil(centre + a.max()).astype(int) + h + 1, n_obj)
+        xs = torch.arange(int(lo[0]), int(hi[0]), device=device, dtype=torch.float64) - h
+        ys = torch.arange(int(lo[1]), int(hi[1]), device=device, dtype=torch.float64) - h
+        zs = torch.arange(int(lo[2]), int(hi[2]), device=device, dtype=torch.float64) - h
+        Z, Y, X = torch.meshgrid(zs, ys, xs, indexing="ij")
+        P = torch.stack([X, Y, Z], dim=-1) - torch.as_tensor(centre, device=device)
+        local = P @ torch.as_tensor(rot, device=device)
+        inside = ((local / torch.as_tensor(a, device=device)) ** 2).sum(-1) <= 1.0
+        sub = vol[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        sub[inside] = dens
     return vol
 
 
@@ -206,10 +237,12 @@ CASES = {
 
 
 def make_case(name: str, request: int = 0, device: str = "cpu", *,
-              N: int | None = None, Np: int | None = None) -> dict:
+              N: int | None = None, Np: int | None = None, raster_on_device: bool = False) -> dict:
     """Build intensities, angles and the padded-box support for a named case.
 
     ``N``/``Np`` override the case's sizes (objects scale to N/2 per side).
+    ``raster_on_device`` rasterises an untextured object on the CUDA
+    ``device`` too (the large configuration's 200-ellipsoid 512^3 object).
     On a CUDA ``device`` the projections and noise are made on the GPU with
     torch (fast for the large cases); the result is a torch float32 tensor
     on that device, otherwise numpy float32.
@@ -219,8 +252,14 @@ def make_case(name: str, request: int = 0, device: str = "cpu", *,
     Np = Np or c.Np
     n_obj = N // 2
     seed = c.index * 1000 + request
-    obj = ellipsoid_phantom(n_obj, c.n_ell, seed, c.texture_sigma)
-    vol = pad_volume(obj, N)
+    if raster_on_device and c.texture_sigma is None:
+        obj = ellipsoid_phantom(n_obj, c.n_ell, seed, None, device=device)
+        vol = torch.zeros((N, N, N), dtype=obj.dtype, device=obj.device)
+        o = N // 2 - n_obj // 2
+        vol[o:o + n_obj, o:o + n_obj, o:o + n_obj] = obj
+    else:
+        obj = ellipsoid_phantom(n_obj, c.n_ell, seed, c.texture_sigma)
+        vol = pad_volume(obj, N)
     th = angles(Np)
     dt = torch.float64 if str(device) == "cpu" else torch.float32
     P = project(vol, th, r_max=n_obj / 2, device=device, dtype=dt)
