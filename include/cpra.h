@@ -453,8 +453,8 @@ int64_t cpra_batch_launches(cpra_batch_t batch, int32_t n_iters);
  * out sets TIMEOUT in the members' status words (reported by their next
  * calls, see cpra_sync) and ends its CTA.  Mode 2 exists to test that path:
  * the first task of every launch waits on a count that no task increments.
- * The paper has no batching; the benchmark spec's batching form.  Waits for the
- * batch's stream. */
+ * The paper has no batching: this serves several reconstructions at once
+ * for throughput.  Waits for the batch's stream. */
 cpra_status cpra_batch_set_persistent(cpra_batch_t batch, int32_t mode, double wait_budget_s);
 
 cpra_status cpra_batch_destroy(cpra_batch_t batch);
