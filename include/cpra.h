@@ -440,10 +440,16 @@ int64_t cpra_batch_launches(cpra_batch_t batch, int32_t n_iters);
  * couples (Eq. 4 at its episode starts); for every such segment the size
  * groups' coupling launches run first, then ONE persistent launch per size
  * group runs all of the segment's column and row passes of every (member,
- * angle) tile: its CTAs take tasks from a device queue ordered (iteration,
- * pass, tile, block) and wait on per-tile completion counts instead of
- * launch boundaries, so an angle's row pass starts as soon as its own
- * column pass is done.  The groups' launches are forked onto a stream each
+ * angle) tile: its CTAs take tasks from a device queue and wait on
+ * per-tile completion counts instead of launch boundaries, so an angle's
+ * row pass starts as soon as its own column pass is done.  The queue runs
+ * the tiles in chunks of chunk_tiles: a chunk takes every iteration of the
+ * segment (column tasks of its tiles, then their row tasks, block by block)
+ * before the next chunk starts, so a chunk's iterates, spectra and
+ * amplitudes stay in L2 between passes.  chunk_tiles = 0 takes as many
+ * tiles as half the device's L2 holds (about 10 N^2 bytes a tile); a value
+ * of at least the group's tile count gives the plain (iteration, pass,
+ * tile, block) order.  The groups' launches are forked onto a stream each
  * (in the CUDA graph when the batch uses one), so one size group's tail
  * overlaps the next group's start.  Every tile computes what the warp
  * engine computes for it alone (states bit for bit; FP64 error sums to
@@ -455,7 +461,8 @@ int64_t cpra_batch_launches(cpra_batch_t batch, int32_t n_iters);
  * the first task of every launch waits on a count that no task increments.
  * The paper has no batching: this serves several reconstructions at once
  * for throughput.  Waits for the batch's stream. */
-cpra_status cpra_batch_set_persistent(cpra_batch_t batch, int32_t mode, double wait_budget_s);
+cpra_status cpra_batch_set_persistent(cpra_batch_t batch, int32_t mode, double wait_budget_s,
+                                      int32_t chunk_tiles);
 
 cpra_status cpra_batch_destroy(cpra_batch_t batch);
 

@@ -111,7 +111,7 @@ def lib() -> C.CDLL:
             "cpra_batch_create": (C.c_int, [C.POINTER(P), C.c_int32, C.c_int32, C.POINTER(P)]),
             "cpra_batch_iterate": (C.c_int, [P, C.c_int32]),
             "cpra_batch_launches": (C.c_int64, [P, C.c_int32]),
-            "cpra_batch_set_persistent": (C.c_int, [P, C.c_int32, C.c_double]),
+            "cpra_batch_set_persistent": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32]),
             "cpra_batch_destroy": (C.c_int, [P]),
             "cpra_autotune": (C.c_int, [C.c_int32, C.c_int32, C.c_char_p, C.POINTER(C.c_int32),
                                         C.POINTER(C.c_double)]),
@@ -514,8 +514,9 @@ class Batch:
     def launches(self, n: int) -> int:
         return cpra_batch_launches(self.h, n)
 
-    def set_persistent(self, mode: int = 1, wait_budget_s: float = 0.0):
-        _check(lib().cpra_batch_set_persistent(self.h, int(mode), float(wait_budget_s)))
+    def set_persistent(self, mode: int = 1, wait_budget_s: float = 0.0, chunk_tiles: int = 0):
+        _check(lib().cpra_batch_set_persistent(self.h, int(mode), float(wait_budget_s),
+                                               int(chunk_tiles)))
 
     def close(self):
         if self.h:

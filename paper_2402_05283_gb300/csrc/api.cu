@@ -1479,6 +1479,8 @@ struct cpra_batch_s {
   int persistent = 0;              // 0 off, 1 on, 2 testing: every device wait runs out
   long long budget = 0;            // clock64 cycles a device wait may take
   int sms = 0;
+  int chunk_tiles = 0;             // tiles a queue chunk (0: from the L2 size)
+  long long l2_bytes = 0;
   std::vector<cudaStream_t> side;  // one per group: the groups' kernels overlap
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
@@ -1497,6 +1499,21 @@ cpra_status bfail(cpra_batch_s* b, cpra_status st, const std::string& msg) {
     cudaError_t _e = (expr);                                                            \
     if (_e != cudaSuccess) return bfail(b, CPRA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(_e)); \
   } while (0)
+
+// Tiles a chunk of the persistent queue: the caller's choice, else as many
+// tiles as half the L2 holds.  A tile's working set over one iteration is
+// its iterate (4 N^2 bytes), packed spectrum (4 N^2), amplitude (2 N^2) and
+// support bits (N^2 / 8).
+int persist_chunk(const cpra_batch_s* b, int N, int ntiles) {
+  long long k = b->chunk_tiles;
+  if (k <= 0) {
+    const long long tile = 10LL * N * N + (long long)N * N / 8;
+    k = b->l2_bytes > 0 ? (b->l2_bytes / 2) / tile : ntiles;
+  }
+  if (k < 1) k = 1;
+  if (k > ntiles) k = ntiles;
+  return (int)(k > 0 ? k : 1);
+}
 
 // (member, angle) tiles of a group: every iterating angle of every member
 cudaError_t group_tiles(cpra_batch_s* b, cpra_batch_s::Group& g) {
@@ -2017,6 +2034,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
         pa.m = (int)g.members.size();
         pa.row0 = a;
         pa.iters = e - a;
+        pa.chunk = persist_chunk(b, g.N, g.ntiles);
         pa.ticket = g.d_queue;
         pa.done = g.d_queue + 2;
         pa.budget = b->budget;
@@ -2168,9 +2186,11 @@ int64_t cpra_batch_launches(cpra_batch_t b, int32_t n_iters) {
   return k;
 }
 
-cpra_status cpra_batch_set_persistent(cpra_batch_t b, int32_t mode, double wait_budget_s) {
+cpra_status cpra_batch_set_persistent(cpra_batch_t b, int32_t mode, double wait_budget_s,
+                                      int32_t chunk_tiles) {
   if (!b) return bfail(nullptr, CPRA_ERR_INVALID_ARG, "batch is NULL");
   if (mode < 0 || mode > 2) return bfail(b, CPRA_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+  if (chunk_tiles < 0) return bfail(b, CPRA_ERR_INVALID_ARG, "chunk_tiles must be >= 0");
   if (!(wait_budget_s >= 0.0) || !(wait_budget_s <= 600.0))
     return bfail(b, CPRA_ERR_INVALID_ARG, "wait budget must be in [0, 600] seconds");
   if (mode != 0)
@@ -2187,6 +2207,9 @@ cpra_status cpra_batch_set_persistent(cpra_batch_t b, int32_t mode, double wait_
     CK_B(cudaGetDevice(&dev), "device");
     CK_B(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     CK_B(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev), "clock rate");
+    int l2 = 0;
+    CK_B(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev), "L2 size");
+    b->l2_bytes = l2;
     const double secs = wait_budget_s > 0.0 ? wait_budget_s : 2.0;
     b->budget = (long long)(secs * (double)khz * 1e3);
     if (cpra_status st = ensure_side_streams(b); st != CPRA_OK) return st;
@@ -2202,6 +2225,7 @@ cpra_status cpra_batch_set_persistent(cpra_batch_t b, int32_t mode, double wait_
     }
   }
   b->persistent = mode;
+  b->chunk_tiles = chunk_tiles;
   if (b->exec) {  // the next call captures the new launch pattern
     cudaGraphExecDestroy(b->exec);
     cudaGraphDestroy(b->graph);

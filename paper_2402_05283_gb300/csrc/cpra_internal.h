@@ -248,6 +248,7 @@ struct PersistArgs {
   const JobStep* st;  // step rows of the call: iteration i of this launch at st + (row0 + i) * m
   const int2* tiles;  // (member, angle) tiles
   int ntiles, m, row0, iters;
+  int chunk;          // tiles a chunk: the queue runs chunk by chunk, all iterations each
   unsigned* ticket;   // [2]: next task; [1] is a count that no task increments
   unsigned* done;     // [2 * ntiles]: column and row blocks done in this launch
   long long budget;   // clock64 cycles a wait may take

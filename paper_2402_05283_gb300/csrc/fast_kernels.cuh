@@ -694,9 +694,16 @@ k_persist_w(const PersistArgs a) {
   using P = PersistCfg<N>;
   __shared__ unsigned task_s;
   __shared__ int ok_s;
-  const unsigned ncol = (unsigned)a.ntiles * P::CB;
-  const unsigned per_iter = ncol + (unsigned)a.ntiles * P::RB;
-  const unsigned total = per_iter * (unsigned)a.iters;
+  // queue order: the tiles in chunks of a.chunk; a chunk runs all of the
+  // launch's iterations (each: the column tasks of its tiles, then their row
+  // tasks) before the next chunk starts, so that a chunk's iterates, spectra
+  // and amplitudes stay in L2 from one pass to the next.  A chunk of every
+  // tile is the plain (iteration, pass, tile, block) order.
+  constexpr unsigned PT = P::CB + P::RB;  // tasks of one tile and iteration
+  const unsigned K = (unsigned)a.chunk, iters = (unsigned)a.iters;
+  const unsigned full = (unsigned)a.ntiles / K;  // chunks of K tiles; the last holds the rest
+  const unsigned full_tasks = full * K * PT * iters;
+  const unsigned total = (unsigned)a.ntiles * PT * iters;
   // thread 0 holds the CTA's next ticket, fetched while the current task
   // runs (a held ticket runs as soon as the current task ends, so the queue
   // still drains: the smallest unfinished task is always running)
@@ -708,11 +715,15 @@ k_persist_w(const PersistArgs a) {
     __syncthreads();
     const unsigned task = task_s;
     if (task >= total) return;
-    const int it = (int)(task / per_iter);
-    const unsigned r = task % per_iter;
-    const bool col = r < ncol;
-    const unsigned rr = col ? r : r - ncol;
-    const int tile = (int)(col ? rr / P::CB : rr / P::RB);
+    const bool in_full = task < full_tasks;
+    const unsigned c = in_full ? task / (K * PT * iters) : full;  // chunk
+    const unsigned kc = in_full ? K : (unsigned)a.ntiles - full * K;  // its tiles
+    const unsigned r0 = in_full ? task % (K * PT * iters) : task - full_tasks;
+    const int it = (int)(r0 / (kc * PT));
+    const unsigned r = r0 % (kc * PT);
+    const bool col = r < kc * P::CB;
+    const unsigned rr = col ? r : r - kc * P::CB;
+    const int tile = (int)(c * K + (col ? rr / P::CB : rr / P::RB));
     const int bx = (int)(col ? rr % P::CB : rr % P::RB);
     if (threadIdx.x == 0) {
       const unsigned* c = col ? a.done + 2 * tile + 1 : a.done + 2 * tile;

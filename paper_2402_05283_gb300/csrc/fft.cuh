@@ -19,13 +19,17 @@ namespace cpra {
 
 struct __align__(8) cf { float x, y; };
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// packed FP32 pairs (one issue slot for both components); every component
+// is rounded once, as the scalar forms are: b * (-1) + a rounds a - b
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 // multiply by -i (DIR = -1) or +i (DIR = +1)
 template <int DIR>
 __device__ __forceinline__ float2 mul_i(float2 a) {
@@ -95,7 +99,11 @@ template <int DIR> struct Dft<2, DIR> {
 template <int DIR> struct Dft<4, DIR> {
   static __device__ __forceinline__ void run(float2* v) {
     float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    float2 s13 = cadd(v[1], v[3]), d13 = mul_i<DIR>(csub(v[1], v[3]));
+    // DIR i (v1 - v3) straight from scalar differences: a swapped pair
+    // would cost moves before the packed adds
+    const float2 d13 = DIR < 0 ? make_float2(v[1].y - v[3].y, v[3].x - v[1].x)
+                               : make_float2(v[3].y - v[1].y, v[1].x - v[3].x);
+    float2 s13 = cadd(v[1], v[3]);
     v[0] = cadd(s02, s13);
     v[2] = csub(s02, s13);
     v[1] = cadd(d02, d13);

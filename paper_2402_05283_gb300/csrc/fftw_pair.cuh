@@ -89,7 +89,7 @@ struct PairLines512 {
       const float2 mine = v[j];
       const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, 1),
                                    __shfl_xor_sync(0xffffffffu, mine.y, 1));
-      v[j] = make_float2(fmaf(sg, mine.x, p.x), fmaf(sg, mine.y, p.y));
+      v[j] = __ffma2_rn(make_float2(sg, sg), mine, p);
     });
     if constexpr (DIR > 0) twiddle_odd<DIR>(v, h);
   }

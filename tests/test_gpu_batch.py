@@ -107,18 +107,20 @@ def _warp_plans(cp, mix):
     return _plans(cp, [(N, Np, seed, {**kw, "engine": cp.ENGINE_WARP}) for N, Np, seed, kw in mix])
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_persistent_batch_uneven_n_equals_alone(cp, use_graph):
+@pytest.mark.parametrize("use_graph,chunk", [(False, 0), (True, 0), (True, 2), (False, 5)])
+def test_persistent_batch_uneven_n_equals_alone(cp, use_graph, chunk):
     """One persistent work-queue launch per size group and segment (split at
     the coupling steps), the groups forked onto their own streams: every
     member's iterates equal the plan run alone bit for bit, over calls that
-    cross episode boundaries and the HIO -> ER switch."""
+    cross episode boundaries and the HIO -> ER switch.  chunk_tiles 2 and 5
+    run the queue in chunks (with a shorter last chunk where the tile count
+    is not a multiple); 0 takes the chunk from the L2 size (here every tile)."""
     alone = _warp_plans(cp, UNEVEN)
     for p in alone:
         p.iterate(23)
     mixed = _warp_plans(cp, UNEVEN)
     b = cp.Batch(mixed, use_graph=use_graph)
-    b.set_persistent(1)
+    b.set_persistent(1, chunk_tiles=chunk)
     b.iterate(11)  # the first call also runs each member's seeded start
     expect = b.launches(12)
     n0 = cp.cpra_launch_count()
@@ -167,5 +169,8 @@ def test_persistent_needs_the_warp_engine(cp):
     assert e.value.status == cp.ERR_UNSUPPORTED
     with pytest.raises(cp.CpraError) as e:
         b.set_persistent(3)
+    assert e.value.status == cp.ERR_INVALID_ARG
+    with pytest.raises(cp.CpraError) as e:
+        b.set_persistent(0, chunk_tiles=-1)
     assert e.value.status == cp.ERR_INVALID_ARG
     b.close()
