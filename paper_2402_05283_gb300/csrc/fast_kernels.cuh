@@ -448,11 +448,29 @@ template <int N, int PREC> struct ColW {
   static constexpr int NT = WARPS * 32;
   static constexpr int MINB = kSlimLines<FL> ? 3 : (NT <= 256 ? 2 : 1);
   static constexpr int SP = CB + 1;  // staging pitch
+  static constexpr int N2 = N / 2;
   static constexpr int STAGE = N * SP;
   static constexpr int TILES = WARPS * FL::TSIZE;
   static constexpr int BUF = STAGE > TILES ? STAGE : TILES;
-  static constexpr size_t SMEM = sizeof(float2) * (N + BUF) + sizeof(float) * CB * N;
+  // A_sym of the block in shared memory, column c at c * AP, frequency ky at
+  // a_pos(ky): the upper half moved on by 16 floats, so lanes reading ky and
+  // ky + N/2 (the one-line plan's lane pairs) or the same ky of neighbouring
+  // columns (the L-line plans) fall in different banks
+  static constexpr int AP = N + 16;
+  static __device__ __forceinline__ int a_pos(int ky) { return ky + (ky >= N / 2 ? 16 : 0); }
+  static constexpr size_t SMEM = sizeof(float2) * (N + BUF) + sizeof(float) * CB * AP;
 };
+// a_pos of the B-layout frequency b_k(t, j) of a column-pass task: the half
+// is fixed by t in the one-line plan and by j in the L-line plans, so the
+// offset over j stays a compile-time constant
+template <class C, int j>
+__device__ __forceinline__ int col_a_pos(int t) {
+  using FL = typename C::FL;
+  if constexpr (std::is_same_v<FL, PairLines512>)
+    return FL::b_k(t, 0) + ((t & 1) ? 16 : 0) + 16 * j;
+  else
+    return FL::b_k(t, 0) + FL::E1 * j + (FL::E1 * j >= C::N2 ? 16 : 0);
+}
 template <int N, int PREC>
 constexpr size_t col_smem() {
   return ColW<N, PREC>::SMEM + TcSmem<N, PREC>::template bytes<ColW<N, PREC>::WARPS>();
@@ -506,17 +524,20 @@ __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* As = reinterpret_cast<float*>(buf + C::BUF);  // A_sym of the block, [c][ky]
   uint32_t tc_phase = 0;
-  const TcCtx tc = tc_setup<N, PREC, C::WARPS>(reinterpret_cast<char*>(As + C::CB * N), J->tcw, J->status,
+  const TcCtx tc = tc_setup<N, PREC, C::WARPS>(reinterpret_cast<char*>(As + C::CB * C::AP), J->tcw, J->status,
                                                &tc_phase);
   float2* T = buf + warp * FL::TSIZE;
   const int n = tl.y;
   const int c0 = bx * C::CB;
   float2* Hn = Hp + (size_t)n * N * H;
   // thread (row y0 + k RS, column cc) of the block: constant strides, so
-  // the unrolled copies differ only in immediate offsets
+  // the unrolled copies differ only in immediate offsets.  A warp's 32 / CB
+  // rows are WARPS apart: with 8 columns (pitch 9) rows 8 apart start 16
+  // banks apart, so a warp's 256 bytes take the minimum two wavefronts
   constexpr int RS = C::NT / C::CB;
-  static_assert(C::NT % C::CB == 0 && N % RS == 0 && (C::CB * N / 4) % C::NT == 0, "column staging");
-  const int y0 = threadIdx.x / C::CB, cc = threadIdx.x % C::CB;
+  static_assert(C::NT % C::CB == 0 && 32 % C::CB == 0 && N % RS == 0 && (C::CB * N / 4) % C::NT == 0,
+                "column staging");
+  const int y0 = warp + C::WARPS * (lane / C::CB), cc = lane % C::CB;
   {
     const float2* src = Hn + (size_t)y0 * H + c0 + cc;
     float2* dst = buf + y0 * C::SP + cc;
@@ -527,9 +548,12 @@ __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
 #pragma unroll
       for (int k = 0; k < N / RS; ++k) cp_async8(dst + k * RS * C::SP, src + (size_t)k * RS * H);
     }
-    const float* Ablk = A_T + ((size_t)n * H + c0) * N + 4 * threadIdx.x;  // CB contiguous columns
+    const float* Ablk = A_T + ((size_t)n * H + c0) * N;  // CB contiguous columns
 #pragma unroll
-    for (int k = 0; k < C::CB * N / 4 / C::NT; ++k) cp_async16(As + 4 * (threadIdx.x + k * C::NT), Ablk + 4 * k * C::NT);
+    for (int k = 0; k < C::CB * N / 4 / C::NT; ++k) {
+      const int f = 4 * (threadIdx.x + k * C::NT);  // 4 floats, never across a half (4 | N/2)
+      cp_async16(As + (f / N) * C::AP + C::a_pos(f % N), Ablk + f);
+    }
   }
   cp_async_commit();
   load_xtw<N>(xs, xtw, C::NT);
@@ -555,10 +579,10 @@ __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
     const int t = lane + 32 * i;
     const int col = warp * FL::L + FL::b_line(t);
     if (c0 + col != 0) {
-      const float* Ac = As + col * N;
+      const float* Ac = As + col * C::AP;
       static_for<0, FL::E2>([&](auto KK) {
         constexpr int j = decltype(KK)::value;
-        b[i][j] = project_w<MASKED>(b[i][j], Ac[FL::b_k(t, j)], err2);
+        b[i][j] = project_w<MASKED>(b[i][j], Ac[col_a_pos<C, j>(t)], err2);
       });
     }
   });
@@ -587,7 +611,7 @@ __device__ __forceinline__ void colpass_tile(const JobStatic* __restrict__ js,
           const float2 z = T[ky], zm = T[(N - ky) % N];
           const float2 g0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
           const float2 gn = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
-          const float2 p0 = project_w<MASKED>(g0, A0[ky], err1);
+          const float2 p0 = project_w<MASKED>(g0, A0[col_a_pos<C, j>(t)], err1);
           const float2 pn = project_w<MASKED>(gn, __ldg(An + ky), err1);
           b[i][j] = make_float2(p0.x - pn.y, p0.y + pn.x);
         });
