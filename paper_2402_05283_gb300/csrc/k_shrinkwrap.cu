@@ -13,40 +13,72 @@
 
 namespace cpra {
 
-// image rows a block of the blur kernels
+// image rows a block of the row blur; output rows a thread of the column blur
 constexpr int kSwRows = 4;
+constexpr int kSwColRows = 8;
+// outputs a thread of the row blur (consecutive x)
+constexpr int kSwRowX = 4;
 
 // Row blur: out[x] = sum_t taps[t] rho[(x - lo - t) mod N], reading the row
 // staged once with a halo, h[k] = rho[(k - lo - ntaps + 1) mod N] (the same
-// terms in the same order as the definition).  Rows y0 .. y0 + kSwRows - 1
-// of angle n a block, one after the other.
+// terms in the same order as the definition).  The block stages rows
+// y0 .. y0 + kSwRows - 1 of angle n; a thread then sums kSwRowX consecutive
+// outputs of one row, tap by tap, keeping the kSwRowX staged values the
+// current tap needs in registers: each tap costs one shared load for all of
+// them.  Every output still adds its terms in the order t = 0, 1, ...
 __global__ void k_sw_rows(const float* __restrict__ g, const uint32_t* __restrict__ S, float* tmp,
                           const float* __restrict__ taps, int ntaps, int lo, int N, int W) {
   extern __shared__ float sm[];
-  float* tp = sm;          // [ntaps]
-  float* h = sm + ntaps;   // [N + ntaps - 1]
+  float* tp = sm;                      // [ntaps]
+  const int HP = N + ntaps + kSwRowX;  // a staged row: one zero in front, the halo, a zero tail
+  float* hs = sm + ntaps;              // [kSwRows][HP]
   const int n = blockIdx.y;
+  const int y0 = blockIdx.x * kSwRows;
+  const int rows = min(kSwRows, N - y0);
   const int hb = -lo - ntaps + 1;
   for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
-  for (int yy = 0; yy < kSwRows; ++yy) {
-    const int y = blockIdx.x * kSwRows + yy;
-    if (y >= N) break;  // uniform over the block
-    const size_t base = ((size_t)n * N + y) * N;
-    const size_t srow = ((size_t)n * N + y) * W;
-    __syncthreads();  // the previous row is done with h
-    for (int k = threadIdx.x; k < N + ntaps - 1; k += blockDim.x) {
+  for (int i = threadIdx.x; i < rows * HP; i += blockDim.x) {
+    const int yy = i / HP, k = i - yy * HP - 1;  // k = -1 .. N + ntaps + kSwRowX - 2
+    float v = 0.0f;
+    if (k >= 0 && k < N + ntaps - 1) {
+      const int y = y0 + yy;
       const int x = ((k + hb) % N + N) % N;
-      const float v = g[base + x];
-      h[k] = (sbit(S, srow, x) && v >= 0.0f) ? v : 0.0f;
+      const float gv = g[((size_t)n * N + y) * N + x];
+      v = (sbit(S, ((size_t)n * N + y) * W, x) && gv >= 0.0f) ? gv : 0.0f;
     }
-    __syncthreads();
-    for (int x = threadIdx.x; x < N; x += blockDim.x) {
-      float acc = 0.0f;
-      const float* hx = h + x + ntaps - 1;
-      for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], hx[-t], acc);
-      tmp[base + x] = acc;
-    }
+    hs[i] = v;
   }
+  __syncthreads();
+  const int XG = (N + kSwRowX - 1) / kSwRowX;  // output groups a row
+  for (int i = threadIdx.x; i < rows * XG; i += blockDim.x) {
+    const int yy = i / XG, x0 = (i - yy * XG) * kSwRowX;
+    // output x0 + q at tap t reads h[x0 + q + ntaps - 1 - t] = hx[q - t]
+    const float* hx = hs + yy * HP + 1 + x0 + ntaps - 1;
+    float w[kSwRowX], acc[kSwRowX];
+#pragma unroll
+    for (int q = 0; q < kSwRowX; ++q) {
+      w[q] = hx[q];
+      acc[q] = 0.0f;
+    }
+#pragma unroll 4
+    for (int t = 0; t < ntaps; ++t) {
+      const float c = tp[t];
+#pragma unroll
+      for (int q = 0; q < kSwRowX; ++q) acc[q] = fmaf(c, w[q], acc[q]);
+#pragma unroll
+      for (int q = kSwRowX - 1; q > 0; --q) w[q] = w[q - 1];
+      w[0] = hx[-t - 1];  // the zero in front for x0 = 0 at the last tap
+    }
+    float* out = tmp + ((size_t)n * N + y0 + yy) * N;
+#pragma unroll
+    for (int q = 0; q < kSwRowX; ++q)
+      if (x0 + q < N) out[x0 + q] = acc[q];
+  }
+}
+
+// dynamic shared memory of k_sw_rows: the taps and kSwRows staged rows
+size_t sw_rows_smem(int N, int ntaps) {
+  return sizeof(float) * ((size_t)ntaps + (size_t)kSwRows * (N + ntaps + kSwRowX));
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -54,30 +86,48 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Column blur of output rows y0 .. y0 + kSwRows - 1 of angle n (the terms
-// of each pixel in the order of the definition), and the rows' maximum.
+// Column blur b[y][x] = sum_t taps[t] tmp[(y - lo - t) mod N][x] (terms in
+// the order of the definition) and the maximum over the block's outputs.  A
+// thread sums output rows y0 .. y0 + kSwColRows - 1 of its columns, tap by
+// tap, holding the kSwColRows input rows the current tap needs in
+// registers: one load a tap for all of them.
 __global__ void k_sw_cols(const float* __restrict__ tmp, float* b, unsigned* mx,
                           const float* __restrict__ taps, int ntaps, int lo, int N) {
   extern __shared__ float sm[];
   __shared__ float red[32];
-  float* tp = sm;                                   // [ntaps]
-  int* rows = reinterpret_cast<int*>(sm + ntaps);   // [ntaps]: (y - lo - t) mod N
+  float* tp = sm;  // [ntaps]
   const int n = blockIdx.y;
+  const int y0 = blockIdx.x * kSwColRows;
   const float* tn = tmp + (size_t)n * N * N;
   for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
+  __syncthreads();
   float m = 0.0f;
-  for (int yy = 0; yy < kSwRows; ++yy) {
-    const int y = blockIdx.x * kSwRows + yy;
-    if (y >= N) break;  // uniform over the block
-    __syncthreads();  // the previous row is done with rows[]
-    for (int t = threadIdx.x; t < ntaps; t += blockDim.x) rows[t] = ((y - (lo + t)) % N + N) % N;
-    __syncthreads();
-    for (int x = threadIdx.x; x < N; x += blockDim.x) {
-      float acc = 0.0f;
-      for (int t = 0; t < ntaps; ++t) acc = fmaf(tp[t], tn[(size_t)rows[t] * N + x], acc);
-      b[((size_t)n * N + y) * N + x] = acc;
-      m = fmaxf(m, acc);
+  const int r0 = ((y0 - lo) % N + N) % N;  // input row of output y0 at tap 0
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    float w[kSwColRows], acc[kSwColRows];
+    int r = r0;  // input row of output y0 at the current tap
+#pragma unroll
+    for (int q = 0; q < kSwColRows; ++q) {
+      const int rq = r + q < N ? r + q : r + q - N;  // q < kSwColRows <= N
+      w[q] = tn[(size_t)(rq % N) * N + x];
+      acc[q] = 0.0f;
     }
+#pragma unroll 4
+    for (int t = 0; t < ntaps; ++t) {
+      const float c = tp[t];
+#pragma unroll
+      for (int q = 0; q < kSwColRows; ++q) acc[q] = fmaf(c, w[q], acc[q]);
+#pragma unroll
+      for (int q = kSwColRows - 1; q > 0; --q) w[q] = w[q - 1];
+      r = r == 0 ? N - 1 : r - 1;
+      if (t + 1 < ntaps) w[0] = tn[(size_t)r * N + x];
+    }
+#pragma unroll
+    for (int q = 0; q < kSwColRows; ++q)
+      if (y0 + q < N) {
+        b[((size_t)n * N + y0 + q) * N + x] = acc[q];
+        m = fmaxf(m, acc[q]);
+      }
   }
   m = warp_max(m);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -114,12 +164,11 @@ cudaError_t launch_shrinkwrap(cpra_plan_s* p) {
   cudaError_t e = cudaMemsetAsync(p->sw_max, 0, sizeof(unsigned) * Np, p->stream);
   if (e != cudaSuccess) return e;
   g_launches += 3;
-  const int rb = (N + kSwRows - 1) / kSwRows;
-  k_sw_rows<<<dim3(rb, Np), threads, (N + 2 * p->sw_ntaps) * sizeof(float), p->stream>>>(p->g, p->S, p->sw_tmp,
-                                                                    p->sw_taps, p->sw_ntaps, lo,
-                                                                    N, p->W);
-  k_sw_cols<<<dim3(rb, Np), threads, 2 * p->sw_ntaps * sizeof(float), p->stream>>>(p->sw_tmp, p->g_alt, p->sw_max, p->sw_taps,
-                                                    p->sw_ntaps, lo, N);
+  const int rb = (N + kSwRows - 1) / kSwRows, cb = (N + kSwColRows - 1) / kSwColRows;
+  k_sw_rows<<<dim3(rb, Np), threads, sw_rows_smem(N, p->sw_ntaps), p->stream>>>(p->g, p->S, p->sw_tmp, p->sw_taps,
+                                                                               p->sw_ntaps, lo, N, p->W);
+  k_sw_cols<<<dim3(cb, Np), threads, p->sw_ntaps * sizeof(float), p->stream>>>(p->sw_tmp, p->g_alt, p->sw_max,
+                                                                               p->sw_taps, p->sw_ntaps, lo, N);
   k_sw_thresh<<<dim3((N + 7) / 8, Np), 256, 0, p->stream>>>(p->g_alt, p->sw_max, p->S, p->cfg.sw_tau, N,
                                                  p->W);
   return cudaGetLastError();
@@ -257,10 +306,10 @@ extern "C" cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_i
   if (e == cudaSuccess) e = launch_bits_from_u8(sc.bits, S_in, N, count, st);
   if (e == cudaSuccess) {
     g_launches += 3;
-    const int rb = (N + kSwRows - 1) / kSwRows;
-    k_sw_rows<<<dim3(rb, count), threads, (N + 2 * ntaps) * sizeof(float), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps,
-                                                                   lo, N, W);
-    k_sw_cols<<<dim3(rb, count), threads, 2 * ntaps * sizeof(float), st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
+    const int rb = (N + kSwRows - 1) / kSwRows, cb = (N + kSwColRows - 1) / kSwColRows;
+    k_sw_rows<<<dim3(rb, count), threads, sw_rows_smem(N, ntaps), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps, lo, N,
+                                                                        W);
+    k_sw_cols<<<dim3(cb, count), threads, ntaps * sizeof(float), st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
     k_sw_thresh<<<dim3((N + 7) / 8, count), 256, 0, st>>>(sc.b, sc.mx, sc.bits, tau, N, W);
     e = cudaGetLastError();
   }

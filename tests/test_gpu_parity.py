@@ -323,6 +323,37 @@ def test_shrinkwrap(cp):
     plan.close()
 
 
+@pytest.mark.parametrize("N,count,sigma,tau", [(700, 2, 2.0, 0.5), (160, 3, 9.5, 0.5), (64, 4, 40.0, 0.9995),
+                                               (1024, 1, 2.0, 0.5)])
+def test_shrinkwrap_blur_sizes(cp, N, count, sigma, tau):
+    """The shrink-wrap kernels (periodic Gaussian blur of P_{S+} g by rows and
+    columns, per-pattern maximum, threshold) against the oracle's dense
+    W rho W^T at sizes whose blocks have ragged edges (N = 700: column blocks
+    of 8 rows), wide kernels (sigma 9.5 at N = 160) and a kernel wider than
+    the image (sigma 40 at N = 64: every tap, wrapped; the blurred field then
+    varies by 1e-3, hence the threshold 0.9995).  The masks may differ only
+    where the blurred value sits within 1e-5 (relative) of the threshold."""
+    import torch
+    rng = np.random.default_rng(N + count)
+    y, x = np.mgrid[0:N, 0:N] - N / 3
+    blob = np.exp(-(x * x + y * y) / (2 * (N / 8) ** 2))  # structure that survives a wide blur
+    g = (blob + 0.3 * rng.standard_normal((count, N, N))).astype(np.float32)
+    S = rng.random((count, N, N)) < 0.6
+    out = torch.full((count, N, N), 7, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    cp.cpra_shrinkwrap_static(torch.from_numpy(g).cuda(), torch.from_numpy(S.astype(np.uint8)).cuda(),
+                              out, N, count, sigma, tau, stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(bool)
+    ref = O.shrinkwrap(g.astype(np.float64), S, sigma, tau)
+    b = O.blur(O.object_estimate(g.astype(np.float64), S), sigma)
+    mx = b.reshape(count, -1).max(1)[:, None, None]
+    edge = np.abs(b - tau * mx) <= 1e-5 * mx
+    diff = got != ref
+    assert not np.any(diff & ~edge), f"{int((diff & ~edge).sum())} support pixels differ"
+    assert 0 < got.sum() < got.size
+
+
 def test_assembly_matches_oracle(cp):
     d = synth.make_case("tiny", N=32, Np=8)
     rng = np.random.default_rng(8)
