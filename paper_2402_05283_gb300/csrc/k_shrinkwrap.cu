@@ -37,21 +37,24 @@ __global__ void k_sw_rows(const float* __restrict__ g, const uint32_t* __restric
   const int rows = min(kSwRows, N - y0);
   const int hb = -lo - ntaps + 1;
   for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
-  for (int i = threadIdx.x; i < rows * HP; i += blockDim.x) {
-    const int yy = i / HP, k = i - yy * HP - 1;  // k = -1 .. N + ntaps + kSwRowX - 2
-    float v = 0.0f;
-    if (k >= 0 && k < N + ntaps - 1) {
-      const int y = y0 + yy;
-      const int x = ((k + hb) % N + N) % N;
-      const float gv = g[((size_t)n * N + y) * N + x];
-      v = (sbit(S, ((size_t)n * N + y) * W, x) && gv >= 0.0f) ? gv : 0.0f;
+  for (int yy = 0; yy < rows; ++yy) {
+    const float* gy = g + ((size_t)n * N + y0 + yy) * N;
+    const size_t srow = ((size_t)n * N + y0 + yy) * W;
+    for (int k = (int)threadIdx.x - 1; k < HP - 1; k += blockDim.x) {  // k = -1 .. HP - 2
+      float v = 0.0f;
+      if (k >= 0 && k < N + ntaps - 1) {
+        int x = k + hb;  // within [-N, 2N): ntaps <= N
+        x = x < 0 ? x + N : (x >= N ? x - N : x);
+        const float gv = gy[x];
+        v = (sbit(S, srow, x) && gv >= 0.0f) ? gv : 0.0f;
+      }
+      hs[yy * HP + k + 1] = v;
     }
-    hs[i] = v;
   }
   __syncthreads();
   const int XG = (N + kSwRowX - 1) / kSwRowX;  // output groups a row
   for (int i = threadIdx.x; i < rows * XG; i += blockDim.x) {
-    const int yy = i / XG, x0 = (i - yy * XG) * kSwRowX;
+    const int yy = i >= XG ? i / XG : 0, x0 = (i - yy * XG) * kSwRowX;
     // output x0 + q at tap t reads h[x0 + q + ntaps - 1 - t] = hx[q - t]
     const float* hx = hs + yy * HP + 1 + x0 + ntaps - 1;
     float w[kSwRowX], acc[kSwRowX];
@@ -112,7 +115,7 @@ __global__ void k_sw_cols(const float* __restrict__ tmp, float* b, unsigned* mx,
       w[q] = tn[(size_t)(rq % N) * N + x];
       acc[q] = 0.0f;
     }
-#pragma unroll 4
+#pragma unroll 8
     for (int t = 0; t < ntaps; ++t) {
       const float c = tp[t];
 #pragma unroll
@@ -120,7 +123,7 @@ __global__ void k_sw_cols(const float* __restrict__ tmp, float* b, unsigned* mx,
 #pragma unroll
       for (int q = kSwColRows - 1; q > 0; --q) w[q] = w[q - 1];
       r = r == 0 ? N - 1 : r - 1;
-      if (t + 1 < ntaps) w[0] = tn[(size_t)r * N + x];
+      if (t + 1 < ntaps) w[0] = __ldg(tn + (size_t)r * N + x);
     }
 #pragma unroll
     for (int q = 0; q < kSwColRows; ++q)

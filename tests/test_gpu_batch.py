@@ -134,6 +134,27 @@ def test_persistent_batch_uneven_n_equals_alone(cp, use_graph, chunk):
     b.close()
 
 
+def test_persistent_512_chunks_equal_alone(cp):
+    """The bench size's angle loop in the persistent queue in L2 chunks: two
+    plans of N = 512 with 12 angles each, 24 tiles in chunks of 5 (the last
+    of 4; one chunk crosses from the first member to the second), 14
+    iterations across a coupling step, states equal to the plans alone bit
+    for bit."""
+    mix = [(512, 12, 31, {}), (512, 12, 32, {"hio_iters": 6})]
+    alone = _warp_plans(cp, mix)
+    for p in alone:
+        p.iterate(14)
+    mixed = _warp_plans(cp, mix)
+    b = cp.Batch(mixed, use_graph=True)
+    b.set_persistent(1, chunk_tiles=5)
+    b.iterate(14)
+    for pa, pm in zip(alone, mixed):
+        assert np.array_equal(pa.result(cp.RESULT_STATE), pm.result(cp.RESULT_STATE))
+        np.testing.assert_allclose(pa.result(cp.RESULT_ERRORS), pm.result(cp.RESULT_ERRORS),
+                                   rtol=1e-12)
+    b.close()
+
+
 def test_persistent_wait_runs_out_and_recovers(cp):
     """The bounded device wait: in mode 2 the first task of every launch
     waits on a count that no task increments, so its wait runs out after the
