@@ -3,7 +3,9 @@
 // With n = l + 32 m (l < 32, m < 16) and k = k1 + 16 k2 (k1 < 16, k2 < 32),
 //   X[k1 + 16 k2] = sum_l W32^(l k2) W512^(l k1) [ sum_m x[l + 32 m] W16^(m k1) ].
 // Step A: lane l takes the 16-point DFT over m in registers and applies the
-// cross twiddle W512^(l k1) (the table xtw[k1 * 32 + l] of fftw.cuh).
+// cross twiddle W512^(l k1) (the table xtw[k1 * 32 + l] of fftw.cuh): read
+// for k1 <= 8, and W^(l (8 + j)) = W^(8 l) W^(l j) for the rest (seven
+// loads fewer from shared memory, seven complex products more).
 // One transpose through the warp tile hands lane (k1 = lane / 2, h = lane % 2)
 // the values l = h + 2 l2 (l2 < 16).  Step B splits the 32-point DFT over l
 // into 16-point DFTs over l2 in registers, the twiddle W32^(h k2) and a
@@ -34,10 +36,16 @@ struct PairLines512 {
   static __device__ __forceinline__ void fwd(float2 (&a)[1][16], float2 (&b)[1][16], float2* T,
                                              const float2* xs, int lane) {
     reg_fft<16, -1>(a[0]);
-    static_for<1, 16>([&](auto KK) {
-      constexpr int k1 = decltype(KK)::value;
-      a[0][k1] = cmul(a[0][k1], xs[k1 * 32 + lane]);
-    });
+    {
+      const float2 w8 = xs[8 * 32 + lane];
+      static_for<1, 8>([&](auto KK) {
+        constexpr int j = decltype(KK)::value;
+        const float2 wj = xs[j * 32 + lane];
+        a[0][j] = cmul(a[0][j], wj);
+        a[0][j + 8] = cmul(a[0][j + 8], cmul(w8, wj));
+      });
+      a[0][8] = cmul(a[0][8], w8);
+    }
     static_for<0, 16>([&](auto KK) {
       constexpr int k1 = decltype(KK)::value;
       T[k1 * TP + lane] = a[0][k1];
@@ -69,10 +77,16 @@ struct PairLines512 {
       a[0][kk] = T[kk * TP + lane];
     });
     __syncwarp();
-    static_for<1, 16>([&](auto KK) {
-      constexpr int kk = decltype(KK)::value;
-      a[0][kk] = cmul(a[0][kk], cconj(xs[kk * 32 + lane]));
-    });
+    {
+      const float2 w8 = cconj(xs[8 * 32 + lane]);
+      static_for<1, 8>([&](auto KK) {
+        constexpr int j = decltype(KK)::value;
+        const float2 wj = cconj(xs[j * 32 + lane]);
+        a[0][j] = cmul(a[0][j], wj);
+        a[0][j + 8] = cmul(a[0][j + 8], cmul(w8, wj));
+      });
+      a[0][8] = cmul(a[0][8], w8);
+    }
     reg_fft<16, +1>(a[0]);
   }
 
