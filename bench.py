@@ -128,11 +128,11 @@ def method_bytes_per_angle_iteration(n: int) -> int:
 # date and a fingerprint of the kernel sources it was taken on.  The bench
 # reports it only while the sources still have that fingerprint.
 NCU_ITERATION_TRAFFIC = {
-    # k_colpass_w<512> 418.85 MB + k_rowpass_w<512> 699.75 MB for 180 angles
+    # k_colpass_w<512> 423.21 MB + k_rowpass_w<512> 700.20 MB for 180 angles
     # (one launch each, --set full); the coupling prime (one launch in ten
     # iterations, 5 % of the time) was not captured and is not included
-    (("k_colpass", "k_rowpass", "k_prime"), 512): ((418.850816e6 + 699.752448e6) / 180,
-                                                   "2026-12-04", "1d113a1f3f6644fe"),
+    (("k_colpass", "k_rowpass", "k_prime"), 512): ((423.20512e6 + 700.200704e6) / 180,
+                                                   "2026-12-04", "d69998230edda895"),
 }  # {(kernel classes that ran, N): (bytes per angle-iteration, capture date, fingerprint)}
 KERNEL_SOURCES = ("fast_kernels.cuh", "fftw.cuh", "fftw_pair.cuh", "fft.cuh", "cpra_internal.h",
                   "k_fast.cu", "k_fused.cu", "taps.cuh")
