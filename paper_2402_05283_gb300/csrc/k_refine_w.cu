@@ -120,11 +120,17 @@ k_vw(float2* X, const float2* __restrict__ V, const uint8_t* __restrict__ M,
   const int c0 = blockIdx.x * C::CB;
   float2* base = X + blockIdx.y * outer + c0;
   float2* vbuf = buf + C::BUF;  // kVConstrain: the data of the block's columns
-  for (int idx = threadIdx.x; idx < N * C::CB; idx += C::NT) {
-    const int y = idx / C::CB, c = idx - y * C::CB;
-    cp_async8(buf + y * C::SP + c, base + y * estride + c);
+  // thread (row y0 + k RS, column cc): a warp's rows WARPS apart, so its
+  // 8-byte pieces fall on distinct banks of the odd-pitch staging rows
+  constexpr int RS = C::NT / C::CB;
+  static_assert(32 % C::CB == 0 && N % RS == 0, "line staging");
+  const int y0 = warp + C::WARPS * (lane / C::CB), cc = lane % C::CB;
+#pragma unroll 4
+  for (int k = 0; k < N / RS; ++k) {
+    const int y = y0 + k * RS;
+    cp_async8(buf + y * C::SP + cc, base + y * estride + cc);
     if constexpr (MODE == kVConstrain)
-      cp_async8(vbuf + y * C::SP + c, V + blockIdx.y * outer + c0 + y * estride + c);
+      cp_async8(vbuf + y * C::SP + cc, V + blockIdx.y * outer + c0 + y * estride + cc);
   }
   cp_async_commit();
   load_xtw<N>(xs, xtw, C::NT);
@@ -201,9 +207,10 @@ k_vw(float2* X, const float2* __restrict__ V, const uint8_t* __restrict__ M,
     });
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < N * C::CB; idx += C::NT) {
-    const int y = idx / C::CB, c = idx - y * C::CB;
-    base[y * estride + c] = buf[y * C::SP + c];
+#pragma unroll 4
+  for (int k = 0; k < N / RS; ++k) {
+    const int y = y0 + k * RS;
+    base[y * estride + cc] = buf[y * C::SP + cc];
   }
   if constexpr (MODE == kVConstrain) {
     double e = ef, d = df;
