@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "blur.h"
 #include "cpra_internal.h"
 #include "fft.cuh"
 #include "tiling.cuh"
@@ -268,131 +269,26 @@ __global__ void k_backproject(const uint32_t* __restrict__ S2, const double2* __
   if (mine) S3[((size_t)z * N + y) * W + w] = bits;
 }
 
-// The periodic blur out[i] = sum_t taps[t] v[(i - lo - t) mod N] reads, for
-// output i, the staged values h[i + ntaps - 1 - t] of a line copied once with
-// a halo: h[k] = v[(k - lo - ntaps + 1) mod N], k < N + ntaps - 1.
+// The 3D shrink-wrap blurs P_{S3+} rho along x (the 2D step's row blur over
+// the N z-planes), then along y and z in place (its column blur), with the
+// maximum of the last pass; see blur.h.
 
-// blur along x of P_{S3+} rho into B (one row a CTA)
-__global__ void k_blur3_x(const float* __restrict__ R, const uint32_t* __restrict__ S3, float* Bv,
-                          const float* __restrict__ taps, int ntaps, int lo, int N, int W) {
-  extern __shared__ float sm[];
-  float* tp = sm;           // [ntaps]
-  float* h = sm + ntaps;    // [N + ntaps - 1]
-  const size_t row = blockIdx.x;
-  const int base = -lo - ntaps + 1;
-  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
-  for (int k = threadIdx.x; k < N + ntaps - 1; k += blockDim.x) {
-    const int x = ((k + base) % N + N) % N;
-    const float v = R[row * N + x];
-    h[k] = (sbit(S3, row * W, x) && v >= 0.0f) ? v : 0.0f;
-  }
-  __syncthreads();
-  // four consecutive outputs a thread (N is a multiple of 4): a window of
-  // four staged values slides down one place a tap, one load a tap
-  for (int x0 = 4 * threadIdx.x; x0 < N; x0 += 4 * blockDim.x) {
-    const float* hx = h + x0 + ntaps - 1;
-    float w0 = hx[0], w1 = hx[1], w2 = hx[2], w3 = hx[3];
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    for (int t = 0; t < ntaps; ++t) {
-      const float c = tp[t];
-      a0 = fmaf(c, w0, a0);
-      a1 = fmaf(c, w1, a1);
-      a2 = fmaf(c, w2, a2);
-      a3 = fmaf(c, w3, a3);
-      w3 = w2;
-      w2 = w1;
-      w1 = w0;
-      if (t + 1 < ntaps) w0 = hx[-t - 1];
-    }
-    float4* dst = reinterpret_cast<float4*>(Bv + row * N + x0);
-    *dst = make_float4(a0, a1, a2, a3);
-  }
-}
-
-__device__ __forceinline__ float warp_max3(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// blur along y or z in place: cw adjacent x columns of one line set a CTA
-// (blockIdx.x = x block, blockIdx.y = the other index), the lines staged
-// with their halo in shared memory (pitch cw + 1); with mx the maximum of the
-// result (float bits, values >= 0)
-__global__ void k_blur3_v(float* Bv, const float* __restrict__ taps, int ntaps, int lo, int N,
-                          size_t outer, size_t estride, unsigned* mx, int cw) {
-  extern __shared__ float sm[];
-  __shared__ float red[32];
-  float* tp = sm;             // [ntaps]
-  float* cols = sm + ntaps;   // [N + ntaps - 1][cw + 1]
-  const int pitch = cw + 1;
-  const int x0 = blockIdx.x * cw;
-  float* bp = Bv + blockIdx.y * outer + x0;
-  const int nx = min(cw, N - x0);
-  const int base = -lo - ntaps + 1;
-  const int ext = N + ntaps - 1;
-  for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
-  for (int idx = threadIdx.x; idx < ext * cw; idx += blockDim.x) {
-    const int k = idx / cw, b = idx - k * cw;
-    const int j = ((k + base) % N + N) % N;
-    if (b < nx) cols[k * pitch + b] = bp[j * estride + b];
-  }
-  __syncthreads();
-  float m = 0.0f;
-  // four consecutive outputs of one column a thread, with the sliding window
-  // of k_blur3_x
-  for (int idx = threadIdx.x; idx < (N / 4) * cw; idx += blockDim.x) {
-    const int jb = idx / cw, b = idx - jb * cw;
-    if (b >= nx) continue;
-    const int j0 = 4 * jb;
-    const float* cj = cols + (j0 + ntaps - 1) * pitch + b;
-    float w0 = cj[0], w1 = cj[pitch], w2 = cj[2 * pitch], w3 = cj[3 * pitch];
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    for (int t = 0; t < ntaps; ++t) {
-      const float c = tp[t];
-      a0 = fmaf(c, w0, a0);
-      a1 = fmaf(c, w1, a1);
-      a2 = fmaf(c, w2, a2);
-      a3 = fmaf(c, w3, a3);
-      w3 = w2;
-      w2 = w1;
-      w1 = w0;
-      if (t + 1 < ntaps) w0 = cj[-(t + 1) * pitch];
-    }
-    bp[(size_t)j0 * estride + b] = a0;
-    bp[(size_t)(j0 + 1) * estride + b] = a1;
-    bp[(size_t)(j0 + 2) * estride + b] = a2;
-    bp[(size_t)(j0 + 3) * estride + b] = a3;
-    m = fmaxf(m, fmaxf(fmaxf(a0, a1), fmaxf(a2, a3)));
-  }
-  if (mx) {
-    m = warp_max3(m);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float t = 0.0f;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
-      atomicMax(mx, __float_as_uint(t));
-    }
-  }
-}
-
-// S3 <- {B >= tau * max} (unchanged when the maximum is 0); a thread a word
+// S3 <- {B >= tau * max} (unchanged when the maximum is 0): a warp a row,
+// lane l tests voxel 32 w + l and the warp's ballot is word w
 __global__ void k_thresh3(const float* __restrict__ Bv, const unsigned* __restrict__ mx, uint32_t* S3,
-                          float tau, int N, int W) {
-  const size_t words = (size_t)N * N * W;
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= words) return;
+                          float tau, int N, int W, size_t rows) {
+  const int lane = threadIdx.x & 31;
+  const size_t row = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= rows) return;  // whole warps
   const float m = __uint_as_float(*mx);
   if (!(m > 0.0f)) return;
   const float thr = tau * m;
-  const int w = (int)(i % W);
-  const size_t row = i / W;
-  uint32_t bits = 0;
-  for (int j = 0; j < 32; ++j) {
-    const int x = w * 32 + j;
-    if (x < N && Bv[row * N + x] >= thr) bits |= 1u << j;
+  const float* br = Bv + row * N;
+  for (int w = 0; w < W; ++w) {
+    const int x = w * 32 + lane;
+    const uint32_t bits = __ballot_sync(0xffffffffu, x < N && br[x] >= thr);
+    if (lane == 0) S3[row * W + w] = bits;
   }
-  S3[i] = bits;
 }
 
 // ------------------------------------------------------------------ launchers
@@ -513,29 +409,13 @@ cudaError_t launch_refine_shrink(const RefineArgs& a, const float* taps, int nta
   const int N = a.N;
   const size_t NN = (size_t)N * N;
   const int lo = -(ntaps / 2) + ((ntaps % 2) ? 0 : 1);
-  const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t ea = smem_attr3(k_blur3_v, 200 * 1024);
-    if (ea != cudaSuccess) return ea;
-    attr = true;
-  }
   cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = launch_sw_rows(a.R, a.S3, a.Bv, taps, ntaps, lo, N, a.W, N, st);  // x
+  if (e == cudaSuccess) e = launch_blur_cols(a.Bv, a.Bv, taps, ntaps, lo, N, N, NN, (size_t)N, nullptr, false, st);  // y
+  if (e == cudaSuccess) e = launch_blur_cols(a.Bv, a.Bv, taps, ntaps, lo, N, N, (size_t)N, NN, mx, false, st);  // z
   if (e != cudaSuccess) return e;
-  // columns a CTA for the y and z blurs: 32, or fewer while the haloed
-  // lines would not fit in 200 KB of shared memory (ntaps <= N)
-  int cw = 32;
-  while (cw > 4 && sizeof(float) * ((size_t)(N + ntaps - 1) * (cw + 1) + ntaps) > 200 * 1024) cw /= 2;
-  const size_t vsm = sizeof(float) * ((size_t)(N + ntaps - 1) * (cw + 1) + ntaps);
-  const size_t xsm = sizeof(float) * (N + 2 * ntaps);
-  g_launches += 4;
-  k_blur3_x<<<(unsigned)NN, threads, xsm, st>>>(a.R, a.S3, a.Bv, taps, ntaps, lo, N, a.W);
-  k_blur3_v<<<dim3((N + cw - 1) / cw, N), 256, vsm, st>>>(a.Bv, taps, ntaps, lo, N, NN, (size_t)N,
-                                                        nullptr, cw);
-  k_blur3_v<<<dim3((N + cw - 1) / cw, N), 256, vsm, st>>>(a.Bv, taps, ntaps, lo, N, (size_t)N, NN,
-                                                        mx, cw);
-  const size_t words = NN * a.W;
-  k_thresh3<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(a.Bv, mx, a.S3, tau, N, a.W);
+  g_launches += 1;
+  k_thresh3<<<(unsigned)((NN + 7) / 8), 256, 0, st>>>(a.Bv, mx, a.S3, tau, N, a.W, NN);
   return cudaGetLastError();
 }
 

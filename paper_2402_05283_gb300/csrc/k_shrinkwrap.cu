@@ -8,14 +8,14 @@
 #include <cmath>
 #include <mutex>
 
+#include "blur.h"
 #include "cpra_internal.h"
 #include "fft.cuh"
 
 namespace cpra {
 
-// image rows a block of the row blur; output rows a thread of the column blur
+// image rows a block of the row blur
 constexpr int kSwRows = 4;
-constexpr int kSwColRows = 8;
 // outputs a thread of the row blur (consecutive x)
 constexpr int kSwRowX = 4;
 
@@ -89,56 +89,83 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Column blur b[y][x] = sum_t taps[t] tmp[(y - lo - t) mod N][x] (terms in
-// the order of the definition) and the maximum over the block's outputs.  A
-// thread sums output rows y0 .. y0 + kSwColRows - 1 of its columns, tap by
-// tap, holding the kSwColRows input rows the current tap needs in
-// registers: one load a tap for all of them.
-__global__ void k_sw_cols(const float* __restrict__ tmp, float* b, unsigned* mx,
-                          const float* __restrict__ taps, int ntaps, int lo, int N) {
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+// Blur along lines of stride estride: out[j] = sum_t taps[t] in[(j - lo - t)
+// mod N] for CW adjacent columns of plane blockIdx.y (planes outer apart),
+// the terms in the order of the definition, and the maximum of the outputs
+// (float bits, values >= 0) into mx[blockIdx.y] (mx_per_plane) or mx[0].
+// The block stages its CW columns with the halo, h[k] = in[(k - lo - ntaps
+// + 1) mod N], by 4-byte asynchronous copies (a row of CW floats a group of
+// CW threads, all copies in flight at once), then a thread sums four
+// consecutive outputs of one column from a register window (one shared load
+// a tap).  in and out may be the same array: a block reads only its own
+// columns, all of them before it writes.
+template <int CW>
+__global__ void __launch_bounds__(256) k_blur_cols(const float* in, float* out, const float* __restrict__ taps,
+                                                   int ntaps, int lo, int N, size_t outer, size_t estride,
+                                                   unsigned* mx, int mx_per_plane) {
   extern __shared__ float sm[];
   __shared__ float red[32];
-  float* tp = sm;  // [ntaps]
-  const int n = blockIdx.y;
-  const int y0 = blockIdx.x * kSwColRows;
-  const float* tn = tmp + (size_t)n * N * N;
+  constexpr int RPP = 256 / CW;  // staged rows a pass of the block
+  constexpr int pitch = CW + 1;  // odd: a column read by 32 lanes hits 32 banks
+  float* tp = sm;                // [ntaps]
+  float* cols = sm + ntaps;      // [N + ntaps - 1][pitch]
+  const int x0 = blockIdx.x * CW;
+  const size_t off = blockIdx.y * outer + x0;
+  const int nx = min(CW, N - x0);
+  const int hb = -lo - ntaps + 1;
+  const int ext = N + ntaps - 1;
+  const int c = threadIdx.x % CW, r = threadIdx.x / CW;
   for (int t = threadIdx.x; t < ntaps; t += blockDim.x) tp[t] = taps[t];
+  if (c < nx)
+    for (int k = r; k < ext; k += RPP) {
+      int j = k + hb;  // within [-N, 2N): ntaps <= N
+      j = j < 0 ? j + N : (j >= N ? j - N : j);
+      cp_async4(cols + k * pitch + c, in + off + (size_t)j * estride + c);
+    }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   float m = 0.0f;
-  const int r0 = ((y0 - lo) % N + N) % N;  // input row of output y0 at tap 0
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    float w[kSwColRows], acc[kSwColRows];
-    int r = r0;  // input row of output y0 at the current tap
-#pragma unroll
-    for (int q = 0; q < kSwColRows; ++q) {
-      const int rq = r + q < N ? r + q : r + q - N;  // q < kSwColRows <= N
-      w[q] = tn[(size_t)(rq % N) * N + x];
-      acc[q] = 0.0f;
-    }
-#pragma unroll 8
-    for (int t = 0; t < ntaps; ++t) {
-      const float c = tp[t];
-#pragma unroll
-      for (int q = 0; q < kSwColRows; ++q) acc[q] = fmaf(c, w[q], acc[q]);
-#pragma unroll
-      for (int q = kSwColRows - 1; q > 0; --q) w[q] = w[q - 1];
-      r = r == 0 ? N - 1 : r - 1;
-      if (t + 1 < ntaps) w[0] = __ldg(tn + (size_t)r * N + x);
-    }
-#pragma unroll
-    for (int q = 0; q < kSwColRows; ++q)
-      if (y0 + q < N) {
-        b[((size_t)n * N + y0 + q) * N + x] = acc[q];
-        m = fmaxf(m, acc[q]);
+  if (c < nx)
+    for (int jb = r; jb < N / 4; jb += RPP) {
+      const int j0 = 4 * jb;
+      // output j0 + q at tap t reads cols[j0 + q + ntaps - 1 - t]
+      const float* cj = cols + (j0 + ntaps - 1) * pitch + c;
+      float w0 = cj[0], w1 = cj[pitch], w2 = cj[2 * pitch], w3 = cj[3 * pitch];
+      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll 4
+      for (int t = 0; t < ntaps; ++t) {
+        const float tc = tp[t];
+        a0 = fmaf(tc, w0, a0);
+        a1 = fmaf(tc, w1, a1);
+        a2 = fmaf(tc, w2, a2);
+        a3 = fmaf(tc, w3, a3);
+        w3 = w2;
+        w2 = w1;
+        w1 = w0;
+        if (t + 1 < ntaps) w0 = cj[-(t + 1) * pitch];  // staged row j0 + ntaps - 2 - t >= j0
       }
-  }
-  m = warp_max(m);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.0f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
-    atomicMax(mx + n, __float_as_uint(t));  // b >= 0: the bit order is the value order
+      float* o = out + off + c;
+      o[(size_t)j0 * estride] = a0;
+      o[(size_t)(j0 + 1) * estride] = a1;
+      o[(size_t)(j0 + 2) * estride] = a2;
+      o[(size_t)(j0 + 3) * estride] = a3;
+      m = fmaxf(m, fmaxf(fmaxf(a0, a1), fmaxf(a2, a3)));
+    }
+  if (mx) {
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
+      atomicMax(mx + (mx_per_plane ? blockIdx.y : 0), __float_as_uint(t));  // bit order = value order
+    }
   }
 }
 
@@ -160,18 +187,59 @@ __global__ void k_sw_thresh(const float* __restrict__ b, const unsigned* __restr
   }
 }
 
+template <int CW>
+static cudaError_t blur_cols_go(dim3 grid, size_t smem, const float* in, float* out, const float* taps,
+                                int ntaps, int lo, int N, size_t outer, size_t estride, unsigned* mx,
+                                int per_plane, cudaStream_t st) {
+  static bool big = false;  // the opt-in to more than 48 KB, once
+  if (smem > 48 * 1024 && !big) {
+    cudaError_t e = cudaFuncSetAttribute(k_blur_cols<CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    big = true;
+  }
+  k_blur_cols<CW><<<grid, 256, smem, st>>>(in, out, taps, ntaps, lo, N, outer, estride, mx, per_plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blur_cols(const float* in, float* out, const float* taps, int ntaps, int lo, int N,
+                             int planes, size_t outer, size_t estride, unsigned* mx, bool mx_per_plane,
+                             cudaStream_t st) {
+  // 32 columns a block, fewer while the staged lines would pass 200 KB
+  auto bytes = [&](int w) { return sizeof(float) * ((size_t)(N + ntaps - 1) * (w + 1) + ntaps); };
+  int cw = 32;
+  while (cw > 4 && bytes(cw) > 200 * 1024) cw /= 2;
+  const dim3 grid((N + cw - 1) / cw, planes);
+  const size_t smem = bytes(cw);
+  const int pp = mx_per_plane ? 1 : 0;
+  g_launches += 1;
+  switch (cw) {
+    case 32: return blur_cols_go<32>(grid, smem, in, out, taps, ntaps, lo, N, outer, estride, mx, pp, st);
+    case 16: return blur_cols_go<16>(grid, smem, in, out, taps, ntaps, lo, N, outer, estride, mx, pp, st);
+    case 8: return blur_cols_go<8>(grid, smem, in, out, taps, ntaps, lo, N, outer, estride, mx, pp, st);
+    default: return blur_cols_go<4>(grid, smem, in, out, taps, ntaps, lo, N, outer, estride, mx, pp, st);
+  }
+}
+
+cudaError_t launch_sw_rows(const float* g, const uint32_t* S, float* out, const float* taps, int ntaps,
+                           int lo, int N, int W, int planes, cudaStream_t st) {
+  const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  g_launches += 1;
+  k_sw_rows<<<dim3((N + kSwRows - 1) / kSwRows, planes), threads, sw_rows_smem(N, ntaps), st>>>(
+      g, S, out, taps, ntaps, lo, N, W);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_shrinkwrap(cpra_plan_s* p) {
   const int N = p->N, Np = p->Np;
-  const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
   const int lo = -(p->sw_ntaps / 2) + ((p->sw_ntaps % 2) ? 0 : 1);
   cudaError_t e = cudaMemsetAsync(p->sw_max, 0, sizeof(unsigned) * Np, p->stream);
   if (e != cudaSuccess) return e;
-  g_launches += 3;
-  const int rb = (N + kSwRows - 1) / kSwRows, cb = (N + kSwColRows - 1) / kSwColRows;
-  k_sw_rows<<<dim3(rb, Np), threads, sw_rows_smem(N, p->sw_ntaps), p->stream>>>(p->g, p->S, p->sw_tmp, p->sw_taps,
-                                                                               p->sw_ntaps, lo, N, p->W);
-  k_sw_cols<<<dim3(cb, Np), threads, p->sw_ntaps * sizeof(float), p->stream>>>(p->sw_tmp, p->g_alt, p->sw_max,
-                                                                               p->sw_taps, p->sw_ntaps, lo, N);
+  e = launch_sw_rows(p->g, p->S, p->sw_tmp, p->sw_taps, p->sw_ntaps, lo, N, p->W, Np, p->stream);
+  if (e == cudaSuccess)
+    e = launch_blur_cols(p->sw_tmp, p->g_alt, p->sw_taps, p->sw_ntaps, lo, N, Np, (size_t)N * N, (size_t)N,
+                         p->sw_max, true, p->stream);
+  if (e != cudaSuccess) return e;
+  g_launches += 1;
   k_sw_thresh<<<dim3((N + 7) / 8, Np), 256, 0, p->stream>>>(p->g_alt, p->sw_max, p->S, p->cfg.sw_tau, N,
                                                  p->W);
   return cudaGetLastError();
@@ -300,19 +368,17 @@ extern "C" cpra_status cpra_shrinkwrap_static(const float* g, const uint8_t* S_i
   for (int t = 0; t < ntaps; ++t) taps.v[t] = (float)w[((lo0 + t) % N + N) % N];
   cudaStream_t st = (cudaStream_t)stream;
   const int W = (N + 31) / 32;
-  const int threads = N >= 256 ? 256 : ((N + 31) / 32) * 32;
   const int lo = -(ntaps / 2) + ((ntaps % 2) ? 0 : 1);
   g_launches += 1;
   k_sw_static_taps<<<1, 256, 0, st>>>(taps, sc.taps, ntaps);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(sc.mx, 0, sizeof(unsigned) * count, st);
   if (e == cudaSuccess) e = launch_bits_from_u8(sc.bits, S_in, N, count, st);
+  if (e == cudaSuccess) e = launch_sw_rows(g, sc.bits, sc.tmp, sc.taps, ntaps, lo, N, W, count, st);
+  if (e == cudaSuccess)
+    e = launch_blur_cols(sc.tmp, sc.b, sc.taps, ntaps, lo, N, count, (size_t)N * N, (size_t)N, sc.mx, true, st);
   if (e == cudaSuccess) {
-    g_launches += 3;
-    const int rb = (N + kSwRows - 1) / kSwRows, cb = (N + kSwColRows - 1) / kSwColRows;
-    k_sw_rows<<<dim3(rb, count), threads, sw_rows_smem(N, ntaps), st>>>(g, sc.bits, sc.tmp, sc.taps, ntaps, lo, N,
-                                                                        W);
-    k_sw_cols<<<dim3(cb, count), threads, ntaps * sizeof(float), st>>>(sc.tmp, sc.b, sc.mx, sc.taps, ntaps, lo, N);
+    g_launches += 1;
     k_sw_thresh<<<dim3((N + 7) / 8, count), 256, 0, st>>>(sc.b, sc.mx, sc.bits, tau, N, W);
     e = cudaGetLastError();
   }
