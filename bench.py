@@ -134,8 +134,10 @@ NCU_ITERATION_TRAFFIC = {
     (("k_colpass", "k_rowpass", "k_prime"), 512): ((423.20512e6 + 700.200704e6) / 180,
                                                    "2026-12-04", "d69998230edda895"),
 }  # {(kernel classes that ran, N): (bytes per angle-iteration, capture date, fingerprint)}
+# the kernels' sources and the host code that orders their launches and
+# tiles (the order decides what the L2 still holds between passes)
 KERNEL_SOURCES = ("fast_kernels.cuh", "fftw.cuh", "fftw_pair.cuh", "fft.cuh", "cpra_internal.h",
-                  "k_fast.cu", "k_fused.cu", "taps.cuh")
+                  "k_fast.cu", "k_fused.cu", "taps.cuh", "api.cu")
 
 
 def kernel_fingerprint() -> str:

@@ -393,7 +393,10 @@ cpra_status upload_steps(cpra_plan_s* p, const std::vector<JobStep>& steps) {
   return CPRA_OK;
 }
 
-Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles, int first_tile = 0) {
+// reversed: the present tiles in reverse order (stored from offset Np).  The
+// row passes run the angles backwards, so that each pass starts on the
+// angles whose data the previous pass left in L2 last.
+Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles, int first_tile = 0, bool reversed = false) {
   Launch L;
   L.N = p->N;
   L.engine = p->engine;
@@ -402,7 +405,7 @@ Launch plan_launch(const cpra_plan_s* p, int64_t step, int ntiles, int first_til
   L.stream = p->stream;
   L.js = p->d_js;
   L.st = p->d_steps + step;
-  L.tiles = p->d_tiles + first_tile;
+  L.tiles = p->d_tiles + (reversed ? p->Np : 0) + first_tile;
   L.ntiles = ntiles;
   return L;
 }
@@ -668,7 +671,7 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   p->stage = (float*)A(Np * NN * 4);
   p->bad = (uint8_t*)A(Np);
   p->d_js = (JobStatic*)A(sizeof(JobStatic));
-  p->d_tiles = (int2*)A(sizeof(int2) * Np);
+  p->d_tiles = (int2*)A(sizeof(int2) * 2 * Np);
   if (ok && cfg->shrinkwrap_every > 0) {
     std::vector<float> taps = gaussian_taps(p->N, cfg->sw_sigma, p->sw_ntaps);
     p->sw_tmp = (float*)A(Np * NN * 4);
@@ -759,12 +762,13 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(p->err_acc, 0, Np * 8, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->bad, 0, Np, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->g, 0, Np * NN * 4, p->stream);
-  std::vector<int2> tiles(Np);
-  for (size_t n = 0; n < Np; ++n) tiles[n] = make_int2(0, (int)n);
+  // the angle tiles in order, then in reverse order (for the row passes)
+  std::vector<int2> tiles(2 * Np);
+  for (size_t n = 0; n < Np; ++n) tiles[n] = tiles[2 * Np - 1 - n] = make_int2(0, (int)n);
+  p->n_present = (int)Np;
+  p->present_h.assign(Np, 1);
   if (e == cudaSuccess)
-    p->n_present = (int)Np;
-    p->present_h.assign(Np, 1);
-    e = cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * Np, cudaMemcpyHostToDevice, p->stream);
+    e = cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * 2 * Np, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) {
     JobStatic j = job_static(p);
     e = cudaMemcpyAsync(p->d_js, &j, sizeof(j), cudaMemcpyHostToDevice, p->stream);
@@ -1035,7 +1039,8 @@ static cpra_status iterate_core(cpra_plan_s* p, int32_t n_iters, double* err_out
       if (s.ca.store_g) std::swap(p->g, p->g_alt);
     }
     CK(timed(p, CPRA_KERNEL_COLPASS, [&] { return launch_colpass(plan_launch(p, k, p->n_present)); }), "colpass");
-    CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(plan_launch(p, k, p->n_present)); }), "rowpass");
+    CK(timed(p, CPRA_KERNEL_ROWPASS, [&] { return launch_rowpass(plan_launch(p, k, p->n_present, 0, true)); }),
+       "rowpass");
     p->hp_valid = s.forward != 0;
     if (c.shrinkwrap_every > 0 && (p->t + 1) % c.shrinkwrap_every == 0)
       CK(timed(p, CPRA_KERNEL_SHRINKWRAP, [&] { return launch_shrinkwrap(p); }), "shrinkwrap");
@@ -1368,8 +1373,13 @@ cpra_status cpra_set_present(cpra_plan_t p, const uint8_t* mask) {
     if (!p->present) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "present mask allocation failed");
   }
   CK(cudaMemcpyAsync(p->present, m.data(), (size_t)p->Np, cudaMemcpyHostToDevice, p->stream), "mask");
+  const size_t nt = tiles.size();
+  tiles.resize((size_t)p->Np + nt);  // the reversed list at offset Np
+  for (size_t i = 0; i < nt; ++i) tiles[(size_t)p->Np + i] = tiles[nt - 1 - i];
+  for (size_t i = nt; i < (size_t)p->Np; ++i) tiles[i] = make_int2(0, 0);  // unused gap
   CK(cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice,
                      p->stream), "tiles");
+  tiles.resize(nt);
   CK(cudaStreamSynchronize(p->stream), "mask sync");
   p->present_h = m;
   p->n_present = (int)tiles.size();
@@ -1451,7 +1461,7 @@ struct cpra_batch_s {
     int N = 0, engine = 0, prec = 0;
     std::vector<int> members;
     JobStatic* d_js = nullptr;
-    int2* d_tiles = nullptr;   // room for every angle of every member
+    int2* d_tiles = nullptr;   // every angle of every member, in order then reversed
     int ntiles = 0;
     // Gauss-Seidel groups: one launch per angle of the sweep over all members
     int sweep = 0, n_ei = 0, np_max = 0;
@@ -1526,6 +1536,8 @@ cudaError_t group_tiles(cpra_batch_s* b, cpra_batch_s::Group& g) {
     g.versions.push_back(p->present_version);
   }
   g.ntiles = (int)tiles.size();
+  // then the same tiles in reverse order, for the row passes (see plan_launch)
+  for (int i = g.ntiles - 1; i >= 0; --i) tiles.push_back(tiles[i]);
   return cudaMemcpyAsync(g.d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
                          cudaMemcpyHostToDevice, b->stream);
 }
@@ -1672,7 +1684,7 @@ cpra_status cpra_batch_create(const cpra_plan_t* plans, int32_t n, int32_t use_g
     size_t room = 0;
     for (int mi : g.members) room += (size_t)b->plans[mi]->Np;
     g.d_js = (JobStatic*)balloc(b, sizeof(JobStatic) * g.members.size());
-    g.d_tiles = (int2*)balloc(b, sizeof(int2) * room);
+    g.d_tiles = (int2*)balloc(b, sizeof(int2) * 2 * room);
     if (!g.d_js || !g.d_tiles) {
       cpra_batch_destroy(b);
       return bfail(nullptr, CPRA_ERR_OUT_OF_MEMORY, "batch tables");
@@ -2082,6 +2094,7 @@ cpra_status cpra_batch_iterate(cpra_batch_t b, int32_t n_iters) {
           ++kernels;
         }
         if (e == cudaSuccess) e = launch_colpass(L);
+        L.tiles = g.d_tiles + g.ntiles;  // reversed
         if (e == cudaSuccess) e = launch_rowpass(L);
         kernels += 2;
         if (e != cudaSuccess) return e;
