@@ -110,6 +110,16 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def bench_config(world: int) -> dict:
+    """The workload both arms name (the reference arm times a bounded sample
+    of it, described in its cpu_baseline and ms_per_step_note)."""
+    return {"workload": f"CPRA N={N} Np={NP}: {T_HIO} HIO + {T_ER} ER iterations, "
+                        "coupling alpha=(0.2,0.6,0.2) every 10, 512^3 assembly",
+            "N": N, "Np": NP, "iterations": ITERS,
+            "l2": "inputs larger than L2 (state 0.75 GB, intensities 0.38 GB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def make_inputs(device, n_angles=NP):
     import synth
     return synth.make_case("metric", device=device, Np=n_angles)
@@ -756,8 +766,7 @@ def run_reference(args):
                                 "the sampled rate; each timed step is a 6 s sample",
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"CPRA N={N} Np={NP} {ITERS} iterations (bounded oracle sample)",
-                       "N": N, "Np": NP},
+            "config": bench_config(1),
             "wall_s": round(time.perf_counter() - t_run, 1),
             "cpu_baseline": {**cb, "value": v},
             "e2e": {"value": v, "unit": "angle-iterations/s", "h2d_bytes_per_step": 0,
@@ -882,12 +891,7 @@ def run_gpu(args):
             "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.precision], "data": "synthetic",
-            "config": {"workload": f"CPRA N={N} Np={NP}: {T_HIO} HIO + {T_ER} ER iterations, "
-                                   "coupling alpha=(0.2,0.6,0.2) every 10, 512^3 assembly",
-                       "N": N, "Np": NP, "iterations": ITERS,
-                       "engine": "two-pass, warp-resident FFTs",
-                       "l2": "inputs larger than L2 (state 0.75 GB, intensities 0.38 GB)",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(world),
             "p50_ms": round(float(qs[0]), 3), "p99_ms": round(float(qs[1]), 3),
             "wall_s": round(wall, 3),
             "roofline": roof,
