@@ -132,7 +132,7 @@ __all__ = [
     "fftshift3", "amplitudes", "a_sym", "splitmix64", "initial_guess",
     "modulus_projection", "fourier_error_terms", "support_update", "constrained_pairs",
     "iterate_2d", "positivity_margin", "couple", "couple_sweep_one", "wrapped_gaussian", "blur", "shrinkwrap",
-    "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d",
+    "object_estimate", "centre_of_mass", "signed_freq", "spectra", "grid_3d", "grid_plane",
     "volume", "assemble", "OracleConfig", "OracleRun", "real_space_error",
     "r_factor", "raar_update", "episode_error", "select_best", "centrally_inverted", "prtf",
     "merge_episodes", "assemble_spectra", "measured_cells", "backprojected_support", "blur3",
@@ -473,6 +473,34 @@ def grid_3d(E: np.ndarray, thetas, wmin: float = 1e-12) -> np.ndarray:
                 jj = (j0.astype(np.int64) + dj) % N
                 np.add.at(num, (slice(None), jj, ii), w[None, :] * E[n])
                 np.add.at(wsum, (slice(None), jj, ii), np.broadcast_to(w[None, :], (N, N)))
+    return np.where(wsum >= wmin, num / np.where(wsum >= wmin, wsum, 1.0), 0.0)
+
+
+def grid_plane(E_kz: np.ndarray, thetas, wmin: float = 1e-12) -> np.ndarray:
+    """One kz plane of grid_3d: the literal bilinear scatter of the samples
+    E_kz[n][ku] = E_n(kz, ku) of every slice into the (ky, kx) plane, divided
+    by the summed weight (Eq. 2-3: the slice of angle n passes through
+    (ku cos, ku sin, kz) for every kz, so each plane gathers its own samples
+    only).  The same loops in the same order as grid_3d, restricted to one
+    plane, so it equals grid_3d(E)[kz] bit for bit.  Returns V[ky][kx]."""
+    Np, N = E_kz.shape
+    k = signed_freq(N)
+    num = np.zeros((N, N), dtype=np.complex128)
+    wsum = np.zeros((N, N), dtype=np.float64)
+    for n in range(Np):
+        px = k * math.cos(thetas[n])
+        py = k * math.sin(thetas[n])
+        i0 = np.floor(px)
+        j0 = np.floor(py)
+        fx = px - i0
+        fy = py - j0
+        for di in (0, 1):
+            for dj in (0, 1):
+                w = (fx if di else 1 - fx) * (fy if dj else 1 - fy)
+                ii = (i0.astype(np.int64) + di) % N
+                jj = (j0.astype(np.int64) + dj) % N
+                np.add.at(num, (jj, ii), w * E_kz[n])
+                np.add.at(wsum, (jj, ii), w)
     return np.where(wsum >= wmin, num / np.where(wsum >= wmin, wsum, 1.0), 0.0)
 
 

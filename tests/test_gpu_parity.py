@@ -688,6 +688,40 @@ def test_n512_np8_distinct_neighbours(cp, engine):
     print(f"N=512 Np=8 {engine}: HIO step {rel.max():.2e}, 6 ER iterates {worst:.2e}")
 
 
+def test_assembly_metric_size_sampled_kz(cp, metric_case):
+    """The bench's assembly path (N = 512, Np = 360: its moments, spectra,
+    z-IDFT, 512^3 gather from the 360-angle lists and inverse transforms)
+    against the oracle.  The GPU volume is taken back to the gridded
+    spectrum (V = FFT3 of the uncentred volume) and sampled kz planes are
+    compared with the oracle's literal scatter of that plane (grid_plane on
+    the oracle's spectra, Eq. 2-3), each within 1e-4 relative L2."""
+    import scipy.fft
+    mc = metric_case
+    N, Np, th = mc["N"], mc["Np"], mc["thetas"]
+    S = mc["support"].astype(bool)
+    rng = np.random.default_rng(512)
+    g = np.zeros((Np, N, N), np.float32)
+    g[:, S] = rng.standard_normal((Np, int(S.sum())), dtype=np.float32)  # negatives too
+    plan = cp.Plan(cp.make_config(N, Np))
+    plan.load_intensities(mc["I_dev"], 0, th)
+    plan.load_support(mc["support"])
+    plan.load_state(g, 0)
+    vol = np.empty((N, N, N), np.complex64)
+    plan.assemble_3d(vol)
+    plan.close()
+    V = scipy.fft.fftn(np.fft.ifftshift(vol), workers=-1)
+    del vol
+    E = O.spectra(g.astype(np.float64), np.broadcast_to(S, (Np, N, N)))
+    planes = (0, 1, 2, 100, 255, 256, 257, 400, 511)
+    worst = 0.0
+    for kz in planes:
+        ref = O.grid_plane(E[:, kz, :], th)
+        rel = float(np.linalg.norm(V[kz] - ref) / np.linalg.norm(ref))
+        worst = max(worst, rel)
+        assert rel < TOL, (kz, rel)
+    print(f"assembly N=512 Np=360: {len(planes)} kz planes compared, worst rel-L2 {worst:.2e}")
+
+
 def test_assembly_cfg2_size(cp):
     """Step D at the large configuration's sizes (N = 256, Np = 180, 256^3
     grid): the whole volume within 1e-4 of the oracle's literal scatter and

@@ -586,6 +586,23 @@ def test_grid_bilinear_weights_hand_case():
     assert np.all(V[1:] == 0)  # other kz planes carry no data
 
 
+def test_grid_plane_is_a_plane_of_grid_3d():
+    """grid_plane (one kz plane, Eq. 2-3) against grid_3d on 16 angles at
+    N = 16, every plane, bit for bit; and on the 45-degree hand case above."""
+    N, Np = 16, 16
+    E = _rand(Np, N, N) + 1j * _rand(Np, N, N)
+    th = np.arange(Np) * math.pi / Np + 0.013
+    V = O.grid_3d(E, th)
+    for kz in range(N):
+        assert np.array_equal(O.grid_plane(E[:, kz, :], th), V[kz])
+    E1 = np.zeros((1, 4), complex)
+    E1[0, 1] = 1.0
+    c = 1 / math.sqrt(2)
+    w00 = (1 - c) ** 2
+    P = O.grid_plane(E1, [math.pi / 4])
+    assert abs(P[1, 1] - 1.0) < 1e-12 and abs(P[0, 0] - w00 / (1.0 + 2 * w00)) < 1e-12
+
+
 def test_volume_of_exact_spectrum_is_object():
     N = 10
     vol = rng.random((N, N, N))
