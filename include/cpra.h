@@ -260,6 +260,24 @@ cpra_status cpra_set_present(cpra_plan_t plan, const uint8_t* mask);
  * NULL (N^3 * 8 bytes, host or device). */
 cpra_status cpra_assemble_3d(cpra_plan_t plan, void* out_volume);
 
+/* cpra_assemble_3d, then a download of the volume to out that the call does
+ * not wait for: the volume is copied device-to-device into a plan-owned
+ * staging buffer (N^3 * 8 bytes, allocated on first use through the plan's
+ * allocator) on the plan's stream, and from there to out on a second,
+ * plan-owned stream, so that whatever the caller queues next on the plan
+ * (the next reconstruction's upload and iterations) overlaps the download.
+ * out: page-locked host memory (cudaHostAlloc or cudaHostRegister), N^3
+ * complex floats; INVALID_ARG for any other memory.  The caller must leave
+ * out alone until cpra_download_wait returns.  A later call orders its
+ * staging copy after the previous download on the device; the host never
+ * waits here.  Errors as cpra_assemble_3d. */
+cpra_status cpra_assemble_3d_async(cpra_plan_t plan, void* out);
+
+/* Wait until every download cpra_assemble_3d_async queued has landed in host
+ * memory, then report the plan's status word as a waiting call does
+ * (CPRA_OK when nothing is pending). */
+cpra_status cpra_download_wait(cpra_plan_t plan);
+
 /* Step C (repeating and merging): combine n_r finished reconstructions of
  * the same patterns, each from its own random start (its own seed), into one
  * episode and assemble it (Step D) into dst's volume.

@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
             "cpra_load_state": (C.c_int, [P, P, C.c_int64]),
             "cpra_iterate": (C.c_int, [P, C.c_int32, P]),
             "cpra_assemble_3d": (C.c_int, [P, P]),
+            "cpra_assemble_3d_async": (C.c_int, [P, P]),
+            "cpra_download_wait": (C.c_int, [P]),
             "cpra_result": (C.c_int, [P, C.c_int32, P, C.c_size_t]),
             "cpra_iteration": (C.c_int64, [P]),
             "cpra_reset": (C.c_int, [P]),
@@ -216,6 +218,27 @@ def cpra_assemble_3d(plan, out=None):
     p, keep = _ptr(out)
     _check(lib().cpra_assemble_3d(plan, p), plan)
     return keep
+
+
+def cpra_assemble_3d_async(plan, out):
+    """Queue the assembly and a download of the volume into out without
+    waiting.  out: page-locked host memory (a pinned torch tensor or a
+    registered numpy array), contiguous, N^3 complex64 (or N^3 x 2 float32);
+    it is written in place, so no copy is made, and must stay alive and
+    untouched until cpra_download_wait."""
+    if isinstance(out, np.ndarray):
+        ok, ptr = out.flags.c_contiguous, out.ctypes.data
+    elif hasattr(out, "data_ptr"):
+        ok, ptr = out.is_contiguous(), out.data_ptr()
+    else:
+        raise TypeError(f"unsupported array type {type(out)}")
+    if not ok:
+        raise ValueError("out must be contiguous (the download writes it in place)")
+    _check(lib().cpra_assemble_3d_async(plan, ptr), plan)
+
+
+def cpra_download_wait(plan):
+    _check(lib().cpra_download_wait(plan), plan)
 
 
 def cpra_result(plan, what: int, dst, nbytes: int):
@@ -409,6 +432,7 @@ class Plan:
         self.stream = stream
         self.h = cpra_plan(cfg, stream)
         self.N, self.Np = cfg.N, cfg.Np
+        self._downloads = []  # host buffers of queued downloads (assemble_3d_async)
 
     def load_intensities(self, I, first: int = 0, thetas=None):
         count = I.shape[0] if I.ndim == 3 else 1
@@ -440,6 +464,21 @@ class Plan:
     def assemble_3d(self, out=None):
         cpra_assemble_3d(self.h, out)
         return out
+
+    def assemble_3d_async(self, out):
+        """Assemble and queue the volume's download into out (pinned host
+        memory); the plan keeps out alive until download_wait()."""
+        need = self.N ** 3 * 8
+        nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        if nbytes < need:
+            raise ValueError(f"out holds {nbytes} bytes, N^3 complex64 = {need} needed")
+        cpra_assemble_3d_async(self.h, out)
+        self._downloads.append(out)
+        return out
+
+    def download_wait(self):
+        cpra_download_wait(self.h)
+        self._downloads.clear()
 
     def refine_3d(self, n: int, shrink_every: int = 0, sigma: float = 2.0, tau: float = 0.1):
         """Step D refinement; returns the n per-iteration errors."""

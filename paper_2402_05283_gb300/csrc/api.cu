@@ -1430,9 +1430,53 @@ cpra_status cpra_sync(cpra_plan_t p) {
   return check_status(p);
 }
 
+cpra_status cpra_assemble_3d_async(cpra_plan_t p, void* out) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (!out) return fail(p, CPRA_ERR_INVALID_ARG, "out is NULL");
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, out) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+    cudaGetLastError();
+    return fail(p, CPRA_ERR_INVALID_ARG, "out must be page-locked host memory");
+  }
+  cpra_status st = cpra_assemble_3d(p, nullptr);
+  if (st != CPRA_OK) return st;
+  const size_t bytes = (size_t)p->N * p->N * p->N * 8;
+  if (!p->dl_stream) CK(cudaStreamCreateWithFlags(&p->dl_stream, cudaStreamNonBlocking), "download stream");
+  if (!p->dl_ready) CK(cudaEventCreateWithFlags(&p->dl_ready, cudaEventDisableTiming), "download event");
+  if (!p->dl_done) CK(cudaEventCreateWithFlags(&p->dl_done, cudaEventDisableTiming), "download event");
+  if (!p->dl_buf) {
+    p->dl_buf = (float2*)dev_alloc(p, bytes);
+    if (!p->dl_buf) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "download staging allocation failed");
+  }
+  // the staging buffer is free once the previous download has read it
+  if (p->dl_pending) CK(cudaStreamWaitEvent(p->stream, p->dl_done, 0), "download order");
+  CK(cudaMemcpyAsync(p->dl_buf, p->asmb.vol, bytes, cudaMemcpyDeviceToDevice, p->stream), "staging copy");
+  CK(cudaEventRecord(p->dl_ready, p->stream), "download order");
+  CK(cudaStreamWaitEvent(p->dl_stream, p->dl_ready, 0), "download order");
+  CK(cudaMemcpyAsync(out, p->dl_buf, bytes, cudaMemcpyDeviceToHost, p->dl_stream), "download");
+  CK(cudaEventRecord(p->dl_done, p->dl_stream), "download order");
+  p->dl_pending = true;
+  return CPRA_OK;
+}
+
+cpra_status cpra_download_wait(cpra_plan_t p) {
+  if (!p) return fail(nullptr, CPRA_ERR_INVALID_ARG, "plan is NULL");
+  if (p->dl_pending) {
+    CK(cudaEventSynchronize(p->dl_done), "download wait");
+    p->dl_pending = false;
+  }
+  return check_status(p);
+}
+
 cpra_status cpra_destroy(cpra_plan_t p) {
   if (!p) return CPRA_OK;
   cudaStreamSynchronize(p->stream);
+  if (p->dl_stream) {
+    cudaStreamSynchronize(p->dl_stream);
+    cudaStreamDestroy(p->dl_stream);
+  }
+  if (p->dl_ready) cudaEventDestroy(p->dl_ready);
+  if (p->dl_done) cudaEventDestroy(p->dl_done);
   cudaGetLastError();
   for (auto& ev : p->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto& ev : p->spare) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }

@@ -54,6 +54,11 @@ struct Assembly {
 struct cpra_plan_s {
   cpra_config cfg;
   cudaStream_t stream = nullptr;
+  // volume downloads that overlap later work (cpra_assemble_3d_async)
+  float2* dl_buf = nullptr;  // staging copy of the volume being downloaded
+  cudaStream_t dl_stream = nullptr;
+  cudaEvent_t dl_ready = nullptr, dl_done = nullptr;
+  bool dl_pending = false;
   int N = 0, Np = 0, W = 0;
   int64_t t = 0;
   bool state_ready = false;

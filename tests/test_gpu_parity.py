@@ -374,6 +374,38 @@ def test_assembly_matches_oracle(cp):
         plan.close()
 
 
+def test_assemble_async_download(cp):
+    """cpra_assemble_3d_async: the downloaded volumes equal the waiting form's
+    bit for bit, for two downloads queued back to back with iterations in
+    between (the second staging copy waits for the first download on the
+    device); pageable memory is refused."""
+    import torch
+    d = synth.make_case("tiny", N=64, Np=8)
+    plan = cp.Plan(cp.make_config(64, 8, hio_iters=0, er_iters=20, seed=4))
+    plan.load_intensities(d["I"], 0, d["thetas"])
+    plan.load_support(d["support"])
+    plan.iterate(5)
+    v1 = np.empty((64, 64, 64), np.complex64)
+    plan.assemble_3d(v1)
+    h1 = torch.empty((64, 64, 64, 2), dtype=torch.float32).pin_memory()
+    h2 = torch.empty((64, 64, 64, 2), dtype=torch.float32).pin_memory()
+    plan.assemble_3d_async(h1)
+    plan.iterate(3)
+    plan.assemble_3d_async(h2)
+    plan.download_wait()
+    v2 = np.empty((64, 64, 64), np.complex64)
+    plan.assemble_3d(v2)
+    assert np.array_equal(h1.numpy().view(np.complex64)[..., 0], v1)
+    assert np.array_equal(h2.numpy().view(np.complex64)[..., 0], v2)
+    assert not np.array_equal(v1, v2)
+    with pytest.raises(cp.CpraError) as e:
+        plan.assemble_3d_async(np.empty((64, 64, 64), np.complex64))  # pageable
+    assert e.value.status == cp.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        plan.assemble_3d_async(torch.empty((64, 64, 64, 4), dtype=torch.float32).pin_memory()[..., :2])
+    plan.close()
+
+
 def test_assembly_after_angle_reloads(cp):
     """Reloading the same angles keeps the gridding lists; moving one rebuilds
     them: both volumes equal a fresh plan's, and the oracle's."""
