@@ -199,9 +199,14 @@ cpra_status cpra_plan(const cpra_config* cfg, void* stream, cpra_plan_t* out);
  * (radians, host memory, may be NULL to keep theta_n = n*pi/Np).  Prepares
  * A = sqrt(I) in FFT order, its Hermitian-symmetrised half plane and the FP64
  * error constants (Eq. 1-3).  The call queues the upload and the preparation
- * on the plan's stream and returns without waiting for them: host buffers in
- * pinned memory must stay unchanged until the stream has passed the copy
- * (pageable buffers are copied before the call returns).  Non-finite or
+ * and returns without waiting for them.  An upload from host memory runs on
+ * a second, plan-owned stream into a plan-owned buffer (Np*N*N floats,
+ * allocated on the first host upload through the plan's allocator), so it
+ * overlaps work already queued on the plan's stream; the preparation on the
+ * plan's stream waits for it, and a later upload waits until the
+ * preparation has read the buffer.  Host buffers in pinned memory must stay
+ * unchanged until the plan's stream has passed the preparation (cpra_sync);
+ * pageable buffers are copied before the call returns.  Non-finite or
  * negative intensities are reported by the first iteration on them, through
  * the plan's status word (see above: INVALID_ARG naming the angle). */
 cpra_status cpra_load_intensities(cpra_plan_t plan, const float* I, int32_t first_angle,

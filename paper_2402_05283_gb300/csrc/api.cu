@@ -790,18 +790,37 @@ cpra_status cpra_load_intensities(cpra_plan_t p, const float* I, int32_t first, 
   if (!I || count < 1 || first < 0 || first + count > p->Np)
     return fail(p, CPRA_ERR_INVALID_ARG, "bad intensity range or pointer");
   const size_t NN = (size_t)p->N * p->N;
-  const float* src = I;
-  if (!is_device_ptr(I)) {
-    CK(cudaMemcpyAsync(p->stage, I, sizeof(float) * NN * count, cudaMemcpyHostToDevice, p->stream),
-       "intensity upload");
-    src = p->stage;
-  }
   if (theta)
     for (int i = 0; i < count; ++i)
       if (!std::isfinite(theta[i])) return fail(p, CPRA_ERR_INVALID_ARG, "theta not finite");
+  const float* src = I;
+  const bool from_host = !is_device_ptr(I);
+  if (from_host) {
+    // The upload runs on the plan's upload stream into its own buffer, so it
+    // overlaps whatever is already queued on the plan's stream (the previous
+    // reconstruction); the preparation waits for it, and the next upload
+    // waits until this preparation has read the buffer.
+    if (!p->ul_stream) CK(cudaStreamCreateWithFlags(&p->ul_stream, cudaStreamNonBlocking), "upload stream");
+    if (!p->ul_done) CK(cudaEventCreateWithFlags(&p->ul_done, cudaEventDisableTiming), "upload event");
+    if (!p->ul_free) CK(cudaEventCreateWithFlags(&p->ul_free, cudaEventDisableTiming), "upload event");
+    if (!p->ul_buf) {
+      p->ul_buf = (float*)dev_alloc(p, sizeof(float) * NN * p->Np);
+      if (!p->ul_buf) return fail(p, CPRA_ERR_OUT_OF_MEMORY, "upload buffer allocation failed");
+    }
+    if (p->ul_used) CK(cudaStreamWaitEvent(p->ul_stream, p->ul_free, 0), "upload order");
+    CK(cudaMemcpyAsync(p->ul_buf, I, sizeof(float) * NN * count, cudaMemcpyHostToDevice, p->ul_stream),
+       "intensity upload");
+    CK(cudaEventRecord(p->ul_done, p->ul_stream), "upload order");
+    CK(cudaStreamWaitEvent(p->stream, p->ul_done, 0), "upload order");
+    src = p->ul_buf;
+  }
   // no wait for the device: an invalid pattern is reported through the
   // status word by the first iteration on it (k_prepare)
   CK(timed(p, CPRA_KERNEL_PREPARE, [&] { return launch_prepare(p, src, first, count); }), "prepare");
+  if (from_host) {
+    CK(cudaEventRecord(p->ul_free, p->stream), "upload order");
+    p->ul_used = true;
+  }
   if (theta) {
     bool moved = false;
     for (int i = 0; i < count; ++i)
@@ -1477,6 +1496,12 @@ cpra_status cpra_destroy(cpra_plan_t p) {
   }
   if (p->dl_ready) cudaEventDestroy(p->dl_ready);
   if (p->dl_done) cudaEventDestroy(p->dl_done);
+  if (p->ul_stream) {
+    cudaStreamSynchronize(p->ul_stream);
+    cudaStreamDestroy(p->ul_stream);
+  }
+  if (p->ul_done) cudaEventDestroy(p->ul_done);
+  if (p->ul_free) cudaEventDestroy(p->ul_free);
   cudaGetLastError();
   for (auto& ev : p->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto& ev : p->spare) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }

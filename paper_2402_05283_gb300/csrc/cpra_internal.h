@@ -59,6 +59,12 @@ struct cpra_plan_s {
   cudaStream_t dl_stream = nullptr;
   cudaEvent_t dl_ready = nullptr, dl_done = nullptr;
   bool dl_pending = false;
+  // intensity uploads from host memory, on their own stream and buffer, so
+  // that they overlap work already queued on the plan's stream
+  float* ul_buf = nullptr;  // Np*N*N floats, allocated on the first host upload
+  cudaStream_t ul_stream = nullptr;
+  cudaEvent_t ul_done = nullptr, ul_free = nullptr;
+  bool ul_used = false;  // ul_free has been recorded (the buffer was read)
   int N = 0, Np = 0, W = 0;
   int64_t t = 0;
   bool state_ready = false;
