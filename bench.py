@@ -139,13 +139,13 @@ def method_bytes_per_angle_iteration(n: int) -> int:
 # date and a fingerprint of the kernel sources it was taken on.  The bench
 # reports it only while the sources still have that fingerprint.
 NCU_ITERATION_TRAFFIC = {
-    # k_colpass_w<512> 423.97 MB + k_rowpass_w<512> 699.19 MB for 180 angles
+    # k_colpass_w<512> 423.15 MB + k_rowpass_w<512> 699.45 MB for 180 angles
     # (one launch each, --set full, which starts every replay with a flushed
     # L2, so what a pass inherits in L2 from the previous one is not seen);
     # the coupling prime (one launch in ten iterations, 5 % of the time) was
     # not captured and is not included
-    (("k_colpass", "k_rowpass", "k_prime"), 512): ((423.96928e6 + 699.186176e6) / 180,
-                                                   "2026-12-04", "2faf3bd51032e9c0"),
+    (("k_colpass", "k_rowpass", "k_prime"), 512): ((423.146496e6 + 699.453952e6) / 180,
+                                                   "2026-12-04", "9e401db110ddc5d1"),
 }  # {(kernel classes that ran, N): (bytes per angle-iteration, capture date, fingerprint)}
 # the kernels' sources and the host code that orders their launches and
 # tiles (the order decides what the L2 still holds between passes)
