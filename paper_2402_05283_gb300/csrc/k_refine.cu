@@ -1,6 +1,6 @@
 // k_refine.cu - Step D tomographic refinement on the assembled spectrum.
 //
-// The paper's Step D proceeds "like conventional 3D CXDI but using E(q)":
+// The paper's Step D is conventional 3D CXDI run on the gridded spectrum E(q):
 // alternating projections between the support-positivity set of a 3D
 // support S3 and the spectra equal to the gridded E(q) on the cells the
 // slices reach (the measured mask M, the same for every kz).  Volumes are
