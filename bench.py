@@ -819,6 +819,13 @@ def run_gpu(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if args.form:
+        # one form alone after the warm-up reconstructions (profiler captures)
+        if rank == 0:
+            print(json.dumps({"forms": {f: run_form(f, cp, torch, plan, I_dev, thetas, S_box)
+                                        for f in args.form}}), flush=True)
+        plan.close()
+        return
     if dist:
         dist.barrier()
     launches0 = cp.cpra_launch_count()
@@ -880,17 +887,7 @@ def run_gpu(args):
 
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
-        forms = {"refine_3d": form_refine(cp, torch, plan),
-                 "p0_cufft_pointwise": form_p0(torch, I_dev, S_box),
-                 "precision": form_precision(cp, torch, I_dev, thetas, S_box),
-                 "config5": form_config5(cp, torch),
-                 "batching": form_batch(cp, torch),
-                 "multi_guess_merge": form_multi_guess(cp, torch),
-                 "config2": form_config2(cp, torch),
-                 "serving_config4": form_serving(cp, torch, compress=1.0, early_start=True),
-                 "serving_continuous": form_serving(cp, torch, max_active=0),
-                 "serving_one_at_a_time": form_serving(cp, torch, max_active=1),
-                 "serving_early_start": form_serving(cp, torch, max_active=0, early_start=True)}
+        forms = {f: run_form(f, cp, torch, plan, I_dev, thetas, S_box) for f in FORMS}
     if rank == 0:
         cores = len(os.sched_getaffinity(0))
         cb = cpu_baseline(I_dev[:max(cores, 8)].cpu().numpy(), d["support"]) if world == 1 else None
@@ -921,6 +918,38 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+FORMS = ("refine_3d", "p0_cufft_pointwise", "precision", "config5", "batching", "multi_guess_merge",
+         "config2", "serving_config4", "serving_continuous", "serving_one_at_a_time",
+         "serving_early_start")
+
+
+def run_form(name, cp, torch, plan, I_dev, thetas, S_box):
+    """One of the measurements beside the bench number (FORMS)."""
+    if name == "refine_3d":
+        return form_refine(cp, torch, plan)
+    if name == "p0_cufft_pointwise":
+        return form_p0(torch, I_dev, S_box)
+    if name == "precision":
+        return form_precision(cp, torch, I_dev, thetas, S_box)
+    if name == "config5":
+        return form_config5(cp, torch)
+    if name == "batching":
+        return form_batch(cp, torch)
+    if name == "multi_guess_merge":
+        return form_multi_guess(cp, torch)
+    if name == "config2":
+        return form_config2(cp, torch)
+    if name == "serving_config4":
+        return form_serving(cp, torch, compress=1.0, early_start=True)
+    if name == "serving_continuous":
+        return form_serving(cp, torch, max_active=0)
+    if name == "serving_one_at_a_time":
+        return form_serving(cp, torch, max_active=1)
+    if name == "serving_early_start":
+        return form_serving(cp, torch, max_active=0, early_start=True)
+    raise ValueError(name)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -938,6 +967,8 @@ def main():
                          "bf16/fp16 run them on the tensor cores)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batching / serving / precision measurements")
+    ap.add_argument("--form", action="append", choices=FORMS,
+                    help="run only this measurement after the warm-up reconstructions (repeatable)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
