@@ -67,7 +67,7 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
 
 
 def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
-    """Rank 0 prints one JSON line with the keys the driver reads, its e2e
+    """Rank 0 prints one JSON line with every key of the bench line, its e2e
     moving no bytes and its cpu_baseline describing the same run."""
     import json
     import sys
