@@ -513,6 +513,39 @@ def test_invalid_inputs(cp):
     plan.close()
 
 
+def test_allocator_running_out_is_out_of_memory(cp):
+    """A host-made fault: the caller's allocator callback refuses the k-th
+    request (k = 0, 1, 5).  cpra_plan returns OUT_OF_MEMORY and hands every
+    block it had taken back through the free callback; a plan made afterwards
+    with a working allocator runs."""
+    import torch
+    for budget in (0, 1, 5):
+        taken = {}
+
+        def alloc(n, ctx):
+            if len(taken) >= budget:
+                return None
+            t = torch.empty(int(n), dtype=torch.uint8, device="cuda")
+            taken[t.data_ptr()] = t
+            return t.data_ptr()
+
+        def free(ptr, ctx):
+            taken.pop(ptr, None)
+
+        fa, ff = cp.binding.ALLOC_FN(alloc), cp.binding.FREE_FN(free)
+        cfg = cp.make_config(64, 8)
+        cfg.alloc, cfg.free = fa, ff
+        with pytest.raises(cp.CpraError) as e:
+            cp.cpra_plan(cfg, torch.cuda.current_stream().cuda_stream)
+        assert e.value.status == cp.ERR_OUT_OF_MEMORY
+        assert not taken, f"{len(taken)} blocks not given back (budget {budget})"
+    d = synth.make_case("tiny", N=64, Np=8)
+    p = cp.Plan(cp.make_config(64, 8))
+    p.load_intensities(d["I"], 0, d["thetas"])
+    p.iterate(2)
+    p.close()
+
+
 @pytest.mark.parametrize("engine", ["warp", "fused", "two_pass"])
 def test_nonfinite_state_is_reported(cp, engine):
     """A loaded state holding a NaN makes the next iteration's Fourier error
